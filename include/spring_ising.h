@@ -1,0 +1,174 @@
+/*
+ * spring_ising.h -- C ABI of the GB300 (sm_103a) Spring-Ising hot path.
+ *
+ * The Spring-Ising Algorithm (arXiv 2305.07187) treats every Ising spin as a
+ * mass on a zero-length spring driven by the coupling force F = J q (+ h) and
+ * iterates (Eq. 8, walls of Eq. 6)
+ *
+ *     p <- clip(p + dt_n ( -k (q - q0) + zeta_n F ),  -p_max, p_max)
+ *     q <- clip(q + (dt_n / m) p,                       -q_max, q_max)
+ *
+ * for R independent replicas ("parallel tests", Fig. 3), then reads the spins
+ * as sign(q) and scores them with the Ising energy of Eq. 1.
+ *
+ * General conventions
+ *   - Every pointer argument may be host or device memory; the library tells
+ *     them apart with cudaPointerGetAttributes.  Host inputs are copied in on
+ *     the context's stream; host outputs are copied out and the stream is
+ *     synchronised before the call returns.  With device pointers only, calls
+ *     are asynchronous with respect to the host except where stated.
+ *   - The caller owns every buffer it passes.  The context owns its device
+ *     copy of J, the integrator state, the operand buffers and the
+ *     checkpoints, all allocated in si_create and freed in si_destroy.
+ *   - Layouts: J is n x n row-major (J[i*n + j]); per-replica arrays are
+ *     replica-major, x[r*n + i].
+ *   - No call aborts the process.  Each returns an si_status; si_last_error()
+ *     gives a message for the last failure on the calling thread.  A device
+ *     wait that exceeds its time limit ends the kernel cooperatively and is
+ *     reported as SI_ERR_TIMEOUT; the context stays usable.
+ */
+#ifndef SPRING_ISING_H
+#define SPRING_ISING_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct si_ctx si_ctx;
+
+typedef enum {
+    SI_OK = 0,
+    SI_ERR_INVALID_ARG = 1,   /* bad size, NULL where required, bad enum    */
+    SI_ERR_CUDA = 2,          /* a CUDA runtime call failed                 */
+    SI_ERR_OOM = 3,           /* device allocation failed                   */
+    SI_ERR_TIMEOUT = 4,       /* a bounded device-side wait ran out         */
+    SI_ERR_UNSUPPORTED = 5,   /* valid request this build cannot serve      */
+    SI_ERR_NOT_SYMMETRIC = 6  /* J not symmetric, or non-zero diagonal      */
+} si_status;
+
+/* Arithmetic of the hot path.  The paper does not state its precision. */
+typedef enum {
+    SI_PREC_FP32 = 0,          /* J, q, p, F in FP32 on CUDA cores           */
+    SI_PREC_FP64 = 1,          /* debug: everything FP64 (slow on GB300)     */
+    SI_PREC_J_FP8_Q_BF16 = 2,  /* J validated exact in e4m3 (e.g. +-1),
+                                  q rounded to bf16 as the tensor-core
+                                  operand, FP32 accumulation and state      */
+    SI_PREC_J_BF16_Q_BF16 = 3  /* J rounded once to bf16 (Gaussian J),
+                                  otherwise as above                        */
+} si_prec;
+
+/* Update order of one time step. */
+typedef enum {
+    SI_ORDER_KICK_DRIFT = 0,   /* Eq. 8: p from q(t_n), then q from new p    */
+    SI_ORDER_EULER = 1         /* Eq. 5 literally: both from the old state   */
+} si_order;
+
+typedef struct {
+    int32_t n;              /* number of spins, >= 1                          */
+    int32_t replicas;       /* R, independent runs, >= 1                      */
+    int32_t steps;          /* T, length of the schedules given to si_run     */
+    float   k;              /* spring constant (paper: 0.5)                   */
+    float   m;              /* mass (paper: 1)                                */
+    float   q0;             /* spring origin (paper: 0)                       */
+    float   q_max;          /* position wall, Eq. 6 (paper: sqrt 2)           */
+    float   p_max;          /* momentum wall (paper: 2)                       */
+    int32_t prec;           /* si_prec                                        */
+    int32_t update_order;   /* si_order                                       */
+    int32_t wall_zero_p;    /* 1: zero p of a spin whose q was clipped        */
+    int32_t ckpt_every;     /* si_grad checkpoint interval (0: 50)            */
+    int32_t tile_n;         /* tensor-core replica tile (0: autotuned)        */
+    int32_t reserved[4];    /* must be zero                                   */
+} si_params;
+
+/* Fill *p with the paper's parameters (k=0.5, m=1, q0=0, q_max=sqrt 2,
+ * p_max=2, kick-drift, FP32) and n = replicas = steps = 0. */
+void si_default_params(si_params *p);
+
+/*
+ * Create a context for one Ising instance.
+ *   J      n*n floats, row-major; must be symmetric with a zero diagonal
+ *          (Eq. 1 sums over pairs i < j; the force of Eq. 4 uses full rows),
+ *          else SI_ERR_NOT_SYMMETRIC.  SI_PREC_J_FP8_Q_BF16 additionally
+ *          requires every entry to be exact in e4m3, else SI_ERR_INVALID_ARG.
+ *   h      n floats (external field of Eq. 1) or NULL for h = 0.
+ *   stream cudaStream_t (as void*) on which all work of this context is
+ *          enqueued; NULL is the legacy default stream.
+ * J and h are copied (and converted to the storage precision) before the call
+ * returns; the caller may free them afterwards.
+ */
+si_status si_create(si_ctx **out, const si_params *prm, const float *J,
+                    const float *h, void *stream);
+
+/*
+ * Run prm.steps time steps of Eq. 8 (or Eq. 5) for all replicas.
+ *   zeta    [steps]  coupling coefficient zeta(t_n) (the dynamic-equilibrium
+ *                    ramp of the paper is a host-built schedule)
+ *   dt      [steps]  time step Delta_n
+ *   q_init  [R][n]   initial positions (required)
+ *   p_init  [R][n]   initial momenta, or NULL for zero
+ *   q_out   [R][n]   final positions, or NULL
+ *   p_out   [R][n]   final momenta, or NULL
+ *   spins_out [R][n] final spins sign(q) in {-1,+1} as int8 (sign(0) = +1),
+ *                    or NULL
+ * The run is deterministic: the same inputs give bit-identical outputs.
+ */
+si_status si_run(si_ctx *ctx, const float *zeta, const float *dt,
+                 const float *q_init, const float *p_init, float *q_out,
+                 float *p_out, int8_t *spins_out);
+
+/*
+ * Copy the state after the last si_run at the context's working precision,
+ * widened to double: q_out, p_out [R][n] (either may be NULL).  Used by the
+ * FP64 debug mode, whose state would lose digits through si_run's float
+ * outputs.  Returns SI_ERR_INVALID_ARG if no run has completed.
+ */
+si_status si_get_state(si_ctx *ctx, double *q_out, double *p_out);
+
+/*
+ * Ising energy of Eq. 1 and cut value for R spin vectors.
+ *   spins      [R][n] int8 in {-1,+1}
+ *   energy_out [R] exact int32 energy; requires J and h integer-valued with
+ *              |J_ij|, |h_i| <= 127 (else SI_ERR_UNSUPPORTED); or NULL
+ *   cut_out    [R] exact int32 cut of the MAX-CUT instance with weights
+ *              w_ij = -J_ij (same integrality requirement); or NULL
+ *   energy_f   [R] energy for any J, computed in FP32 and stored as double;
+ *              or NULL
+ * R may differ from the context's replica count.
+ */
+si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R,
+                    int32_t *energy_out, int32_t *cut_out, double *energy_f);
+
+/*
+ * Gradient of the relaxed Ising energy at the final step,
+ *   L = sum_r ( -1/2 q_r^T J q_r - h^T q_r ),  q_r after prm.steps steps,
+ * with respect to the schedules and the spring constant, by an adjoint sweep
+ * that integrates the equation of motion backwards (checkpoints every
+ * prm.ckpt_every steps, recomputation in between).  The derivative of each
+ * wall clamp is taken as 1 strictly inside and 0 on or beyond the wall.
+ *   g_zeta [steps], g_dt [steps], g_k [1], objective [1]; any may be NULL.
+ * Supported for SI_PREC_FP32 and SI_PREC_FP64, kick-drift order, without
+ * wall_zero_p (else SI_ERR_UNSUPPORTED).
+ */
+si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt,
+                  const float *q_init, const float *p_init, float *g_zeta,
+                  float *g_dt, float *g_k, float *objective);
+
+/* Short description of the kernel path and tile shape the context uses. */
+si_status si_describe(const si_ctx *ctx, char *buf, int32_t len);
+
+/* Number of kernel launches the last si_run / si_energy / si_grad made. */
+int32_t si_last_launch_count(const si_ctx *ctx);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char *si_last_error(void);
+
+/* Release everything the context owns.  NULL is ignored. */
+void si_destroy(si_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPRING_ISING_H */

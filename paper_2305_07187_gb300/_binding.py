@@ -1,0 +1,266 @@
+"""ctypes binding of libspring_ising.so (include/spring_ising.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  There is no CPU fallback -- if the library is missing the
+import fails loudly.  Arrays may be NumPy (host) or torch tensors (host or
+CUDA); CUDA tensors are passed by data_ptr() and the context's stream is the
+caller's current torch stream unless another is given.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libspring_ising.so")
+
+SI_OK = 0
+SI_ERR_INVALID_ARG = 1
+SI_ERR_CUDA = 2
+SI_ERR_OOM = 3
+SI_ERR_TIMEOUT = 4
+SI_ERR_UNSUPPORTED = 5
+SI_ERR_NOT_SYMMETRIC = 6
+STATUS_NAMES = {0: "SI_OK", 1: "SI_ERR_INVALID_ARG", 2: "SI_ERR_CUDA", 3: "SI_ERR_OOM",
+                4: "SI_ERR_TIMEOUT", 5: "SI_ERR_UNSUPPORTED", 6: "SI_ERR_NOT_SYMMETRIC"}
+
+SI_PREC_FP32 = 0
+SI_PREC_FP64 = 1
+SI_PREC_J_FP8_Q_BF16 = 2
+SI_PREC_J_BF16_Q_BF16 = 3
+PREC = {"fp32": 0, "fp64": 1, "j_fp8_q_bf16": 2, "j_bf16_q_bf16": 3}
+
+EXPORTS = ("si_default_params", "si_create", "si_run", "si_get_state", "si_energy", "si_grad",
+           "si_describe", "si_last_launch_count", "si_last_error", "si_destroy")
+
+
+class SiParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("replicas", ctypes.c_int32), ("steps", ctypes.c_int32),
+                ("k", ctypes.c_float), ("m", ctypes.c_float), ("q0", ctypes.c_float),
+                ("q_max", ctypes.c_float), ("p_max", ctypes.c_float),
+                ("prec", ctypes.c_int32), ("update_order", ctypes.c_int32),
+                ("wall_zero_p", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
+                ("tile_n", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+
+
+class SpringIsingError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libspring_ising.so not built (run __graft_entry__.build() "
+                          "or python -m paper_2305_07187_gb300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    I32 = ctypes.c_int32
+    lib.si_default_params.argtypes = [ctypes.POINTER(SiParams)]
+    lib.si_default_params.restype = None
+    lib.si_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(SiParams), P, P, P]
+    lib.si_create.restype = ctypes.c_int
+    lib.si_run.argtypes = [P, P, P, P, P, P, P, P]
+    lib.si_run.restype = ctypes.c_int
+    lib.si_get_state.argtypes = [P, P, P]
+    lib.si_get_state.restype = ctypes.c_int
+    lib.si_energy.argtypes = [P, P, I32, P, P, P]
+    lib.si_energy.restype = ctypes.c_int
+    lib.si_grad.argtypes = [P, P, P, P, P, P, P, P, P]
+    lib.si_grad.restype = ctypes.c_int
+    lib.si_describe.argtypes = [P, ctypes.c_char_p, I32]
+    lib.si_describe.restype = ctypes.c_int
+    lib.si_last_launch_count.argtypes = [P]
+    lib.si_last_launch_count.restype = I32
+    lib.si_last_error.argtypes = []
+    lib.si_last_error.restype = ctypes.c_char_p
+    lib.si_destroy.argtypes = [P]
+    lib.si_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != SI_OK:
+        msg = load().si_last_error()
+        raise SpringIsingError(status, msg.decode() if msg else "")
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class _Arg:
+    """Pointer to an array argument; keeps converted copies alive."""
+
+    def __init__(self, x, dtype, size=None, writable=False):
+        self.obj = None
+        self.ptr = None
+        if x is None:
+            return
+        if _is_torch(x):
+            import torch
+            tdt = {np.float32: torch.float32, np.int8: torch.int8, np.int32: torch.int32,
+                   np.float64: torch.float64}[dtype]
+            if x.dtype != tdt or not x.is_contiguous():
+                if writable:
+                    raise TypeError("output tensor must be contiguous %s" % tdt)
+                x = x.to(tdt).contiguous()
+            if size is not None and x.numel() != size:
+                raise ValueError("expected %d elements, got %d" % (size, x.numel()))
+            self.obj = x
+            self.ptr = ctypes.c_void_p(x.data_ptr())
+        else:
+            if writable:
+                if not (isinstance(x, np.ndarray) and x.dtype == dtype and x.flags.c_contiguous):
+                    raise TypeError("output array must be C-contiguous %s" % np.dtype(dtype))
+                a = x
+            else:
+                a = np.ascontiguousarray(x, dtype=dtype)
+            if size is not None and a.size != size:
+                raise ValueError("expected %d elements, got %d" % (size, a.size))
+            self.obj = a
+            self.ptr = a.ctypes.data_as(ctypes.c_void_p)
+
+
+def default_params(**kw) -> SiParams:
+    p = SiParams()
+    load().si_default_params(ctypes.byref(p))
+    for k, v in kw.items():
+        if k == "prec" and isinstance(v, str):
+            v = PREC[v]
+        setattr(p, k, v)
+    return p
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return ctypes.c_void_p(0)
+
+
+class Context:
+    """One Ising instance on the GPU (wraps si_ctx)."""
+
+    def __init__(self, J, h=None, *, n=None, replicas=1, steps=0, prec="fp32", stream=None,
+                 **params):
+        lib = load()
+        if n is None:
+            n = int(J.shape[0])
+        self.n, self.replicas, self.steps = int(n), int(replicas), int(steps)
+        self.params = default_params(n=self.n, replicas=self.replicas, steps=self.steps,
+                                     prec=prec, **params)
+        self._J = _Arg(J, np.float32, self.n * self.n)
+        self._h = _Arg(h, np.float32, self.n)
+        self._stream = _stream_handle(stream)
+        ctx = ctypes.c_void_p()
+        _check(lib.si_create(ctypes.byref(ctx), ctypes.byref(self.params), self._J.ptr,
+                             self._h.ptr, self._stream))
+        self._J = self._h = None
+        self.ctx = ctx
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().si_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def describe(self) -> str:
+        buf = ctypes.create_string_buffer(256)
+        _check(load().si_describe(self.ctx, buf, 256))
+        return buf.value.decode()
+
+    def last_launch_count(self) -> int:
+        return int(load().si_last_launch_count(self.ctx))
+
+    def run_into(self, zeta, dt, q_init, p_init=None, q_out=None, p_out=None, spins_out=None):
+        """si_run with caller-provided outputs (numpy or torch, host or device)."""
+        nR = self.n * self.replicas
+        z = _Arg(zeta, np.float32, self.steps)
+        d = _Arg(dt, np.float32, self.steps)
+        qi = _Arg(q_init, np.float32, nR)
+        pi = _Arg(p_init, np.float32, nR)
+        qo = _Arg(q_out, np.float32, nR, writable=True)
+        po = _Arg(p_out, np.float32, nR, writable=True)
+        so = _Arg(spins_out, np.int8, nR, writable=True)
+        _check(load().si_run(self.ctx, z.ptr, d.ptr, qi.ptr, pi.ptr, qo.ptr, po.ptr, so.ptr))
+
+    def run(self, zeta, dt, q_init, p_init=None):
+        """Host convenience: returns (q, p, spins) as NumPy arrays."""
+        R, n = self.replicas, self.n
+        q = np.empty((R, n), np.float32)
+        p = np.empty((R, n), np.float32)
+        s = np.empty((R, n), np.int8)
+        self.run_into(zeta, dt, q_init, p_init, q, p, s)
+        return q, p, s
+
+    def get_state(self):
+        """si_get_state: the last run's (q, p) at working precision, as float64."""
+        q = np.empty((self.replicas, self.n), np.float64)
+        p = np.empty((self.replicas, self.n), np.float64)
+        _check(load().si_get_state(self.ctx, q.ctypes.data_as(ctypes.c_void_p),
+                                   p.ctypes.data_as(ctypes.c_void_p)))
+        return q, p
+
+    def energy_into(self, spins, R, energy_out=None, cut_out=None, energy_f=None):
+        sp = _Arg(spins, np.int8, R * self.n)
+        eo = _Arg(energy_out, np.int32, R, writable=True)
+        co = _Arg(cut_out, np.int32, R, writable=True)
+        fo = _Arg(energy_f, np.float64, R, writable=True)
+        _check(load().si_energy(self.ctx, sp.ptr, int(R), eo.ptr, co.ptr, fo.ptr))
+
+    def energy(self, spins, exact=True):
+        """Host convenience: returns (energy_int32 or None, cut or None, energy_f)."""
+        s = spins if _is_torch(spins) else np.ascontiguousarray(spins, dtype=np.int8)
+        R = int(s.numel() // self.n) if _is_torch(s) else s.size // self.n
+        e = np.empty(R, np.int32) if exact else None
+        c = np.empty(R, np.int32) if exact else None
+        f = np.empty(R, np.float64)
+        self.energy_into(s, R, e, c, f)
+        return e, c, f
+
+    def grad(self, zeta, dt, q_init, p_init=None):
+        """si_grad: returns (objective, g_zeta, g_dt, g_k) as NumPy/float."""
+        nR = self.n * self.replicas
+        gz = np.empty(max(self.steps, 1), np.float32)
+        gd = np.empty(max(self.steps, 1), np.float32)
+        gk = np.empty(1, np.float32)
+        ob = np.empty(1, np.float32)
+        z = _Arg(zeta, np.float32, self.steps)
+        d = _Arg(dt, np.float32, self.steps)
+        qi = _Arg(q_init, np.float32, nR)
+        pi = _Arg(p_init, np.float32, nR)
+        _check(load().si_grad(self.ctx, z.ptr, d.ptr, qi.ptr, pi.ptr,
+                              gz.ctypes.data_as(ctypes.c_void_p), gd.ctypes.data_as(ctypes.c_void_p),
+                              gk.ctypes.data_as(ctypes.c_void_p), ob.ctypes.data_as(ctypes.c_void_p)))
+        return float(ob[0]), gz[:self.steps], gd[:self.steps], float(gk[0])
+
+
+SQRT2_F32 = float(np.float32(math.sqrt(2.0)))

@@ -1,0 +1,510 @@
+// C ABI of the Spring-Ising hot path: context life cycle, argument checks,
+// host/device staging and dispatch to the kernel families.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "si_internal.cuh"
+
+namespace si {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the sticky-free error of a failed query
+        return false;
+    }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+// A pointer argument staged on the device: either the caller's device
+// pointer or a temporary copy of host data.
+struct DevIn {
+    const void *ptr = nullptr;
+    void *owned = nullptr;
+    ~DevIn() {
+        if (owned) cudaFree(owned);
+    }
+};
+
+static si_status stage_in(DevIn &d, const void *src, size_t bytes, cudaStream_t st) {
+    if (!src) {
+        d.ptr = nullptr;
+        return SI_OK;
+    }
+    if (is_device_ptr(src)) {
+        d.ptr = src;
+        return SI_OK;
+    }
+    SI_CUDA_TRY(cudaMalloc(&d.owned, bytes));
+    SI_CUDA_TRY(cudaMemcpyAsync(d.owned, src, bytes, cudaMemcpyHostToDevice, st));
+    d.ptr = d.owned;
+    return SI_OK;
+}
+
+// Output staging: device destination is written directly; a host destination
+// gets a device temporary that is copied back by finish().
+struct DevOut {
+    void *host = nullptr;
+    void *ptr = nullptr;
+    void *owned = nullptr;
+    size_t bytes = 0;
+    ~DevOut() {
+        if (owned) cudaFree(owned);
+    }
+};
+
+static si_status stage_out(DevOut &d, void *dst, size_t bytes) {
+    d.bytes = bytes;
+    if (!dst) return SI_OK;
+    if (is_device_ptr(dst)) {
+        d.ptr = dst;
+        return SI_OK;
+    }
+    SI_CUDA_TRY(cudaMalloc(&d.owned, bytes));
+    d.ptr = d.owned;
+    d.host = dst;
+    return SI_OK;
+}
+
+static si_status finish_out(DevOut &d, cudaStream_t st) {
+    if (d.host) SI_CUDA_TRY(cudaMemcpyAsync(d.host, d.ptr, d.bytes, cudaMemcpyDeviceToHost, st));
+    return SI_OK;
+}
+
+// Read and clear the device error word; synchronises the stream.
+static si_status check_device_error(Ctx *c) {
+    int herr = 0;
+    SI_CUDA_TRY(cudaMemcpyAsync(&herr, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (herr != DEV_OK) {
+        SI_CUDA_TRY(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
+        SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (herr == DEV_BAD_CONFIG) {
+            set_error("kernel rejected its launch configuration");
+            return SI_ERR_UNSUPPORTED;
+        }
+        set_error(herr == DEV_TIMEOUT_BARRIER ? "inter-CTA step barrier timed out"
+                                              : "mbarrier wait timed out");
+        return SI_ERR_TIMEOUT;
+    }
+    return SI_OK;
+}
+
+static void free_ctx(Ctx *c) {
+    if (!c) return;
+    void *ptrs[] = {c->dJ, c->dJ8, c->dh, c->dhf, c->dh8, c->dq, c->dp, c->dqbuf,
+                    c->dzeta, c->ddt, c->dbar, c->derr, c->dspins, c->dspins_in,
+                    c->dE, c->dC, c->dEf, c->dstage, c->g_ws};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+static si_status check_params(const si_params *p) {
+    if (!p) { set_error("params is NULL"); return SI_ERR_INVALID_ARG; }
+    if (p->n < 1 || p->replicas < 1 || p->steps < 0) {
+        set_error("need n >= 1, replicas >= 1, steps >= 0");
+        return SI_ERR_INVALID_ARG;
+    }
+    if (p->prec < SI_PREC_FP32 || p->prec > SI_PREC_J_BF16_Q_BF16) {
+        set_error("unknown precision");
+        return SI_ERR_INVALID_ARG;
+    }
+    if (p->update_order != 0 && p->update_order != 1) {
+        set_error("update_order must be 0 (kick-drift) or 1 (literal Eq. 5)");
+        return SI_ERR_INVALID_ARG;
+    }
+    if (!(p->m > 0.f) || !(p->q_max > 0.f) || !(p->p_max > 0.f) || !std::isfinite(p->k) ||
+        !std::isfinite(p->q0) || !std::isfinite(p->m) || !std::isfinite(p->q_max) ||
+        !std::isfinite(p->p_max)) {
+        set_error("need finite k, q0 and positive finite m, q_max, p_max");
+        return SI_ERR_INVALID_ARG;
+    }
+    if (p->ckpt_every < 0 || p->tile_n < 0) {
+        set_error("ckpt_every and tile_n must be >= 0");
+        return SI_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < 4; ++i)
+        if (p->reserved[i] != 0) {
+            set_error("reserved fields must be zero");
+            return SI_ERR_INVALID_ARG;
+        }
+    if ((long long)p->n * p->n > (1LL << 34)) {
+        set_error("n too large");
+        return SI_ERR_UNSUPPORTED;
+    }
+    return SI_OK;
+}
+
+template <typename T>
+__global__ void k_copy_h(const float *h, int n, T *out, float *outf, int8_t *out8) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float v = h ? h[i] : 0.f;
+        out[i] = (T)v;
+        outf[i] = v;
+        if (out8) out8[i] = (int8_t)v;
+    }
+}
+
+static si_status create_impl(Ctx *c, const float *J, const float *h) {
+    const si_params &p = c->prm;
+    const int n = p.n;
+    SI_CUDA_TRY(cudaGetDevice(&c->device));
+    SI_CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    if (const char *e = std::getenv("SI_SPIN_LIMIT_NS")) {
+        long long v = std::atoll(e);
+        if (v > 0) c->spin_limit_ns = v;
+    }
+    DevIn Jd, hd;
+    si_status s = stage_in(Jd, J, (size_t)n * n * sizeof(float), c->stream);
+    if (s != SI_OK) return s;
+    s = stage_in(hd, h, (size_t)n * sizeof(float), c->stream);
+    if (s != SI_OK) return s;
+    unsigned long long flags = 0;
+    long long s_upper = 0;
+    s = simt_validate((const float *)Jd.ptr, (const float *)hd.ptr, n, p.prec, &flags, &s_upper, c->stream);
+    if (s != SI_OK) return s;
+    if (flags & (VF_NONFINITE | VF_H_NONFINITE)) {
+        set_error("J or h holds a non-finite value");
+        return SI_ERR_INVALID_ARG;
+    }
+    if (flags & (VF_ASYM | VF_DIAG)) {
+        set_error("J must be symmetric with a zero diagonal");
+        return SI_ERR_NOT_SYMMETRIC;
+    }
+    if (p.prec == SI_PREC_J_FP8_Q_BF16 && (flags & VF_NOT_E4M3)) {
+        set_error("SI_PREC_J_FP8_Q_BF16 needs every J entry exact in e4m3");
+        return SI_ERR_INVALID_ARG;
+    }
+    c->integer_j = !(flags & VF_NOT_INT8);
+    c->has_h = (h != nullptr);
+    c->integer_h = !(flags & VF_H_NOT_INT8);
+    c->s_upper = c->integer_j ? s_upper : 0;
+    c->n = n;
+    c->R = p.replicas;
+    c->ld8 = round_up(n, 16);
+
+    // Coupling storage.
+    const bool tensor = p.prec == SI_PREC_J_FP8_Q_BF16 || p.prec == SI_PREC_J_BF16_Q_BF16;
+    const bool f64 = p.prec == SI_PREC_FP64;
+    const size_t es = f64 ? 8 : 4;
+    if (tensor) {
+        c->path = Path::TENSOR;
+        s = tc_prepare(c, (const float *)Jd.ptr);
+        if (s != SI_OK) return s;
+    } else {
+        c->path = (c->R <= 4) ? Path::PLAIN_PERSISTENT : Path::SIMT_TILED;
+        s = simt_convert_j(c, (const float *)Jd.ptr, n);
+        if (s != SI_OK) return s;
+        SI_CUDA_TRY(cudaMalloc(&c->dp, (size_t)c->R * n * es));
+        c->qbuf_bytes = 2 * (size_t)c->R * c->ldj * es;
+        SI_CUDA_TRY(cudaMalloc(&c->dqbuf, c->qbuf_bytes));
+        SI_CUDA_TRY(cudaMemsetAsync(c->dqbuf, 0, c->qbuf_bytes, c->stream));
+    }
+    if (c->integer_j) SI_CUDA_TRY(cudaMalloc((void **)&c->dJ8, (size_t)n * c->ld8));
+    // h copies.
+    SI_CUDA_TRY(cudaMalloc((void **)&c->dhf, sizeof(float) * n));
+    if (c->integer_h && c->has_h) SI_CUDA_TRY(cudaMalloc((void **)&c->dh8, n));
+    if (f64) {
+        SI_CUDA_TRY(cudaMalloc(&c->dh, sizeof(double) * n));
+        k_copy_h<double><<<std::min(1024, cdiv(n, 256)), 256, 0, c->stream>>>(
+            (const float *)hd.ptr, n, (double *)c->dh, c->dhf, c->dh8);
+    } else {
+        SI_CUDA_TRY(cudaMalloc(&c->dh, sizeof(float) * n));
+        k_copy_h<float><<<std::min(1024, cdiv(n, 256)), 256, 0, c->stream>>>(
+            (const float *)hd.ptr, n, (float *)c->dh, c->dhf, c->dh8);
+    }
+    SI_CUDA_TRY(cudaGetLastError());
+    if (!c->has_h) {
+        // keep the pointers (zero field) but let kernels skip the add
+        cudaFree(c->dh);
+        c->dh = nullptr;
+    }
+    const int sched = std::max(1, p.steps);
+    SI_CUDA_TRY(cudaMalloc((void **)&c->dzeta, sizeof(float) * sched));
+    SI_CUDA_TRY(cudaMalloc((void **)&c->ddt, sizeof(float) * sched));
+    c->nbar = 1024;
+    SI_CUDA_TRY(cudaMalloc((void **)&c->dbar, sizeof(unsigned) * c->nbar));
+    SI_CUDA_TRY(cudaMalloc((void **)&c->derr, sizeof(int)));
+    SI_CUDA_TRY(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
+    SI_CUDA_TRY(cudaMalloc((void **)&c->dspins, (size_t)c->R * c->ld8));
+    SI_CUDA_TRY(cudaMemsetAsync(c->dspins, 0, (size_t)c->R * c->ld8, c->stream));
+    if (c->integer_j) {
+        si_status s8 = convert_j8(c, (const float *)Jd.ptr);
+        if (s8 != SI_OK) return s8;
+    }
+    SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return SI_OK;
+}
+
+// Kernel to pad-copy spins [R][n] (any pointer) into [R][ld] staging.
+__global__ void k_pad_spins(const int8_t *src, int n, int R, int8_t *dst, int ld) {
+    const long long total = (long long)R * ld;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / ld), i = (int)(e % ld);
+        dst[e] = i < n ? src[(size_t)r * n + i] : (int8_t)0;
+    }
+}
+
+__global__ void k_unpad_spins(const int8_t *src, int ld, int n, int R, int8_t *dst) {
+    const long long total = (long long)R * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), i = (int)(e % n);
+        dst[e] = src[(size_t)r * ld + i];
+    }
+}
+
+}  // namespace si
+
+using namespace si;
+
+extern "C" {
+
+void si_default_params(si_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->k = 0.5f;
+    p->m = 1.0f;
+    p->q0 = 0.0f;
+    p->q_max = std::sqrt(2.0f);
+    p->p_max = 2.0f;
+    p->prec = SI_PREC_FP32;
+    p->update_order = SI_ORDER_KICK_DRIFT;
+}
+
+si_status si_create(si_ctx **out, const si_params *prm, const float *J, const float *h,
+                    void *stream) {
+    set_error("");
+    if (!out || !J) {
+        set_error("si_create: out and J are required");
+        return SI_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    si_status s = check_params(prm);
+    if (s != SI_OK) return s;
+    Ctx *c = new (std::nothrow) Ctx();
+    if (!c) return SI_ERR_OOM;
+    c->prm = *prm;
+    c->stream = (cudaStream_t)stream;
+    s = create_impl(c, J, h);
+    if (s != SI_OK) {
+        free_ctx(c);
+        return s;
+    }
+    *out = reinterpret_cast<si_ctx *>(c);
+    return SI_OK;
+}
+
+si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q_init,
+                 const float *p_init, float *q_out, float *p_out, int8_t *spins_out) {
+    set_error("");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !q_init || (c->prm.steps > 0 && (!zeta || !dt))) {
+        set_error("si_run: ctx, q_init, zeta and dt are required");
+        return SI_ERR_INVALID_ARG;
+    }
+    c->launches = 0;
+    const int steps = c->prm.steps, n = c->n, R = c->R;
+    const size_t sb = sizeof(float) * std::max(steps, 1);
+    if (steps > 0) {
+        const cudaMemcpyKind kz = is_device_ptr(zeta) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        const cudaMemcpyKind kd = is_device_ptr(dt) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        SI_CUDA_TRY(cudaMemcpyAsync(c->dzeta, zeta, sizeof(float) * steps, kz, c->stream));
+        SI_CUDA_TRY(cudaMemcpyAsync(c->ddt, dt, sizeof(float) * steps, kd, c->stream));
+    }
+    (void)sb;
+    DevIn qi, pi;
+    si_status s = stage_in(qi, q_init, sizeof(float) * (size_t)R * n, c->stream);
+    if (s != SI_OK) return s;
+    s = stage_in(pi, p_init, sizeof(float) * (size_t)R * n, c->stream);
+    if (s != SI_OK) return s;
+    DevOut qo, po, so;
+    if ((s = stage_out(qo, q_out, sizeof(float) * (size_t)R * n)) != SI_OK) return s;
+    if ((s = stage_out(po, p_out, sizeof(float) * (size_t)R * n)) != SI_OK) return s;
+    if ((s = stage_out(so, spins_out, (size_t)R * n)) != SI_OK) return s;
+
+    if (c->path == Path::TENSOR) {
+        if ((s = tc_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr)) != SI_OK) return s;
+        if ((s = tc_run(c, steps, c->dspins)) != SI_OK) return s;
+    } else {
+        if ((s = simt_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr)) != SI_OK) return s;
+        if ((s = simt_run(c, steps, c->dspins)) != SI_OK) return s;
+        c->cur_parity = steps & 1;
+    }
+    if ((s = check_device_error(c)) != SI_OK) return s;
+    c->have_run = true;
+    if (q_out || p_out) {
+        if (c->path == Path::TENSOR) s = tc_copy_state(c, (float *)qo.ptr, (float *)po.ptr);
+        else s = simt_copy_state(c, (float *)qo.ptr, (float *)po.ptr);
+        if (s != SI_OK) return s;
+    }
+    if (spins_out) {
+        if (steps == 0) {
+            // no step ran: spins of the initial positions
+            if (c->path == Path::TENSOR) {
+                if ((s = tc_spins(c, c->dspins, c->ld8)) != SI_OK) return s;
+            } else if ((s = simt_spins(c, c->dspins, c->ld8)) != SI_OK) {
+                return s;
+            }
+        }
+        k_unpad_spins<<<std::min(4096, cdiv((long long)R * n, 256)), 256, 0, c->stream>>>(
+            c->dspins, c->ld8, n, R, (int8_t *)so.ptr);
+        SI_CUDA_TRY(cudaGetLastError());
+        c->launches += 1;
+    }
+    if ((s = finish_out(qo, c->stream)) != SI_OK) return s;
+    if ((s = finish_out(po, c->stream)) != SI_OK) return s;
+    if ((s = finish_out(so, c->stream)) != SI_OK) return s;
+    SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return SI_OK;
+}
+
+si_status si_get_state(si_ctx *ctx, double *q_out, double *p_out) {
+    set_error("");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !c->have_run) {
+        set_error("si_get_state: no completed run");
+        return SI_ERR_INVALID_ARG;
+    }
+    const size_t bytes = sizeof(double) * (size_t)c->R * c->n;
+    DevOut qo, po;
+    si_status s;
+    if ((s = stage_out(qo, q_out, bytes)) != SI_OK) return s;
+    if ((s = stage_out(po, p_out, bytes)) != SI_OK) return s;
+    if (c->path == Path::TENSOR) s = tc_copy_state_f64(c, (double *)qo.ptr, (double *)po.ptr);
+    else s = simt_copy_state_f64(c, (double *)qo.ptr, (double *)po.ptr);
+    if (s != SI_OK) return s;
+    if ((s = finish_out(qo, c->stream)) != SI_OK) return s;
+    if ((s = finish_out(po, c->stream)) != SI_OK) return s;
+    SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return SI_OK;
+}
+
+si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy_out,
+                    int32_t *cut_out, double *energy_f) {
+    set_error("");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !spins || R < 0) {
+        set_error("si_energy: ctx and spins are required, R >= 0");
+        return SI_ERR_INVALID_ARG;
+    }
+    c->launches = 0;
+    if (R == 0) return SI_OK;
+    if ((energy_out || cut_out) && !c->integer_j) {
+        set_error("exact int32 energy/cut needs integer J with |J_ij| <= 127");
+        return SI_ERR_UNSUPPORTED;
+    }
+    if (energy_out && c->has_h && !c->integer_h) {
+        set_error("exact int32 energy needs integer h with |h_i| <= 127");
+        return SI_ERR_UNSUPPORTED;
+    }
+    const int n = c->n;
+    DevIn sd;
+    si_status s = stage_in(sd, spins, (size_t)R * n, c->stream);
+    if (s != SI_OK) return s;
+    if (R > c->spins_in_cap) {
+        if (c->dspins_in) cudaFree(c->dspins_in);
+        c->dspins_in = nullptr;
+        c->spins_in_cap = 0;
+        SI_CUDA_TRY(cudaMalloc((void **)&c->dspins_in, (size_t)R * c->ld8));
+        c->spins_in_cap = R;
+    }
+    k_pad_spins<<<std::min(4096, cdiv((long long)R * c->ld8, 256)), 256, 0, c->stream>>>(
+        (const int8_t *)sd.ptr, n, R, c->dspins_in, c->ld8);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    DevOut eo, co, fo;
+    if ((s = stage_out(eo, energy_out, sizeof(int32_t) * R)) != SI_OK) return s;
+    if ((s = stage_out(co, cut_out, sizeof(int32_t) * R)) != SI_OK) return s;
+    if ((s = stage_out(fo, energy_f, sizeof(double) * R)) != SI_OK) return s;
+    s = simt_energy(c, c->dspins_in, R, c->ld8, (int32_t *)eo.ptr, (int32_t *)co.ptr, (double *)fo.ptr);
+    if (s != SI_OK) return s;
+    if ((s = finish_out(eo, c->stream)) != SI_OK) return s;
+    if ((s = finish_out(co, c->stream)) != SI_OK) return s;
+    if ((s = finish_out(fo, c->stream)) != SI_OK) return s;
+    SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return SI_OK;
+}
+
+si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt, const float *q_init,
+                  const float *p_init, float *g_zeta, float *g_dt, float *g_k,
+                  float *objective) {
+    set_error("");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || !q_init || (c->prm.steps > 0 && (!zeta || !dt))) {
+        set_error("si_grad: ctx, q_init, zeta and dt are required");
+        return SI_ERR_INVALID_ARG;
+    }
+    if (c->path == Path::TENSOR || c->prm.update_order != 0 || c->prm.wall_zero_p) {
+        set_error("si_grad supports FP32/FP64 contexts, kick-drift order, no wall_zero_p");
+        return SI_ERR_UNSUPPORTED;
+    }
+    c->launches = 0;
+    const int steps = c->prm.steps, n = c->n, R = c->R;
+    if (steps > 0) {
+        const cudaMemcpyKind kz = is_device_ptr(zeta) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        const cudaMemcpyKind kd = is_device_ptr(dt) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        SI_CUDA_TRY(cudaMemcpyAsync(c->dzeta, zeta, sizeof(float) * steps, kz, c->stream));
+        SI_CUDA_TRY(cudaMemcpyAsync(c->ddt, dt, sizeof(float) * steps, kd, c->stream));
+    }
+    DevIn qi, pi;
+    si_status s = stage_in(qi, q_init, sizeof(float) * (size_t)R * n, c->stream);
+    if (s != SI_OK) return s;
+    s = stage_in(pi, p_init, sizeof(float) * (size_t)R * n, c->stream);
+    if (s != SI_OK) return s;
+    DevOut gz, gd, gk, ob;
+    if ((s = stage_out(gz, g_zeta, sizeof(float) * std::max(steps, 1))) != SI_OK) return s;
+    if ((s = stage_out(gd, g_dt, sizeof(float) * std::max(steps, 1))) != SI_OK) return s;
+    if ((s = stage_out(gk, g_k, sizeof(float))) != SI_OK) return s;
+    if ((s = stage_out(ob, objective, sizeof(float))) != SI_OK) return s;
+    if ((s = simt_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr)) != SI_OK) return s;
+    s = adjoint_grad(c, steps, (float *)gz.ptr, (float *)gd.ptr, (float *)gk.ptr, (float *)ob.ptr);
+    if (s != SI_OK) return s;
+    if ((s = check_device_error(c)) != SI_OK) return s;
+    if ((s = finish_out(gz, c->stream)) != SI_OK) return s;
+    if ((s = finish_out(gd, c->stream)) != SI_OK) return s;
+    if ((s = finish_out(gk, c->stream)) != SI_OK) return s;
+    if ((s = finish_out(ob, c->stream)) != SI_OK) return s;
+    SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return SI_OK;
+}
+
+si_status si_describe(const si_ctx *ctx, char *buf, int32_t len) {
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (!c || !buf || len <= 0) return SI_ERR_INVALID_ARG;
+    const char *prec[] = {"fp32", "fp64", "j_fp8_q_bf16", "j_bf16_q_bf16"};
+    if (c->path == Path::TENSOR) {
+        tc_describe(c, buf, len);
+    } else if (c->path == Path::PLAIN_PERSISTENT) {
+        std::snprintf(buf, len, "plain_persistent prec=%s n=%d R=%d", prec[c->prm.prec], c->n, c->R);
+    } else {
+        std::snprintf(buf, len, "simt_tiled prec=%s n=%d R=%d tile=64x64", prec[c->prm.prec], c->n, c->R);
+    }
+    return SI_OK;
+}
+
+int32_t si_last_launch_count(const si_ctx *ctx) {
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    return c ? c->launches : 0;
+}
+
+const char *si_last_error(void) { return g_last_error.c_str(); }
+
+void si_destroy(si_ctx *ctx) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,116 @@
+// Device-side helpers shared by the CUDA translation units: bounded waits,
+// the inter-CTA step barrier and the integrator of one time step.
+#pragma once
+
+#include "si_internal.cuh"
+
+namespace si {
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_gpu_add(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile_int(const int *p) {
+    return *(const volatile int *)p;
+}
+
+// Spin until *ctr >= target (wrap-around safe).  Gives up when another CTA
+// has raised the error word or when limit_ns has passed; in the latter case
+// it raises DEV_TIMEOUT_BARRIER itself.  Returns true on success.
+__device__ __forceinline__ bool wait_counter_geq(const unsigned *ctr, unsigned target,
+                                                 int *err, long long limit_ns) {
+    unsigned long long t0 = globaltimer_ns();
+    for (unsigned it = 1;; ++it) {
+        unsigned v = ld_acquire_gpu(ctr);
+        if ((int)(v - target) >= 0) return true;
+        if ((it & 31u) == 0) {
+            if (ld_volatile_int(err) != 0) return false;
+            if ((long long)(globaltimer_ns() - t0) > limit_ns) {
+                atomicCAS(err, 0, DEV_TIMEOUT_BARRIER);
+                return false;
+            }
+        }
+    }
+}
+
+// Barrier over all CTAs of the grid for step t (counter starts at 0 each
+// launch).  Every thread of the CTA must call it; returns false for all of
+// them if the wait failed.
+__device__ __forceinline__ bool grid_barrier(unsigned *ctr, unsigned target, int *err,
+                                             long long limit_ns) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        red_release_gpu_add(ctr, 1u);
+        ok = wait_counter_geq(ctr, target, err, limit_ns) ? 1 : 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// One time step for one (spin, replica) pair.  F already includes h.
+// order 0 (Eq. 8): p from q(t_n), then q from the new p.
+// order 1 (Eq. 5): both from the old state.
+// Walls (Eq. 6): clamp q to [-q_max, q_max], p to [-p_max, p_max]; with
+// wall_zero_p the momentum of a clipped spin is set to zero.
+template <typename T>
+__device__ __forceinline__ void integrate(T q, T p, T F, T zeta, T dt, T dtm,
+                                          const StepParams &sp, T &q_out, T &p_out) {
+    const T k = (T)sp.k, q0 = (T)sp.q0, qmax = (T)sp.q_max, pmax = (T)sp.p_max;
+    T a = p + dt * (-k * (q - q0) + zeta * F);
+    T b = q + dtm * (sp.order == 0 ? fmin(fmax(a, -pmax), pmax) : p);
+    T pn = fmin(fmax(a, -pmax), pmax);
+    T qn = fmin(fmax(b, -qmax), qmax);
+    if (sp.wall_zero_p && qn != b) pn = (T)0;
+    q_out = qn;
+    p_out = pn;
+}
+
+// Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
+    s = a + b;
+    const T z = s - a;
+    e = (a - (s - z)) + (b - z);
+}
+
+// Compensated accumulator: (hi, lo) carries a running sum whose rounding
+// errors are kept in lo; chunk partial sums are added with two_sum.
+template <typename T>
+struct CompSum {
+    T hi, lo;
+    __device__ __forceinline__ void init() { hi = (T)0; lo = (T)0; }
+    __device__ __forceinline__ void add(T x) {
+        T s, e;
+        two_sum(hi, x, s, e);
+        hi = s;
+        lo += e;
+    }
+    __device__ __forceinline__ void merge(T ohi, T olo) {
+        T s, e;
+        two_sum(hi, ohi, s, e);
+        hi = s;
+        lo += olo + e;
+    }
+    __device__ __forceinline__ T value() const { return hi + lo; }
+};
+
+template <typename T>
+__device__ __forceinline__ int8_t spin_of(T q) {
+    return q >= (T)0 ? (int8_t)1 : (int8_t)-1;
+}
+
+}  // namespace si

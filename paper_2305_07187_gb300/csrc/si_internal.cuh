@@ -1,0 +1,145 @@
+// Internal declarations shared by the translation units of libspring_ising.
+// Nothing here is part of the public ABI (include/spring_ising.h).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "spring_ising.h"
+
+namespace si {
+
+// ------------------------------------------------------------ error plumbing
+void set_error(const std::string &msg);
+
+#define SI_CUDA_TRY(expr)                                                      \
+    do {                                                                       \
+        cudaError_t _e = (expr);                                               \
+        if (_e != cudaSuccess) {                                               \
+            ::si::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+            return _e == cudaErrorMemoryAllocation ? SI_ERR_OOM : SI_ERR_CUDA; \
+        }                                                                      \
+    } while (0)
+
+// Device error word values (written by kernels, read by the host).
+enum : int {
+    DEV_OK = 0,
+    DEV_TIMEOUT_BARRIER = 1,   // inter-CTA step barrier ran out of time
+    DEV_TIMEOUT_MBAR = 2,      // an mbarrier wait ran out of time
+    DEV_BAD_CONFIG = 3         // launch shape the kernel cannot serve
+};
+
+// Integrator parameters, identical for every kernel family.
+struct StepParams {
+    float k, m, q0, q_max, p_max;
+    int order;          // 0 kick-drift (Eq. 8), 1 literal Eq. 5
+    int wall_zero_p;
+};
+
+enum class Path { PLAIN_PERSISTENT, SIMT_TILED, TENSOR };
+
+struct Ctx {
+    si_params prm;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 0;
+    int n = 0, R = 0;
+    Path path = Path::SIMT_TILED;
+    bool integer_j = false;      // every J_ij integer in [-127, 127]
+    bool integer_h = true;       // h NULL or integer in [-127, 127]
+    bool has_h = false;
+    long long s_upper = 0;       // sum_{i<j} J_ij (integer J only)
+    long long spin_limit_ns = 2000000000LL;
+
+    // Storage of J.  FP32/FP64 paths: [n][ldj] in the state precision.
+    // Tensor path: bf16 [mpad][ldk], zero padded.
+    int ldj = 0;                 // row stride (elements) of the SIMT J copy
+    int ldk = 0, mpad = 0;       // tensor path padding
+    void *dJ = nullptr;          // J in working precision
+    int8_t *dJ8 = nullptr;       // int8 copy for the exact energy
+    int ld8 = 0;                 // row stride of dJ8 (multiple of 16)
+    void *dh = nullptr;          // h in state precision (float or double)
+    float *dhf = nullptr;        // h in FP32 (energy readout)
+    int8_t *dh8 = nullptr;       // integer h for the exact energy
+
+    // State and operand buffers.
+    void *dq = nullptr, *dp = nullptr;   // [R][n] state precision
+    void *dqbuf = nullptr;               // q exchange / operand double buffer
+    size_t qbuf_bytes = 0;
+    float *dzeta = nullptr, *ddt = nullptr;  // schedules [steps]
+    unsigned *dbar = nullptr;            // inter-CTA barrier counters
+    int nbar = 0;
+    int *derr = nullptr;                 // device error word
+    int8_t *dspins = nullptr;            // [R][ld8]
+    int8_t *dspins_in = nullptr;         // staging for si_energy
+    int spins_in_cap = 0;                // replicas the staging holds
+    int32_t *dE = nullptr, *dC = nullptr;
+    double *dEf = nullptr;
+    int e_cap = 0;
+    float *dstage = nullptr;             // host-input staging [R][n] x 2
+    int launches = 0;
+    int cur_parity = 0;                  // q exchange buffer holding q(t_T)
+    bool have_run = false;               // a run completed since creation
+
+    // Tensor path configuration.
+    int tile_n = 0;                      // replicas per CTA
+    int stages = 0;
+    int rpad = 0;                        // R rounded up to tile_n
+    CUtensorMap mapA, mapB;              // J tiles, q operand tiles
+
+    // Gradient workspace (allocated lazily by si_grad).
+    void *g_ws = nullptr;
+    size_t g_ws_bytes = 0;
+};
+
+// ------------------------------------------------------------ helpers
+bool is_device_ptr(const void *p);
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+inline int round_up(int a, int b) { return cdiv(a, b) * b; }
+
+// SIMT (FP32 / FP64) paths, si_simt.cu.
+si_status simt_run(Ctx *c, int steps, int8_t *spins_dev);
+si_status simt_energy(Ctx *c, const int8_t *spins_dev, int R, int ld,
+                      int32_t *E, int32_t *C, double *Ef);
+si_status simt_convert_j(Ctx *c, const float *J_dev, int n);
+si_status simt_validate(const float *J_dev, const float *h_dev, int n,
+                        int prec, unsigned long long *flags_host,
+                        long long *s_upper, cudaStream_t st);
+// Writes sign(q) for R replicas of the state into spins [R][ld].
+si_status simt_spins(Ctx *c, int8_t *spins, int ld);
+si_status simt_init_state(Ctx *c, const float *q_init, const float *p_init);
+// int8 copy of J for the exact energy.
+si_status convert_j8(Ctx *c, const float *J_dev);
+// Copies the state of the current run into q_out / p_out (device, [R][n]).
+si_status simt_copy_state(Ctx *c, float *q_out, float *p_out);
+si_status simt_copy_state_f64(Ctx *c, double *q_out, double *p_out);
+
+// Tensor-core path, si_tc.cu.
+si_status tc_prepare(Ctx *c, const float *J_dev);
+si_status tc_run(Ctx *c, int steps, int8_t *spins_dev);
+si_status tc_copy_state(Ctx *c, float *q_out, float *p_out);
+si_status tc_copy_state_f64(Ctx *c, double *q_out, double *p_out);
+si_status tc_init_state(Ctx *c, const float *q_init, const float *p_init);
+si_status tc_spins(Ctx *c, int8_t *spins, int ld);
+const char *tc_describe(const Ctx *c, char *buf, int len);
+
+// Adjoint, si_adjoint.cu.
+si_status adjoint_grad(Ctx *c, int steps, float *g_zeta, float *g_dt,
+                       float *g_k, float *objective);
+
+// Validation flags (bit set = property violated / present).
+enum : unsigned long long {
+    VF_ASYM = 1ull << 0,
+    VF_DIAG = 1ull << 1,
+    VF_NONFINITE = 1ull << 2,
+    VF_NOT_INT8 = 1ull << 3,
+    VF_NOT_E4M3 = 1ull << 4,
+    VF_H_NOT_INT8 = 1ull << 5,
+    VF_H_NONFINITE = 1ull << 6
+};
+
+}  // namespace si

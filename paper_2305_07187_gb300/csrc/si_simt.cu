@@ -1,0 +1,610 @@
+// FP32 / FP64 paths of the Spring-Ising hot path on CUDA cores, plus the
+// validation / conversion kernels and the exact energy readout.
+//
+//  * k_plain: persistent cooperative kernel for few replicas (R <= 4).  Each
+//    CTA owns a contiguous block of rows of J, keeps them resident in shared
+//    memory when they fit (else streams them from L2 with 128-bit loads),
+//    computes F_i = sum_j J_ij q_j with warp-shuffle reductions and applies
+//    the integrator of Eq. 8 in place; a bounded grid barrier separates steps.
+//  * k_tiled_step: one launch per step, 64x64 output tiles of F = J Q^T for
+//    many replicas with the integrator fused into the epilogue.
+//  * k_energy_i8: exact int32 Ising energy (Eq. 1) and cut with dp4a.
+//  * k_energy_f: energy for non-integer J in FP32.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "si_device.cuh"
+
+namespace si {
+
+// ====================================================================== K1
+constexpr int PLAIN_RMAX = 4;
+constexpr int PLAIN_THREADS = 512;
+
+template <typename T>
+struct PlainArgs {
+    const T *J;
+    int ldj;               // row stride of J and of the q buffers (elements)
+    const T *h;            // [n] or null
+    int n, R, steps;
+    const float *zeta, *dt;
+    T *qbuf;               // [2][R][ldj]; step t reads buffer t&1
+    T *p;                  // [R][n]
+    int8_t *spins;         // [R][lds] or null (written after the last step)
+    int lds;
+    unsigned *bar;
+    int *err;
+    long long limit_ns;
+    StepParams sp;
+    int rows_per_block;
+    int j_resident;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(PLAIN_THREADS, 1) k_plain(PlainArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int VEC = 16 / sizeof(T);
+    T *sq = reinterpret_cast<T *>(smem_raw);            // [R][ldj]
+    T *sJ = sq + (size_t)a.R * a.ldj;                    // [rows][ldj]
+    const int row0 = blockIdx.x * a.rows_per_block;
+    const int nrows = max(0, min(a.rows_per_block, a.n - row0));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = blockDim.x >> 5;
+
+    if (a.j_resident && nrows > 0) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(a.J + (size_t)row0 * a.ldj);
+        uint4 *dst = reinterpret_cast<uint4 *>(sJ);
+        const int total = nrows * a.ldj / VEC;
+        for (int e = threadIdx.x; e < total; e += blockDim.x) dst[e] = src[e];
+    }
+    for (int t = 0; t < a.steps; ++t) {
+        const T *qc = a.qbuf + (size_t)(t & 1) * a.R * a.ldj;
+        T *qn = a.qbuf + (size_t)((t + 1) & 1) * a.R * a.ldj;
+        {
+            const uint4 *src = reinterpret_cast<const uint4 *>(qc);
+            uint4 *dst = reinterpret_cast<uint4 *>(sq);
+            const int total = a.R * a.ldj / VEC;
+            for (int e = threadIdx.x; e < total; e += blockDim.x) dst[e] = __ldcg(src + e);
+        }
+        __syncthreads();
+        const T zt = (T)a.zeta[t], dtt = (T)a.dt[t];
+        const T dtm = dtt / (T)a.sp.m;
+        for (int rr = warp; rr < nrows; rr += nwarps) {
+            const int i = row0 + rr;
+            const T *Jrow = a.j_resident ? sJ + (size_t)rr * a.ldj : a.J + (size_t)i * a.ldj;
+            // Per lane: FMA chains over 16-byte chunks, chunk sums added with
+            // compensation; the warp tree carries the compensation too.
+            CompSum<T> acc[PLAIN_RMAX];
+#pragma unroll
+            for (int r = 0; r < PLAIN_RMAX; ++r) acc[r].init();
+            for (int j = lane * VEC; j < a.ldj; j += 32 * VEC) {
+                uint4 jv;
+                if (a.j_resident) jv = *reinterpret_cast<const uint4 *>(Jrow + j);
+                else jv = __ldg(reinterpret_cast<const uint4 *>(Jrow + j));
+                const T *jj = reinterpret_cast<const T *>(&jv);
+#pragma unroll
+                for (int r = 0; r < PLAIN_RMAX; ++r) {
+                    if (r < a.R) {
+                        uint4 qv = *reinterpret_cast<const uint4 *>(sq + (size_t)r * a.ldj + j);
+                        const T *qq = reinterpret_cast<const T *>(&qv);
+                        T d = jj[0] * qq[0];
+#pragma unroll
+                        for (int v = 1; v < VEC; ++v) d = fma(jj[v], qq[v], d);
+                        acc[r].add(d);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < PLAIN_RMAX; ++r) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const T oh = __shfl_down_sync(0xffffffffu, acc[r].hi, off);
+                    const T ol = __shfl_down_sync(0xffffffffu, acc[r].lo, off);
+                    acc[r].merge(oh, ol);
+                }
+            }
+            if (lane == 0) {
+                const T hi = a.h ? a.h[i] : (T)0;
+                for (int r = 0; r < a.R; ++r) {
+                    T q = sq[(size_t)r * a.ldj + i];
+                    T p = a.p[(size_t)r * a.n + i];
+                    T qo, po;
+                    integrate<T>(q, p, acc[r].value() + hi, zt, dtt, dtm, a.sp, qo, po);
+                    qn[(size_t)r * a.ldj + i] = qo;
+                    a.p[(size_t)r * a.n + i] = po;
+                    if (a.spins && t == a.steps - 1) a.spins[(size_t)r * a.lds + i] = spin_of(qo);
+                }
+            }
+        }
+        if (!grid_barrier(a.bar, (unsigned)(t + 1) * gridDim.x, a.err, a.limit_ns)) break;
+    }
+}
+
+// ====================================================================== tiled
+constexpr int TB_M = 64, TB_R = 64, TB_K = 16, TB_THREADS = 256;
+
+template <typename T>
+struct TiledArgs {
+    const T *J;
+    int ldj;
+    const T *h;
+    int n, R;
+    const T *qc;      // [R][ldj] positions at t_n
+    T *qn;            // [R][ldj] positions at t_{n+1}
+    T *p;             // [R][n]
+    int8_t *spins;    // [R][lds] or null
+    int lds;
+    StepParams sp;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(TB_THREADS) k_tiled_step(TiledArgs<T> a, const float *zeta,
+                                                           const float *dt, int t) {
+    __shared__ T As[TB_K][TB_M + 1];
+    __shared__ T Bs[TB_K][TB_R + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int i0 = blockIdx.x * TB_M, r0 = blockIdx.y * TB_R;
+    // Each 16-wide K chunk is an FMA chain; chunk sums are accumulated with
+    // compensation (two_sum) across the K loop.
+    CompSum<T> acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v].init();
+
+    // Loader mapping: 64 rows x 16 k = 1024 elements, 4 per thread.
+    const int lrow = tid / 4, lk = (tid % 4) * 4;
+    for (int k0 = 0; k0 < a.ldj; k0 += TB_K) {
+        {
+            const int i = i0 + lrow;
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                As[lk + v][lrow] = (i < a.n) ? a.J[(size_t)i * a.ldj + k0 + lk + v] : (T)0;
+            const int r = r0 + lrow;
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                Bs[lk + v][lrow] = (r < a.R) ? a.qc[(size_t)r * a.ldj + k0 + lk + v] : (T)0;
+        }
+        __syncthreads();
+        T part[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) part[u][v] = (T)0;
+#pragma unroll
+        for (int kk = 0; kk < TB_K; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) av[u] = As[kk][ty * 4 + u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) bv[v] = Bs[kk][tx * 4 + v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) part[u][v] = fma(av[u], bv[v], part[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v].add(part[u][v]);
+        __syncthreads();
+    }
+    const T zt = (T)zeta[t], dtt = (T)dt[t], dtm = dtt / (T)a.sp.m;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + ty * 4 + u;
+        if (i >= a.n) continue;
+        const T hi = a.h ? a.h[i] : (T)0;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int r = r0 + tx * 4 + v;
+            if (r >= a.R) continue;
+            T q = a.qc[(size_t)r * a.ldj + i];
+            T p = a.p[(size_t)r * a.n + i];
+            T qo, po;
+            integrate<T>(q, p, acc[u][v].value() + hi, zt, dtt, dtm, a.sp, qo, po);
+            a.qn[(size_t)r * a.ldj + i] = qo;
+            a.p[(size_t)r * a.n + i] = po;
+            if (a.spins) a.spins[(size_t)r * a.lds + i] = spin_of(qo);
+        }
+    }
+}
+
+// ====================================================================== misc
+__global__ void k_validate(const float *J, const float *h, int n, int prec,
+                           unsigned long long *flags, long long *s_upper) {
+    const long long total = (long long)n * n;
+    unsigned long long f = 0;
+    long long s = 0;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        const float v = J[e];
+        if (!isfinite(v)) f |= VF_NONFINITE;
+        if (i == j && v != 0.0f) f |= VF_DIAG;
+        if (j > i && J[(size_t)j * n + i] != v) f |= VF_ASYM;
+        const bool is_int = isfinite(v) && v == rintf(v) && fabsf(v) <= 127.0f;
+        if (!is_int) f |= VF_NOT_INT8;
+        else if (j > i) s += (long long)v;
+        if (isfinite(v)) {
+            __nv_fp8_e4m3 e8(v);
+            if ((float)e8 != v) f |= VF_NOT_E4M3;
+        }
+    }
+    if (h) {
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+            const float v = h[e];
+            if (!isfinite(v)) f |= VF_H_NONFINITE;
+            if (!(isfinite(v) && v == rintf(v) && fabsf(v) <= 127.0f)) f |= VF_H_NOT_INT8;
+        }
+    }
+    (void)prec;
+    if (f) atomicOr(flags, f);
+    if (s) atomicAdd(reinterpret_cast<unsigned long long *>(s_upper), (unsigned long long)s);
+}
+
+template <typename T>
+__global__ void k_convert_j(const float *J, int n, T *out, int ld) {
+    const long long total = (long long)n * ld;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ld), j = (int)(e % ld);
+        out[e] = (j < n) ? (T)J[(size_t)i * n + j] : (T)0;
+    }
+}
+
+__global__ void k_convert_j8(const float *J, int n, int8_t *out, int ld) {
+    const long long total = (long long)n * ld;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ld), j = (int)(e % ld);
+        out[e] = (j < n) ? (int8_t)J[(size_t)i * n + j] : (int8_t)0;
+    }
+}
+
+template <typename T>
+__global__ void k_init_state(const float *q_init, const float *p_init, int n, int R,
+                             T *qbuf, int ldq, T *p) {
+    const long long total = (long long)R * ldq;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / ldq), i = (int)(e % ldq);
+        if (i < n) {
+            qbuf[e] = (T)q_init[(size_t)r * n + i];
+            p[(size_t)r * n + i] = p_init ? (T)p_init[(size_t)r * n + i] : (T)0;
+        } else {
+            qbuf[e] = (T)0;
+        }
+    }
+}
+
+template <typename T, typename O>
+__global__ void k_copy_state(const T *qbuf, int ldq, const T *p, int n, int R, O *q_out,
+                             O *p_out) {
+    const long long total = (long long)R * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), i = (int)(e % n);
+        if (q_out) q_out[e] = (O)qbuf[(size_t)r * ldq + i];
+        if (p_out) p_out[e] = (O)p[e];
+    }
+}
+
+template <typename T>
+__global__ void k_spins(const T *qbuf, int ldq, int n, int R, int8_t *spins, int lds) {
+    const long long total = (long long)R * lds;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / lds), i = (int)(e % lds);
+        spins[e] = (i < n) ? spin_of(qbuf[(size_t)r * ldq + i]) : (int8_t)0;
+    }
+}
+
+// ================================================================== energy
+constexpr int EN_RB = 8;          // replicas per CTA
+constexpr int EN_THREADS = 256;
+
+// s_r = sum_ij J_ij s_i s_j exactly in int32 (|s_r| <= 127 n^2 < 2^31 for
+// n <= 4096; larger n uses a 64-bit block sum), E = -s/2 - sum h_i s_i,
+// cut = (s - 2 S_upper) / 4 with S_upper = sum_{i<j} J_ij.
+__global__ void __launch_bounds__(EN_THREADS) k_energy_i8(const int8_t *J8, int ld8,
+                                                         const int8_t *h8, int n, int R,
+                                                         const int8_t *s, int lds,
+                                                         long long s_upper, int32_t *E,
+                                                         int32_t *C) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int8_t *ss = reinterpret_cast<int8_t *>(smem_raw);   // [EN_RB][ld8]
+    __shared__ long long red[EN_RB];
+    __shared__ long long redh[EN_RB];
+    const int r0 = blockIdx.x * EN_RB;
+    const int nr = min(EN_RB, R - r0);
+    for (int e = threadIdx.x; e < EN_RB * ld8; e += blockDim.x) {
+        const int rr = e / ld8, i = e % ld8;
+        ss[e] = (rr < nr && i < n) ? s[(size_t)(r0 + rr) * lds + i] : (int8_t)0;
+    }
+    if (threadIdx.x < EN_RB) { red[threadIdx.x] = 0; redh[threadIdx.x] = 0; }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    long long part[EN_RB];
+#pragma unroll
+    for (int r = 0; r < EN_RB; ++r) part[r] = 0;
+    for (int i = warp; i < n; i += nwarps) {
+        int dot[EN_RB];
+#pragma unroll
+        for (int r = 0; r < EN_RB; ++r) dot[r] = 0;
+        const int8_t *Jrow = J8 + (size_t)i * ld8;
+        for (int j = lane * 16; j < ld8; j += 32 * 16) {
+            const int4 jv = __ldg(reinterpret_cast<const int4 *>(Jrow + j));
+#pragma unroll
+            for (int r = 0; r < EN_RB; ++r) {
+                const int4 sv = *reinterpret_cast<const int4 *>(ss + (size_t)r * ld8 + j);
+                dot[r] = __dp4a(jv.x, sv.x, dot[r]);
+                dot[r] = __dp4a(jv.y, sv.y, dot[r]);
+                dot[r] = __dp4a(jv.z, sv.z, dot[r]);
+                dot[r] = __dp4a(jv.w, sv.w, dot[r]);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < EN_RB; ++r) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) dot[r] += __shfl_down_sync(0xffffffffu, dot[r], off);
+            if (lane == 0) part[r] += (long long)ss[(size_t)r * ld8 + i] * dot[r];
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < EN_RB; ++r) atomicAdd(reinterpret_cast<unsigned long long *>(&red[r]), (unsigned long long)part[r]);
+    }
+    if (h8) {
+        for (int e = threadIdx.x; e < EN_RB * n; e += blockDim.x) {
+            const int rr = e / n, i = e % n;
+            const long long v = (long long)h8[i] * ss[(size_t)rr * ld8 + i];
+            if (v) atomicAdd(reinterpret_cast<unsigned long long *>(&redh[rr]), (unsigned long long)v);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nr) {
+        const long long sr = red[threadIdx.x];
+        if (E) E[r0 + threadIdx.x] = (int32_t)(-(sr / 2) - redh[threadIdx.x]);
+        if (C) C[r0 + threadIdx.x] = (int32_t)((sr - 2 * s_upper) / 4);
+    }
+}
+
+// Energy for any J in FP32: each warp accumulates s_i * (J s)_i over its rows
+// in a fixed order; warps are summed in index order (deterministic).
+template <typename TJ>
+__global__ void __launch_bounds__(EN_THREADS) k_energy_f(const TJ *J, int ldj, const float *h,
+                                                        int n, int R, const int8_t *s, int lds,
+                                                        double *Ef) {
+    __shared__ float wsum[EN_THREADS / 32];
+    __shared__ float hsum[EN_THREADS / 32];
+    const int r = blockIdx.x;
+    const int8_t *sr = s + (size_t)r * lds;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    float part = 0.f, hpart = 0.f;
+    for (int i = warp; i < n; i += nwarps) {
+        const TJ *Jrow = J + (size_t)i * ldj;
+        float dot = 0.f;
+        for (int j = lane; j < n; j += 32) dot += (float)Jrow[j] * (float)sr[j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) dot += __shfl_down_sync(0xffffffffu, dot, off);
+        if (lane == 0) {
+            part += (float)sr[i] * dot;
+            if (h) hpart += h[i] * (float)sr[i];
+        }
+    }
+    if (lane == 0) { wsum[warp] = part; hsum[warp] = hpart; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float a = 0.f, b = 0.f;
+        for (int w = 0; w < nwarps; ++w) { a += wsum[w]; b += hsum[w]; }
+        Ef[r] = (double)(-0.5f * a - b);
+    }
+}
+
+// ================================================================== host side
+static int grid_for(long long total, int threads, int sms) {
+    long long g = (total + threads - 1) / threads;
+    return (int)std::max(1LL, std::min(g, (long long)sms * 8));
+}
+
+si_status simt_validate(const float *J_dev, const float *h_dev, int n, int prec,
+                        unsigned long long *flags_host, long long *s_upper, cudaStream_t st) {
+    unsigned long long *dflags = nullptr;
+    SI_CUDA_TRY(cudaMallocAsync((void **)&dflags, 16, st));
+    SI_CUDA_TRY(cudaMemsetAsync(dflags, 0, 16, st));
+    int dev = 0, sms = 0;
+    SI_CUDA_TRY(cudaGetDevice(&dev));
+    SI_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    k_validate<<<grid_for((long long)n * n, 256, sms), 256, 0, st>>>(
+        J_dev, h_dev, n, prec, dflags, reinterpret_cast<long long *>(dflags + 1));
+    SI_CUDA_TRY(cudaGetLastError());
+    unsigned long long hostv[2];
+    SI_CUDA_TRY(cudaMemcpyAsync(hostv, dflags, 16, cudaMemcpyDeviceToHost, st));
+    SI_CUDA_TRY(cudaStreamSynchronize(st));
+    SI_CUDA_TRY(cudaFreeAsync(dflags, st));
+    *flags_host = hostv[0];
+    *s_upper = (long long)hostv[1];
+    return SI_OK;
+}
+
+si_status simt_convert_j(Ctx *c, const float *J_dev, int n) {
+    const bool f64 = c->prm.prec == SI_PREC_FP64;
+    const size_t es = f64 ? 8 : 4;
+    c->ldj = round_up(n, 16);
+    SI_CUDA_TRY(cudaMalloc(&c->dJ, (size_t)n * c->ldj * es));
+    const int g = grid_for((long long)n * c->ldj, 256, c->num_sms);
+    if (f64) k_convert_j<double><<<g, 256, 0, c->stream>>>(J_dev, n, (double *)c->dJ, c->ldj);
+    else k_convert_j<float><<<g, 256, 0, c->stream>>>(J_dev, n, (float *)c->dJ, c->ldj);
+    SI_CUDA_TRY(cudaGetLastError());
+    return SI_OK;
+}
+
+si_status convert_j8(Ctx *c, const float *J_dev) {
+    k_convert_j8<<<grid_for((long long)c->n * c->ld8, 256, c->num_sms), 256, 0, c->stream>>>(
+        J_dev, c->n, c->dJ8, c->ld8);
+    SI_CUDA_TRY(cudaGetLastError());
+    return SI_OK;
+}
+
+template <typename T>
+static si_status plain_launch(Ctx *c, int steps, int8_t *spins_dev) {
+    PlainArgs<T> a;
+    a.J = (const T *)c->dJ;
+    a.ldj = c->ldj;
+    a.h = (const T *)c->dh;
+    a.n = c->n;
+    a.R = c->R;
+    a.steps = steps;
+    a.zeta = c->dzeta;
+    a.dt = c->ddt;
+    a.qbuf = (T *)c->dqbuf;
+    a.p = (T *)c->dp;
+    a.spins = spins_dev;
+    a.lds = c->ld8;
+    a.bar = c->dbar;
+    a.err = c->derr;
+    a.limit_ns = c->spin_limit_ns;
+    a.sp = StepParams{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max,
+                      c->prm.update_order, c->prm.wall_zero_p};
+    int max_smem = 0;
+    SI_CUDA_TRY(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    const size_t sq_bytes = (size_t)c->R * c->ldj * sizeof(T);
+    int grid = c->num_sms;
+    a.rows_per_block = cdiv(c->n, grid);
+    grid = cdiv(c->n, a.rows_per_block);
+    const size_t sj_bytes = (size_t)a.rows_per_block * c->ldj * sizeof(T);
+    a.j_resident = (sq_bytes + sj_bytes + 1024 <= (size_t)max_smem) ? 1 : 0;
+    const size_t smem = sq_bytes + (a.j_resident ? sj_bytes : 0);
+    if (smem > (size_t)max_smem) {
+        set_error("plain path: q vectors do not fit in shared memory");
+        return SI_ERR_UNSUPPORTED;
+    }
+    SI_CUDA_TRY(cudaFuncSetAttribute(k_plain<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plain<T>, PLAIN_THREADS, smem));
+    if (per_sm * c->num_sms < grid) {
+        set_error("plain path: grid cannot be co-resident");
+        return SI_ERR_UNSUPPORTED;
+    }
+    SI_CUDA_TRY(cudaMemsetAsync(c->dbar, 0, sizeof(unsigned) * c->nbar, c->stream));
+    void *args[] = {&a};
+    SI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_plain<T>, dim3(grid), dim3(PLAIN_THREADS),
+                                            args, smem, c->stream));
+    c->launches += 1;
+    return SI_OK;
+}
+
+template <typename T>
+static si_status tiled_launch(Ctx *c, int steps, int8_t *spins_dev) {
+    TiledArgs<T> a;
+    a.J = (const T *)c->dJ;
+    a.ldj = c->ldj;
+    a.h = (const T *)c->dh;
+    a.n = c->n;
+    a.R = c->R;
+    a.p = (T *)c->dp;
+    a.lds = c->ld8;
+    a.sp = StepParams{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max,
+                      c->prm.update_order, c->prm.wall_zero_p};
+    T *qb = (T *)c->dqbuf;
+    const size_t plane = (size_t)c->R * c->ldj;
+    dim3 grid(cdiv(c->n, TB_M), cdiv(c->R, TB_R));
+    for (int t = 0; t < steps; ++t) {
+        a.qc = qb + (size_t)(t & 1) * plane;
+        a.qn = qb + (size_t)((t + 1) & 1) * plane;
+        a.spins = (t == steps - 1) ? spins_dev : nullptr;
+        k_tiled_step<T><<<grid, TB_THREADS, 0, c->stream>>>(a, c->dzeta, c->ddt, t);
+    }
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += steps;
+    return SI_OK;
+}
+
+si_status simt_run(Ctx *c, int steps, int8_t *spins_dev) {
+    const bool f64 = c->prm.prec == SI_PREC_FP64;
+    if (c->path == Path::PLAIN_PERSISTENT)
+        return f64 ? plain_launch<double>(c, steps, spins_dev) : plain_launch<float>(c, steps, spins_dev);
+    return f64 ? tiled_launch<double>(c, steps, spins_dev) : tiled_launch<float>(c, steps, spins_dev);
+}
+
+si_status simt_init_state(Ctx *c, const float *q_init, const float *p_init) {
+    const int g = grid_for((long long)c->R * c->ldj, 256, c->num_sms);
+    if (c->prm.prec == SI_PREC_FP64)
+        k_init_state<double><<<g, 256, 0, c->stream>>>(q_init, p_init, c->n, c->R, (double *)c->dqbuf, c->ldj, (double *)c->dp);
+    else
+        k_init_state<float><<<g, 256, 0, c->stream>>>(q_init, p_init, c->n, c->R, (float *)c->dqbuf, c->ldj, (float *)c->dp);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    return SI_OK;
+}
+
+template <typename O>
+static si_status copy_state_impl(Ctx *c, O *q_out, O *p_out) {
+    const int parity = c->cur_parity;
+    const int g = grid_for((long long)c->R * c->n, 256, c->num_sms);
+    if (c->prm.prec == SI_PREC_FP64) {
+        const double *qb = (const double *)c->dqbuf + (size_t)parity * c->R * c->ldj;
+        k_copy_state<double, O><<<g, 256, 0, c->stream>>>(qb, c->ldj, (const double *)c->dp, c->n, c->R, q_out, p_out);
+    } else {
+        const float *qb = (const float *)c->dqbuf + (size_t)parity * c->R * c->ldj;
+        k_copy_state<float, O><<<g, 256, 0, c->stream>>>(qb, c->ldj, (const float *)c->dp, c->n, c->R, q_out, p_out);
+    }
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    return SI_OK;
+}
+
+si_status simt_copy_state(Ctx *c, float *q_out, float *p_out) { return copy_state_impl<float>(c, q_out, p_out); }
+si_status simt_copy_state_f64(Ctx *c, double *q_out, double *p_out) {
+    return copy_state_impl<double>(c, q_out, p_out);
+}
+
+si_status simt_spins(Ctx *c, int8_t *spins, int ld) {
+    const int parity = c->cur_parity;
+    const int g = grid_for((long long)c->R * ld, 256, c->num_sms);
+    if (c->prm.prec == SI_PREC_FP64)
+        k_spins<double><<<g, 256, 0, c->stream>>>((const double *)c->dqbuf + (size_t)parity * c->R * c->ldj, c->ldj, c->n, c->R, spins, ld);
+    else
+        k_spins<float><<<g, 256, 0, c->stream>>>((const float *)c->dqbuf + (size_t)parity * c->R * c->ldj, c->ldj, c->n, c->R, spins, ld);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    return SI_OK;
+}
+
+si_status simt_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E, int32_t *C,
+                      double *Ef) {
+    if (E || C) {
+        const size_t smem = (size_t)EN_RB * c->ld8;
+        if (smem > 200 * 1024) {
+            set_error("exact energy: n too large for the shared-memory spin tile");
+            return SI_ERR_UNSUPPORTED;
+        }
+        SI_CUDA_TRY(cudaFuncSetAttribute(k_energy_i8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        k_energy_i8<<<cdiv(R, EN_RB), EN_THREADS, smem, c->stream>>>(
+            c->dJ8, c->ld8, c->dh8, c->n, R, spins_dev, ld, c->s_upper, E, C);
+        SI_CUDA_TRY(cudaGetLastError());
+        c->launches += 1;
+    }
+    if (Ef) {
+        const float *hf = c->dhf;
+        if (c->path == Path::TENSOR) {
+            k_energy_f<__nv_bfloat16><<<R, EN_THREADS, 0, c->stream>>>(
+                (const __nv_bfloat16 *)c->dJ, c->ldk, hf, c->n, R, spins_dev, ld, Ef);
+        } else if (c->prm.prec == SI_PREC_FP64) {
+            k_energy_f<double><<<R, EN_THREADS, 0, c->stream>>>(
+                (const double *)c->dJ, c->ldj, hf, c->n, R, spins_dev, ld, Ef);
+        } else {
+            k_energy_f<float><<<R, EN_THREADS, 0, c->stream>>>(
+                (const float *)c->dJ, c->ldj, hf, c->n, R, spins_dev, ld, Ef);
+        }
+        SI_CUDA_TRY(cudaGetLastError());
+        c->launches += 1;
+    }
+    return SI_OK;
+}
+
+}  // namespace si

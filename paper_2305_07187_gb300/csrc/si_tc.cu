@@ -1,0 +1,652 @@
+// Tensor-core path of the Spring-Ising hot path (sm_103a, tcgen05 + TMA).
+//
+// One persistent launch runs all T steps.  CTA (mt, rb) owns the output tile
+// F[mt*128 .. +128][rb*BN .. +BN] of F = J Q^T (rows = spins, columns =
+// replicas) for the whole run:
+//   warp 0      TMA producer: J tile (128 x 64 bf16) and q tile (BN x 64 bf16)
+//               per K block into an S-stage shared-memory ring (128B swizzle)
+//   warp 1      allocates TMEM and issues tcgen05.mma (M=128, N=BN, K=16)
+//               into an FP32 accumulator in TMEM
+//   warps 2..5  epilogue: tcgen05.ld of the accumulator, the spring
+//               integrator of Eq. 8 with the walls of Eq. 6 on the q, p state
+//               that lives in TMEM next to the accumulator, and the bf16 copy
+//               of the new q that is the next step's MMA operand
+// Steps are separated by a bounded counter barrier over the CTAs that share a
+// replica block (they exchange q through the double-buffered operand array
+// in L2); CTAs of different replica blocks never wait on each other.
+// Every wait (mbarrier or counter) has a time limit; on expiry the kernel
+// raises the device error word, drains its own copies and MMAs, frees TMEM
+// and returns.
+#include <algorithm>
+#include <cstdio>
+
+#include "si_device.cuh"
+
+namespace si {
+
+constexpr int TC_BM = 128;       // spins per CTA (MMA M)
+constexpr int TC_BK = 64;        // K elements per stage (128 bytes of bf16)
+constexpr int TC_THREADS = 192;  // 6 warps
+constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;
+
+struct TcArgs {
+    int n, R, steps;
+    int mtiles, rblocks, kblocks;
+    int ldk, rpad;
+    const float *zeta, *dt, *h;
+    float *q_state, *p_state;    // [R][n], initial in / final out
+    __nv_bfloat16 *qop;          // [2][rpad][ldk] bf16 operand of step t in plane t&1
+    int8_t *spins;               // [R][lds] or null
+    int lds;
+    unsigned *bar;               // [rblocks]
+    int *err;
+    long long limit_ns;
+    StepParams sp;
+};
+
+// ------------------------------------------------------------------ PTX glue
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `bar` with the given parity.  Returns false
+// (and raises the error word on timeout) if the run is being aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err,
+                                          volatile int *abort_flag, long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 15u) == 0) {
+            if (*abort_flag || ld_volatile_int(err) != 0) {
+                *abort_flag = 1;
+                return false;
+            }
+            if ((long long)(globaltimer_ns() - t0) > limit_ns) {
+                atomicCAS(err, 0, DEV_TIMEOUT_MBAR);
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major bf16 tile whose rows are 128
+// bytes, written by TMA with the 128-byte swizzle: 8-row groups are 1024
+// bytes apart (stride byte offset), version 1, layout SWIZZLE_128B.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;               // leading byte offset (unused here)
+    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
+    d |= (uint64_t)1 << 46;               // descriptor version
+    d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D fp32, A bf16, B bf16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+#define TC_REG32(a)                                                                          \
+    "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]),      \
+        "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]),           \
+        "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(a[16]), "=r"(a[17]), "=r"(a[18]),        \
+        "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]), "=r"(a[24]),        \
+        "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]),        \
+        "=r"(a[31])
+#define TC_IN32(a)                                                                             \
+    "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),    \
+        "r"(a[8]), "r"(a[9]), "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]),      \
+        "r"(a[15]), "r"(a[16]), "r"(a[17]), "r"(a[18]), "r"(a[19]), "r"(a[20]), "r"(a[21]),    \
+        "r"(a[22]), "r"(a[23]), "r"(a[24]), "r"(a[25]), "r"(a[26]), "r"(a[27]), "r"(a[28]),    \
+        "r"(a[29]), "r"(a[30]), "r"(a[31])
+
+// 32 consecutive TMEM columns of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : TC_REG32(v)
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        TC_IN32(v)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// ------------------------------------------------------------------ kernel
+template <int BN, int S>
+struct TcSmem {
+    static constexpr int B_BYTES = BN * TC_BK * 2;
+    static constexpr int STAGE_BYTES = TC_A_BYTES + B_BYTES;
+    static constexpr int TILES = S * STAGE_BYTES;
+    static constexpr int BARS = TILES;                    // mbarriers after the tiles
+    static constexpr int NBARS = 2 * S + 4;               // full, empty, accf, tmem_empty, epi_done, drain
+    static constexpr int TOTAL = TILES + NBARS * 8 + 16;  // + tmem slot, abort flag
+    static constexpr int TMEM_COLS = (3 * BN <= 256) ? 256 : 512;
+};
+
+template <int BN, int S>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_tc_run(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+             TcArgs a) {
+    using L = TcSmem<BN, S>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar0 = sbase + L::BARS;
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
+    const uint32_t accf_bar = bar0 + 8u * (2 * S);
+    const uint32_t tmem_empty_bar = bar0 + 8u * (2 * S + 1);
+    const uint32_t epi_done_bar = bar0 + 8u * (2 * S + 2);
+    const uint32_t drain_bar = bar0 + 8u * (2 * S + 3);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::BARS + L::NBARS * 8);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::BARS + L::NBARS * 8 + 4);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt = blockIdx.x % a.mtiles, rb = blockIdx.x / a.mtiles;
+    const int m0 = mt * TC_BM, r0 = rb * BN;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        mbar_init(accf_bar, 1);
+        mbar_init(tmem_empty_bar, 4);
+        mbar_init(epi_done_bar, 4);
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"((uint32_t)L::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t it = 0;  // pipeline slot counter
+            bool ok = true;
+            for (int t = 0; t < a.steps && ok; ++t) {
+                if (t > 0) {
+                    ok = wait_counter_geq(a.bar + rb, (unsigned)t * a.mtiles, a.err, a.limit_ns);
+                    if (!ok) { *abort_flag = 1; break; }
+                    fence_proxy_async_global();
+                }
+                const int yb = (t & 1) * a.rpad + r0;
+                for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+                    const int s = it % S;
+                    const uint32_t ph = (it / S) & 1u;
+                    if (!mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                    const uint32_t dA = sbase + s * L::STAGE_BYTES;
+                    const uint32_t dB = dA + TC_A_BYTES;
+                    mbar_arrive_expect_tx(full_bar(s), (uint32_t)L::STAGE_BYTES);
+                    tma_load_2d(dA, &mapA, full_bar(s), kb * TC_BK, m0);
+                    tma_load_2d(dB, &mapB, full_bar(s), kb * TC_BK, yb);
+                }
+            }
+            // Let every copy this thread issued land before the CTA exits.
+            const uint32_t first = it > (uint32_t)S ? it - S : 0u;
+            for (uint32_t k = first; k < it; ++k) {
+                const unsigned long long t0 = globaltimer_ns();
+                while (!mbar_try_wait(full_bar(k % S), (k / S) & 1u)) {
+                    if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                        atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
+                        break;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = 0; t < a.steps && ok; ++t) {
+                if (t > 0) {
+                    if (!mbar_wait(tmem_empty_bar, (uint32_t)((t - 1) & 1), a.err, abort_flag, a.limit_ns)) break;
+                }
+                tc_fence_after();
+                for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+                    const int s = it % S;
+                    const uint32_t ph = (it / S) & 1u;
+                    if (!mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t aA = sbase + s * L::STAGE_BYTES;
+                    const uint32_t aB = aA + TC_A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                        mma_bf16(tmem, sdesc_sw128(aA + kk * 32), sdesc_sw128(aB + kk * 32), idesc,
+                                 (kb | kk) != 0 ? 1u : 0u);
+                    }
+                    mma_commit(empty_bar(s));
+                }
+                if (ok) mma_commit(accf_bar);
+            }
+            // Drain: wait until every MMA this thread issued has completed.
+            mma_commit(drain_bar);
+            const unsigned long long t0 = globaltimer_ns();
+            while (!mbar_try_wait(drain_bar, 0u)) {
+                if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                    atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
+                    break;
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue
+        const int quad = warp & 3;                  // TMEM lane quadrant of this warp
+        const int row = quad * 32 + lane;
+        const int i = m0 + row;
+        const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+        const bool row_ok = i < a.n;
+        const float hi = (a.h && row_ok) ? a.h[i] : 0.f;
+        const size_t plane = (size_t)a.rpad * a.ldk;
+        // Load the initial state into TMEM: q at columns [BN, 2BN), p at [2BN, 3BN).
+#pragma unroll 1
+        for (int c = 0; c < BN / 32; ++c) {
+            uint32_t vq[32], vp[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int r = r0 + c * 32 + j;
+                const bool ok = row_ok && r < a.R;
+                vq[j] = __float_as_uint(ok ? a.q_state[(size_t)r * a.n + i] : 0.f);
+                vp[j] = __float_as_uint(ok ? a.p_state[(size_t)r * a.n + i] : 0.f);
+            }
+            tmem_st32(tl + BN + c * 32, vq);
+            tmem_st32(tl + 2 * BN + c * 32, vp);
+        }
+        tmem_wait_st();
+#pragma unroll 1
+        for (int t = 0; t < a.steps; ++t) {
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(accf_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+            tc_fence_after();
+            const float zt = a.zeta[t], dtt = a.dt[t];
+            const float dtm = dtt / a.sp.m;
+            const bool last = (t == a.steps - 1);
+            __nv_bfloat16 *qn = a.qop + (size_t)((t + 1) & 1) * plane;
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t vf[32], vq[32], vp[32];
+                tmem_ld32(tl + c * 32, vf);
+                tmem_ld32(tl + BN + c * 32, vq);
+                tmem_ld32(tl + 2 * BN + c * 32, vp);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    float qo, po;
+                    integrate<float>(__uint_as_float(vq[j]), __uint_as_float(vp[j]),
+                                     __uint_as_float(vf[j]) + hi, zt, dtt, dtm, a.sp, qo, po);
+                    vq[j] = __float_as_uint(qo);
+                    vp[j] = __float_as_uint(po);
+                }
+                tmem_st32(tl + BN + c * 32, vq);
+                tmem_st32(tl + 2 * BN + c * 32, vp);
+                if (row_ok) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int r = r0 + c * 32 + j;
+                        if (r < a.R) {
+                            const float qv = __uint_as_float(vq[j]);
+                            if (!last) {
+                                qn[(size_t)r * a.ldk + i] = __float2bfloat16_rn(qv);
+                            } else {
+                                a.q_state[(size_t)r * a.n + i] = qv;
+                                a.p_state[(size_t)r * a.n + i] = __uint_as_float(vp[j]);
+                                if (a.spins) a.spins[(size_t)r * a.lds + i] = spin_of(qv);
+                            }
+                        }
+                    }
+                }
+            }
+            tmem_wait_st();
+            tc_fence_before();
+            __threadfence();
+            fence_proxy_async_global();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(tmem_empty_bar);
+                mbar_arrive(epi_done_bar);
+            }
+            // One thread publishes "this CTA finished step t" to its replica block.
+            if (warp == 2 && !last) {
+                bool ok2 = true;
+                if (lane == 0) {
+                    ok2 = mbar_wait(epi_done_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns);
+                    if (ok2) {
+                        __threadfence();
+                        red_release_gpu_add(a.bar + rb, 1u);
+                    }
+                }
+                ok2 = __shfl_sync(0xffffffffu, ok2 ? 1 : 0, 0) != 0;
+                if (!ok2) break;
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)L::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------------ host side
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                     const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                     const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                     CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled get_encode() {
+    static PFN_encodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_encodeTiled>(p);
+    }
+    return fn;
+}
+
+static si_status make_map_bf16(CUtensorMap *m, void *base, int inner, int outer, int box_inner,
+                               int box_outer) {
+    PFN_encodeTiled enc = get_encode();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled unavailable");
+        return SI_ERR_CUDA;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)inner * 2};
+    cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char msg[96];
+        std::snprintf(msg, sizeof msg, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        set_error(msg);
+        return SI_ERR_CUDA;
+    }
+    return SI_OK;
+}
+
+__global__ void k_convert_j_bf16(const float *J, int n, __nv_bfloat16 *out, int ldk, int mpad) {
+    const long long total = (long long)mpad * ldk;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ldk), j = (int)(e % ldk);
+        out[e] = __float2bfloat16_rn((i < n && j < n) ? J[(size_t)i * n + j] : 0.f);
+    }
+}
+
+__global__ void k_tc_init(const float *q_init, const float *p_init, int n, int R, float *q_state,
+                          float *p_state, __nv_bfloat16 *qop, int ldk) {
+    const long long total = (long long)R * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), i = (int)(e % n);
+        const float q = q_init[e];
+        q_state[e] = q;
+        p_state[e] = p_init ? p_init[e] : 0.f;
+        qop[(size_t)r * ldk + i] = __float2bfloat16_rn(q);
+    }
+}
+
+template <typename O>
+__global__ void k_tc_copy(const float *q_state, const float *p_state, long long total, O *q_out,
+                          O *p_out) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        if (q_out) q_out[e] = (O)q_state[e];
+        if (p_out) p_out[e] = (O)p_state[e];
+    }
+}
+
+__global__ void k_tc_spins(const float *q_state, int n, int R, int8_t *spins, int ld) {
+    const long long total = (long long)R * ld;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / ld), i = (int)(e % ld);
+        spins[e] = i < n ? spin_of(q_state[(size_t)r * n + i]) : (int8_t)0;
+    }
+}
+
+template <int BN, int S>
+static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
+    using L = TcSmem<BN, S>;
+    TcArgs a;
+    a.n = c->n;
+    a.R = c->R;
+    a.steps = steps;
+    a.mtiles = c->mpad / TC_BM;
+    a.rblocks = c->rpad / BN;
+    a.kblocks = c->ldk / TC_BK;
+    a.ldk = c->ldk;
+    a.rpad = c->rpad;
+    a.zeta = c->dzeta;
+    a.dt = c->ddt;
+    a.h = c->has_h ? c->dhf : nullptr;
+    a.q_state = (float *)c->dq;
+    a.p_state = (float *)c->dp;
+    a.qop = (__nv_bfloat16 *)c->dqbuf;
+    a.spins = spins_dev;
+    a.lds = c->ld8;
+    a.bar = c->dbar;
+    a.err = c->derr;
+    a.limit_ns = c->spin_limit_ns;
+    a.sp = StepParams{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max,
+                      c->prm.update_order, c->prm.wall_zero_p};
+    const int grid = a.mtiles * a.rblocks;
+    if (a.rblocks > c->nbar) {
+        set_error("tensor path: too many replica blocks");
+        return SI_ERR_UNSUPPORTED;
+    }
+    const int smem = L::TOTAL + 1024;
+    SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int per_sm = 0;
+    SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_run<BN, S>, TC_THREADS, smem));
+    if (per_sm * c->num_sms < grid) {
+        set_error("tensor path: grid cannot be co-resident (reduce replicas per context)");
+        return SI_ERR_UNSUPPORTED;
+    }
+    SI_CUDA_TRY(cudaMemsetAsync(c->dbar, 0, sizeof(unsigned) * c->nbar, c->stream));
+    void *args[] = {(void *)&c->mapA, (void *)&c->mapB, (void *)&a};
+    SI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_tc_run<BN, S>, dim3(grid), dim3(TC_THREADS),
+                                            args, smem, c->stream));
+    c->launches += 1;
+    return SI_OK;
+}
+
+si_status tc_run(Ctx *c, int steps, int8_t *spins_dev) {
+    if (steps == 0) return SI_OK;
+    switch (c->tile_n) {
+        case 64: return tc_launch_t<64, 4>(c, steps, spins_dev);
+        case 128: return tc_launch_t<128, 6>(c, steps, spins_dev);
+        default: set_error("tensor path: unsupported tile"); return SI_ERR_UNSUPPORTED;
+    }
+}
+
+// Replica tile: 128 if the grid of 128-wide tiles fits on the GPU at one CTA
+// per SM, else 64 (two CTAs per SM), unless the caller fixed tile_n.
+static int choose_tile(const Ctx *c) {
+    if (c->prm.tile_n == 64 || c->prm.tile_n == 128) return c->prm.tile_n;
+    const int mtiles = c->mpad / TC_BM;
+    const int g128 = mtiles * cdiv(c->R, 128);
+    if (g128 <= c->num_sms && c->R > 64) return 128;
+    return 64;
+}
+
+si_status tc_prepare(Ctx *c, const float *J_dev) {
+    const int n = c->n;
+    c->ldk = round_up(n, TC_BK);
+    c->mpad = round_up(n, TC_BM);
+    c->tile_n = choose_tile(c);
+    c->rpad = round_up(c->R, c->tile_n);
+    SI_CUDA_TRY(cudaMalloc(&c->dJ, (size_t)c->mpad * c->ldk * 2));
+    k_convert_j_bf16<<<std::min(8 * c->num_sms, cdiv((long long)c->mpad * c->ldk, 256)), 256, 0, c->stream>>>(
+        J_dev, n, (__nv_bfloat16 *)c->dJ, c->ldk, c->mpad);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->qbuf_bytes = 2ull * c->rpad * c->ldk * 2;
+    SI_CUDA_TRY(cudaMalloc(&c->dqbuf, c->qbuf_bytes));
+    SI_CUDA_TRY(cudaMemsetAsync(c->dqbuf, 0, c->qbuf_bytes, c->stream));
+    SI_CUDA_TRY(cudaMalloc(&c->dq, sizeof(float) * (size_t)c->R * n));
+    SI_CUDA_TRY(cudaMalloc(&c->dp, sizeof(float) * (size_t)c->R * n));
+    si_status s = make_map_bf16(&c->mapA, c->dJ, c->ldk, c->mpad, TC_BK, TC_BM);
+    if (s != SI_OK) return s;
+    s = make_map_bf16(&c->mapB, c->dqbuf, c->ldk, 2 * c->rpad, TC_BK, c->tile_n);
+    if (s != SI_OK) return s;
+    const int mtiles = c->mpad / TC_BM;
+    const int grid = mtiles * (c->rpad / c->tile_n);
+    const int per_sm = c->tile_n == 128 ? 1 : 2;
+    if (grid > per_sm * c->num_sms) {
+        set_error("tensor path: n x replicas too large for one co-resident launch");
+        return SI_ERR_UNSUPPORTED;
+    }
+    return SI_OK;
+}
+
+si_status tc_init_state(Ctx *c, const float *q_init, const float *p_init) {
+    const long long total = (long long)c->R * c->n;
+    k_tc_init<<<std::min(8 * c->num_sms, cdiv(total, 256)), 256, 0, c->stream>>>(
+        q_init, p_init, c->n, c->R, (float *)c->dq, (float *)c->dp, (__nv_bfloat16 *)c->dqbuf, c->ldk);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    return SI_OK;
+}
+
+si_status tc_copy_state(Ctx *c, float *q_out, float *p_out) {
+    const long long total = (long long)c->R * c->n;
+    k_tc_copy<float><<<std::min(8 * c->num_sms, cdiv(total, 256)), 256, 0, c->stream>>>(
+        (const float *)c->dq, (const float *)c->dp, total, q_out, p_out);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    return SI_OK;
+}
+
+si_status tc_copy_state_f64(Ctx *c, double *q_out, double *p_out) {
+    const long long total = (long long)c->R * c->n;
+    k_tc_copy<double><<<std::min(8 * c->num_sms, cdiv(total, 256)), 256, 0, c->stream>>>(
+        (const float *)c->dq, (const float *)c->dp, total, q_out, p_out);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    return SI_OK;
+}
+
+si_status tc_spins(Ctx *c, int8_t *spins, int ld) {
+    const long long total = (long long)c->R * ld;
+    k_tc_spins<<<std::min(8 * c->num_sms, cdiv(total, 256)), 256, 0, c->stream>>>(
+        (const float *)c->dq, c->n, c->R, spins, ld);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    return SI_OK;
+}
+
+const char *tc_describe(const Ctx *c, char *buf, int len) {
+    std::snprintf(buf, len,
+                  "tcgen05 prec=%s n=%d R=%d tile=128x%d stages=%d grid=%d (mtiles=%d rblocks=%d) kblocks=%d",
+                  c->prm.prec == SI_PREC_J_FP8_Q_BF16 ? "j_fp8_q_bf16" : "j_bf16_q_bf16", c->n, c->R,
+                  c->tile_n, c->tile_n == 128 ? 6 : 4, (c->mpad / TC_BM) * (c->rpad / c->tile_n),
+                  c->mpad / TC_BM, c->rpad / c->tile_n, c->ldk / TC_BK);
+    return buf;
+}
+
+}  // namespace si
