@@ -1,0 +1,370 @@
+"""Benchmark of the Spring-Ising hot path on GB300.
+
+One bench step = one pass of the hot path over one batch: si_run of the
+batched workload (N=2000 spins, R=1024 replicas, T=2000 time steps: coupling
+force fused with the spring integrator and walls, on tensor cores) followed by
+the exact int32 energy/cut readout of the final spins (si_energy).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank runs its own replica
+batch (weak scaling, no data-path collective); rank 0 prints the line with the
+maximum time over ranks.  --impl reference times the FP64 CPU oracle on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2305_07187_gb300 import inputs  # noqa: E402
+
+N_SPINS, REPLICAS, T_STEPS = 2000, 1024, 2000
+METRIC = "replica-spin-updates/s"
+UNIT = "RSU/s"
+WORKLOAD = ("K2000-shaped complete graph N=2000, J_ij=+-1 (seeded), h=0; R=1024 replicas, "
+            "q0~U[-0.1,0.1], p0=0; T=2000 steps, zeta linear 0.04->0.5, dt=0.2, k=0.5, m=1, "
+            "walls q_max=sqrt2 p_max=2; J e4m3-exact, q bf16 MMA operand, FP32 accumulation/state; "
+            "exact int32 energy+cut readout of the final spins")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_BF16_TFLOPS = 1900.0
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"bf16_tflops": FALLBACK_BF16_TFLOPS, "hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                   "reasons": sorted(reasons), "samples": len(sm)}
+        return out
+
+
+def cpu_baseline(seconds=12.0):
+    """Time the FP64 oracle as it stands on the host cores on a bounded sample
+    of the workload (same N, J, schedule; a few replicas, the first steps)."""
+    import oracle
+    J = inputs.pm1_coupling(N_SPINS, seed=1).astype(np.float64)
+    zeta, dt = inputs.zeta_ramp(T_STEPS), inputs.dt_const(T_STEPS)
+    cores = oracle.num_threads()
+    R_s = max(1, cores)
+    q = inputs.positions(N_SPINS, R_s, seed0=100).astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.run(J, None, zeta[:2], dt[:2], q)
+    per_step = (time.perf_counter() - t0) / 2
+    T_s = int(max(2, min(T_STEPS, seconds / max(per_step, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(J, None, zeta[:T_s], dt[:T_s], q)
+    el = time.perf_counter() - t0
+    value = R_s * N_SPINS * T_s / el
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "N=2000, %d replicas x first %d of the 2000 steps (FP64, OpenMP over replicas), "
+                      "%.1f s" % (R_s, T_s, el)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    J = inputs.pm1_coupling(N_SPINS, seed=1).astype(np.float64)
+    zeta, dt = inputs.zeta_ramp(T_STEPS), inputs.dt_const(T_STEPS)
+    cores = oracle.num_threads()
+    R_s = max(1, cores)
+    q = inputs.positions(N_SPINS, R_s, seed0=100).astype(np.float64)
+    # size each step so the whole --steps/--warmup run stays within minutes
+    t0 = time.perf_counter()
+    oracle.run(J, None, zeta[:1], dt[:1], q)
+    per = time.perf_counter() - t0
+    T_s = int(max(1, min(T_STEPS, 6.0 / max(per, 1e-6))))
+    for _ in range(args.warmup):
+        oracle.run(J, None, zeta[:T_s], dt[:T_s], q)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        qq, _ = oracle.run(J, None, zeta[:T_s], dt[:T_s], q)
+        oracle.energy(J, None, oracle.sign(qq[:1]))
+        times.append(time.perf_counter() - t0)
+    el = sum(times) / len(times)
+    value = R_s * N_SPINS * T_s / el
+    sample = ("N=2000, %d replicas x first %d of the 2000 steps per bench step (FP64, OpenMP "
+              "over replicas) + one exact energy" % (R_s, T_s))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def smi_index(local):
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        ids = [x.strip() for x in cvd.split(",") if x.strip()]
+        if local < len(ids):
+            return ids[local]
+    return str(local)
+
+
+def ncu_case(args):
+    """One warm-up and one profiled si_run (for ncu captures)."""
+    import torch
+
+    from paper_2305_07187_gb300 import _binding as b
+    T = args.time_steps
+    dev = torch.device("cuda", 0)
+    J = inputs.pm1_coupling(N_SPINS, seed=1)
+    zeta, dt = inputs.zeta_ramp(T), inputs.dt_const(T)
+    q0 = torch.from_numpy(inputs.positions(N_SPINS, REPLICAS, seed0=100)).to(dev)
+    with b.Context(J, replicas=REPLICAS, steps=T, prec="j_fp8_q_bf16", tile_n=args.tile_n) as ctx:
+        z_d = torch.from_numpy(zeta).to(dev)
+        d_d = torch.from_numpy(dt).to(dev)
+        s_d = torch.empty((REPLICAS, N_SPINS), dtype=torch.int8, device=dev)
+        for _ in range(2):
+            ctx.run_into(z_d, d_d, q0, None, None, None, s_d)
+        torch.cuda.synchronize()
+        print(ctx.describe())
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile-n", type=int, default=0)
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="profiling case: one warm-up and one si_run of the batched "
+                         "workload with --time-steps steps, no timing output")
+    ap.add_argument("--time-steps", type=int, default=T_STEPS)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    from paper_2305_07187_gb300 import _binding as b
+    if not os.path.exists(b.LIB_PATH):
+        from paper_2305_07187_gb300 import build as _build
+        _build.build()
+    if args.ncu_case:
+        return ncu_case(args)
+
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    # inputs: every rank its own replicas (seeds offset by rank)
+    J = inputs.pm1_coupling(N_SPINS, seed=1)
+    zeta = inputs.zeta_ramp(T_STEPS)
+    dt = inputs.dt_const(T_STEPS)
+    q0 = inputs.positions(N_SPINS, REPLICAS, seed0=100 + rank * REPLICAS)
+    ctx = b.Context(J, replicas=REPLICAS, steps=T_STEPS, prec="j_fp8_q_bf16",
+                    stream=stream.cuda_stream, tile_n=args.tile_n)
+    desc = ctx.describe()
+    z_d = torch.from_numpy(zeta).to(dev)
+    d_d = torch.from_numpy(dt).to(dev)
+    q_d = torch.from_numpy(q0).to(dev)
+    s_d = torch.empty((REPLICAS, N_SPINS), dtype=torch.int8, device=dev)
+    e_d = torch.empty(REPLICAS, dtype=torch.int32, device=dev)
+    c_d = torch.empty(REPLICAS, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ctx.enable_timing(True)
+
+    def step():
+        ctx.run_into(z_d, d_d, q_d, None, None, None, s_d)
+        n_l = ctx.last_launch_count()
+        k_ms = ctx.last_kernel_ms()
+        ctx.energy_into(s_d, REPLICAS, e_d, c_d, None)
+        return n_l + ctx.last_launch_count(), k_ms
+
+    for _ in range(max(3, args.warmup)):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(smi_index(local))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    step_ms, kern_ms, launches = [], [], 0
+    for _ in range(args.steps):
+        flush.zero_()             # L2 flush between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nl, km = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(km)
+        launches += nl
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+    ms = sum(step_ms) / len(step_ms)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+
+    # end to end through the C ABI with host buffers (copies inside the region)
+    q_h = torch.from_numpy(q0).pin_memory()
+    z_h = torch.from_numpy(zeta).pin_memory()
+    d_h = torch.from_numpy(dt).pin_memory()
+    s_h = torch.empty((REPLICAS, N_SPINS), dtype=torch.int8).pin_memory()
+    e_h = torch.empty(REPLICAS, dtype=torch.int32).pin_memory()
+    c_h = torch.empty(REPLICAS, dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for it in range(args.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.run_into(z_h, d_h, q_h, None, None, None, s_h)
+        ctx.energy_into(s_h, REPLICAS, e_h, c_h, None)
+        el = (time.perf_counter() - t0) * 1e3
+        if it > 0:
+            e2e_ms.append(el)
+    t2 = torch.tensor([sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
+    e2e_max = float(t2.item())
+    # results agree between the two paths (same inputs, deterministic kernels)
+    assert torch.equal(s_h, s_d.cpu()) and torch.equal(e_h, e_d.cpu())
+
+    units = REPLICAS * N_SPINS * T_STEPS
+    value = world * units / (ms_max * 1e-3)
+    e2e_value = world * units / (e2e_max * 1e-3)
+    peaks, peak_src = load_peaks()
+    flops = 2.0 * N_SPINS * N_SPINS * REPLICAS * T_STEPS
+    k_avg = sum(kern_ms) / len(kern_ms)
+    achieved = flops / (k_avg * 1e-3) / 1e12
+    peak = float(peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS))
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            with open(tfile) as f:
+                tj = json.load(f)
+            if tj.get("kernel_desc") == desc:
+                traffic = tj.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "replicas_per_gpu": REPLICAS, "n": N_SPINS,
+                   "time_steps": T_STEPS, "kernel": desc,
+                   "l2": "flushed (256 MiB write) between timed steps, outside the events",
+                   "parallelism": "replicas sharded, J replicated, no collective"},
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": int(q0.nbytes + zeta.nbytes + dt.nbytes),
+                "d2h_bytes_per_step": int(s_h.numel() + e_h.numel() * 4 + c_h.numel() * 4)},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_tc_run (tcgen05 GEMM + fused integrator, all T steps in one launch)",
+                     "kernel_ms": k_avg,
+                     "peak_source": "%s bf16_tflops (burst)" % peak_src,
+                     "algorithmic_flop_per_launch": flops},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

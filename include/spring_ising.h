@@ -155,6 +155,16 @@ si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt,
                   const float *q_init, const float *p_init, float *g_zeta,
                   float *g_dt, float *g_k, float *objective);
 
+/*
+ * Kernel timing.  With timing enabled, si_run records CUDA events on the
+ * context's stream immediately before and after the launch(es) of the
+ * time-step kernel (the coupling force fused with the integrator) and
+ * si_last_kernel_time returns their elapsed time in milliseconds.  Off by
+ * default; the events cost two records per si_run.
+ */
+si_status si_enable_timing(si_ctx *ctx, int32_t on);
+si_status si_last_kernel_time(const si_ctx *ctx, float *ms);
+
 /* Short description of the kernel path and tile shape the context uses. */
 si_status si_describe(const si_ctx *ctx, char *buf, int32_t len);
 

@@ -34,7 +34,8 @@ SI_PREC_J_BF16_Q_BF16 = 3
 PREC = {"fp32": 0, "fp64": 1, "j_fp8_q_bf16": 2, "j_bf16_q_bf16": 3}
 
 EXPORTS = ("si_default_params", "si_create", "si_run", "si_get_state", "si_energy", "si_grad",
-           "si_describe", "si_last_launch_count", "si_last_error", "si_destroy")
+           "si_enable_timing", "si_last_kernel_time", "si_describe", "si_last_launch_count",
+           "si_last_error", "si_destroy")
 
 
 class SiParams(ctypes.Structure):
@@ -78,6 +79,10 @@ def load():
     lib.si_energy.restype = ctypes.c_int
     lib.si_grad.argtypes = [P, P, P, P, P, P, P, P, P]
     lib.si_grad.restype = ctypes.c_int
+    lib.si_enable_timing.argtypes = [P, I32]
+    lib.si_enable_timing.restype = ctypes.c_int
+    lib.si_last_kernel_time.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+    lib.si_last_kernel_time.restype = ctypes.c_int
     lib.si_describe.argtypes = [P, ctypes.c_char_p, I32]
     lib.si_describe.restype = ctypes.c_int
     lib.si_last_launch_count.argtypes = [P]
@@ -196,6 +201,14 @@ class Context:
         buf = ctypes.create_string_buffer(256)
         _check(load().si_describe(self.ctx, buf, 256))
         return buf.value.decode()
+
+    def enable_timing(self, on=True):
+        _check(load().si_enable_timing(self.ctx, 1 if on else 0))
+
+    def last_kernel_ms(self) -> float:
+        v = ctypes.c_float(0.0)
+        _check(load().si_last_kernel_time(self.ctx, ctypes.byref(v)))
+        return float(v.value)
 
     def last_launch_count(self) -> int:
         return int(load().si_last_launch_count(self.ctx))

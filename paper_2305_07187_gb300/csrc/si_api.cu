@@ -105,6 +105,8 @@ static void free_ctx(Ctx *c) {
                     c->dE, c->dC, c->dEf, c->dstage, c->g_ws};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;
 }
 
@@ -333,13 +335,20 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
     if ((s = stage_out(po, p_out, sizeof(float) * (size_t)R * n)) != SI_OK) return s;
     if ((s = stage_out(so, spins_out, (size_t)R * n)) != SI_OK) return s;
 
+    c->ev_valid = false;
     if (c->path == Path::TENSOR) {
         if ((s = tc_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr)) != SI_OK) return s;
+        if (c->timing) SI_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
         if ((s = tc_run(c, steps, c->dspins)) != SI_OK) return s;
     } else {
         if ((s = simt_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr)) != SI_OK) return s;
+        if (c->timing) SI_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
         if ((s = simt_run(c, steps, c->dspins)) != SI_OK) return s;
         c->cur_parity = steps & 1;
+    }
+    if (c->timing) {
+        SI_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+        c->ev_valid = true;
     }
     if ((s = check_device_error(c)) != SI_OK) return s;
     c->have_run = true;
@@ -490,6 +499,30 @@ si_status si_describe(const si_ctx *ctx, char *buf, int32_t len) {
     } else {
         std::snprintf(buf, len, "simt_tiled prec=%s n=%d R=%d tile=64x64", prec[c->prm.prec], c->n, c->R);
     }
+    return SI_OK;
+}
+
+si_status si_enable_timing(si_ctx *ctx, int32_t on) {
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) return SI_ERR_INVALID_ARG;
+    if (on && !c->ev0) {
+        SI_CUDA_TRY(cudaEventCreate(&c->ev0));
+        SI_CUDA_TRY(cudaEventCreate(&c->ev1));
+    }
+    c->timing = on != 0;
+    c->ev_valid = false;
+    return SI_OK;
+}
+
+si_status si_last_kernel_time(const si_ctx *ctx, float *ms) {
+    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    if (!c || !ms) return SI_ERR_INVALID_ARG;
+    if (!c->ev_valid) {
+        set_error("no timed run (enable timing before si_run)");
+        return SI_ERR_INVALID_ARG;
+    }
+    SI_CUDA_TRY(cudaEventSynchronize(c->ev1));
+    SI_CUDA_TRY(cudaEventElapsedTime(ms, c->ev0, c->ev1));
     return SI_OK;
 }
 

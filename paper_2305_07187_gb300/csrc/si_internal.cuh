@@ -84,6 +84,9 @@ struct Ctx {
     int launches = 0;
     int cur_parity = 0;                  // q exchange buffer holding q(t_T)
     bool have_run = false;               // a run completed since creation
+    bool timing = false;                 // record events around the step kernel
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool ev_valid = false;
 
     // Tensor path configuration.
     int tile_n = 0;                      // replicas per CTA
