@@ -165,6 +165,37 @@ si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt,
 si_status si_enable_timing(si_ctx *ctx, int32_t on);
 si_status si_last_kernel_time(const si_ctx *ctx, float *ms);
 
+/*
+ * Allocation-free single-replica run.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory (a
+ * plugin whose host application owns every device allocation, a real-time
+ * loop that must not enter the allocator, code running while a memory pool
+ * is captured or exhausted).  It runs prm->steps steps of the FP32 plain
+ * path for ONE replica (prm->replicas must be 1, prm->prec SI_PREC_FP32)
+ * and calls no cudaMalloc, cudaFree or other allocating routine: its scratch
+ * (two position vectors, a step counter, an error word) is a fixed device
+ * array of 256 + 8 * SI_NOALLOC_MAX_N bytes inside the library, which every
+ * GPU that loads the library holds until the process exits.
+ *   J          device, n*n floats, row-major, symmetric with zero diagonal
+ *              (not re-checked here)
+ *   h          device, n floats, or NULL
+ *   zeta, dt   device, [steps]
+ *   q, p       device, [n], initial state in, final state out
+ *   spins_out  device, [n] int8 sign(q) after the last step, or NULL
+ *   stream     cudaStream_t as void*
+ * n > SI_NOALLOC_MAX_N is rejected with SI_ERR_INVALID_ARG.  The first call
+ * on a device looks up the scratch array's device address (once per device),
+ * so make that first call before any stream capture.  All calls share the
+ * one scratch array and it keeps the last call's contents (the call clears
+ * what must start at zero), so calls whose work overlaps on the GPU race:
+ * serialise them, e.g. on one stream.  The call synchronises the stream
+ * before it returns (it reads the device error word).
+ */
+#define SI_NOALLOC_MAX_N 16384
+si_status si_run_noalloc(const si_params *prm, const float *J, const float *h,
+                         const float *zeta, const float *dt, float *q, float *p,
+                         int8_t *spins_out, void *stream);
+
 /* Short description of the kernel path and tile shape the context uses. */
 si_status si_describe(const si_ctx *ctx, char *buf, int32_t len);
 

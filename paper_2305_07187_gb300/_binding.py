@@ -35,7 +35,7 @@ PREC = {"fp32": 0, "fp64": 1, "j_fp8_q_bf16": 2, "j_bf16_q_bf16": 3}
 
 EXPORTS = ("si_default_params", "si_create", "si_run", "si_get_state", "si_energy", "si_grad",
            "si_enable_timing", "si_last_kernel_time", "si_describe", "si_last_launch_count",
-           "si_last_error", "si_destroy")
+           "si_last_error", "si_destroy", "si_run_noalloc")
 
 
 class SiParams(ctypes.Structure):
@@ -83,6 +83,8 @@ def load():
     lib.si_enable_timing.restype = ctypes.c_int
     lib.si_last_kernel_time.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
     lib.si_last_kernel_time.restype = ctypes.c_int
+    lib.si_run_noalloc.argtypes = [ctypes.POINTER(SiParams), P, P, P, P, P, P, P, P]
+    lib.si_run_noalloc.restype = ctypes.c_int
     lib.si_describe.argtypes = [P, ctypes.c_char_p, I32]
     lib.si_describe.restype = ctypes.c_int
     lib.si_last_launch_count.argtypes = [P]
@@ -277,3 +279,16 @@ class Context:
 
 
 SQRT2_F32 = float(np.float32(math.sqrt(2.0)))
+NOALLOC_MAX_N = 16384
+
+
+def run_noalloc(J, h, zeta, dt, q, p, spins_out=None, stream=None, **params):
+    """si_run_noalloc: one replica, FP32, no device allocation by the library.
+
+    All arrays must be CUDA tensors; q and p (shape [n]) are updated in place."""
+    n = int(q.numel())
+    prm = default_params(n=n, replicas=1, steps=int(zeta.numel()), **params)
+    args = [_Arg(J, np.float32, n * n), _Arg(h, np.float32, n), _Arg(zeta, np.float32),
+            _Arg(dt, np.float32), _Arg(q, np.float32, n, writable=True),
+            _Arg(p, np.float32, n, writable=True), _Arg(spins_out, np.int8, n, writable=True)]
+    _check(load().si_run_noalloc(ctypes.byref(prm), *[a.ptr for a in args], _stream_handle(stream)))
