@@ -332,7 +332,10 @@ def main():
         try:
             with open(tfile) as f:
                 tj = json.load(f)
-            if tj.get("kernel_desc") == desc:
+            import hashlib
+            src = os.path.join(ROOT, "paper_2305_07187_gb300", "csrc", "si_tc.cu")
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+            if tj.get("kernel_desc") == desc and tj.get("source_sha") == sha:
                 traffic = tj.get("bytes_per_launch")
         except Exception:
             traffic = None

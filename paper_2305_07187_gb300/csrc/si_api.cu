@@ -233,7 +233,7 @@ static si_status create_impl(Ctx *c, const float *J, const float *h) {
     const int sched = std::max(1, p.steps);
     SI_CUDA_TRY(cudaMalloc((void **)&c->dzeta, sizeof(float) * sched));
     SI_CUDA_TRY(cudaMalloc((void **)&c->ddt, sizeof(float) * sched));
-    c->nbar = 1024;
+    c->nbar = 4096;
     SI_CUDA_TRY(cudaMalloc((void **)&c->dbar, sizeof(unsigned) * c->nbar));
     SI_CUDA_TRY(cudaMalloc((void **)&c->derr, sizeof(int)));
     SI_CUDA_TRY(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));

@@ -5,15 +5,19 @@
 // replicas) for the whole run:
 //   warp 0      TMA producer: J tile (128 x 64 bf16) and q tile (BN x 64 bf16)
 //               per K block into an S-stage shared-memory ring (128B swizzle)
-//   warp 1      allocates TMEM and issues tcgen05.mma (M=128, N=BN, K=16)
-//               into an FP32 accumulator in TMEM
-//   warps 2..5  epilogue: tcgen05.ld of the accumulator, the spring
+//   warps 1, 2  issue tcgen05.mma (M=128, N=BN, K=16) for alternating K
+//               blocks into two FP32 accumulators in TMEM (warp 1 also
+//               allocates TMEM)
+//   warps 3..10 epilogue: tcgen05.ld of the accumulators, the spring
 //               integrator of Eq. 8 with the walls of Eq. 6 on the q, p state
-//               that lives in TMEM next to the accumulator, and the bf16 copy
-//               of the new q that is the next step's MMA operand
-// Steps are separated by a bounded counter barrier over the CTAs that share a
-// replica block (they exchange q through the double-buffered operand array
-// in L2); CTAs of different replica blocks never wait on each other.
+//               that lives in TMEM next to the accumulators, and the bf16
+//               copy of the new q (the next step's MMA operand), staged in
+//               shared memory and written back with one TMA store
+// CTAs of one replica block exchange q through the double-buffered operand
+// array in L2.  There is no step barrier: each CTA publishes a per-CTA step
+// counter after writing its rows of q, and a consumer waits only for the
+// owner of the K block it is about to load (dataflow), starting its K loop at
+// its own rows.  CTAs of different replica blocks never wait on each other.
 // Every wait (mbarrier or counter) has a time limit; on expiry the kernel
 // raises the device error word, drains its own copies and MMAs, frees TMEM
 // and returns.
@@ -26,7 +30,7 @@ namespace si {
 
 constexpr int TC_BM = 128;       // spins per CTA (MMA M)
 constexpr int TC_BK = 64;        // K elements per stage (128 bytes of bf16)
-constexpr int TC_THREADS = 192;  // 6 warps
+constexpr int TC_THREADS = 352;  // 11 warps: producer, 2 MMA issuers, 8 epilogue
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;
 
 struct TcArgs {
@@ -190,16 +194,32 @@ __device__ __forceinline__ void tmem_wait_st() {
 }
 
 // ------------------------------------------------------------------ kernel
+// Shared memory: S ring stages (J tile + q tile), the staging tile of the
+// next q (bf16, two 64-spin halves in the 128-byte swizzled layout that the
+// TMA store and the MMA both read), then the mbarriers.
 template <int BN, int S>
 struct TcSmem {
     static constexpr int B_BYTES = BN * TC_BK * 2;
     static constexpr int STAGE_BYTES = TC_A_BYTES + B_BYTES;
     static constexpr int TILES = S * STAGE_BYTES;
-    static constexpr int BARS = TILES;                    // mbarriers after the tiles
-    static constexpr int NBARS = 2 * S + 4;               // full, empty, accf, tmem_empty, epi_done, drain
-    static constexpr int TOTAL = TILES + NBARS * 8 + 16;  // + tmem slot, abort flag
-    static constexpr int TMEM_COLS = (3 * BN <= 256) ? 256 : 512;
+    static constexpr int HALF_BYTES = BN * 128;           // BN replicas x 64 spins bf16
+    static constexpr int STAGING = TILES;                 // 1024-aligned
+    static constexpr int BARS = STAGING + 2 * HALF_BYTES;
+    // full[S], empty[S], accf, tmem_empty, epi_done, drain
+    static constexpr int NBARS = 2 * S + 4;
+    static constexpr int TOTAL = BARS + NBARS * 8 + 16;   // + tmem slot, abort flag
+    static constexpr int TMEM_COLS = (4 * BN <= 256) ? 256 : 512;
 };
+
+constexpr int TC_MMA_WARPS = 2;
+constexpr int TC_EPI_WARP0 = 1 + TC_MMA_WARPS;             // first epilogue warp
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(src), "r"(x), "r"(y)
+                 : "memory");
+}
 
 template <int BN, int S>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -210,6 +230,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
+    const uint32_t stage_q = sbase + L::STAGING;
     const uint32_t bar0 = sbase + L::BARS;
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
@@ -223,16 +244,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt = blockIdx.x % a.mtiles, rb = blockIdx.x / a.mtiles;
     const int m0 = mt * TC_BM, r0 = rb * BN;
+    // TMEM columns: two partial accumulators, then the q and p state.
+    constexpr uint32_t COL_ACC0 = 0, COL_ACC1 = BN, COL_Q = 2 * BN, COL_P = 3 * BN;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
-        mbar_init(accf_bar, 1);
-        mbar_init(tmem_empty_bar, 4);
-        mbar_init(epi_done_bar, 4);
-        mbar_init(drain_bar, 1);
+        mbar_init(accf_bar, TC_MMA_WARPS);
+        mbar_init(tmem_empty_bar, 8);
+        mbar_init(epi_done_bar, 8);
+        mbar_init(drain_bar, TC_MMA_WARPS);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -252,29 +275,75 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        // ------------------------------------------------ TMA producer
-        if (lane == 0) {
-            uint32_t it = 0;  // pipeline slot counter
-            bool ok = true;
-            for (int t = 0; t < a.steps && ok; ++t) {
-                if (t > 0) {
-                    ok = wait_counter_geq(a.bar + rb, (unsigned)t * a.mtiles, a.err, a.limit_ns);
-                    if (!ok) { *abort_flag = 1; break; }
-                    fence_proxy_async_global();
+        // ------------------------------------------------ TMA producer (whole warp)
+        // Step t needs the positions q(t) of its replica block.  The K block kb
+        // (spins 64kb .. 64kb+63) of q(t) is written by the CTA owning M tile
+        // kb/2 at the end of its step t-1 and announced through that CTA's flag
+        // (number of steps published).  The K loop starts at this CTA's own
+        // rows and the warp polls all owners' flags in parallel only when the
+        // next block's owner is not yet known to be ready.  J tiles do not
+        // depend on the step and are issued before the wait.
+        uint32_t it = 0;
+        bool ok = true;
+        const int kb0 = mt * (TC_BM / TC_BK);
+        const unsigned *flags = a.bar + (size_t)rb * a.mtiles;
+        for (int t = 0; t < a.steps && ok; ++t) {
+            uint32_t ready0 = 0u, ready1 = 0u;
+            if (t == 0) ready0 = ready1 = 0xffffffffu;
+            const int yb = (t & 1) * a.rpad + r0;
+            for (int j = 0; j < a.kblocks; ++j, ++it) {
+                int kb = kb0 + j;
+                if (kb >= a.kblocks) kb -= a.kblocks;
+                const int s = it % S;
+                const uint32_t ph = (it / S) & 1u;
+                const uint32_t dA = sbase + s * L::STAGE_BYTES;
+                const uint32_t dB = dA + TC_A_BYTES;
+                int okw = 1;
+                if (lane == 0) {
+                    okw = mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns) ? 1 : 0;
+                    if (okw) {
+                        mbar_arrive_expect_tx(full_bar(s), (uint32_t)L::STAGE_BYTES);
+                        tma_load_2d(dA, &mapA, full_bar(s), kb * TC_BK, m0);
+                    }
                 }
-                const int yb = (t & 1) * a.rpad + r0;
-                for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
-                    const int s = it % S;
-                    const uint32_t ph = (it / S) & 1u;
-                    if (!mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
-                    const uint32_t dA = sbase + s * L::STAGE_BYTES;
-                    const uint32_t dB = dA + TC_A_BYTES;
-                    mbar_arrive_expect_tx(full_bar(s), (uint32_t)L::STAGE_BYTES);
-                    tma_load_2d(dA, &mapA, full_bar(s), kb * TC_BK, m0);
-                    tma_load_2d(dB, &mapB, full_bar(s), kb * TC_BK, yb);
+                okw = __shfl_sync(0xffffffffu, okw, 0);
+                if (!okw) { ok = false; break; }
+                const int mo = kb >> 1;
+                bool have = mo < 32 ? ((ready0 >> mo) & 1u) != 0u : ((ready1 >> (mo - 32)) & 1u) != 0u;
+                if (!have) {
+                    const unsigned long long t0 = globaltimer_ns();
+                    for (unsigned pit = 1;; ++pit) {
+                        bool r_lo = false, r_hi = false;
+                        if (lane < a.mtiles) r_lo = (int)(ld_acquire_gpu(flags + lane) - (unsigned)t) >= 0;
+                        if (lane + 32 < a.mtiles) r_hi = (int)(ld_acquire_gpu(flags + lane + 32) - (unsigned)t) >= 0;
+                        ready0 |= __ballot_sync(0xffffffffu, r_lo);
+                        ready1 |= __ballot_sync(0xffffffffu, r_hi);
+                        have = mo < 32 ? ((ready0 >> mo) & 1u) != 0u : ((ready1 >> (mo - 32)) & 1u) != 0u;
+                        if (have) break;
+                        int stop = 0;
+                        if (lane == 0 && (pit & 7u) == 0u) {
+                            if (*abort_flag || ld_volatile_int(a.err) != 0) {
+                                stop = 1;
+                            } else if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                                atomicCAS(a.err, 0, DEV_TIMEOUT_BARRIER);
+                                stop = 1;
+                            }
+                            if (stop) *abort_flag = 1;
+                        }
+                        if (__shfl_sync(0xffffffffu, stop, 0)) break;
+                    }
+                    // Order this lane's TMA after the other lanes' acquire loads.
+                    __syncwarp();
+                    if (lane == 0) fence_proxy_async_global();
                 }
+                // The q tile is issued even on abort so that the stage's
+                // transaction count completes and the drain below ends.
+                if (lane == 0) tma_load_2d(dB, &mapB, full_bar(s), kb * TC_BK, yb);
+                if (!have) { ++it; ok = false; break; }
             }
-            // Let every copy this thread issued land before the CTA exits.
+        }
+        // Let every copy this warp issued land before the CTA exits.
+        if (lane == 0) {
             const uint32_t first = it > (uint32_t)S ? it - S : 0u;
             for (uint32_t k = first; k < it; ++k) {
                 const unsigned long long t0 = globaltimer_ns();
@@ -286,29 +355,33 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
             }
         }
-    } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer
+    } else if (warp <= TC_MMA_WARPS) {
+        // ------------------------------------------------ MMA issuers
+        // Warp 1 takes the even positions of the K loop into accumulator 0,
+        // warp 2 the odd ones into accumulator 1; the epilogue adds the two.
+        // Two issuing threads keep the tensor pipe fed: one thread alone
+        // issues a 128x128x16 MMA no faster than the pipe executes it.
         if (lane == 0) {
+            const int w = warp - 1;
             constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
-            uint32_t it = 0;
+            const uint32_t d_tmem = tmem + (w == 0 ? COL_ACC0 : COL_ACC1);
             bool ok = true;
             for (int t = 0; t < a.steps && ok; ++t) {
                 if (t > 0) {
                     if (!mbar_wait(tmem_empty_bar, (uint32_t)((t - 1) & 1), a.err, abort_flag, a.limit_ns)) break;
                 }
                 tc_fence_after();
-                for (int kb = 0; kb < a.kblocks; ++kb, ++it) {
+                for (int j = w; j < a.kblocks; j += TC_MMA_WARPS) {
+                    const uint32_t it = (uint32_t)t * a.kblocks + j;
                     const int s = it % S;
                     const uint32_t ph = (it / S) & 1u;
                     if (!mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t aA = sbase + s * L::STAGE_BYTES;
-                    const uint32_t aB = aA + TC_A_BYTES;
+                    const uint64_t ad = sdesc_sw128(sbase + s * L::STAGE_BYTES);
+                    const uint64_t bd = ad + (uint64_t)(TC_A_BYTES >> 4);
 #pragma unroll
-                    for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                        mma_bf16(tmem, sdesc_sw128(aA + kk * 32), sdesc_sw128(aB + kk * 32), idesc,
-                                 (kb | kk) != 0 ? 1u : 0u);
-                    }
+                    for (int kk = 0; kk < TC_BK / 16; ++kk)
+                        mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (j != w || kk != 0) ? 1u : 0u);
                     mma_commit(empty_bar(s));
                 }
                 if (ok) mma_commit(accf_bar);
@@ -324,17 +397,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
         }
     } else {
-        // ------------------------------------------------ epilogue
-        const int quad = warp & 3;                  // TMEM lane quadrant of this warp
+        // ------------------------------------------------ epilogue (8 warps)
+        // Warp w reads TMEM lanes 32*(w%4) .. +31 (one spin per thread) and
+        // half (w-3)/4 of the replica columns.
+        const int quad = warp & 3;
+        const int half = (warp - TC_EPI_WARP0) >> 2;
+        constexpr int CPH = BN / 64;                // 32-column chunks per half
+        const int c_begin = half * CPH;
         const int row = quad * 32 + lane;
         const int i = m0 + row;
         const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
         const bool row_ok = i < a.n;
+        const bool two_acc = a.kblocks > 1;
         const float hi = (a.h && row_ok) ? a.h[i] : 0.f;
-        const size_t plane = (size_t)a.rpad * a.ldk;
-        // Load the initial state into TMEM: q at columns [BN, 2BN), p at [2BN, 3BN).
+        // This thread's byte offset inside the staging tile of the next q:
+        // half hq = row/64 holds spins 64hq..64hq+63 as BN rows of 128 bytes,
+        // 16-byte chunks swizzled by (replica row % 8).
+        const int kq = row & 63;
+        const uint32_t st_base = stage_q + (uint32_t)(row >> 6) * L::HALF_BYTES + (uint32_t)(kq & 7) * 2u;
+        const bool publisher = (warp == TC_EPI_WARP0 && lane == 0);
+        // Load the initial state into TMEM.
 #pragma unroll 1
-        for (int c = 0; c < BN / 32; ++c) {
+        for (int c = c_begin; c < c_begin + CPH; ++c) {
             uint32_t vq[32], vp[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
@@ -343,8 +427,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 vq[j] = __float_as_uint(ok ? a.q_state[(size_t)r * a.n + i] : 0.f);
                 vp[j] = __float_as_uint(ok ? a.p_state[(size_t)r * a.n + i] : 0.f);
             }
-            tmem_st32(tl + BN + c * 32, vq);
-            tmem_st32(tl + 2 * BN + c * 32, vp);
+            tmem_st32(tl + COL_Q + c * 32, vq);
+            tmem_st32(tl + COL_P + c * 32, vp);
         }
         tmem_wait_st();
 #pragma unroll 1
@@ -357,62 +441,80 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const float zt = a.zeta[t], dtt = a.dt[t];
             const float dtm = dtt / a.sp.m;
             const bool last = (t == a.steps - 1);
-            __nv_bfloat16 *qn = a.qop + (size_t)((t + 1) & 1) * plane;
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                uint32_t vf[32], vq[32], vp[32];
-                tmem_ld32(tl + c * 32, vf);
-                tmem_ld32(tl + BN + c * 32, vq);
-                tmem_ld32(tl + 2 * BN + c * 32, vp);
+            for (int c = c_begin; c < c_begin + CPH; ++c) {
+                uint32_t vf[32], vp[32], vq[32];
+                tmem_ld32(tl + COL_ACC0 + c * 32, vf);
+                if (two_acc) {
+                    tmem_ld32(tl + COL_ACC1 + c * 32, vp);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        vf[j] = __float_as_uint(__uint_as_float(vf[j]) + __uint_as_float(vp[j]));
+                }
+                tmem_ld32(tl + COL_Q + c * 32, vq);
+                tmem_ld32(tl + COL_P + c * 32, vp);
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
+                    const float F = __uint_as_float(vf[j]);
                     float qo, po;
-                    integrate<float>(__uint_as_float(vq[j]), __uint_as_float(vp[j]),
-                                     __uint_as_float(vf[j]) + hi, zt, dtt, dtm, a.sp, qo, po);
+                    integrate<float>(__uint_as_float(vq[j]), __uint_as_float(vp[j]), F + hi, zt, dtt,
+                                     dtm, a.sp, qo, po);
                     vq[j] = __float_as_uint(qo);
                     vp[j] = __float_as_uint(po);
                 }
-                tmem_st32(tl + BN + c * 32, vq);
-                tmem_st32(tl + 2 * BN + c * 32, vp);
-                if (row_ok) {
+                tmem_st32(tl + COL_Q + c * 32, vq);
+                tmem_st32(tl + COL_P + c * 32, vp);
+                if (!last) {
+                    // bf16 copy into the staging tile (zeros outside n x R).
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int rl = c * 32 + j;
+                        const bool ok2 = row_ok && (r0 + rl) < a.R;
+                        const __nv_bfloat16 v = __float2bfloat16_rn(ok2 ? __uint_as_float(vq[j]) : 0.f);
+                        const uint32_t addr = st_base + (uint32_t)rl * 128u +
+                                              ((uint32_t)(((kq >> 3) ^ (rl & 7)) << 4));
+                        asm volatile("st.shared.b16 [%0], %1;" ::"r"(addr),
+                                     "h"(*reinterpret_cast<const unsigned short *>(&v))
+                                     : "memory");
+                    }
+                } else if (row_ok) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int r = r0 + c * 32 + j;
                         if (r < a.R) {
                             const float qv = __uint_as_float(vq[j]);
-                            if (!last) {
-                                qn[(size_t)r * a.ldk + i] = __float2bfloat16_rn(qv);
-                            } else {
-                                a.q_state[(size_t)r * a.n + i] = qv;
-                                a.p_state[(size_t)r * a.n + i] = __uint_as_float(vp[j]);
-                                if (a.spins) a.spins[(size_t)r * a.lds + i] = spin_of(qv);
-                            }
+                            a.q_state[(size_t)r * a.n + i] = qv;
+                            a.p_state[(size_t)r * a.n + i] = __uint_as_float(vp[j]);
+                            if (a.spins) a.spins[(size_t)r * a.lds + i] = spin_of(qv);
                         }
                     }
                 }
             }
             tmem_wait_st();
             tc_fence_before();
-            __threadfence();
-            fence_proxy_async_global();
+            // Generic-proxy writes of the staging tile become visible to the
+            // TMA store (async proxy) issued below.
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(tmem_empty_bar);
                 mbar_arrive(epi_done_bar);
             }
-            // One thread publishes "this CTA finished step t" to its replica block.
-            if (warp == 2 && !last) {
-                bool ok2 = true;
-                if (lane == 0) {
-                    ok2 = mbar_wait(epi_done_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns);
-                    if (ok2) {
-                        __threadfence();
-                        red_release_gpu_add(a.bar + rb, 1u);
-                    }
+            if (publisher && !last) {
+                // All 8 warps have written their part: store the tile to the
+                // operand plane of step t+1, wait for the writes, publish.
+                if (mbar_wait(epi_done_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns)) {
+                    const int y = ((t + 1) & 1) * a.rpad + r0;
+                    tma_store_2d(&mapB, stage_q, m0, y);
+                    if (m0 + 64 < a.ldk) tma_store_2d(&mapB, stage_q + L::HALF_BYTES, m0 + 64, y);
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+                    fence_proxy_async_global();
+                    __threadfence();
+                    red_release_gpu_add(a.bar + (size_t)rb * a.mtiles + mt, 1u);
                 }
-                ok2 = __shfl_sync(0xffffffffu, ok2 ? 1 : 0, 0) != 0;
-                if (!ok2) break;
             }
         }
     }
@@ -536,8 +638,8 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
     a.sp = StepParams{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max,
                       c->prm.update_order, c->prm.wall_zero_p};
     const int grid = a.mtiles * a.rblocks;
-    if (a.rblocks > c->nbar) {
-        set_error("tensor path: too many replica blocks");
+    if (a.rblocks * a.mtiles > c->nbar || a.mtiles > 64) {
+        set_error("tensor path: too many tiles for the step flags (n <= 8192 per context)");
         return SI_ERR_UNSUPPORTED;
     }
     const int smem = L::TOTAL + 1024;
@@ -559,27 +661,47 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
 si_status tc_run(Ctx *c, int steps, int8_t *spins_dev) {
     if (steps == 0) return SI_OK;
     switch (c->tile_n) {
-        case 64: return tc_launch_t<64, 4>(c, steps, spins_dev);
+        case 64: return tc_launch_t<64, 8>(c, steps, spins_dev);
         case 128: return tc_launch_t<128, 6>(c, steps, spins_dev);
         default: set_error("tensor path: unsupported tile"); return SI_ERR_UNSUPPORTED;
     }
 }
 
-// Replica tile: 128 if the grid of 128-wide tiles fits on the GPU at one CTA
-// per SM, else 64 (two CTAs per SM), unless the caller fixed tile_n.
-static int choose_tile(const Ctx *c) {
-    if (c->prm.tile_n == 64 || c->prm.tile_n == 128) return c->prm.tile_n;
+template <int BN, int S>
+static int tc_occupancy() {
+    using L = TcSmem<BN, S>;
+    const int smem = L::TOTAL + 1024;
+    if (cudaFuncSetAttribute(k_tc_run<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return 0;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_run<BN, S>, TC_THREADS, smem) != cudaSuccess)
+        return 0;
+    return per_sm;
+}
+
+// Replica tile: 128 when the grid of 128-wide tiles is co-resident, else 64,
+// unless the caller fixed tile_n.  Returns the CTAs per SM of the choice.
+static int choose_tile(const Ctx *c, int *per_sm) {
     const int mtiles = c->mpad / TC_BM;
-    const int g128 = mtiles * cdiv(c->R, 128);
-    if (g128 <= c->num_sms && c->R > 64) return 128;
-    return 64;
+    const int occ128 = tc_occupancy<128, 6>(), occ64 = tc_occupancy<64, 8>();
+    int bn;
+    if (c->prm.tile_n == 64 || c->prm.tile_n == 128) {
+        bn = c->prm.tile_n;
+    } else if (c->R > 64 && mtiles * cdiv(c->R, 128) <= occ128 * c->num_sms) {
+        bn = 128;
+    } else {
+        bn = 64;
+    }
+    *per_sm = bn == 128 ? occ128 : occ64;
+    return bn;
 }
 
 si_status tc_prepare(Ctx *c, const float *J_dev) {
     const int n = c->n;
     c->ldk = round_up(n, TC_BK);
     c->mpad = round_up(n, TC_BM);
-    c->tile_n = choose_tile(c);
+    int per_sm = 0;
+    c->tile_n = choose_tile(c, &per_sm);
     c->rpad = round_up(c->R, c->tile_n);
     SI_CUDA_TRY(cudaMalloc(&c->dJ, (size_t)c->mpad * c->ldk * 2));
     k_convert_j_bf16<<<std::min(8 * c->num_sms, cdiv((long long)c->mpad * c->ldk, 256)), 256, 0, c->stream>>>(
@@ -596,7 +718,6 @@ si_status tc_prepare(Ctx *c, const float *J_dev) {
     if (s != SI_OK) return s;
     const int mtiles = c->mpad / TC_BM;
     const int grid = mtiles * (c->rpad / c->tile_n);
-    const int per_sm = c->tile_n == 128 ? 1 : 2;
     if (grid > per_sm * c->num_sms) {
         set_error("tensor path: n x replicas too large for one co-resident launch");
         return SI_ERR_UNSUPPORTED;
@@ -644,7 +765,7 @@ const char *tc_describe(const Ctx *c, char *buf, int len) {
     std::snprintf(buf, len,
                   "tcgen05 prec=%s n=%d R=%d tile=128x%d stages=%d grid=%d (mtiles=%d rblocks=%d) kblocks=%d",
                   c->prm.prec == SI_PREC_J_FP8_Q_BF16 ? "j_fp8_q_bf16" : "j_bf16_q_bf16", c->n, c->R,
-                  c->tile_n, c->tile_n == 128 ? 6 : 4, (c->mpad / TC_BM) * (c->rpad / c->tile_n),
+                  c->tile_n, c->tile_n == 128 ? 6 : 8, (c->mpad / TC_BM) * (c->rpad / c->tile_n),
                   c->mpad / TC_BM, c->rpad / c->tile_n, c->ldk / TC_BK);
     return buf;
 }
