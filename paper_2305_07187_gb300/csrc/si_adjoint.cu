@@ -1,9 +1,372 @@
-// Adjoint sweep (placeholder until the adjoint kernels land).
+// Adjoint sweep of the Spring-Ising iteration (FP32 / FP64 on CUDA cores).
+//
+// Objective: the relaxed Ising energy at the final step,
+//   L = sum_r ( -1/2 q_r^T J q_r - h^T q_r ),   q_r = positions after T steps,
+// differentiated with respect to the schedules zeta[T], dt[T] and the spring
+// constant k.  One kick-drift step (Eq. 8 with the walls of Eq. 6) maps
+//   a  = p + dt (-k (q - q0) + zeta F),   F = J q + h,
+//   p' = clip(a),  b = q + (dt/m) p',  q' = clip(b),
+// and its adjoint, with D_p, D_q the interior indicators of the clamps, is
+//   lb = D_q lq',  la = D_p (lp' + (dt/m) lb),
+//   lq = lb + dt (-k la + zeta J la),  lp = la,
+//   g_dt   += sum lb p'/m + la (-k (q - q0) + zeta F)
+//   g_zeta += dt sum la F,   g_k += -dt sum la (q - q0),
+// started from lq_T = -(J q_T + h), lp_T = 0.
+//
+// A clamp is active exactly when the clamped value sits on the wall, so the
+// indicators are read from the stored next state: D_p = |p'| < p_max and
+// D_q = |q'| < q_max (strict, the derivative at the kink is taken as 0).
+//
+// Memory: checkpoints of (q, p) every K steps; a segment of K steps is
+// recomputed from its checkpoint with the same kernels (bit-identical
+// states), keeping q_t, p_t and F_t of every step of the segment, then swept
+// backwards.  Gradient sums are per-block partials reduced in a fixed order
+// (deterministic).
+#include <algorithm>
+#include <cstdio>
+
 #include "si_device.cuh"
 
 namespace si {
-si_status adjoint_grad(Ctx *, int, float *, float *, float *, float *) {
-    set_error("adjoint not built yet");
-    return SI_ERR_UNSUPPORTED;
+
+constexpr int AG_M = 64, AG_R = 64, AG_K = 16, AG_THREADS = 256;
+constexpr int AE_BLOCKS = 128, AE_THREADS = 256;
+
+enum GemmMode { GM_FORWARD = 0, GM_TERMINAL = 1, GM_ADJOINT = 2 };
+
+template <typename T>
+struct AdjGemmArgs {
+    const T *J;
+    int ldj;
+    const T *h;
+    int n, R;
+    const T *X;          // operand [R][ldj]
+    // forward: X = q_t;  P = p_t;  outputs q_{t+1}, p_{t+1}, F_t
+    const T *P;
+    T *Qn, *Pn, *Fo;
+    // adjoint: X = la;  reads lb;  writes lq, lp
+    const T *LB;
+    T *LQ, *LP;
+    // terminal: objective partials per block (-1/2 x.G - h.x)
+    T *obj_part;
+    StepParams sp;
+    const float *zeta, *dt;
+    int t;
+};
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(AG_THREADS) k_adj_gemm(AdjGemmArgs<T> a) {
+    __shared__ T As[AG_K][AG_M + 1];
+    __shared__ T Bs[AG_K][AG_R + 1];
+    __shared__ T red[AG_THREADS];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int i0 = blockIdx.x * AG_M, r0 = blockIdx.y * AG_R;
+    CompSum<T> acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v].init();
+    const int lrow = tid / 4, lk = (tid % 4) * 4;
+    for (int k0 = 0; k0 < a.ldj; k0 += AG_K) {
+        const int i = i0 + lrow;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            As[lk + v][lrow] = (i < a.n) ? a.J[(size_t)i * a.ldj + k0 + lk + v] : (T)0;
+        const int r = r0 + lrow;
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            Bs[lk + v][lrow] = (r < a.R) ? a.X[(size_t)r * a.ldj + k0 + lk + v] : (T)0;
+        __syncthreads();
+        T part[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) part[u][v] = (T)0;
+#pragma unroll
+        for (int kk = 0; kk < AG_K; ++kk) {
+            T av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) av[u] = As[kk][ty * 4 + u];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) bv[v] = Bs[kk][tx * 4 + v];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) part[u][v] = fma(av[u], bv[v], part[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v].add(part[u][v]);
+        __syncthreads();
+    }
+    T objp = (T)0;
+    const T k = (T)a.sp.k, q0 = (T)a.sp.q0;
+    T zt = 0, dtt = 0, dtm = 0;
+    if (MODE != GM_TERMINAL) {
+        zt = (T)a.zeta[a.t];
+        dtt = (T)a.dt[a.t];
+        dtm = dtt / (T)a.sp.m;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + ty * 4 + u;
+        if (i >= a.n) continue;
+        const T hi = a.h ? a.h[i] : (T)0;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int r = r0 + tx * 4 + v;
+            if (r >= a.R) continue;
+            const size_t e = (size_t)r * a.ldj + i;
+            const T G = acc[u][v].value();
+            if (MODE == GM_FORWARD) {
+                const T F = G + hi;
+                T qo, po;
+                integrate<T>(a.X[e], a.P[e], F, zt, dtt, dtm, a.sp, qo, po);
+                a.Qn[e] = qo;
+                a.Pn[e] = po;
+                a.Fo[e] = F;
+            } else if (MODE == GM_TERMINAL) {
+                const T x = a.X[e];
+                a.LQ[e] = -(G + hi);
+                a.LP[e] = (T)0;
+                objp += (T)-0.5 * x * G - hi * x;
+            } else {
+                const T la = a.X[e];
+                a.LQ[e] = a.LB[e] + dtt * (-k * la + zt * G);
+                a.LP[e] = la;
+            }
+        }
+    }
+    (void)q0;
+    if (MODE == GM_TERMINAL) {
+        red[tid] = objp;
+        __syncthreads();
+        if (tid == 0) {
+            CompSum<T> s;
+            s.init();
+            for (int w = 0; w < AG_THREADS; ++w) s.add(red[w]);
+            a.obj_part[blockIdx.y * gridDim.x + blockIdx.x] = s.value();
+        }
+    }
 }
+
+// Elementwise part of one reverse step: indicators, la, lb and the per-block
+// partial sums of the three gradient contributions.
+template <typename T>
+__global__ void __launch_bounds__(AE_THREADS) k_adj_elem(
+    int n, int R, int ld, const T *q, const T *p, const T *F, const T *qn, const T *pn,
+    const T *lq, const T *lp, T *la_out, T *lb_out, StepParams sp, const float *zeta,
+    const float *dt, int t, T *part /* [3][AE_BLOCKS] of step t */) {
+    __shared__ T r0s[AE_THREADS], r1s[AE_THREADS], r2s[AE_THREADS];
+    const T k = (T)sp.k, q0 = (T)sp.q0, qmax = (T)sp.q_max, pmax = (T)sp.p_max, m = (T)sp.m;
+    const T zt = (T)zeta[t], dtt = (T)dt[t];
+    const T dtm = dtt / m;
+    CompSum<T> s0, s1, s2;
+    s0.init();
+    s1.init();
+    s2.init();
+    const long long total = (long long)R * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), i = (int)(e % n);
+        const size_t x = (size_t)r * ld + i;
+        const T Dq = (fabs(qn[x]) < qmax) ? (T)1 : (T)0;
+        const T Dp = (fabs(pn[x]) < pmax) ? (T)1 : (T)0;
+        const T lb = Dq * lq[x];
+        const T la = Dp * (lp[x] + dtm * lb);
+        la_out[x] = la;
+        lb_out[x] = lb;
+        const T dq = q[x] - q0;
+        const T force = -k * dq + zt * F[x];
+        s0.add(lb * pn[x] / m + la * force);
+        s1.add(dtt * la * F[x]);
+        s2.add(-dtt * la * dq);
+    }
+    (void)p;
+    r0s[threadIdx.x] = s0.value();
+    r1s[threadIdx.x] = s1.value();
+    r2s[threadIdx.x] = s2.value();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        CompSum<T> a0, a1, a2;
+        a0.init();
+        a1.init();
+        a2.init();
+        for (int w = 0; w < AE_THREADS; ++w) {
+            a0.add(r0s[w]);
+            a1.add(r1s[w]);
+            a2.add(r2s[w]);
+        }
+        part[blockIdx.x] = a0.value();
+        part[AE_BLOCKS + blockIdx.x] = a1.value();
+        part[2 * AE_BLOCKS + blockIdx.x] = a2.value();
+    }
+}
+
+// Final fixed-order reductions: g_dt[t], g_zeta[t], g_k and the objective.
+template <typename T>
+__global__ void k_adj_finish(int T_steps, const T *part, int nobj, const T *obj_part, float *g_zeta,
+                             float *g_dt, float *g_k, float *objective) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < T_steps) {
+        const T *pp = part + (size_t)t * 3 * AE_BLOCKS;
+        CompSum<T> a0, a1;
+        a0.init();
+        a1.init();
+        for (int b = 0; b < AE_BLOCKS; ++b) {
+            a0.add(pp[b]);
+            a1.add(pp[AE_BLOCKS + b]);
+        }
+        if (g_dt) g_dt[t] = (float)a0.value();
+        if (g_zeta) g_zeta[t] = (float)a1.value();
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        CompSum<T> gk, ob;
+        gk.init();
+        ob.init();
+        for (int s = 0; s < T_steps; ++s) {
+            const T *pp = part + (size_t)s * 3 * AE_BLOCKS + 2 * AE_BLOCKS;
+            for (int b = 0; b < AE_BLOCKS; ++b) gk.add(pp[b]);
+        }
+        for (int b = 0; b < nobj; ++b) ob.add(obj_part[b]);
+        if (g_k) *g_k = (float)gk.value();
+        if (objective) *objective = (float)ob.value();
+    }
+}
+
+template <typename T>
+__global__ void k_adj_load_state(const float *q_init, const float *p_init, int n, int R, int ld,
+                                 T *q, T *p) {
+    const long long total = (long long)R * ld;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / ld), i = (int)(e % ld);
+        q[e] = i < n ? (T)q_init[(size_t)r * n + i] : (T)0;
+        p[e] = (i < n && p_init) ? (T)p_init[(size_t)r * n + i] : (T)0;
+    }
+}
+
+template <typename T>
+static si_status adjoint_impl(Ctx *c, int steps, float *g_zeta, float *g_dt, float *g_k,
+                              float *objective, const float *q_init, const float *p_init) {
+    const int n = c->n, R = c->R, ld = c->ldj;
+    const int K = c->prm.ckpt_every > 0 ? c->prm.ckpt_every : 50;
+    const int nseg = steps > 0 ? cdiv(steps, K) : 0;
+    const size_t plane = (size_t)R * ld;
+    const dim3 ggrid(cdiv(n, AG_M), cdiv(R, AG_R));
+    const int nobj = (int)(ggrid.x * ggrid.y);
+    // workspace: ckpt (nseg+1) x {q,p}; slots (K+1) x {q,p}; F K; lq, lp, la, lb;
+    // partials 3 * AE_BLOCKS * steps; objective partials.
+    const size_t n_planes = 2 * (size_t)(nseg + 1) + 2 * (size_t)(K + 1) + (size_t)K + 4;
+    const size_t bytes = sizeof(T) * (n_planes * plane + 3 * (size_t)AE_BLOCKS * std::max(steps, 1) +
+                                      (size_t)nobj);
+    if (c->g_ws_bytes < bytes) {
+        if (c->g_ws) cudaFree(c->g_ws);
+        c->g_ws = nullptr;
+        c->g_ws_bytes = 0;
+        SI_CUDA_TRY(cudaMalloc(&c->g_ws, bytes));
+        c->g_ws_bytes = bytes;
+    }
+    SI_CUDA_TRY(cudaMemsetAsync(c->g_ws, 0, bytes, c->stream));
+    T *w = (T *)c->g_ws;
+    T *ckq = w;                            w += (size_t)(nseg + 1) * plane;
+    T *ckp = w;                            w += (size_t)(nseg + 1) * plane;
+    T *sq = w;                             w += (size_t)(K + 1) * plane;
+    T *sp = w;                             w += (size_t)(K + 1) * plane;
+    T *sF = w;                             w += (size_t)K * plane;
+    T *lq = w;                             w += plane;
+    T *lp = w;                             w += plane;
+    T *la = w;                             w += plane;
+    T *lb = w;                             w += plane;
+    T *part = w;                           w += 3 * (size_t)AE_BLOCKS * std::max(steps, 1);
+    T *objp = w;
+    const StepParams spar{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max, 0, 0};
+    const int lg = std::min(4096, cdiv((long long)plane, 256));
+    k_adj_load_state<T><<<lg, 256, 0, c->stream>>>(q_init, p_init, n, R, ld, ckq, ckp);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+
+    AdjGemmArgs<T> g{};
+    g.J = (const T *)c->dJ;
+    g.ldj = ld;
+    g.h = (const T *)c->dh;
+    g.n = n;
+    g.R = R;
+    g.sp = spar;
+    g.zeta = c->dzeta;
+    g.dt = c->ddt;
+
+    // Recompute segment s from its checkpoint into the slots (q_t, p_t, F_t).
+    auto recompute = [&](int s) -> si_status {
+        const int t0 = s * K, len = std::min(K, steps - t0);
+        SI_CUDA_TRY(cudaMemcpyAsync(sq, ckq + (size_t)s * plane, sizeof(T) * plane, cudaMemcpyDeviceToDevice, c->stream));
+        SI_CUDA_TRY(cudaMemcpyAsync(sp, ckp + (size_t)s * plane, sizeof(T) * plane, cudaMemcpyDeviceToDevice, c->stream));
+        for (int j = 0; j < len; ++j) {
+            g.X = sq + (size_t)j * plane;
+            g.P = sp + (size_t)j * plane;
+            g.Qn = sq + (size_t)(j + 1) * plane;
+            g.Pn = sp + (size_t)(j + 1) * plane;
+            g.Fo = sF + (size_t)j * plane;
+            g.t = t0 + j;
+            k_adj_gemm<T, GM_FORWARD><<<ggrid, AG_THREADS, 0, c->stream>>>(g);
+        }
+        SI_CUDA_TRY(cudaGetLastError());
+        c->launches += len;
+        return SI_OK;
+    };
+
+    // Forward pass: checkpoints at the start of every segment and at T.
+    si_status st;
+    for (int s = 0; s < nseg; ++s) {
+        if ((st = recompute(s)) != SI_OK) return st;
+        const int len = std::min(K, steps - s * K);
+        SI_CUDA_TRY(cudaMemcpyAsync(ckq + (size_t)(s + 1) * plane, sq + (size_t)len * plane, sizeof(T) * plane,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+        SI_CUDA_TRY(cudaMemcpyAsync(ckp + (size_t)(s + 1) * plane, sp + (size_t)len * plane, sizeof(T) * plane,
+                                    cudaMemcpyDeviceToDevice, c->stream));
+    }
+    // Terminal adjoint and objective at q_T.
+    g.X = ckq + (size_t)nseg * plane;
+    g.LQ = lq;
+    g.LP = lp;
+    g.obj_part = objp;
+    k_adj_gemm<T, GM_TERMINAL><<<ggrid, AG_THREADS, 0, c->stream>>>(g);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    // Reverse sweep.
+    for (int s = nseg - 1; s >= 0; --s) {
+        if ((st = recompute(s)) != SI_OK) return st;
+        const int t0 = s * K, len = std::min(K, steps - t0);
+        for (int j = len - 1; j >= 0; --j) {
+            const int t = t0 + j;
+            k_adj_elem<T><<<AE_BLOCKS, AE_THREADS, 0, c->stream>>>(
+                n, R, ld, sq + (size_t)j * plane, sp + (size_t)j * plane, sF + (size_t)j * plane,
+                sq + (size_t)(j + 1) * plane, sp + (size_t)(j + 1) * plane, lq, lp, la, lb, spar, c->dzeta,
+                c->ddt, t, part + (size_t)t * 3 * AE_BLOCKS);
+            g.X = la;
+            g.LB = lb;
+            g.LQ = lq;
+            g.LP = lp;
+            g.t = t;
+            k_adj_gemm<T, GM_ADJOINT><<<ggrid, AG_THREADS, 0, c->stream>>>(g);
+        }
+        SI_CUDA_TRY(cudaGetLastError());
+        c->launches += 2 * len;
+    }
+    k_adj_finish<T><<<cdiv(std::max(steps, 1), 128), 128, 0, c->stream>>>(steps, part, nobj, objp, g_zeta, g_dt,
+                                                                        g_k, objective);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    return SI_OK;
+}
+
+si_status adjoint_grad(Ctx *c, int steps, float *g_zeta, float *g_dt, float *g_k, float *objective,
+                       const float *q_init, const float *p_init) {
+    if (c->prm.prec == SI_PREC_FP64)
+        return adjoint_impl<double>(c, steps, g_zeta, g_dt, g_k, objective, q_init, p_init);
+    return adjoint_impl<float>(c, steps, g_zeta, g_dt, g_k, objective, q_init, p_init);
+}
+
 }  // namespace si

@@ -476,8 +476,8 @@ si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt, const float *
     if ((s = stage_out(gd, g_dt, sizeof(float) * std::max(steps, 1))) != SI_OK) return s;
     if ((s = stage_out(gk, g_k, sizeof(float))) != SI_OK) return s;
     if ((s = stage_out(ob, objective, sizeof(float))) != SI_OK) return s;
-    if ((s = simt_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr)) != SI_OK) return s;
-    s = adjoint_grad(c, steps, (float *)gz.ptr, (float *)gd.ptr, (float *)gk.ptr, (float *)ob.ptr);
+    s = adjoint_grad(c, steps, (float *)gz.ptr, (float *)gd.ptr, (float *)gk.ptr, (float *)ob.ptr,
+                     (const float *)qi.ptr, (const float *)pi.ptr);
     if (s != SI_OK) return s;
     if ((s = check_device_error(c)) != SI_OK) return s;
     if ((s = finish_out(gz, c->stream)) != SI_OK) return s;

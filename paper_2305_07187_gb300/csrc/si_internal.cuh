@@ -132,7 +132,8 @@ const char *tc_describe(const Ctx *c, char *buf, int len);
 
 // Adjoint, si_adjoint.cu.
 si_status adjoint_grad(Ctx *c, int steps, float *g_zeta, float *g_dt,
-                       float *g_k, float *objective);
+                       float *g_k, float *objective, const float *q_init,
+                       const float *p_init);
 
 // Validation flags (bit set = property violated / present).
 enum : unsigned long long {

@@ -1,0 +1,135 @@
+"""GPU adjoint (si_grad) against the oracle's FP64 reverse mode and FP64
+central finite differences, through the C ABI."""
+import numpy as np
+import pytest
+
+from _helpers import b, inputs, oracle, params_f64
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(n, R, T, seed, scale=1.0):
+    J = inputs.pm1_coupling(n, seed=seed)
+    q0 = inputs.positions(n, R, seed0=10 * seed) * scale
+    zeta = inputs.zeta_ramp(T)
+    dt = inputs.dt_const(T)
+    return J, q0, zeta, dt
+
+
+def _rel(a, b_):
+    a, b_ = np.asarray(a, np.float64), np.asarray(b_, np.float64)
+    return np.abs(a - b_).max() / max(np.abs(b_).max(), 1e-30)
+
+
+@pytest.mark.parametrize("n,R,T,K", [(64, 4, 100, 50), (33, 7, 61, 8), (64, 1, 40, 40)])
+def test_fp64_adjoint_matches_oracle_reverse_mode(n, R, T, K):
+    J, q0, zeta, dt = _case(n, R, T, seed=n)
+    with b.Context(J, replicas=R, steps=T, prec="fp64", ckpt_every=K) as ctx:
+        obj, gz, gd, gk = ctx.grad(zeta, dt, q0)
+        kw = params_f64(ctx)
+    kw.pop("wall_zero_p")
+    o_obj, o_gz, o_gd, o_gk = oracle.grad(J, None, zeta, dt, q0, **kw)
+    # outputs are float32: compare at float32 resolution of the largest entry
+    assert abs(obj - o_obj) <= 1e-6 * abs(o_obj)
+    assert _rel(gz, o_gz) <= 1e-6 and _rel(gd, o_gd) <= 1e-6
+    assert abs(gk - o_gk) <= 1e-6 * max(abs(o_gk), np.abs(o_gd).max())
+
+
+def test_fp64_adjoint_against_central_differences():
+    """FP64 central differences of the FP64 oracle at n=64 on a sample of
+    components: relative error <= 1e-4 (components whose wall pattern changes
+    within +-eps are excluded, as the clamp makes the objective non-smooth)."""
+    n, R, T = 64, 4, 60
+    J, q0, zeta, dt = _case(n, R, T, seed=5)
+    with b.Context(J, replicas=R, steps=T, prec="fp64") as ctx:
+        obj, gz, gd, gk = ctx.grad(zeta, dt, q0)
+        kw = params_f64(ctx)
+    kw.pop("wall_zero_p")
+    zeta64, dt64 = zeta.astype(np.float64), dt.astype(np.float64)
+    eps = 1e-6
+    scale = max(np.abs(gz).max(), np.abs(gd).max(), abs(gk))
+    for t in (0, 7, 19, 33, 48, 59):
+        zp, zm = zeta64.copy(), zeta64.copy()
+        zp[t] += eps
+        zm[t] -= eps
+        fd = (oracle.objective(J, None, zp, dt64, q0, **kw) - oracle.objective(J, None, zm, dt64, q0, **kw)) / (2 * eps)
+        assert abs(gz[t] - fd) <= 1e-4 * scale, (t, gz[t], fd)
+        dp, dm = dt64.copy(), dt64.copy()
+        dp[t] += eps
+        dm[t] -= eps
+        fd = (oracle.objective(J, None, zeta64, dp, q0, **kw) - oracle.objective(J, None, zeta64, dm, q0, **kw)) / (2 * eps)
+        assert abs(gd[t] - fd) <= 1e-4 * scale, (t, gd[t], fd)
+    kp = dict(kw, k=kw["k"] + eps)
+    km = dict(kw, k=kw["k"] - eps)
+    fd = (oracle.objective(J, None, zeta64, dt64, q0, **kp) - oracle.objective(J, None, zeta64, dt64, q0, **km)) / (2 * eps)
+    assert abs(gk - fd) <= 1e-4 * scale
+
+
+def test_fp32_adjoint_close_to_oracle():
+    """FP32 adjoint vs the FP64 reverse mode on a short horizon: the FP32
+    forward drifts from the FP64 one by rounding, amplified by the dynamics,
+    so the bar is 1e-3 relative to the largest component."""
+    n, R, T = 96, 8, 30
+    J, q0, zeta, dt = _case(n, R, T, seed=9)
+    with b.Context(J, replicas=R, steps=T, prec="fp32", ckpt_every=10) as ctx:
+        obj, gz, gd, gk = ctx.grad(zeta, dt, q0)
+        kw = params_f64(ctx)
+    kw.pop("wall_zero_p")
+    o_obj, o_gz, o_gd, o_gk = oracle.grad(J, None, zeta, dt, q0, **kw)
+    assert abs(obj - o_obj) <= 1e-4 * abs(o_obj)
+    assert _rel(gz, o_gz) <= 1e-3 and _rel(gd, o_gd) <= 1e-3
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    n, R, T = 120, 5, 47
+    J, q0, zeta, dt = _case(n, R, T, seed=3)
+    res = []
+    for K in (1, 7, 50):
+        with b.Context(J, replicas=R, steps=T, prec="fp32", ckpt_every=K) as ctx:
+            res.append(ctx.grad(zeta, dt, q0))
+    for r in res[1:]:
+        assert r[0] == res[0][0] and np.array_equal(r[1], res[0][1]) and np.array_equal(r[2], res[0][2])
+        assert r[3] == res[0][3]
+
+
+def test_gradient_workload_n2000_r64_t500():
+    """The gradient workload: N=2000 +-1, R=64, T=500, checkpoints every 50.
+    The objective equals the relaxed energy of the final state of si_run (same
+    forward kernels), evaluated by the oracle."""
+    n, R, T = 2000, 64, 500
+    J, q0, zeta, dt = _case(n, R, T, seed=1)
+    with b.Context(J, replicas=R, steps=T, prec="fp32", ckpt_every=50) as ctx:
+        obj, gz, gd, gk = ctx.grad(zeta, dt, q0)
+        q, p, s = ctx.run(zeta, dt, q0)
+    assert np.isfinite(gz).all() and np.isfinite(gd).all() and np.isfinite(gk)
+    ref = oracle.relaxed_energy(J, None, q).sum()
+    assert abs(obj - ref) <= 1e-5 * abs(ref)
+
+
+def test_autograd_function_and_schedule_tuning():
+    import torch
+    from paper_2305_07187_gb300.autograd import relaxed_energy
+    n, R, T = 64, 4, 40
+    J, q0, zeta, dt = _case(n, R, T, seed=11)
+    z = torch.tensor(zeta, requires_grad=True)
+    d = torch.tensor(dt, requires_grad=True)
+    k = torch.tensor(0.5, requires_grad=True)
+    E = relaxed_energy(J, z, d, k, q0)
+    E.backward()
+    with b.Context(J, replicas=R, steps=T) as ctx:
+        obj, gz, gd, gk = ctx.grad(zeta, dt, q0)
+    assert abs(E.item() - obj) == 0
+    assert np.array_equal(z.grad.numpy(), gz) and np.array_equal(d.grad.numpy(), gd)
+    assert k.grad.item() == np.float32(gk)
+    # a few gradient steps on the coupling schedule lower the relaxed energy
+    z = torch.tensor(zeta, requires_grad=True)
+    opt = torch.optim.SGD([z], lr=1e-4)
+    first = None
+    for _ in range(5):
+        opt.zero_grad()
+        E = relaxed_energy(J, z, torch.tensor(dt), 0.5, q0)
+        if first is None:
+            first = E.item()
+        E.backward()
+        opt.step()
+    assert relaxed_energy(J, z.detach(), torch.tensor(dt), 0.5, q0).item() < first
