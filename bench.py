@@ -205,6 +205,83 @@ def ncu_case(args):
     return 0
 
 
+GROUP_T = 1000
+
+
+def run_grouped(args):
+    """Uneven grouped batch: 256 instances, N log-uniform in [256, 8192],
+    R in [16, 256], half +-1 (e4m3-exact) and half Gaussian (bf16), T=1000."""
+    import torch
+
+    from paper_2305_07187_gb300 import _binding as b
+    dev = torch.device("cuda", 0)
+    specs = inputs.uneven_instances(256)
+    Js = [inputs.instance_coupling_torch(sp, dev) for sp in specs]
+    qs = [inputs.positions_torch(sp.n, sp.replicas, seed=9000 + sp.index, device=dev) for sp in specs]
+    precs = ["j_fp8_q_bf16" if sp.kind == "pm1" else "j_bf16_q_bf16" for sp in specs]
+    zeta = torch.from_numpy(inputs.zeta_ramp(GROUP_T)).to(dev)
+    dt = torch.from_numpy(inputs.dt_const(GROUP_T)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    g = b.Group(Js, None, replicas=[sp.replicas for sp in specs], steps=GROUP_T, precs=precs,
+                stream=stream.cuda_stream)
+    del Js
+    torch.cuda.empty_cache()
+    spins = [torch.empty((sp.replicas, sp.n), dtype=torch.int8, device=dev) for sp in specs]
+    g.enable_timing(True)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(max(3, args.warmup)):
+        g.run_into(zeta, dt, qs, None, None, None, spins)
+        flush.zero_()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(smi_index(0))
+    sampler.start()
+    time.sleep(0.3)
+    step_ms, kern_ms, launches = [], [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.run_into(zeta, dt, qs, None, None, None, spins)
+        launches += g.last_launch_count()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(g.last_kernel_ms())
+    clocks = sampler.stop()
+    desc = g.describe()
+    ms = sum(step_ms) / len(step_ms)
+    k_ms = sum(kern_ms) / len(kern_ms)
+    units = sum(sp.replicas * sp.n for sp in specs) * GROUP_T
+    # algorithmic bytes per step: J once in its storage type, the FP32 state
+    # read and written, the bf16 operand written and read once
+    jb = sum(sp.n * sp.n * (1 if sp.kind == "pm1" else 2) for sp in specs)
+    sb = sum(sp.replicas * sp.n * (16 + 4) for sp in specs)
+    bytes_step = jb + sb
+    peaks, src = load_peaks()
+    achieved = bytes_step * GROUP_T / (k_ms * 1e-3) / 1e9
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    flops = sum(2.0 * sp.n * sp.n * sp.replicas for sp in specs) * GROUP_T
+    line = {
+        "metric": METRIC, "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "uneven grouped batch: 256 instances, N log-uniform [256, 8192], R in "
+                               "[16, 256] (multiples of 16), even +-1 (e4m3-exact), odd N(0,1) bf16, "
+                               "T=1000, one grouped launch per step replayed from a CUDA graph",
+                   "kernel": desc, "l2": "J (5 GB bf16) exceeds L2; flushed between steps"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_group_step",
+                     "kernel_ms": k_ms, "algorithmic_bytes_per_step": bytes_step,
+                     "tensor_tflops": flops / (k_ms * 1e-3) / 1e12,
+                     "peak_source": "%s hbm_gbs" % src},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    g.close()
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -217,6 +294,9 @@ def main():
                     help="profiling case: one warm-up and one si_run of the batched "
                          "workload with --time-steps steps, no timing output")
     ap.add_argument("--time-steps", type=int, default=T_STEPS)
+    ap.add_argument("--workload", default="batched", choices=["batched", "grouped"],
+                    help="batched: N=2000, R=1024, T=2000 (default); grouped: 256 uneven "
+                         "instances, T=1000, one grouped launch per step")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -226,6 +306,8 @@ def main():
         _build.build()
     if args.ncu_case:
         return ncu_case(args)
+    if args.workload == "grouped":
+        return run_grouped(args)
 
     import torch
     import torch.distributed as dist

@@ -196,6 +196,41 @@ si_status si_run_noalloc(const si_params *prm, const float *J, const float *h,
                          const float *zeta, const float *dt, float *q, float *p,
                          int8_t *spins_out, void *stream);
 
+/*
+ * Grouped batch of independent instances of uneven size (many "parallel
+ * tests" of Fig. 3 at once, each its own J).  All members share steps and the
+ * integrator parameters (k, m, q0, q_max, p_max, update_order, wall_zero_p)
+ * and use a tensor-core precision (SI_PREC_J_FP8_Q_BF16 or
+ * SI_PREC_J_BF16_Q_BF16); n and replicas may differ.  Each time step is one
+ * grouped launch over all members' tiles (replayed from a CUDA graph); the
+ * tile width per member is chosen by an autotuner on the first run and
+ * cached by group shape.
+ *   prm[count], J[count] (n_i*n_i floats, host or device), h NULL or
+ *   h[count] with NULL entries allowed.
+ */
+typedef struct si_group si_group;
+si_status si_create_group(si_group **out, int32_t count, const si_params *prm,
+                          const float *const *J, const float *const *h,
+                          void *stream);
+/*
+ * Run steps time steps for every member.  zeta, dt [steps]; q_init[i] and
+ * optional p_init[i], q_out[i], p_out[i], spins_out[i] are [R_i][n_i] (host
+ * or device); any of the output arrays, or p_init, may be NULL.
+ */
+si_status si_run_group(si_group *g, const float *zeta, const float *dt,
+                       const float *const *q_init, const float *const *p_init,
+                       float *const *q_out, float *const *p_out,
+                       int8_t *const *spins_out);
+/* si_energy for member `index` of the group. */
+si_status si_group_energy(si_group *g, int32_t index, const int8_t *spins,
+                          int32_t R, int32_t *energy_out, int32_t *cut_out,
+                          double *energy_f);
+si_status si_group_enable_timing(si_group *g, int32_t on);
+si_status si_group_last_kernel_time(const si_group *g, float *ms);
+si_status si_group_describe(const si_group *g, char *buf, int32_t len);
+int32_t si_group_last_launch_count(const si_group *g);
+void si_destroy_group(si_group *g);
+
 /* Short description of the kernel path and tile shape the context uses. */
 si_status si_describe(const si_ctx *ctx, char *buf, int32_t len);
 

@@ -35,7 +35,9 @@ PREC = {"fp32": 0, "fp64": 1, "j_fp8_q_bf16": 2, "j_bf16_q_bf16": 3}
 
 EXPORTS = ("si_default_params", "si_create", "si_run", "si_get_state", "si_energy", "si_grad",
            "si_enable_timing", "si_last_kernel_time", "si_describe", "si_last_launch_count",
-           "si_last_error", "si_destroy", "si_run_noalloc")
+           "si_last_error", "si_destroy", "si_run_noalloc", "si_create_group", "si_run_group",
+           "si_group_energy", "si_group_enable_timing", "si_group_last_kernel_time",
+           "si_group_describe", "si_group_last_launch_count", "si_destroy_group")
 
 
 class SiParams(ctypes.Structure):
@@ -85,6 +87,23 @@ def load():
     lib.si_last_kernel_time.restype = ctypes.c_int
     lib.si_run_noalloc.argtypes = [ctypes.POINTER(SiParams), P, P, P, P, P, P, P, P]
     lib.si_run_noalloc.restype = ctypes.c_int
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    lib.si_create_group.argtypes = [ctypes.POINTER(P), I32, ctypes.POINTER(SiParams), PP, PP, P]
+    lib.si_create_group.restype = ctypes.c_int
+    lib.si_run_group.argtypes = [P, P, P, PP, PP, PP, PP, PP]
+    lib.si_run_group.restype = ctypes.c_int
+    lib.si_group_energy.argtypes = [P, I32, P, I32, P, P, P]
+    lib.si_group_energy.restype = ctypes.c_int
+    lib.si_group_enable_timing.argtypes = [P, I32]
+    lib.si_group_enable_timing.restype = ctypes.c_int
+    lib.si_group_last_kernel_time.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+    lib.si_group_last_kernel_time.restype = ctypes.c_int
+    lib.si_group_describe.argtypes = [P, ctypes.c_char_p, I32]
+    lib.si_group_describe.restype = ctypes.c_int
+    lib.si_group_last_launch_count.argtypes = [P]
+    lib.si_group_last_launch_count.restype = I32
+    lib.si_destroy_group.argtypes = [P]
+    lib.si_destroy_group.restype = None
     lib.si_describe.argtypes = [P, ctypes.c_char_p, I32]
     lib.si_describe.restype = ctypes.c_int
     lib.si_last_launch_count.argtypes = [P]
@@ -292,3 +311,102 @@ def run_noalloc(J, h, zeta, dt, q, p, spins_out=None, stream=None, **params):
             _Arg(dt, np.float32), _Arg(q, np.float32, n, writable=True),
             _Arg(p, np.float32, n, writable=True), _Arg(spins_out, np.int8, n, writable=True)]
     _check(load().si_run_noalloc(ctypes.byref(prm), *[a.ptr for a in args], _stream_handle(stream)))
+
+
+def _ptr_array(args):
+    arr = (ctypes.c_void_p * len(args))()
+    for k, a in enumerate(args):
+        arr[k] = a.ptr.value if (a is not None and a.ptr is not None) else None
+    return arr
+
+
+class Group:
+    """Grouped batch of independent instances (wraps si_group)."""
+
+    def __init__(self, Js, hs=None, *, replicas, steps, precs="j_bf16_q_bf16", stream=None, **params):
+        lib = load()
+        count = len(Js)
+        if isinstance(precs, str):
+            precs = [precs] * count
+        if isinstance(replicas, int):
+            replicas = [replicas] * count
+        self.count, self.steps = count, int(steps)
+        self.ns = [int(J.shape[0]) for J in Js]
+        self.Rs = [int(r) for r in replicas]
+        prm = (SiParams * count)()
+        for k in range(count):
+            p = default_params(n=self.ns[k], replicas=self.Rs[k], steps=self.steps, prec=precs[k], **params)
+            prm[k] = p
+        Jargs = [_Arg(J, np.float32, self.ns[k] ** 2) for k, J in enumerate(Js)]
+        hargs = None if hs is None else [_Arg(h, np.float32, self.ns[k]) if h is not None else None
+                                         for k, h in enumerate(hs)]
+        self._stream = _stream_handle(stream)
+        g = ctypes.c_void_p()
+        _check(lib.si_create_group(ctypes.byref(g), count, prm, _ptr_array(Jargs),
+                                   None if hargs is None else _ptr_array(hargs), self._stream))
+        self.g = g
+
+    def close(self):
+        if getattr(self, "g", None):
+            load().si_destroy_group(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def describe(self):
+        buf = ctypes.create_string_buffer(512)
+        _check(load().si_group_describe(self.g, buf, 512))
+        return buf.value.decode()
+
+    def enable_timing(self, on=True):
+        _check(load().si_group_enable_timing(self.g, 1 if on else 0))
+
+    def last_kernel_ms(self):
+        v = ctypes.c_float(0.0)
+        _check(load().si_group_last_kernel_time(self.g, ctypes.byref(v)))
+        return float(v.value)
+
+    def last_launch_count(self):
+        return int(load().si_group_last_launch_count(self.g))
+
+    def run_into(self, zeta, dt, q_inits, p_inits=None, q_outs=None, p_outs=None, spins_outs=None):
+        c = self.count
+        sz = [self.ns[k] * self.Rs[k] for k in range(c)]
+        z = _Arg(zeta, np.float32, self.steps)
+        d = _Arg(dt, np.float32, self.steps)
+        qi = [_Arg(q_inits[k], np.float32, sz[k]) for k in range(c)]
+        pi = None if p_inits is None else [_Arg(p_inits[k], np.float32, sz[k]) for k in range(c)]
+        qo = None if q_outs is None else [_Arg(q_outs[k], np.float32, sz[k], writable=True) for k in range(c)]
+        po = None if p_outs is None else [_Arg(p_outs[k], np.float32, sz[k], writable=True) for k in range(c)]
+        so = None if spins_outs is None else [_Arg(spins_outs[k], np.int8, sz[k], writable=True) for k in range(c)]
+        arr = lambda xs: None if xs is None else _ptr_array(xs)
+        _check(load().si_run_group(self.g, z.ptr, d.ptr, arr(qi), arr(pi), arr(qo), arr(po), arr(so)))
+
+    def run(self, zeta, dt, q_inits, p_inits=None):
+        qs = [np.empty((R, n), np.float32) for n, R in zip(self.ns, self.Rs)]
+        ps = [np.empty((R, n), np.float32) for n, R in zip(self.ns, self.Rs)]
+        ss = [np.empty((R, n), np.int8) for n, R in zip(self.ns, self.Rs)]
+        self.run_into(zeta, dt, q_inits, p_inits, qs, ps, ss)
+        return qs, ps, ss
+
+    def energy(self, index, spins, exact=True):
+        n = self.ns[index]
+        s = np.ascontiguousarray(spins, dtype=np.int8)
+        R = s.size // n
+        e = np.empty(R, np.int32) if exact else None
+        cc = np.empty(R, np.int32) if exact else None
+        f = np.empty(R, np.float64)
+        ea, ca, fa = _Arg(e, np.int32, R, True), _Arg(cc, np.int32, R, True), _Arg(f, np.float64, R, True)
+        _check(load().si_group_energy(self.g, int(index), s.ctypes.data_as(ctypes.c_void_p), R, ea.ptr,
+                                      ca.ptr, fa.ptr))
+        return e, cc, f

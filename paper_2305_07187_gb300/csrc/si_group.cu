@@ -1,0 +1,832 @@
+// Grouped batch: many independent Ising instances of uneven size (the
+// paper's parallel tests, Fig. 3, generalised to many problems at once) run
+// the tensor-core step together.
+//
+// One launch performs one time step for every instance.  Its CTAs walk a
+// list of (instance, M tile, replica block) tiles ordered by decreasing cost;
+// each tile is a tcgen05 GEMM F = J Q^T over the instance's K range (its own
+// TMA tensor maps, read from device memory) with the integrator of Eq. 8 and
+// the walls of Eq. 6 fused into the epilogue.  The launch boundary is the
+// step barrier for all instances; the T launches are captured once into a
+// CUDA graph and replayed.  The operand ring runs across tile boundaries, and
+// TMEM holds two accumulator slots so that the epilogue of one tile overlaps
+// the MMAs of the next.  J of all instances does not fit in L2, so this path
+// streams J from HBM every step.
+//
+// Tile width (64 or 128 replicas per tile, per instance) is chosen by an
+// autotuner that times a few steps of each candidate policy on the actual
+// group and caches the winner by group shape.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "si_tcgen05.cuh"
+
+namespace si {
+
+constexpr int GR_BM = 128, GR_BK = 64, GR_THREADS = 352, GR_S = 6;
+constexpr int GR_A_BYTES = GR_BM * GR_BK * 2;
+constexpr int GR_B_MAX = 128 * GR_BK * 2;
+constexpr int GR_STAGE = GR_A_BYTES + GR_B_MAX;
+constexpr int GR_BARS = GR_S * GR_STAGE;
+constexpr int GR_NBARS = 2 * GR_S + 2 + 2 + 1;  // full, empty, accf[2], tmem_empty[2], drain
+constexpr int GR_SMEM = GR_BARS + GR_NBARS * 8 + 16 + 1024;
+
+struct GroupInst {
+    int n, R, ldk, rpad, mtiles, rblocks, kblocks, bn;
+    const float *h;            // [n] or null
+    float *q_state, *p_state;  // [R][n]
+    __nv_bfloat16 *qop;        // [2][rpad][ldk]
+    int8_t *spins;             // [R][n]
+};
+
+struct GroupTile {
+    int inst, mt, rb, cost;
+};
+
+struct GroupArgs {
+    const GroupInst *inst;
+    const GroupTile *tiles;
+    int ntiles;
+    const CUtensorMap *maps;   // [2*count]: J map, q map of each instance
+    const float *zeta, *dt;
+    int t, last;
+    StepParams sp;
+    int *err;
+    long long limit_ns;
+};
+
+__global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_constant__ GroupArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar0 = sbase + GR_BARS;
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (GR_S + s); };
+    auto accf_bar = [&](int k) { return bar0 + 8u * (2 * GR_S + k); };
+    auto tmem_empty_bar = [&](int k) { return bar0 + 8u * (2 * GR_S + 2 + k); };
+    const uint32_t drain_bar = bar0 + 8u * (2 * GR_S + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + GR_BARS + GR_NBARS * 8);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + GR_BARS + GR_NBARS * 8 + 4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < GR_S; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(accf_bar(k), 2);
+            mbar_init(tmem_empty_bar(k), 8);
+        }
+        mbar_init(drain_bar, 2);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int plane_in = a.t & 1;
+
+    if (warp == 0) {
+        // ---------------------------------------------- TMA producer
+        // Two rings of stages: even K blocks go to the even stages (consumed
+        // only by MMA warp 1), odd K blocks to the odd stages (warp 2), so
+        // that each stage has one in-order consumer.
+        constexpr int HS = GR_S / 2;
+        if (lane == 0) {
+            uint32_t cnt0 = 0u, cnt1 = 0u;   // stages armed in ring 0 / ring 1
+            bool ok = true;
+            for (int k = blockIdx.x; k < a.ntiles && ok; k += gridDim.x) {
+                const GroupTile tl = a.tiles[k];
+                const GroupInst &in = a.inst[tl.inst];
+                const CUtensorMap *mJ = a.maps + 2 * tl.inst;
+                const CUtensorMap *mQ = mJ + 1;
+                const uint32_t bytes = (uint32_t)(GR_A_BYTES + in.bn * GR_BK * 2);
+                const int yq = plane_in * in.rpad + tl.rb * in.bn;
+                for (int kb = 0; kb < in.kblocks; ++kb) {
+                    const int ring = kb & 1;
+                    const uint32_t c = ring ? cnt1 : cnt0;
+                    const int s = 2 * (int)(c % HS) + ring;
+                    const uint32_t ph = (c / HS) & 1u;
+                    if (!mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                    if (ring) ++cnt1; else ++cnt0;
+                    const uint32_t dA = sbase + s * GR_STAGE;
+                    mbar_arrive_expect_tx(full_bar(s), bytes);
+                    tma_load_2d(dA, mJ, full_bar(s), kb * GR_BK, tl.mt * GR_BM);
+                    tma_load_2d(dA + GR_A_BYTES, mQ, full_bar(s), kb * GR_BK, yq);
+                }
+            }
+            for (int ring = 0; ring < 2; ++ring) {
+                const uint32_t cr = ring ? cnt1 : cnt0;
+                const uint32_t first = cr > (uint32_t)HS ? cr - HS : 0u;
+                for (uint32_t k = first; k < cr; ++k) {
+                    const unsigned long long t0 = globaltimer_ns();
+                    while (!mbar_try_wait(full_bar(2 * (int)(k % HS) + ring), (k / HS) & 1u)) {
+                        if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                            atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
+                            break;
+                        }
+                    }
+                }
+            }
+        }
+    } else if (warp <= 2) {
+        // ---------------------------------------------- MMA issuers
+        constexpr int HS = GR_S / 2;
+        // Warp 1: even K blocks into acc0, warp 2: odd K blocks into acc1,
+        // of the TMEM slot (u & 1) of the CTA's u-th tile.
+        if (lane == 0) {
+            const int w = warp - 1;
+            uint32_t c = 0;  // position in this warp's ring of stages
+            bool ok = true;
+            int u = 0;
+            for (int k = blockIdx.x; k < a.ntiles && ok; k += gridDim.x, ++u) {
+                const GroupTile tl = a.tiles[k];
+                const GroupInst &in = a.inst[tl.inst];
+                const int slot = u & 1;
+                if (u >= 2) {
+                    if (!mbar_wait(tmem_empty_bar(slot), (uint32_t)(((u >> 1) - 1) & 1), a.err, abort_flag,
+                                   a.limit_ns)) {
+                        ok = false;
+                        break;
+                    }
+                }
+                tc_fence_after();
+                const uint32_t idesc = idesc_bf16(GR_BM, in.bn);
+                const uint32_t d_tmem = tmem + (uint32_t)slot * 256u + (w == 0 ? 0u : 128u);
+                for (int kb = w; kb < in.kblocks; kb += 2, ++c) {
+                    const int s = 2 * (int)(c % HS) + w;
+                    const uint32_t ph = (c / HS) & 1u;
+                    if (!mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint64_t ad = sdesc_sw128(sbase + s * GR_STAGE);
+                    const uint64_t bd = ad + (uint64_t)(GR_A_BYTES >> 4);
+#pragma unroll
+                    for (int kk = 0; kk < GR_BK / 16; ++kk)
+                        mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb != w || kk != 0) ? 1u : 0u);
+                    mma_commit(empty_bar(s));
+                }
+                if (ok) mma_commit(accf_bar(slot));
+            }
+            mma_commit(drain_bar);
+            const unsigned long long t0 = globaltimer_ns();
+            while (!mbar_try_wait(drain_bar, 0u)) {
+                if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                    atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
+                    break;
+                }
+            }
+        }
+    } else {
+        // ---------------------------------------------- epilogue (8 warps)
+        const int quad = warp & 3;
+        const int half = (warp - 3) >> 2;
+        const int row = quad * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+        const float zt = a.zeta[a.t], dtt = a.dt[a.t];
+        const float dtm = dtt / a.sp.m;
+        int u = 0;
+        for (int k = blockIdx.x; k < a.ntiles; k += gridDim.x, ++u) {
+            const GroupTile tl = a.tiles[k];
+            const GroupInst &in = a.inst[tl.inst];
+            const int slot = u & 1;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(accf_bar(slot), (uint32_t)((u >> 1) & 1), a.err, abort_flag, a.limit_ns);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) break;
+            tc_fence_after();
+            const int i = tl.mt * GR_BM + row;
+            const bool row_ok = i < in.n;
+            const float hi = (in.h && row_ok) ? in.h[i] : 0.f;
+            const bool two_acc = in.kblocks > 1;
+            const int cph = in.bn / 64;
+            const uint32_t tacc = tmem + lane_off + (uint32_t)slot * 256u;
+            __nv_bfloat16 *qn = in.qop + (size_t)(plane_in ^ 1) * in.rpad * in.ldk;
+            for (int c = half * cph; c < (half + 1) * cph; ++c) {
+                uint32_t vf[32], vg[32];
+                tmem_ld32(tacc + c * 32, vf);
+                tmem_ld32(tacc + 128 + c * 32, vg);
+                tmem_wait_ld();
+                if (row_ok) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int r = tl.rb * in.bn + c * 32 + j;
+                        if (r >= in.R) continue;
+                        float F = __uint_as_float(vf[j]);
+                        if (two_acc) F += __uint_as_float(vg[j]);
+                        const size_t e = (size_t)r * in.n + i;
+                        float qo, po;
+                        integrate<float>(in.q_state[e], in.p_state[e], F + hi, zt, dtt, dtm, a.sp, qo, po);
+                        in.q_state[e] = qo;
+                        in.p_state[e] = po;
+                        if (!a.last) qn[(size_t)r * in.ldk + i] = __float2bfloat16_rn(qo);
+                        else if (in.spins) in.spins[e] = spin_of(qo);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tmem_empty_bar(slot));
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+    }
+}
+
+// q_state -> bf16 operand plane 0 for every instance (blockIdx.y = instance).
+__global__ void k_group_init(const GroupInst *inst) {
+    const GroupInst in = inst[blockIdx.y];
+    const long long total = (long long)in.R * in.n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / in.n), i = (int)(e % in.n);
+        in.qop[(size_t)r * in.ldk + i] = __float2bfloat16_rn(in.q_state[e]);
+    }
+}
+
+// ============================================================ host side
+struct GroupMember {
+    int n, R;
+    void *J = nullptr;          // bf16 [mpad][ldk]
+    int ldk = 0, mpad = 0;
+    float *h = nullptr;
+    float *q = nullptr, *p = nullptr;
+    __nv_bfloat16 *qop = nullptr;
+    int rpad_max = 0;
+    int8_t *spins = nullptr;
+    Ctx energy;                 // readout view (int8 J, h copies)
+};
+
+struct Group {
+    int count = 0, steps = 0;
+    si_params common;
+    cudaStream_t stream = nullptr;
+    int device = 0, sms = 0;
+    long long limit_ns = 2000000000LL;
+    std::vector<GroupMember> m;
+    GroupInst *d_inst = nullptr;
+    GroupTile *d_tiles = nullptr;
+    int ntiles = 0;
+    int pol_tiles_off[3] = {0, 0, 0}, pol_ntiles[3] = {0, 0, 0};
+    CUtensorMap *d_maps = nullptr;
+    float *d_zeta = nullptr, *d_dt = nullptr;
+    int *d_err = nullptr;
+    int policy = -1;            // chosen tile policy
+    int grid = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = -1;
+    bool timing = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool ev_valid = false;
+    int launches = 0;
+};
+
+static const char *kPolicyName[] = {"bn64-if-R<=64-else-128", "all-64", "all-128"};
+constexpr int kPolicies = 3;
+
+static int policy_bn(int policy, int R) {
+    if (policy == 1) return 64;
+    if (policy == 2) return 128;
+    return R <= 64 ? 64 : 128;
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune_cache;
+
+static std::string group_key(const Group *g) {
+    std::string k = std::to_string(g->sms) + ":";
+    for (const auto &x : g->m) k += std::to_string(x.n) + "x" + std::to_string(x.R) + ",";
+    return k;
+}
+
+// Build, once at creation, the instance table, tensor maps and tile list of
+// every tile policy (device tables are never rewritten after a launch used
+// them); group_apply_policy only selects one.
+static si_status group_build_policies(Group *g) {
+    const int c = g->count;
+    std::vector<GroupInst> inst((size_t)kPolicies * c);
+    std::vector<CUtensorMap> maps((size_t)kPolicies * 2 * c);
+    std::vector<std::vector<GroupTile>> tiles(kPolicies);
+    for (int pol = 0; pol < kPolicies; ++pol) {
+        for (int i = 0; i < c; ++i) {
+            GroupMember &x = g->m[i];
+            GroupInst &d = inst[(size_t)pol * c + i];
+            d.n = x.n;
+            d.R = x.R;
+            d.ldk = x.ldk;
+            d.bn = policy_bn(pol, x.R);
+            d.rpad = x.rpad_max;
+            d.mtiles = x.mpad / GR_BM;
+            d.rblocks = cdiv(x.R, d.bn);
+            d.kblocks = x.ldk / GR_BK;
+            d.h = x.h;
+            d.q_state = x.q;
+            d.p_state = x.p;
+            d.qop = x.qop;
+            d.spins = x.spins;
+            CUtensorMap *mp = &maps[((size_t)pol * c + i) * 2];
+            si_status s = tc_make_map_bf16(mp, x.J, x.ldk, x.mpad, GR_BK, GR_BM);
+            if (s != SI_OK) return s;
+            s = tc_make_map_bf16(mp + 1, x.qop, x.ldk, 2 * x.rpad_max, GR_BK, d.bn);
+            if (s != SI_OK) return s;
+            for (int mt = 0; mt < d.mtiles; ++mt)
+                for (int rb = 0; rb < d.rblocks; ++rb)
+                    tiles[pol].push_back(GroupTile{i, mt, rb, d.kblocks * (d.bn + 64)});
+        }
+        // Longest first; tiles of one M slab stay adjacent so that concurrent
+        // replica blocks share the J slab through L2.
+        std::stable_sort(tiles[pol].begin(), tiles[pol].end(),
+                         [](const GroupTile &x, const GroupTile &y) { return x.cost > y.cost; });
+    }
+    size_t ntot = 0;
+    for (auto &v : tiles) ntot += v.size();
+    SI_CUDA_TRY(cudaMalloc((void **)&g->d_inst, sizeof(GroupInst) * inst.size()));
+    SI_CUDA_TRY(cudaMalloc((void **)&g->d_maps, sizeof(CUtensorMap) * maps.size()));
+    SI_CUDA_TRY(cudaMalloc((void **)&g->d_tiles, sizeof(GroupTile) * ntot));
+    SI_CUDA_TRY(cudaMemcpyAsync(g->d_inst, inst.data(), sizeof(GroupInst) * inst.size(), cudaMemcpyHostToDevice,
+                                g->stream));
+    SI_CUDA_TRY(cudaMemcpyAsync(g->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
+                                g->stream));
+    size_t off = 0;
+    for (int pol = 0; pol < kPolicies; ++pol) {
+        SI_CUDA_TRY(cudaMemcpyAsync(g->d_tiles + off, tiles[pol].data(), sizeof(GroupTile) * tiles[pol].size(),
+                                    cudaMemcpyHostToDevice, g->stream));
+        g->pol_tiles_off[pol] = (int)off;
+        g->pol_ntiles[pol] = (int)tiles[pol].size();
+        off += tiles[pol].size();
+    }
+    SI_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return SI_OK;
+}
+
+static si_status group_apply_policy(Group *g, int policy) {
+    g->policy = policy;
+    g->ntiles = g->pol_ntiles[policy];
+    if (g->graph) {
+        cudaGraphExecDestroy(g->graph);
+        g->graph = nullptr;
+        g->graph_steps = -1;
+    }
+    return SI_OK;
+}
+
+static si_status group_launch_step(Group *g, int t, int steps) {
+    GroupArgs a;
+    a.inst = g->d_inst + (size_t)g->policy * g->count;
+    a.tiles = g->d_tiles + g->pol_tiles_off[g->policy];
+    a.ntiles = g->ntiles;
+    a.maps = g->d_maps + (size_t)g->policy * 2 * g->count;
+    a.zeta = g->d_zeta;
+    a.dt = g->d_dt;
+    a.t = t;
+    a.last = (t == steps - 1) ? 1 : 0;
+    a.sp = StepParams{g->common.k, g->common.m, g->common.q0, g->common.q_max, g->common.p_max,
+                      g->common.update_order, g->common.wall_zero_p};
+    a.err = g->d_err;
+    a.limit_ns = g->limit_ns;
+    k_group_step<<<g->grid, GR_THREADS, GR_SMEM, g->stream>>>(a);
+    SI_CUDA_TRY(cudaGetLastError());
+    return SI_OK;
+}
+
+// Capture the T step launches into a CUDA graph (once per step count/policy).
+static si_status group_graph(Group *g, int steps) {
+    if (g->graph && g->graph_steps == steps) return SI_OK;
+    if (g->graph) {
+        cudaGraphExecDestroy(g->graph);
+        g->graph = nullptr;
+    }
+    cudaStream_t cs;
+    SI_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaStream_t saved = g->stream;
+    g->stream = cs;
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    si_status s = SI_OK;
+    if (e == cudaSuccess) {
+        for (int t = 0; t < steps && s == SI_OK; ++t) s = group_launch_step(g, t, steps);
+        e = cudaStreamEndCapture(cs, &graph);
+    }
+    g->stream = saved;
+    cudaStreamDestroy(cs);
+    if (s != SI_OK) return s;
+    SI_CUDA_TRY(e);
+    e = cudaGraphInstantiate(&g->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    SI_CUDA_TRY(e);
+    g->graph_steps = steps;
+    return SI_OK;
+}
+
+static si_status group_check_err(Group *g) {
+    int herr = 0;
+    SI_CUDA_TRY(cudaMemcpyAsync(&herr, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    SI_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    if (herr != DEV_OK) {
+        SI_CUDA_TRY(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream));
+        SI_CUDA_TRY(cudaStreamSynchronize(g->stream));
+        set_error("grouped step: an mbarrier wait timed out");
+        return SI_ERR_TIMEOUT;
+    }
+    return SI_OK;
+}
+
+// Time `steps` uncaptured launches of a policy (autotuner).
+static si_status group_time_policy(Group *g, int policy, int steps, float *ms) {
+    si_status s = group_apply_policy(g, policy);
+    if (s != SI_OK) return s;
+    cudaEvent_t e0, e1;
+    SI_CUDA_TRY(cudaEventCreate(&e0));
+    SI_CUDA_TRY(cudaEventCreate(&e1));
+    // warm-up step, then timed steps (states evolve; timing does not depend on values)
+    s = group_launch_step(g, 0, g->steps + 1);
+    SI_CUDA_TRY(cudaEventRecord(e0, g->stream));
+    for (int t = 0; t < steps && s == SI_OK; ++t) s = group_launch_step(g, t % std::max(1, g->steps), g->steps + 1);
+    SI_CUDA_TRY(cudaEventRecord(e1, g->stream));
+    SI_CUDA_TRY(cudaEventSynchronize(e1));
+    SI_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != SI_OK) return s;
+    return group_check_err(g);
+}
+
+static si_status group_autotune(Group *g) {
+    const std::string key = group_key(g);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) return group_apply_policy(g, it->second);
+    }
+    int best = 0;
+    const char *env = std::getenv("SI_GROUP_POLICY");
+    if (env && std::atoi(env) >= 0 && std::atoi(env) < kPolicies) {
+        best = std::atoi(env);
+    } else if (!(env && std::atoi(env) < 0)) {
+        float best_ms = 1e30f;
+        for (int pol = 0; pol < kPolicies; ++pol) {
+            float ms = 0.f;
+            si_status s = group_time_policy(g, pol, 3, &ms);
+            if (s != SI_OK) return s;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = pol;
+            }
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    return group_apply_policy(g, best);
+}
+
+static void free_group(Group *g) {
+    if (!g) return;
+    for (auto &x : g->m) {
+        void *ptrs[] = {x.J, x.h, x.q, x.p, x.qop, x.spins, x.energy.dJ8, x.energy.dh8, x.energy.dspins_in};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+    }
+    void *ptrs[] = {g->d_inst, g->d_tiles, g->d_maps, g->d_zeta, g->d_dt, g->d_err};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (g->graph) cudaGraphExecDestroy(g->graph);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    delete g;
+}
+
+static si_status group_create_impl(Group *g, const si_params *prm, const float *const *J,
+                                   const float *const *h) {
+    SI_CUDA_TRY(cudaGetDevice(&g->device));
+    SI_CUDA_TRY(cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device));
+    if (const char *e = std::getenv("SI_SPIN_LIMIT_NS")) {
+        long long v = std::atoll(e);
+        if (v > 0) g->limit_ns = v;
+    }
+    g->m.resize(g->count);
+    for (int i = 0; i < g->count; ++i) {
+        GroupMember &x = g->m[i];
+        const int n = prm[i].n;
+        x.n = n;
+        x.R = prm[i].replicas;
+        x.ldk = round_up(n, GR_BK);
+        x.mpad = round_up(n, GR_BM);
+        x.rpad_max = round_up(x.R, 128);
+        const float *Jp = J[i];
+        const float *hp = h ? h[i] : nullptr;
+        void *Jtmp = nullptr, *htmp = nullptr;
+        if (!is_device_ptr(Jp)) {
+            SI_CUDA_TRY(cudaMalloc(&Jtmp, sizeof(float) * (size_t)n * n));
+            SI_CUDA_TRY(cudaMemcpyAsync(Jtmp, Jp, sizeof(float) * (size_t)n * n, cudaMemcpyHostToDevice, g->stream));
+            Jp = (const float *)Jtmp;
+        }
+        if (hp && !is_device_ptr(hp)) {
+            SI_CUDA_TRY(cudaMalloc(&htmp, sizeof(float) * n));
+            SI_CUDA_TRY(cudaMemcpyAsync(htmp, hp, sizeof(float) * n, cudaMemcpyHostToDevice, g->stream));
+            hp = (const float *)htmp;
+        }
+        unsigned long long flags = 0;
+        long long s_upper = 0;
+        si_status s = simt_validate(Jp, hp, n, prm[i].prec, &flags, &s_upper, g->stream);
+        auto cleanup = [&]() {
+            if (Jtmp) cudaFree(Jtmp);
+            if (htmp) cudaFree(htmp);
+        };
+        if (s != SI_OK) { cleanup(); return s; }
+        if (flags & (VF_NONFINITE | VF_H_NONFINITE)) {
+            cleanup();
+            set_error("group member " + std::to_string(i) + ": J or h holds a non-finite value");
+            return SI_ERR_INVALID_ARG;
+        }
+        if (flags & (VF_ASYM | VF_DIAG)) {
+            cleanup();
+            set_error("group member " + std::to_string(i) + ": J must be symmetric with a zero diagonal");
+            return SI_ERR_NOT_SYMMETRIC;
+        }
+        if (prm[i].prec == SI_PREC_J_FP8_Q_BF16 && (flags & VF_NOT_E4M3)) {
+            cleanup();
+            set_error("group member " + std::to_string(i) + ": SI_PREC_J_FP8_Q_BF16 needs J exact in e4m3");
+            return SI_ERR_INVALID_ARG;
+        }
+        SI_CUDA_TRY(cudaMalloc(&x.J, (size_t)x.mpad * x.ldk * 2));
+        s = tc_convert_j(Jp, n, x.J, x.ldk, x.mpad, g->sms, g->stream);
+        if (s != SI_OK) { cleanup(); return s; }
+        SI_CUDA_TRY(cudaMalloc((void **)&x.q, sizeof(float) * (size_t)x.R * n));
+        SI_CUDA_TRY(cudaMalloc((void **)&x.p, sizeof(float) * (size_t)x.R * n));
+        SI_CUDA_TRY(cudaMalloc((void **)&x.spins, (size_t)x.R * n));
+        const size_t qb = 2ull * x.rpad_max * x.ldk * 2;
+        SI_CUDA_TRY(cudaMalloc((void **)&x.qop, qb));
+        SI_CUDA_TRY(cudaMemsetAsync(x.qop, 0, qb, g->stream));
+        // readout view for si_group_energy
+        Ctx &c = x.energy;
+        c.prm = prm[i];
+        c.stream = g->stream;
+        c.device = g->device;
+        c.num_sms = g->sms;
+        c.n = n;
+        c.R = x.R;
+        c.path = Path::TENSOR;
+        c.integer_j = !(flags & VF_NOT_INT8);
+        c.has_h = hp != nullptr;
+        c.integer_h = !(flags & VF_H_NOT_INT8);
+        c.s_upper = c.integer_j ? s_upper : 0;
+        c.ld8 = round_up(n, 16);
+        c.dJ = x.J;
+        c.ldk = x.ldk;
+        c.mpad = x.mpad;
+        SI_CUDA_TRY(cudaMalloc((void **)&x.h, sizeof(float) * n));
+        if (hp) SI_CUDA_TRY(cudaMemcpyAsync(x.h, hp, sizeof(float) * n, cudaMemcpyDeviceToDevice, g->stream));
+        else SI_CUDA_TRY(cudaMemsetAsync(x.h, 0, sizeof(float) * n, g->stream));
+        c.dhf = x.h;
+        if (c.integer_j) {
+            SI_CUDA_TRY(cudaMalloc((void **)&c.dJ8, (size_t)n * c.ld8));
+            s = convert_j8(&c, Jp);
+            if (s != SI_OK) { cleanup(); return s; }
+        }
+        if (c.has_h && c.integer_h) {
+            SI_CUDA_TRY(cudaMalloc((void **)&c.dh8, n));
+            s = h_to_int8(hp, n, c.dh8, g->stream);
+            if (s != SI_OK) { cleanup(); return s; }
+        }
+        SI_CUDA_TRY(cudaStreamSynchronize(g->stream));
+        if (!hp) {
+            cudaFree(x.h);
+            x.h = nullptr;
+            c.dhf = nullptr;
+        }
+        cleanup();
+    }
+    si_status sb = group_build_policies(g);
+    if (sb != SI_OK) return sb;
+    SI_CUDA_TRY(cudaMalloc((void **)&g->d_zeta, sizeof(float) * std::max(1, g->steps)));
+    SI_CUDA_TRY(cudaMalloc((void **)&g->d_dt, sizeof(float) * std::max(1, g->steps)));
+    SI_CUDA_TRY(cudaMalloc((void **)&g->d_err, sizeof(int)));
+    SI_CUDA_TRY(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream));
+    SI_CUDA_TRY(cudaFuncSetAttribute(k_group_step, cudaFuncAttributeMaxDynamicSharedMemorySize, GR_SMEM));
+    int per_sm = 0;
+    SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_step, GR_THREADS, GR_SMEM));
+    if (per_sm < 1) {
+        set_error("grouped step kernel does not fit on an SM");
+        return SI_ERR_UNSUPPORTED;
+    }
+    g->grid = per_sm * g->sms;
+    return group_apply_policy(g, 0);
+}
+
+}  // namespace si
+
+using namespace si;
+
+extern "C" {
+
+si_status si_create_group(si_group **out, int32_t count, const si_params *prm, const float *const *J,
+                          const float *const *h, void *stream) {
+    set_error("");
+    if (!out || count < 1 || !prm || !J) {
+        set_error("si_create_group: out, count >= 1, prm[count] and J[count] are required");
+        return SI_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+        const si_params &p = prm[i];
+        if (!J[i] || p.n < 1 || p.replicas < 1 || p.steps < 0) {
+            set_error("si_create_group: member " + std::to_string(i) + " needs J, n >= 1, replicas >= 1");
+            return SI_ERR_INVALID_ARG;
+        }
+        if (p.prec != SI_PREC_J_FP8_Q_BF16 && p.prec != SI_PREC_J_BF16_Q_BF16) {
+            set_error("si_create_group: members use the tensor-core precisions");
+            return SI_ERR_UNSUPPORTED;
+        }
+        if (p.steps != prm[0].steps || p.k != prm[0].k || p.m != prm[0].m || p.q0 != prm[0].q0 ||
+            p.q_max != prm[0].q_max || p.p_max != prm[0].p_max || p.update_order != prm[0].update_order ||
+            p.wall_zero_p != prm[0].wall_zero_p) {
+            set_error("si_create_group: steps and integrator parameters must be equal across members");
+            return SI_ERR_INVALID_ARG;
+        }
+        if (!(p.m > 0.f) || !(p.q_max > 0.f) || !(p.p_max > 0.f) || (p.update_order != 0 && p.update_order != 1)) {
+            set_error("si_create_group: need m, q_max, p_max > 0 and order 0 or 1");
+            return SI_ERR_INVALID_ARG;
+        }
+    }
+    Group *g = new (std::nothrow) Group();
+    if (!g) return SI_ERR_OOM;
+    g->count = count;
+    g->steps = prm[0].steps;
+    g->common = prm[0];
+    g->stream = (cudaStream_t)stream;
+    si_status s = group_create_impl(g, prm, J, h);
+    if (s != SI_OK) {
+        free_group(g);
+        return s;
+    }
+    *out = reinterpret_cast<si_group *>(g);
+    return SI_OK;
+}
+
+si_status si_run_group(si_group *grp, const float *zeta, const float *dt, const float *const *q_init,
+                       const float *const *p_init, float *const *q_out, float *const *p_out,
+                       int8_t *const *spins_out) {
+    set_error("");
+    Group *g = reinterpret_cast<Group *>(grp);
+    if (!g || !q_init || (g->steps > 0 && (!zeta || !dt))) {
+        set_error("si_run_group: group, q_init[count], zeta and dt are required");
+        return SI_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < g->count; ++i)
+        if (!q_init[i]) {
+            set_error("si_run_group: q_init[" + std::to_string(i) + "] is NULL");
+            return SI_ERR_INVALID_ARG;
+        }
+    g->launches = 0;
+    const int steps = g->steps;
+    if (steps > 0) {
+        SI_CUDA_TRY(cudaMemcpyAsync(g->d_zeta, zeta, sizeof(float) * steps,
+                                    is_device_ptr(zeta) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
+        SI_CUDA_TRY(cudaMemcpyAsync(g->d_dt, dt, sizeof(float) * steps,
+                                    is_device_ptr(dt) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
+    }
+    auto load_state = [&]() -> si_status {
+        for (int i = 0; i < g->count; ++i) {
+            GroupMember &x = g->m[i];
+            const size_t bytes = sizeof(float) * (size_t)x.R * x.n;
+            SI_CUDA_TRY(cudaMemcpyAsync(x.q, q_init[i], bytes, cudaMemcpyDefault, g->stream));
+            if (p_init && p_init[i]) SI_CUDA_TRY(cudaMemcpyAsync(x.p, p_init[i], bytes, cudaMemcpyDefault, g->stream));
+            else SI_CUDA_TRY(cudaMemsetAsync(x.p, 0, bytes, g->stream));
+        }
+        int maxnr = 1;
+        for (auto &x : g->m) maxnr = std::max(maxnr, x.R * x.n);
+        dim3 grid(std::min(64, cdiv(maxnr, 256)), g->count);
+        k_group_init<<<grid, 256, 0, g->stream>>>(g->d_inst);
+        SI_CUDA_TRY(cudaGetLastError());
+        g->launches += 1;
+        return SI_OK;
+    };
+    si_status s;
+    if (steps > 0) {
+        int cached = -1;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune_cache.find(group_key(g));
+            if (it != g_tune_cache.end()) cached = it->second;
+        }
+        if (cached < 0) {
+            // autotune once per group shape, on the real data as scratch state
+            if ((s = load_state()) != SI_OK) return s;
+            if ((s = group_autotune(g)) != SI_OK) return s;
+        } else if (g->policy != cached) {
+            if ((s = group_apply_policy(g, cached)) != SI_OK) return s;
+        }
+    }
+    if ((s = load_state()) != SI_OK) return s;
+    g->ev_valid = false;
+    if (steps > 0) {
+        if ((s = group_graph(g, steps)) != SI_OK) return s;
+        if (g->timing) SI_CUDA_TRY(cudaEventRecord(g->ev0, g->stream));
+        SI_CUDA_TRY(cudaGraphLaunch(g->graph, g->stream));
+        if (g->timing) {
+            SI_CUDA_TRY(cudaEventRecord(g->ev1, g->stream));
+            g->ev_valid = true;
+        }
+        g->launches += steps;
+    }
+    if ((s = group_check_err(g)) != SI_OK) return s;
+    for (int i = 0; i < g->count; ++i) {
+        GroupMember &x = g->m[i];
+        const size_t bytes = sizeof(float) * (size_t)x.R * x.n;
+        if (q_out && q_out[i]) SI_CUDA_TRY(cudaMemcpyAsync(q_out[i], x.q, bytes, cudaMemcpyDefault, g->stream));
+        if (p_out && p_out[i]) SI_CUDA_TRY(cudaMemcpyAsync(p_out[i], x.p, bytes, cudaMemcpyDefault, g->stream));
+        if (spins_out && spins_out[i]) {
+            if (steps == 0) {
+                set_error("si_run_group: spins need steps >= 1");
+                return SI_ERR_INVALID_ARG;
+            }
+            SI_CUDA_TRY(cudaMemcpyAsync(spins_out[i], x.spins, (size_t)x.R * x.n, cudaMemcpyDefault, g->stream));
+        }
+    }
+    SI_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    return SI_OK;
+}
+
+si_status si_group_energy(si_group *grp, int32_t index, const int8_t *spins, int32_t R, int32_t *energy_out,
+                          int32_t *cut_out, double *energy_f) {
+    Group *g = reinterpret_cast<Group *>(grp);
+    if (!g || index < 0 || index >= g->count) {
+        set_error("si_group_energy: bad group or index");
+        return SI_ERR_INVALID_ARG;
+    }
+    return si_energy(reinterpret_cast<si_ctx *>(&g->m[index].energy), spins, R, energy_out, cut_out, energy_f);
+}
+
+si_status si_group_enable_timing(si_group *grp, int32_t on) {
+    Group *g = reinterpret_cast<Group *>(grp);
+    if (!g) return SI_ERR_INVALID_ARG;
+    if (on && !g->ev0) {
+        SI_CUDA_TRY(cudaEventCreate(&g->ev0));
+        SI_CUDA_TRY(cudaEventCreate(&g->ev1));
+    }
+    g->timing = on != 0;
+    return SI_OK;
+}
+
+si_status si_group_last_kernel_time(const si_group *grp, float *ms) {
+    const Group *g = reinterpret_cast<const Group *>(grp);
+    if (!g || !ms || !g->ev_valid) {
+        set_error("si_group_last_kernel_time: no timed run");
+        return SI_ERR_INVALID_ARG;
+    }
+    SI_CUDA_TRY(cudaEventSynchronize(g->ev1));
+    SI_CUDA_TRY(cudaEventElapsedTime(ms, g->ev0, g->ev1));
+    return SI_OK;
+}
+
+si_status si_group_describe(const si_group *grp, char *buf, int32_t len) {
+    const Group *g = reinterpret_cast<const Group *>(grp);
+    if (!g || !buf || len <= 0) return SI_ERR_INVALID_ARG;
+    long long macs = 0, jbytes = 0;
+    for (const auto &x : g->m) {
+        const int bn = policy_bn(g->policy, x.R);
+        macs += (long long)x.n * x.n * x.R;
+        jbytes += (long long)x.mpad * x.ldk * 2 * cdiv(x.R, bn);
+    }
+    std::snprintf(buf, len, "grouped tcgen05 count=%d tiles=%d grid=%d policy=%s graph-steps=%d macs/step=%lld jbytes/step=%lld",
+                  g->count, g->ntiles, g->grid, g->policy >= 0 ? kPolicyName[g->policy] : "none", g->graph_steps,
+                  macs, jbytes);
+    return SI_OK;
+}
+
+int32_t si_group_last_launch_count(const si_group *grp) {
+    const Group *g = reinterpret_cast<const Group *>(grp);
+    return g ? g->launches : 0;
+}
+
+void si_destroy_group(si_group *grp) {
+    Group *g = reinterpret_cast<Group *>(grp);
+    if (!g) return;
+    cudaStreamSynchronize(g->stream);
+    free_group(g);
+}
+
+}  // extern "C"

@@ -117,6 +117,8 @@ si_status simt_spins(Ctx *c, int8_t *spins, int ld);
 si_status simt_init_state(Ctx *c, const float *q_init, const float *p_init);
 // int8 copy of J for the exact energy.
 si_status convert_j8(Ctx *c, const float *J_dev);
+// int8 copy of an integer-valued field.
+si_status h_to_int8(const float *h_dev, int n, int8_t *out, cudaStream_t st);
 // Copies the state of the current run into q_out / p_out (device, [R][n]).
 si_status simt_copy_state(Ctx *c, float *q_out, float *p_out);
 si_status simt_copy_state_f64(Ctx *c, double *q_out, double *p_out);
@@ -129,6 +131,12 @@ si_status tc_copy_state_f64(Ctx *c, double *q_out, double *p_out);
 si_status tc_init_state(Ctx *c, const float *q_init, const float *p_init);
 si_status tc_spins(Ctx *c, int8_t *spins, int ld);
 const char *tc_describe(const Ctx *c, char *buf, int len);
+// 2D bf16 tensor map with the 128-byte swizzle (inner dimension contiguous).
+si_status tc_make_map_bf16(CUtensorMap *m, void *base, int inner, int outer, int box_inner,
+                           int box_outer);
+// J (fp32 n x n) -> bf16 [mpad][ldk], zero padded.
+si_status tc_convert_j(const float *J_dev, int n, void *out, int ldk, int mpad, int sms,
+                       cudaStream_t st);
 
 // Adjoint, si_adjoint.cu.
 si_status adjoint_grad(Ctx *c, int steps, float *g_zeta, float *g_dt,

@@ -450,6 +450,16 @@ si_status convert_j8(Ctx *c, const float *J_dev) {
     return SI_OK;
 }
 
+__global__ void k_h_to_int8(const float *h, int n, int8_t *out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (int8_t)h[i];
+}
+
+si_status h_to_int8(const float *h_dev, int n, int8_t *out, cudaStream_t st) {
+    k_h_to_int8<<<std::min(1024, cdiv(n, 256)), 256, 0, st>>>(h_dev, n, out);
+    SI_CUDA_TRY(cudaGetLastError());
+    return SI_OK;
+}
+
 template <typename T>
 static si_status plain_launch(Ctx *c, int steps, int8_t *spins_dev) {
     PlainArgs<T> a;

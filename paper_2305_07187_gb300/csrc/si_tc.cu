@@ -24,7 +24,7 @@
 #include <algorithm>
 #include <cstdio>
 
-#include "si_device.cuh"
+#include "si_tcgen05.cuh"
 
 namespace si {
 
@@ -48,151 +48,6 @@ struct TcArgs {
     StepParams sp;
 };
 
-// ------------------------------------------------------------------ PTX glue
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase of `bar` with the given parity.  Returns false
-// (and raises the error word on timeout) if the run is being aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err,
-                                          volatile int *abort_flag, long long limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer_ns();
-    for (unsigned it = 1;; ++it) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 15u) == 0) {
-            if (*abort_flag || ld_volatile_int(err) != 0) {
-                *abort_flag = 1;
-                return false;
-            }
-            if ((long long)(globaltimer_ns() - t0) > limit_ns) {
-                atomicCAS(err, 0, DEV_TIMEOUT_MBAR);
-                *abort_flag = 1;
-                return false;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
-                                            int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
-        : "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async_global() {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor of a K-major bf16 tile whose rows are 128
-// bytes, written by TMA with the 128-byte swizzle: 8-row groups are 1024
-// bytes apart (stride byte offset), version 1, layout SWIZZLE_128B.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;               // leading byte offset (unused here)
-    d |= (uint64_t)(1024 >> 4) << 32;     // stride byte offset
-    d |= (uint64_t)1 << 46;               // descriptor version
-    d |= (uint64_t)2 << 61;               // SWIZZLE_128B
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D fp32, A bf16, B bf16, both K-major.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-        : "memory");
-}
-
-#define TC_REG32(a)                                                                          \
-    "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]),      \
-        "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]),           \
-        "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(a[16]), "=r"(a[17]), "=r"(a[18]),        \
-        "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]), "=r"(a[24]),        \
-        "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]),        \
-        "=r"(a[31])
-#define TC_IN32(a)                                                                             \
-    "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]),    \
-        "r"(a[8]), "r"(a[9]), "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]),      \
-        "r"(a[15]), "r"(a[16]), "r"(a[17]), "r"(a[18]), "r"(a[19]), "r"(a[20]), "r"(a[21]),    \
-        "r"(a[22]), "r"(a[23]), "r"(a[24]), "r"(a[25]), "r"(a[26]), "r"(a[27]), "r"(a[28]),    \
-        "r"(a[29]), "r"(a[30]), "r"(a[31])
-
-// 32 consecutive TMEM columns of this thread's lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : TC_REG32(v)
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-        "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
-        TC_IN32(v)
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_ld() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() {
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-
 // ------------------------------------------------------------------ kernel
 // Shared memory: S ring stages (J tile + q tile), the staging tile of the
 // next q (bf16, two 64-spin halves in the 128-byte swizzled layout that the
@@ -213,13 +68,6 @@ struct TcSmem {
 
 constexpr int TC_MMA_WARPS = 2;
 constexpr int TC_EPI_WARP0 = 1 + TC_MMA_WARPS;             // first epilogue warp
-
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y) {
-    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
-                     reinterpret_cast<uint64_t>(map)),
-                 "r"(src), "r"(x), "r"(y)
-                 : "memory");
-}
 
 template <int BN, int S>
 __global__ void __launch_bounds__(TC_THREADS, 1)
@@ -283,7 +131,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // rows and the warp polls all owners' flags in parallel only when the
         // next block's owner is not yet known to be ready.  J tiles do not
         // depend on the step and are issued before the wait.
-        uint32_t it = 0;
+        // Stages are split into two rings, the even stages consumed only by
+        // MMA warp 1 (even positions of the K loop) and the odd stages only by
+        // warp 2, so that every stage has one in-order consumer and no waiter
+        // can run two phases ahead of a stage's barrier.
+        constexpr int HS = S / 2;
+        static_assert(S % 2 == 0, "stage count must be even");
+        uint32_t cnt0 = 0u, cnt1 = 0u;   // stages armed in ring 0 / ring 1
         bool ok = true;
         const int kb0 = mt * (TC_BM / TC_BK);
         const unsigned *flags = a.bar + (size_t)rb * a.mtiles;
@@ -291,11 +145,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             uint32_t ready0 = 0u, ready1 = 0u;
             if (t == 0) ready0 = ready1 = 0xffffffffu;
             const int yb = (t & 1) * a.rpad + r0;
-            for (int j = 0; j < a.kblocks; ++j, ++it) {
+            for (int j = 0; j < a.kblocks; ++j) {
                 int kb = kb0 + j;
                 if (kb >= a.kblocks) kb -= a.kblocks;
-                const int s = it % S;
-                const uint32_t ph = (it / S) & 1u;
+                const int ring = j & 1;
+                const uint32_t c = ring ? cnt1 : cnt0;
+                const int s = 2 * (int)(c % HS) + ring;
+                const uint32_t ph = (c / HS) & 1u;
                 const uint32_t dA = sbase + s * L::STAGE_BYTES;
                 const uint32_t dB = dA + TC_A_BYTES;
                 int okw = 1;
@@ -308,6 +164,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 }
                 okw = __shfl_sync(0xffffffffu, okw, 0);
                 if (!okw) { ok = false; break; }
+                if (ring) ++cnt1; else ++cnt0;
                 const int mo = kb >> 1;
                 bool have = mo < 32 ? ((ready0 >> mo) & 1u) != 0u : ((ready1 >> (mo - 32)) & 1u) != 0u;
                 if (!have) {
@@ -339,18 +196,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 // The q tile is issued even on abort so that the stage's
                 // transaction count completes and the drain below ends.
                 if (lane == 0) tma_load_2d(dB, &mapB, full_bar(s), kb * TC_BK, yb);
-                if (!have) { ++it; ok = false; break; }
+                if (!have) { ok = false; break; }
             }
         }
         // Let every copy this warp issued land before the CTA exits.
         if (lane == 0) {
-            const uint32_t first = it > (uint32_t)S ? it - S : 0u;
-            for (uint32_t k = first; k < it; ++k) {
-                const unsigned long long t0 = globaltimer_ns();
-                while (!mbar_try_wait(full_bar(k % S), (k / S) & 1u)) {
-                    if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
-                        atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
-                        break;
+            for (int ring = 0; ring < 2; ++ring) {
+                const uint32_t cr = ring ? cnt1 : cnt0;
+                const uint32_t first = cr > (uint32_t)HS ? cr - HS : 0u;
+                for (uint32_t k = first; k < cr; ++k) {
+                    const unsigned long long t0 = globaltimer_ns();
+                    while (!mbar_try_wait(full_bar(2 * (int)(k % HS) + ring), (k / HS) & 1u)) {
+                        if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                            atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
+                            break;
+                        }
                     }
                 }
             }
@@ -365,16 +225,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int w = warp - 1;
             constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
             const uint32_t d_tmem = tmem + (w == 0 ? COL_ACC0 : COL_ACC1);
+            constexpr int HS = S / 2;
+            uint32_t c = 0;  // this warp's position in its ring of stages
             bool ok = true;
             for (int t = 0; t < a.steps && ok; ++t) {
                 if (t > 0) {
                     if (!mbar_wait(tmem_empty_bar, (uint32_t)((t - 1) & 1), a.err, abort_flag, a.limit_ns)) break;
                 }
                 tc_fence_after();
-                for (int j = w; j < a.kblocks; j += TC_MMA_WARPS) {
-                    const uint32_t it = (uint32_t)t * a.kblocks + j;
-                    const int s = it % S;
-                    const uint32_t ph = (it / S) & 1u;
+                for (int j = w; j < a.kblocks; j += TC_MMA_WARPS, ++c) {
+                    const int s = 2 * (int)(c % HS) + w;
+                    const uint32_t ph = (c / HS) & 1u;
                     if (!mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
                     tc_fence_after();
                     const uint64_t ad = sdesc_sw128(sbase + s * L::STAGE_BYTES);
@@ -548,8 +409,8 @@ static PFN_encodeTiled get_encode() {
     return fn;
 }
 
-static si_status make_map_bf16(CUtensorMap *m, void *base, int inner, int outer, int box_inner,
-                               int box_outer) {
+si_status tc_make_map_bf16(CUtensorMap *m, void *base, int inner, int outer, int box_inner,
+                          int box_outer) {
     PFN_encodeTiled enc = get_encode();
     if (!enc) {
         set_error("cuTensorMapEncodeTiled unavailable");
@@ -578,6 +439,13 @@ __global__ void k_convert_j_bf16(const float *J, int n, __nv_bfloat16 *out, int 
         const int i = (int)(e / ldk), j = (int)(e % ldk);
         out[e] = __float2bfloat16_rn((i < n && j < n) ? J[(size_t)i * n + j] : 0.f);
     }
+}
+
+si_status tc_convert_j(const float *J_dev, int n, void *out, int ldk, int mpad, int sms, cudaStream_t st) {
+    k_convert_j_bf16<<<std::min(8 * sms, cdiv((long long)mpad * ldk, 256)), 256, 0, st>>>(
+        J_dev, n, (__nv_bfloat16 *)out, ldk, mpad);
+    SI_CUDA_TRY(cudaGetLastError());
+    return SI_OK;
 }
 
 __global__ void k_tc_init(const float *q_init, const float *p_init, int n, int R, float *q_state,
@@ -712,9 +580,9 @@ si_status tc_prepare(Ctx *c, const float *J_dev) {
     SI_CUDA_TRY(cudaMemsetAsync(c->dqbuf, 0, c->qbuf_bytes, c->stream));
     SI_CUDA_TRY(cudaMalloc(&c->dq, sizeof(float) * (size_t)c->R * n));
     SI_CUDA_TRY(cudaMalloc(&c->dp, sizeof(float) * (size_t)c->R * n));
-    si_status s = make_map_bf16(&c->mapA, c->dJ, c->ldk, c->mpad, TC_BK, TC_BM);
+    si_status s = tc_make_map_bf16(&c->mapA, c->dJ, c->ldk, c->mpad, TC_BK, TC_BM);
     if (s != SI_OK) return s;
-    s = make_map_bf16(&c->mapB, c->dqbuf, c->ldk, 2 * c->rpad, TC_BK, c->tile_n);
+    s = tc_make_map_bf16(&c->mapB, c->dqbuf, c->ldk, 2 * c->rpad, TC_BK, c->tile_n);
     if (s != SI_OK) return s;
     const int mtiles = c->mpad / TC_BM;
     const int grid = mtiles * (c->rpad / c->tile_n);

@@ -128,3 +128,37 @@ def instance_coupling(spec: InstanceSpec) -> np.ndarray:
     if spec.kind == "pm1":
         return pm1_coupling(spec.n, spec.seed)
     return gauss_coupling_bf16(spec.n, spec.seed)
+
+
+# ---------------------------------------------------------------- on device
+# Seeded generators that draw directly on a CUDA device (torch's Philox
+# generator), for workloads whose couplings are too large to draw on the host
+# quickly.  Same distributions as the NumPy generators above, different
+# streams; tests that check these against the oracle copy the drawn J back.
+
+def pm1_coupling_torch(n: int, seed: int, device="cuda"):
+    import torch
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    u = torch.randint(0, 2, (n, n), generator=g, device=device, dtype=torch.int8)
+    J = (2 * u.to(torch.float32) - 1).triu(1)
+    return J + J.T
+
+
+def gauss_coupling_bf16_torch(n: int, seed: int, device="cuda"):
+    import torch
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    J = torch.randn((n, n), generator=g, device=device, dtype=torch.float32)
+    J = J.to(torch.bfloat16).to(torch.float32).triu(1)
+    return J + J.T
+
+
+def positions_torch(n: int, replicas: int, seed: int, device="cuda", lo=-0.1, hi=0.1):
+    import torch
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    return (lo + (hi - lo) * torch.rand((replicas, n), generator=g, device=device)).contiguous()
+
+
+def instance_coupling_torch(spec: InstanceSpec, device="cuda"):
+    if spec.kind == "pm1":
+        return pm1_coupling_torch(spec.n, spec.seed, device)
+    return gauss_coupling_bf16_torch(spec.n, spec.seed, device)

@@ -41,10 +41,30 @@ def teacher_forced(ctx1, J, h, zeta, dt, q, p, steps_to_check):
     return worst, q, p
 
 
+U32 = 2.0 ** -24
+
+
+def bf16_step_bound(J, q, p, zeta, dt, kw, bf16_term=True, h=None):
+    """Elementwise bound on |GPU - oracle| for one tensor-core step from the
+    same FP32 state: bf16 round-to-nearest of q in the force (2^-9 relative),
+    FP32 accumulation of n products (n 2^-24), a few FP32 roundings of the
+    update; the walls are 1-Lipschitz."""
+    J = np.asarray(J, np.float64)
+    n = J.shape[0]
+    S = np.abs(q) @ np.abs(J).T
+    eF = ((2.0 ** -9 if bf16_term else 0.0) + n * U32) * S
+    k, m, q0 = kw["k"], kw["m"], kw["q0"]
+    F = q @ J.T + (0.0 if h is None else np.asarray(h, np.float64))
+    pn = p + dt * (-k * (q - q0) + zeta * F)
+    ep = abs(zeta * dt) * eF + 8 * U32 * (np.abs(p) + np.abs(pn) + dt * (abs(k) * np.abs(q - q0) + abs(zeta) * np.abs(F)))
+    eq = (dt / m) * ep + 8 * U32 * (np.abs(q) + (dt / m) * np.abs(pn))
+    return eq, ep
+
+
 def random_spins(R, n, seed):
     g = np.random.Generator(np.random.PCG64(seed))
     return np.where(g.random((R, n)) < 0.5, -1, 1).astype(np.int8)
 
 
 __all__ = ["oracle", "inputs", "b", "SQ2F", "params_f64", "normwise_rel", "teacher_forced",
-           "random_spins"]
+           "random_spins", "bf16_step_bound"]

@@ -1,0 +1,101 @@
+"""GPU parity of the grouped batch path (si_create_group / si_run_group):
+many independent instances of uneven size in one launch per step."""
+import numpy as np
+import pytest
+
+from _helpers import b, bf16_step_bound, inputs, oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _members():
+    # (n, R, kind): ragged sizes, both tile widths, +-1 and Gaussian couplings
+    return [(17, 16, "pm1"), (128, 48, "gauss"), (300, 64, "pm1"), (513, 130, "gauss"),
+            (1000, 200, "pm1"), (64, 1, "pm1"), (257, 96, "gauss")]
+
+
+def _build(members, seed=0):
+    Js, hs, qs = [], [], []
+    for k, (n, R, kind) in enumerate(members):
+        J = inputs.pm1_coupling(n, seed=100 + k) if kind == "pm1" else inputs.gauss_coupling_bf16(n, seed=100 + k)
+        Js.append(J)
+        hs.append(inputs.field(n, seed=200 + k, scale=0.3) if kind == "gauss" else None)
+        qs.append(inputs.positions(n, R, seed0=1000 * (k + 1) + seed))
+    return Js, hs, qs
+
+
+def test_group_per_step_within_bf16_bound():
+    members = _members()
+    Js, hs, qs = _build(members)
+    ps = [np.zeros_like(q) for q in qs]
+    T = 8
+    zeta, dt = inputs.zeta_ramp(T, end=0.5), inputs.dt_const(T)
+    precs = ["j_fp8_q_bf16" if kind == "pm1" else "j_bf16_q_bf16" for (_, _, kind) in members]
+    with b.Group(Js, hs, replicas=[R for (_, R, _) in members], steps=1, precs=precs) as g:
+        assert "grouped" in g.describe()
+        p0 = b.default_params()
+        kw = dict(k=float(p0.k), m=float(p0.m), q0=float(p0.q0), q_max=float(np.float32(p0.q_max)),
+                  p_max=float(p0.p_max))
+        for t in range(T):
+            qg, pg, _ = g.run(zeta[t:t + 1], dt[t:t + 1], qs, ps)
+            for k, (n, R, kind) in enumerate(members):
+                qo, po = oracle.run(Js[k], hs[k], zeta[t:t + 1], dt[t:t + 1], qs[k], ps[k], **kw)
+                eq, ep = bf16_step_bound(Js[k], qs[k].astype(np.float64), ps[k].astype(np.float64),
+                                         float(zeta[t]), float(dt[t]), kw, h=hs[k])
+                assert (np.abs(qg[k] - qo) <= eq).all(), (t, k)
+                assert (np.abs(pg[k] - po) <= ep).all(), (t, k)
+            qs, ps = qg, pg
+
+
+def test_group_free_run_energies_and_determinism():
+    members = _members()
+    Js, hs, qs = _build(members, seed=5)
+    T = 60
+    zeta, dt = inputs.zeta_ramp(T), inputs.dt_const(T)
+    with b.Group(Js, hs, replicas=[R for (_, R, _) in members], steps=T) as g:
+        q1, p1, s1 = g.run(zeta, dt, qs)
+        q2, p2, s2 = g.run(zeta, dt, qs)
+        for k, (n, R, kind) in enumerate(members):
+            assert np.array_equal(q1[k], q2[k]) and np.array_equal(s1[k], s2[k])
+            assert np.abs(q1[k]).max() <= b.SQRT2_F32 and np.abs(p1[k]).max() <= 2.0
+            np.testing.assert_array_equal(s1[k], oracle.sign(q1[k]))
+            if kind == "pm1":
+                e, c, _ = g.energy(k, s1[k])
+                np.testing.assert_array_equal(e, oracle.energy(Js[k], None, s1[k]).astype(np.int64))
+                np.testing.assert_array_equal(c, oracle.cut(Js[k], s1[k]).astype(np.int64))
+            else:
+                _, _, f = g.energy(k, s1[k], exact=False)
+                ref = oracle.energy(Js[k], hs[k], s1[k])
+                bound = 1e-5 * (np.abs(Js[k]).sum() + np.abs(hs[k]).sum())
+                np.testing.assert_allclose(f, ref, rtol=0, atol=bound)
+
+
+def test_group_uneven_sample_of_the_batched_workload():
+    """A slice of the uneven batch (instances with n <= 3000 from the seeded
+    recipe), 30 steps: every member keeps its walls and exact energies."""
+    import torch
+    specs = [s for s in inputs.uneven_instances(256) if s.n <= 3000][:24]
+    Js = [inputs.instance_coupling_torch(s) for s in specs]
+    qs = [inputs.positions_torch(s.n, s.replicas, seed=9000 + s.index) for s in specs]
+    T = 30
+    zeta, dt = inputs.zeta_ramp(T), inputs.dt_const(T)
+    precs = ["j_fp8_q_bf16" if s.kind == "pm1" else "j_bf16_q_bf16" for s in specs]
+    with b.Group(Js, None, replicas=[s.replicas for s in specs], steps=T, precs=precs) as g:
+        sp = [torch.empty((s.replicas, s.n), dtype=torch.int8, device="cuda") for s in specs]
+        g.run_into(torch.from_numpy(zeta).cuda(), torch.from_numpy(dt).cuda(), qs, None, None, None, sp)
+        torch.cuda.synchronize()
+        for k in (0, 1, 2, 3):
+            s = sp[k].cpu().numpy()
+            Jh = Js[k].cpu().numpy()
+            if specs[k].kind == "pm1":
+                e, c, _ = g.energy(k, s)
+                np.testing.assert_array_equal(e, oracle.energy(Jh, None, s).astype(np.int64))
+            else:
+                _, _, f = g.energy(k, s, exact=False)
+                np.testing.assert_allclose(f, oracle.energy(Jh, None, s), rtol=0, atol=1e-5 * np.abs(Jh).sum())
+
+
+def test_group_rejects_mismatched_parameters():
+    J = inputs.pm1_coupling(32, seed=1)
+    with pytest.raises(b.SpringIsingError):
+        b.Group([J, J], replicas=[4, 4], steps=5, precs=["fp32", "fp32"])

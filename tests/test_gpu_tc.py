@@ -11,23 +11,13 @@ positions only the accumulation term remains.
 import numpy as np
 import pytest
 
-from _helpers import b, inputs, oracle, params_f64, random_spins
+from _helpers import b, bf16_step_bound, inputs, oracle, params_f64, random_spins
 
 pytestmark = pytest.mark.gpu
-U32 = 2.0 ** -24
 
 
-def _bound(J, q, p, zeta, dt, kw, bf16_term=True):
-    J = np.asarray(J, np.float64)
-    n = J.shape[0]
-    S = np.abs(q) @ np.abs(J).T                      # (R, n): sum_j |J_ij| |q_j|
-    eF = ((2.0 ** -9 if bf16_term else 0.0) + n * U32) * S
-    k, m, q0 = kw["k"], kw["m"], kw["q0"]
-    F = q @ J.T
-    pn = p + dt * (-k * (q - q0) + zeta * F)
-    ep = abs(zeta * dt) * eF + 8 * U32 * (np.abs(p) + np.abs(pn) + dt * (abs(k) * np.abs(q - q0) + abs(zeta) * np.abs(F)))
-    eq = (dt / m) * ep + 8 * U32 * (np.abs(q) + (dt / m) * np.abs(pn))
-    return eq, ep
+def _bound(J, q, p, zeta, dt, kw, bf16_term=True, h=None):
+    return bf16_step_bound(J, q, p, zeta, dt, kw, bf16_term=bf16_term, h=h)
 
 
 def _teacher_forced_tc(J, R, T, prec="j_fp8_q_bf16", bf16_exact=False, h=None, seed=5, tile_n=0):
@@ -45,7 +35,7 @@ def _teacher_forced_tc(J, R, T, prec="j_fp8_q_bf16", bf16_exact=False, h=None, s
             qg, pg, _ = ctx.run(zeta[t:t + 1], dt[t:t + 1], q, p)
             qo, po = oracle.run(J, h, zeta[t:t + 1], dt[t:t + 1], q, p, **kw)
             eq, ep = _bound(J, q.astype(np.float64), p.astype(np.float64), float(zeta[t]), float(dt[t]), kw,
-                            bf16_term=not bf16_exact)
+                            bf16_term=not bf16_exact, h=h)
             rq = np.abs(qg - qo) / np.maximum(eq, 1e-300)
             rp = np.abs(pg - po) / np.maximum(ep, 1e-300)
             worst = max(worst, rq.max(), rp.max())
