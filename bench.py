@@ -175,6 +175,77 @@ def run_reference(args):
     return 0
 
 
+def time_to_target(b, torch, dev, stream, seeds=10, every=10):
+    """Time-to-target-cut at N=2000 (+-1 complete graph, seed 1).
+
+    Target C*: median final cut of the plain FP32 path over 1000 replicas
+    (T=1000, linear zeta ramp, seeds 100..1099).  Batched path (tensor cores,
+    R=1024, the T=2000 schedule): wall time from the first launch to the first
+    readout (every `every` steps; exact int32 cuts of all replicas, readout
+    included) at which any replica reaches C*; the run is advanced segment by
+    segment from its own FP32 state.  Median over `seeds` initial-position
+    seeds.  FP32 plain (R=1): TTS99 = t_run ln(0.01)/ln(1 - p_s), p_s the
+    fraction of the 1000 FP32 replicas that reach C*."""
+    n = N_SPINS
+    J = inputs.pm1_coupling(n, seed=1)
+    T1 = 1000
+    z1, d1 = inputs.zeta_ramp(T1), inputs.dt_const(T1)
+    with b.Context(J, replicas=1000, steps=T1, prec="fp32", stream=stream.cuda_stream) as c1:
+        _, _, s1 = c1.run(z1, d1, inputs.positions(n, 1000, seed0=100))
+        _, cuts, _ = c1.energy(s1)
+    c_star = float(np.median(cuts))
+    p_s = float(np.mean(cuts >= c_star))
+    with b.Context(J, replicas=1, steps=T1, prec="fp32", stream=stream.cuda_stream) as cp:
+        q0 = inputs.positions(n, 1, seed0=100)
+        cp.run(z1, d1, q0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cp.run(z1, d1, q0)
+        e1.record(stream)
+        e1.synchronize()
+        t_run_fp32 = e0.elapsed_time(e1) * 1e-3
+    tts99 = t_run_fp32 * math.log(0.01) / math.log(max(1e-12, 1.0 - p_s)) if p_s < 1 else t_run_fp32
+    R = REPLICAS
+    zb = torch.from_numpy(inputs.zeta_ramp(T_STEPS)).to(dev)
+    db = torch.from_numpy(inputs.dt_const(T_STEPS)).to(dev)
+    ttts, hit_steps = [], []
+    with b.Context(J, replicas=R, steps=every, prec="j_fp8_q_bf16", stream=stream.cuda_stream) as cb:
+        qa = torch.empty((R, n), dtype=torch.float32, device=dev)
+        pa = torch.zeros_like(qa)
+        qb = torch.empty_like(qa)
+        pb = torch.empty_like(qa)
+        sp = torch.empty((R, n), dtype=torch.int8, device=dev)
+        cut_d = torch.empty(R, dtype=torch.int32, device=dev)
+        for seed in range(seeds + 1):
+            q_init = torch.from_numpy(inputs.positions(n, R, seed0=200000 + 4096 * seed)).to(dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            qa.copy_(q_init)
+            pa.zero_()
+            hit = None
+            for seg in range(T_STEPS // every):
+                sl = slice(seg * every, (seg + 1) * every)
+                cb.run_into(zb[sl], db[sl], qa, pa, qb, pb, sp)
+                cb.energy_into(sp, R, None, cut_d, None)
+                if int(cut_d.max().item()) >= c_star:
+                    hit = (seg + 1) * every
+                    break
+                qa, qb = qb, qa
+                pa, pb = pb, pa
+            el = time.perf_counter() - t0
+            if seed == 0:
+                continue          # warm-up
+            ttts.append(el if hit is not None else float("inf"))
+            hit_steps.append(hit)
+    ttt = float(np.median(ttts))
+    return {"target_cut": c_star, "target_from": "median final cut of the FP32 plain path, 1000 replicas, T=1000",
+            "batched_ttt_s": ttt, "batched_hit_steps_median": float(np.median([h or T_STEPS for h in hit_steps])),
+            "batched_seeds": seeds, "readout_every_steps": every,
+            "fp32_plain_tts99_s": tts99, "fp32_plain_run_s": t_run_fp32, "fp32_plain_p_success": p_s,
+            "speedup_vs_fp32_plain": (tts99 / ttt) if ttt > 0 else None}
+
+
 def smi_index(local):
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
     if cvd:
@@ -206,6 +277,28 @@ def ncu_case(args):
 
 
 GROUP_T = 1000
+
+
+def ncu_case_grouped(args):
+    """Profiling case of the grouped path: the first --group-count instances
+    of the uneven batch, autotuned, then one run of --time-steps steps."""
+    import torch
+
+    from paper_2305_07187_gb300 import _binding as b
+    dev = torch.device("cuda", 0)
+    specs = inputs.uneven_instances(256)[:args.group_count]
+    Js = [inputs.instance_coupling_torch(sp, dev) for sp in specs]
+    qs = [inputs.positions_torch(sp.n, sp.replicas, seed=9000 + sp.index, device=dev) for sp in specs]
+    precs = ["j_fp8_q_bf16" if sp.kind == "pm1" else "j_bf16_q_bf16" for sp in specs]
+    T = args.time_steps
+    zeta = torch.from_numpy(inputs.zeta_ramp(T)).to(dev)
+    dt = torch.from_numpy(inputs.dt_const(T)).to(dev)
+    with b.Group(Js, None, replicas=[sp.replicas for sp in specs], steps=T, precs=precs) as g:
+        del Js
+        g.run_into(zeta, dt, qs)
+        torch.cuda.synchronize()
+        print(g.describe())
+    return 0
 
 
 def run_grouped(args):
@@ -289,11 +382,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-target-cut measurement")
     ap.add_argument("--tile-n", type=int, default=0)
     ap.add_argument("--ncu-case", action="store_true",
                     help="profiling case: one warm-up and one si_run of the batched "
                          "workload with --time-steps steps, no timing output")
     ap.add_argument("--time-steps", type=int, default=T_STEPS)
+    ap.add_argument("--group-count", type=int, default=256,
+                    help="grouped workload: number of instances (profiling uses a prefix)")
     ap.add_argument("--workload", default="batched", choices=["batched", "grouped"],
                     help="batched: N=2000, R=1024, T=2000 (default); grouped: 256 uneven "
                          "instances, T=1000, one grouped launch per step")
@@ -304,6 +400,8 @@ def main():
     if not os.path.exists(b.LIB_PATH):
         from paper_2305_07187_gb300 import build as _build
         _build.build()
+    if args.ncu_case and args.workload == "grouped":
+        return ncu_case_grouped(args)
     if args.ncu_case:
         return ncu_case(args)
     if args.workload == "grouped":
@@ -441,6 +539,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if rank == 0 and world == 1 and not args.no_ttt:
+        line["ttt"] = time_to_target(b, torch, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     ctx.close()
