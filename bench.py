@@ -49,6 +49,25 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def replica_seed0(rank):
+    """First per-replica seed of a rank: ranks draw disjoint replica seeds."""
+    return 100 + rank * REPLICAS
+
+
+def max_over_ranks(value, dist=None, device="cpu"):
+    """Maximum of a per-rank scalar over all ranks (timing only, no data)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank, world, ms_max):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 def load_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -421,7 +440,7 @@ def main():
     J = inputs.pm1_coupling(N_SPINS, seed=1)
     zeta = inputs.zeta_ramp(T_STEPS)
     dt = inputs.dt_const(T_STEPS)
-    q0 = inputs.positions(N_SPINS, REPLICAS, seed0=100 + rank * REPLICAS)
+    q0 = inputs.positions(N_SPINS, REPLICAS, seed0=replica_seed0(rank))
     ctx = b.Context(J, replicas=REPLICAS, steps=T_STEPS, prec="j_fp8_q_bf16",
                     stream=stream.cuda_stream, tile_n=args.tile_n)
     desc = ctx.describe()
@@ -469,10 +488,7 @@ def main():
     if world > 1:
         dist.barrier()
     ms = sum(step_ms) / len(step_ms)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, dist, dev)
 
     # end to end through the C ABI with host buffers (copies inside the region)
     q_h = torch.from_numpy(q0).pin_memory()
@@ -491,16 +507,13 @@ def main():
         el = (time.perf_counter() - t0) * 1e3
         if it > 0:
             e2e_ms.append(el)
-    t2 = torch.tensor([sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t2, op=dist.ReduceOp.MAX)
-    e2e_max = float(t2.item())
+    e2e_max = max_over_ranks(sum(e2e_ms) / len(e2e_ms), dist, dev)
     # results agree between the two paths (same inputs, deterministic kernels)
     assert torch.equal(s_h, s_d.cpu()) and torch.equal(e_h, e_d.cpu())
 
     units = REPLICAS * N_SPINS * T_STEPS
-    value = world * units / (ms_max * 1e-3)
-    e2e_value = world * units / (e2e_max * 1e-3)
+    value = whole_job_value(units, world, ms_max)
+    e2e_value = whole_job_value(units, world, e2e_max)
     peaks, peak_src = load_peaks()
     flops = 2.0 * N_SPINS * N_SPINS * REPLICAS * T_STEPS
     k_avg = sum(kern_ms) / len(kern_ms)
