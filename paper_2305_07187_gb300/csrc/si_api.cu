@@ -102,7 +102,7 @@ static void free_ctx(Ctx *c) {
     if (!c) return;
     void *ptrs[] = {c->dJ, c->dJ8, c->dh, c->dhf, c->dh8, c->dq, c->dp, c->dqbuf,
                     c->dzeta, c->ddt, c->dbar, c->derr, c->dspins, c->dspins_in,
-                    c->dE, c->dC, c->dEf, c->dstage, c->g_ws};
+                    c->dE, c->dC, c->dEf, c->dstage, c->g_ws, c->e_sig, c->e_sum};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -438,6 +438,7 @@ si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy
     if ((s = stage_out(fo, energy_f, sizeof(double) * R)) != SI_OK) return s;
     s = simt_energy(c, c->dspins_in, R, c->ld8, (int32_t *)eo.ptr, (int32_t *)co.ptr, (double *)fo.ptr);
     if (s != SI_OK) return s;
+    if (c->derr && (s = check_device_error(c)) != SI_OK) return s;
     if ((s = finish_out(eo, c->stream)) != SI_OK) return s;
     if ((s = finish_out(co, c->stream)) != SI_OK) return s;
     if ((s = finish_out(fo, c->stream)) != SI_OK) return s;

@@ -36,9 +36,9 @@ __device__ __forceinline__ bool wait_counter_geq(const unsigned *ctr, unsigned t
         unsigned v = ld_acquire_gpu(ctr);
         if ((int)(v - target) >= 0) return true;
         if ((it & 31u) == 0) {
-            if (ld_volatile_int(err) != 0) return false;
+            if (err && ld_volatile_int(err) != 0) return false;
             if ((long long)(globaltimer_ns() - t0) > limit_ns) {
-                atomicCAS(err, 0, DEV_TIMEOUT_BARRIER);
+                if (err) atomicCAS(err, 0, DEV_TIMEOUT_BARRIER);
                 return false;
             }
         }

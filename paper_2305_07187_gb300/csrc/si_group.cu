@@ -505,7 +505,8 @@ static si_status group_autotune(Group *g) {
 static void free_group(Group *g) {
     if (!g) return;
     for (auto &x : g->m) {
-        void *ptrs[] = {x.J, x.h, x.q, x.p, x.qop, x.spins, x.energy.dJ8, x.energy.dh8, x.energy.dspins_in};
+        void *ptrs[] = {x.J, x.h, x.q, x.p, x.qop, x.spins, x.energy.dJ8, x.energy.dh8, x.energy.dspins_in,
+                        x.energy.e_sig, x.energy.e_sum};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
@@ -625,6 +626,10 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
     SI_CUDA_TRY(cudaMalloc((void **)&g->d_dt, sizeof(float) * std::max(1, g->steps)));
     SI_CUDA_TRY(cudaMalloc((void **)&g->d_err, sizeof(int)));
     SI_CUDA_TRY(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream));
+    for (auto &x : g->m) {            // readout views share the group's error word
+        x.energy.derr = g->d_err;
+        x.energy.spin_limit_ns = g->limit_ns;
+    }
     SI_CUDA_TRY(cudaFuncSetAttribute(k_group_step, cudaFuncAttributeMaxDynamicSharedMemorySize, GR_SMEM));
     int per_sm = 0;
     SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_step, GR_THREADS, GR_SMEM));

@@ -94,6 +94,12 @@ struct Ctx {
     int rpad = 0;                        // R rounded up to tile_n
     CUtensorMap mapA, mapB;              // J tiles, q operand tiles
 
+    // Tensor-core energy readout workspace (allocated lazily).
+    void *e_sig = nullptr;               // bf16 spin operand
+    size_t e_sig_bytes = 0;
+    unsigned long long *e_sum = nullptr; // per-replica sigma^T J sigma
+    int e_sum_cap = 0;
+
     // Gradient workspace (allocated lazily by si_grad).
     void *g_ws = nullptr;
     size_t g_ws_bytes = 0;
@@ -130,6 +136,9 @@ si_status tc_copy_state(Ctx *c, float *q_out, float *p_out);
 si_status tc_copy_state_f64(Ctx *c, double *q_out, double *p_out);
 si_status tc_init_state(Ctx *c, const float *q_init, const float *p_init);
 si_status tc_spins(Ctx *c, int8_t *spins, int ld);
+// Exact energy/cut on the tensor cores (integer J, tensor-path contexts);
+// SI_ERR_UNSUPPORTED when it does not apply.
+si_status tc_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E, int32_t *C);
 const char *tc_describe(const Ctx *c, char *buf, int len);
 // 2D bf16 tensor map with the 128-byte swizzle (inner dimension contiguous).
 si_status tc_make_map_bf16(CUtensorMap *m, void *base, int inner, int outer, int box_inner,

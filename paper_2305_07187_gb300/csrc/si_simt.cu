@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 
 #include "si_device.cuh"
 
@@ -587,7 +588,11 @@ si_status simt_spins(Ctx *c, int8_t *spins, int ld) {
 
 si_status simt_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E, int32_t *C,
                       double *Ef) {
-    if (E || C) {
+    si_status st_tc = SI_ERR_UNSUPPORTED;
+    if ((E || C) && c->path == Path::TENSOR && !std::getenv("SI_ENERGY_DP4A"))
+        st_tc = tc_energy(c, spins_dev, R, ld, E, C);
+    if (st_tc != SI_OK && st_tc != SI_ERR_UNSUPPORTED) return st_tc;
+    if ((E || C) && st_tc != SI_OK) {
         const size_t smem = (size_t)EN_RB * c->ld8;
         if (smem > 200 * 1024) {
             set_error("exact energy: n too large for the shared-memory spin tile");

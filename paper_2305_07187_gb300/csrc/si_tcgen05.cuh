@@ -45,12 +45,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *er
     for (unsigned it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 15u) == 0) {
-            if (*abort_flag || ld_volatile_int(err) != 0) {
+            if (*abort_flag || (err && ld_volatile_int(err) != 0)) {
                 *abort_flag = 1;
                 return false;
             }
             if ((long long)(globaltimer_ns() - t0) > limit_ns) {
-                atomicCAS(err, 0, DEV_TIMEOUT_MBAR);
+                if (err) atomicCAS(err, 0, DEV_TIMEOUT_MBAR);
                 *abort_flag = 1;
                 return false;
             }

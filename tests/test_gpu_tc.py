@@ -123,3 +123,22 @@ def test_tc_energy_of_random_spins():
         e, c, f = ctx.energy(s)
     np.testing.assert_array_equal(e, oracle.energy(J, None, s).astype(np.int64))
     np.testing.assert_array_equal(c, oracle.cut(J, s).astype(np.int64))
+
+
+@pytest.mark.parametrize("n,R", [(17, 1), (300, 100), (2000, 1024), (3001, 130)])
+def test_tensor_core_energy_readout_exact(n, R, monkeypatch):
+    """Tensor-path contexts compute the exact energy on the tensor cores
+    (sigma and integer J exact in bf16, integer sums below 2^24); it must
+    equal the oracle and the dp4a readout bit for bit."""
+    J = inputs.pm1_coupling(n, seed=n) * 3
+    h = np.round(inputs.field(n, seed=n + 1) * 10).astype(np.float32)
+    s = random_spins(R, n, seed=n + 2)
+    with b.Context(J, h, replicas=1, steps=1, prec="j_bf16_q_bf16") as ctx:
+        e, c, _ = ctx.energy(s)
+        monkeypatch.setenv("SI_ENERGY_DP4A", "1")
+        e2, c2, _ = ctx.energy(s)
+        monkeypatch.delenv("SI_ENERGY_DP4A")
+    np.testing.assert_array_equal(e, oracle.energy(J, h, s).astype(np.int64))
+    np.testing.assert_array_equal(c, oracle.cut(J, s).astype(np.int64))
+    np.testing.assert_array_equal(e, e2)
+    np.testing.assert_array_equal(c, c2)
