@@ -296,6 +296,94 @@ def ncu_case(args):
 
 
 GROUP_T = 1000
+SCALE_N, SCALE_R, SCALE_T, SCALE_EVERY = 32768, 512, 5000, 100
+
+
+def run_scale(args):
+    """Scale workload: N=32768 +-1 complete graph (J e4m3-exact, 1 GiB as
+    e4m3), R=512, T=5000, exact int32 energy of all replicas every 100 steps.
+    Runs as a one-member group (J streamed from HBM every step) in segments
+    of 100 steps resumed from the FP32 state, with the tensor-core readout in
+    between.  The FP32 plain path on the same GPU is timed on 3 steps and
+    extrapolated to T (stated in the line)."""
+    import torch
+
+    from paper_2305_07187_gb300 import _binding as b
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    n, R, T, every = SCALE_N, SCALE_R, SCALE_T, SCALE_EVERY
+    J = inputs.pm1_coupling_torch(n, seed=11, device=dev)
+    q0 = inputs.positions_torch(n, R, seed=12, device=dev)
+    zeta = torch.from_numpy(inputs.zeta_ramp(T)).to(dev)
+    dt = torch.from_numpy(inputs.dt_const(T)).to(dev)
+    g = b.Group([J], None, replicas=[R], steps=every, precs=["j_fp8_q_bf16"], stream=stream.cuda_stream)
+    qa, pa = q0.clone(), torch.zeros_like(q0)
+    qb, pb = torch.empty_like(q0), torch.empty_like(q0)
+    sp = torch.empty((R, n), dtype=torch.int8, device=dev)
+    g.enable_timing(True)
+
+    def one_run():
+        nonlocal qa, pa, qb, pb
+        qa.copy_(q0)
+        pa.zero_()
+        best = None
+        kern = 0.0
+        for seg in range(T // every):
+            sl = slice(seg * every, (seg + 1) * every)
+            g.run_into(zeta[sl], dt[sl], [qa], [pa], [qb], [pb], [sp])
+            kern += g.last_kernel_ms()
+            e, c, _ = g.energy(0, sp)
+            best = int(c.max()) if best is None else max(best, int(c.max()))
+            qa, qb = qb, qa
+            pa, pb = pb, pa
+        return kern, best
+
+    one_run()                                   # warm-up (autotune, graph capture)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(smi_index(0))
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    kern_ms, best_cut = one_run()
+    e1.record(stream)
+    e1.synchronize()
+    run_ms = e0.elapsed_time(e1)
+    clocks = sampler.stop()
+    desc = g.describe()
+    g.close()
+    # FP32 plain path on the same GPU, 3 steps, extrapolated to T
+    Jc = J.cpu().numpy()
+    del J
+    torch.cuda.empty_cache()
+    with b.Context(Jc, replicas=R, steps=3, prec="fp32", stream=stream.cuda_stream) as cf:
+        cf.enable_timing(True)
+        qh = q0.cpu().numpy()
+        cf.run(np.zeros(3, np.float32) + 0.04, np.full(3, 0.2, np.float32), qh)
+        cf.run(np.zeros(3, np.float32) + 0.04, np.full(3, 0.2, np.float32), qh)
+        fp32_ms_step = cf.last_kernel_ms() / 3
+    flops = 2.0 * n * n * R * T
+    peaks, src = load_peaks()
+    peak = float(peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS))
+    achieved = flops / (kern_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": R * n * T / (run_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": run_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "N=32768 +-1 complete graph (J e4m3-exact, bf16 working copy 2 GiB), R=512, "
+                               "T=5000, linear zeta ramp, exact int32 energy+cut of all replicas every 100 steps",
+                   "kernel": desc, "best_cut": best_cut},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_group_step (one member)",
+                     "kernel_ms": kern_ms, "peak_source": "%s bf16_tflops (burst)" % src},
+        "fp32_plain": {"ms_per_step": fp32_ms_step, "extrapolated_run_ms": fp32_ms_step * T,
+                       "note": "k_tiled_step (CUDA cores), 3 steps timed, extrapolated to T=5000",
+                       "speedup": fp32_ms_step * T / run_ms},
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    return 0
 
 
 def ncu_case_grouped(args):
@@ -409,7 +497,7 @@ def main():
     ap.add_argument("--time-steps", type=int, default=T_STEPS)
     ap.add_argument("--group-count", type=int, default=256,
                     help="grouped workload: number of instances (profiling uses a prefix)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "grouped"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "grouped", "scale"],
                     help="batched: N=2000, R=1024, T=2000 (default); grouped: 256 uneven "
                          "instances, T=1000, one grouped launch per step")
     args = ap.parse_args()
@@ -425,6 +513,8 @@ def main():
         return ncu_case(args)
     if args.workload == "grouped":
         return run_grouped(args)
+    if args.workload == "scale":
+        return run_scale(args)
 
     import torch
     import torch.distributed as dist

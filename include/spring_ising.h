@@ -133,7 +133,8 @@ si_status si_get_state(si_ctx *ctx, double *q_out, double *p_out);
  *              |J_ij|, |h_i| <= 127 (else SI_ERR_UNSUPPORTED); or NULL
  *   cut_out    [R] exact int32 cut of the MAX-CUT instance with weights
  *              w_ij = -J_ij (same integrality requirement); or NULL
- *   energy_f   [R] energy for any J, computed in FP32 and stored as double;
+ *   energy_f   [R] energy as double for any J; exact (the integer energy)
+ *              when J and h are integer-valued, else computed in FP32;
  *              or NULL
  * R may differ from the context's replica count.
  */

@@ -400,13 +400,14 @@ class Group:
         return qs, ps, ss
 
     def energy(self, index, spins, exact=True):
+        """si_group_energy for member `index`; spins may be NumPy or a torch tensor."""
         n = self.ns[index]
-        s = np.ascontiguousarray(spins, dtype=np.int8)
-        R = s.size // n
+        s = spins if _is_torch(spins) else np.ascontiguousarray(spins, dtype=np.int8)
+        R = (int(s.numel()) if _is_torch(s) else s.size) // n
         e = np.empty(R, np.int32) if exact else None
         cc = np.empty(R, np.int32) if exact else None
         f = np.empty(R, np.float64)
+        sa = _Arg(s, np.int8, R * n)
         ea, ca, fa = _Arg(e, np.int32, R, True), _Arg(cc, np.int32, R, True), _Arg(f, np.float64, R, True)
-        _check(load().si_group_energy(self.g, int(index), s.ctypes.data_as(ctypes.c_void_p), R, ea.ptr,
-                                      ca.ptr, fa.ptr))
+        _check(load().si_group_energy(self.g, int(index), sa.ptr, R, ea.ptr, ca.ptr, fa.ptr))
         return e, cc, f

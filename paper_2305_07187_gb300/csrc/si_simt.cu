@@ -586,13 +586,31 @@ si_status simt_spins(Ctx *c, int8_t *spins, int ld) {
     return SI_OK;
 }
 
+__global__ void k_energy_int_to_f(const int32_t *E, int R, double *Ef) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) Ef[r] = (double)E[r];
+}
+
 si_status simt_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E, int32_t *C,
                       double *Ef) {
+    // With integer J and integer (or no) field the energy is an exact integer:
+    // the floating-point request is served from the exact readout.
+    const bool exact_ok = c->integer_j && (!c->has_h || c->integer_h);
+    int32_t *Euse = E;
+    if (Ef && exact_ok && !E) {
+        if (R > c->e_cap) {
+            if (c->dE) cudaFree(c->dE);
+            c->dE = nullptr;
+            c->e_cap = 0;
+            SI_CUDA_TRY(cudaMalloc((void **)&c->dE, sizeof(int32_t) * R));
+            c->e_cap = R;
+        }
+        Euse = c->dE;
+    }
     si_status st_tc = SI_ERR_UNSUPPORTED;
-    if ((E || C) && c->path == Path::TENSOR && !std::getenv("SI_ENERGY_DP4A"))
-        st_tc = tc_energy(c, spins_dev, R, ld, E, C);
+    if ((Euse || C) && c->path == Path::TENSOR && !std::getenv("SI_ENERGY_DP4A"))
+        st_tc = tc_energy(c, spins_dev, R, ld, Euse, C);
     if (st_tc != SI_OK && st_tc != SI_ERR_UNSUPPORTED) return st_tc;
-    if ((E || C) && st_tc != SI_OK) {
+    if ((Euse || C) && st_tc != SI_OK) {
         const size_t smem = (size_t)EN_RB * c->ld8;
         if (smem > 200 * 1024) {
             set_error("exact energy: n too large for the shared-memory spin tile");
@@ -600,11 +618,15 @@ si_status simt_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E
         }
         SI_CUDA_TRY(cudaFuncSetAttribute(k_energy_i8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_energy_i8<<<cdiv(R, EN_RB), EN_THREADS, smem, c->stream>>>(
-            c->dJ8, c->ld8, c->dh8, c->n, R, spins_dev, ld, c->s_upper, E, C);
+            c->dJ8, c->ld8, c->dh8, c->n, R, spins_dev, ld, c->s_upper, Euse, C);
         SI_CUDA_TRY(cudaGetLastError());
         c->launches += 1;
     }
-    if (Ef) {
+    if (Ef && exact_ok) {
+        k_energy_int_to_f<<<cdiv(R, 256), 256, 0, c->stream>>>(Euse, R, Ef);
+        SI_CUDA_TRY(cudaGetLastError());
+        c->launches += 1;
+    } else if (Ef) {
         const float *hf = c->dhf;
         if (c->path == Path::TENSOR) {
             k_energy_f<__nv_bfloat16><<<R, EN_THREADS, 0, c->stream>>>(
