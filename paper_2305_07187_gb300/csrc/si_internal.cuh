@@ -54,6 +54,11 @@ struct Ctx {
     bool has_h = false;
     long long s_upper = 0;       // sum_{i<j} J_ij (integer J only)
     long long spin_limit_ns = 2000000000LL;
+    // Failure-detection test hook: at this step the inter-CTA wait targets a
+    // count that no CTA will ever reach, so the bounded wait must run out and
+    // the call must return SI_ERR_TIMEOUT (-1: off).  Set from
+    // SI_DEBUG_STALL_STEP at creation.
+    int stall_step = -1;
 
     // Storage of J.  FP32/FP64 paths: [n][ldj] in the state precision.
     // Tensor path: bf16 [mpad][ldk], zero padded.

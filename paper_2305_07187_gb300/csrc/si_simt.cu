@@ -41,6 +41,7 @@ struct PlainArgs {
     StepParams sp;
     int rows_per_block;
     int j_resident;
+    int stall_step;        // failure-detection test hook (-1: off)
 };
 
 template <typename T>
@@ -119,7 +120,8 @@ __global__ void __launch_bounds__(PLAIN_THREADS, 1) k_plain(PlainArgs<T> a) {
                 }
             }
         }
-        if (!grid_barrier(a.bar, (unsigned)(t + 1) * gridDim.x, a.err, a.limit_ns)) break;
+        const unsigned target = (unsigned)(t + 1) * gridDim.x + (t == a.stall_step ? 1u : 0u);
+        if (!grid_barrier(a.bar, target, a.err, a.limit_ns)) break;
     }
 }
 
@@ -479,6 +481,7 @@ static si_status plain_launch(Ctx *c, int steps, int8_t *spins_dev) {
     a.bar = c->dbar;
     a.err = c->derr;
     a.limit_ns = c->spin_limit_ns;
+    a.stall_step = c->stall_step;
     a.sp = StepParams{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max,
                       c->prm.update_order, c->prm.wall_zero_p};
     int max_smem = 0;

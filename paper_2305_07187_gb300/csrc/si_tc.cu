@@ -30,7 +30,9 @@ namespace si {
 
 constexpr int TC_BM = 128;       // spins per CTA (MMA M)
 constexpr int TC_BK = 64;        // K elements per stage (128 bytes of bf16)
-constexpr int TC_THREADS = 352;  // 11 warps: producer, 2 MMA issuers, 8 epilogue
+// Threads: producer warp, 2 MMA-issuing warps, EPI epilogue warps (4 or 8).
+template <int EPI>
+constexpr int tc_threads() { return 32 * (3 + EPI); }
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;
 
 struct TcArgs {
@@ -42,10 +44,12 @@ struct TcArgs {
     __nv_bfloat16 *qop;          // [2][rpad][ldk] bf16 operand of step t in plane t&1
     int8_t *spins;               // [R][lds] or null
     int lds;
-    unsigned *bar;               // [rblocks]
+    unsigned *bar;               // [rblocks * mtiles] published-step flags
     int *err;
     long long limit_ns;
     StepParams sp;
+    int stall_step;              // failure-detection test hook (-1: off)
+    int smem_bytes;              // dynamic shared memory the launch provides
 };
 
 // ------------------------------------------------------------------ kernel
@@ -69,14 +73,23 @@ struct TcSmem {
 constexpr int TC_MMA_WARPS = 2;
 constexpr int TC_EPI_WARP0 = 1 + TC_MMA_WARPS;             // first epilogue warp
 
-template <int BN, int S>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+// EPI: epilogue warps (8 in both tile instantiations; a CTA that allocates
+// tensor memory occupies its SM alone, so a lighter CTA buys no second CTA).
+template <int BN, int S, int EPI>
+__global__ void __launch_bounds__(tc_threads<EPI>(), EPI == 4 ? 2 : 1)
     k_tc_run(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
              TcArgs a) {
     using L = TcSmem<BN, S>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    // The 128-byte swizzled tiles need a 1024-aligned base; the launch provides
+    // only a little slack, so check that the aligned layout fits before
+    // touching any barrier or TMEM (uniform for the whole CTA).
+    if ((int)(smem - smem_raw) + L::TOTAL > a.smem_bytes) {
+        if (threadIdx.x == 0) atomicCAS(a.err, 0, DEV_BAD_CONFIG);
+        return;
+    }
     const uint32_t sbase = smem_u32(smem);
     const uint32_t stage_q = sbase + L::STAGING;
     const uint32_t bar0 = sbase + L::BARS;
@@ -101,8 +114,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(empty_bar(s), 1);
         }
         mbar_init(accf_bar, TC_MMA_WARPS);
-        mbar_init(tmem_empty_bar, 8);
-        mbar_init(epi_done_bar, 8);
+        mbar_init(tmem_empty_bar, EPI);
+        mbar_init(epi_done_bar, EPI);
         mbar_init(drain_bar, TC_MMA_WARPS);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -113,7 +126,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"((uint32_t)L::TMEM_COLS)
+                     "n"(L::TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -171,8 +184,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const unsigned long long t0 = globaltimer_ns();
                     for (unsigned pit = 1;; ++pit) {
                         bool r_lo = false, r_hi = false;
-                        if (lane < a.mtiles) r_lo = (int)(ld_acquire_gpu(flags + lane) - (unsigned)t) >= 0;
-                        if (lane + 32 < a.mtiles) r_hi = (int)(ld_acquire_gpu(flags + lane + 32) - (unsigned)t) >= 0;
+                        const unsigned need = (unsigned)t + (t == a.stall_step ? 1000000u : 0u);
+                        if (lane < a.mtiles) r_lo = (int)(ld_acquire_gpu(flags + lane) - need) >= 0;
+                        if (lane + 32 < a.mtiles) r_hi = (int)(ld_acquire_gpu(flags + lane + 32) - need) >= 0;
                         ready0 |= __ballot_sync(0xffffffffu, r_lo);
                         ready1 |= __ballot_sync(0xffffffffu, r_hi);
                         have = mo < 32 ? ((ready0 >> mo) & 1u) != 0u : ((ready1 >> (mo - 32)) & 1u) != 0u;
@@ -263,7 +277,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // half (w-3)/4 of the replica columns.
         const int quad = warp & 3;
         const int half = (warp - TC_EPI_WARP0) >> 2;
-        constexpr int CPH = BN / 64;                // 32-column chunks per half
+        constexpr int CPH = BN / 32 / (EPI / 4);    // 32-column chunks per warp
         const int c_begin = half * CPH;
         const int row = quad * 32 + lane;
         const int i = m0 + row;
@@ -385,7 +399,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_fence_after();
     if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"((uint32_t)L::TMEM_COLS)
+                     "n"(L::TMEM_COLS)
                      : "memory");
     }
 }
@@ -480,7 +494,7 @@ __global__ void k_tc_spins(const float *q_state, int n, int R, int8_t *spins, in
     }
 }
 
-template <int BN, int S>
+template <int BN, int S, int EPI>
 static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
     using L = TcSmem<BN, S>;
     TcArgs a;
@@ -503,6 +517,7 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
     a.bar = c->dbar;
     a.err = c->derr;
     a.limit_ns = c->spin_limit_ns;
+    a.stall_step = c->stall_step;
     a.sp = StepParams{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max,
                       c->prm.update_order, c->prm.wall_zero_p};
     const int grid = a.mtiles * a.rblocks;
@@ -510,17 +525,20 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
         set_error("tensor path: too many tiles for the step flags (n <= 8192 per context)");
         return SI_ERR_UNSUPPORTED;
     }
-    const int smem = L::TOTAL + 1024;
-    SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int smem = L::TOTAL + (EPI == 4 ? 256 : 1024);
+    a.smem_bytes = smem;
+    SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S, EPI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
     int per_sm = 0;
-    SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_run<BN, S>, TC_THREADS, smem));
+    SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_run<BN, S, EPI>, tc_threads<EPI>(), smem));
     if (per_sm * c->num_sms < grid) {
         set_error("tensor path: grid cannot be co-resident (reduce replicas per context)");
         return SI_ERR_UNSUPPORTED;
     }
     SI_CUDA_TRY(cudaMemsetAsync(c->dbar, 0, sizeof(unsigned) * c->nbar, c->stream));
     void *args[] = {(void *)&c->mapA, (void *)&c->mapB, (void *)&a};
-    SI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_tc_run<BN, S>, dim3(grid), dim3(TC_THREADS),
+    SI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_tc_run<BN, S, EPI>, dim3(grid), dim3(tc_threads<EPI>()),
                                             args, smem, c->stream));
     c->launches += 1;
     return SI_OK;
@@ -529,20 +547,24 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
 si_status tc_run(Ctx *c, int steps, int8_t *spins_dev) {
     if (steps == 0) return SI_OK;
     switch (c->tile_n) {
-        case 64: return tc_launch_t<64, 8>(c, steps, spins_dev);
-        case 128: return tc_launch_t<128, 6>(c, steps, spins_dev);
+        case 64: return tc_launch_t<64, 8, 8>(c, steps, spins_dev);
+        case 128: return tc_launch_t<128, 6, 8>(c, steps, spins_dev);
         default: set_error("tensor path: unsupported tile"); return SI_ERR_UNSUPPORTED;
     }
 }
 
-template <int BN, int S>
+template <int BN, int S, int EPI>
 static int tc_occupancy() {
     using L = TcSmem<BN, S>;
-    const int smem = L::TOTAL + 1024;
-    if (cudaFuncSetAttribute(k_tc_run<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    const int smem = L::TOTAL + (EPI == 4 ? 256 : 1024);
+    if (cudaFuncSetAttribute(k_tc_run<BN, S, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return 0;
+    if (cudaFuncSetAttribute(k_tc_run<BN, S, EPI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
         return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_run<BN, S>, TC_THREADS, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_run<BN, S, EPI>, tc_threads<EPI>(), smem) !=
+        cudaSuccess)
         return 0;
     return per_sm;
 }
@@ -551,7 +573,7 @@ static int tc_occupancy() {
 // unless the caller fixed tile_n.  Returns the CTAs per SM of the choice.
 static int choose_tile(const Ctx *c, int *per_sm) {
     const int mtiles = c->mpad / TC_BM;
-    const int occ128 = tc_occupancy<128, 6>(), occ64 = tc_occupancy<64, 8>();
+    const int occ128 = tc_occupancy<128, 6, 8>(), occ64 = tc_occupancy<64, 8, 8>();
     int bn;
     if (c->prm.tile_n == 64 || c->prm.tile_n == 128) {
         bn = c->prm.tile_n;

@@ -1,0 +1,32 @@
+"""Failure detection on the GPU without a GPU fault: a step wait is pointed at
+a count that no CTA will ever publish (SI_DEBUG_STALL_STEP), so the bounded
+wait must run out; the call returns SI_ERR_TIMEOUT, the kernel ends on its
+own, and the device stays usable for the next context."""
+import numpy as np
+import pytest
+
+from _helpers import b, inputs, oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec,R", [("fp32", 1), ("j_fp8_q_bf16", 256)])
+def test_stalled_wait_times_out_and_device_recovers(prec, R, monkeypatch):
+    n, T = 300, 12
+    J = inputs.pm1_coupling(n, seed=4)
+    zeta, dt = inputs.zeta_ramp(T), inputs.dt_const(T)
+    q0 = inputs.positions(n, R, seed0=40)
+    monkeypatch.setenv("SI_DEBUG_STALL_STEP", "3")
+    monkeypatch.setenv("SI_SPIN_LIMIT_NS", "200000000")
+    with b.Context(J, replicas=R, steps=T, prec=prec) as ctx:
+        for _ in range(2):
+            with pytest.raises(b.SpringIsingError) as ei:
+                ctx.run(zeta, dt, q0)
+            assert ei.value.status == b.SI_ERR_TIMEOUT
+    monkeypatch.delenv("SI_DEBUG_STALL_STEP")
+    monkeypatch.delenv("SI_SPIN_LIMIT_NS")
+    with b.Context(J, replicas=R, steps=T, prec=prec) as ctx:
+        q, p, s = ctx.run(zeta, dt, q0)
+        e, _, _ = ctx.energy(s)
+    assert np.abs(q).max() <= b.SQRT2_F32 and np.abs(p).max() <= 2.0
+    np.testing.assert_array_equal(e, oracle.energy(J, None, s).astype(np.int64))
