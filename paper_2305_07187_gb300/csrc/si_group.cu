@@ -29,13 +29,12 @@
 
 namespace si {
 
-constexpr int GR_BM = 128, GR_BK = 64, GR_THREADS = 352, GR_S = 6;
+constexpr int GR_BM = 128, GR_BK = 64, GR_THREADS = 352;
 constexpr int GR_A_BYTES = GR_BM * GR_BK * 2;
-constexpr int GR_B_MAX = 128 * GR_BK * 2;
-constexpr int GR_STAGE = GR_A_BYTES + GR_B_MAX;
-constexpr int GR_BARS = GR_S * GR_STAGE;
-constexpr int GR_NBARS = 2 * GR_S + 2 + 2 + 1;  // full, empty, accf[2], tmem_empty[2], drain
-constexpr int GR_SMEM = GR_BARS + GR_NBARS * 8 + 16 + 1024;
+constexpr int GR_SMAX = 8;                       // most ring stages of any policy
+constexpr int GR_TILES = 196608;                 // shared memory for the ring
+constexpr int GR_NBARS = 2 * GR_SMAX + 2 + 2 + 1;  // full, empty, accf[2], tmem_empty[2], drain
+constexpr int GR_SMEM = GR_TILES + GR_NBARS * 8 + 16 + 1024;
 
 struct GroupInst {
     int n, R, ldk, rpad, mtiles, rblocks, kblocks, bn;
@@ -59,6 +58,9 @@ struct GroupArgs {
     StepParams sp;
     int *err;
     long long limit_ns;
+    int single;                // 1: one accumulator per tile (N = bn <= 256), one MMA warp
+    int stages;                // ring stages (even, <= GR_SMAX)
+    int stage_bytes;           // A tile + largest B tile of the policy (multiple of 1024)
 };
 
 __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_constant__ GroupArgs a) {
@@ -66,18 +68,19 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bar0 = sbase + GR_BARS;
+    const uint32_t bar0 = sbase + GR_TILES;
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
-    auto empty_bar = [&](int s) { return bar0 + 8u * (GR_S + s); };
-    auto accf_bar = [&](int k) { return bar0 + 8u * (2 * GR_S + k); };
-    auto tmem_empty_bar = [&](int k) { return bar0 + 8u * (2 * GR_S + 2 + k); };
-    const uint32_t drain_bar = bar0 + 8u * (2 * GR_S + 4);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + GR_BARS + GR_NBARS * 8);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + GR_BARS + GR_NBARS * 8 + 4);
+    auto empty_bar = [&](int s) { return bar0 + 8u * (GR_SMAX + s); };
+    auto accf_bar = [&](int k) { return bar0 + 8u * (2 * GR_SMAX + k); };
+    auto tmem_empty_bar = [&](int k) { return bar0 + 8u * (2 * GR_SMAX + 2 + k); };
+    const uint32_t drain_bar = bar0 + 8u * (2 * GR_SMAX + 4);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + GR_TILES + GR_NBARS * 8);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + GR_TILES + GR_NBARS * 8 + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = a.stages, HS = a.stages / 2;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < GR_S; ++s) {
+        for (int s = 0; s < GR_SMAX; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
@@ -93,7 +96,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tmem_slot)),
-                     "r"(512u)
+                     "n"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -102,13 +105,17 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int plane_in = a.t & 1;
+    // Stage of the c-th use of ring `ring`: split mode has two rings (even /
+    // odd stages, one per MMA warp), single mode one ring of all stages.
+    auto stage_of = [&](uint32_t c, int ring) -> int {
+        return a.single ? (int)(c % (uint32_t)S) : 2 * (int)(c % (uint32_t)HS) + ring;
+    };
+    auto phase_of = [&](uint32_t c) -> uint32_t {
+        return a.single ? (c / (uint32_t)S) & 1u : (c / (uint32_t)HS) & 1u;
+    };
 
     if (warp == 0) {
         // ---------------------------------------------- TMA producer
-        // Two rings of stages: even K blocks go to the even stages (consumed
-        // only by MMA warp 1), odd K blocks to the odd stages (warp 2), so
-        // that each stage has one in-order consumer.
-        constexpr int HS = GR_S / 2;
         if (lane == 0) {
             uint32_t cnt0 = 0u, cnt1 = 0u;   // stages armed in ring 0 / ring 1
             bool ok = true;
@@ -120,13 +127,13 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                 const uint32_t bytes = (uint32_t)(GR_A_BYTES + in.bn * GR_BK * 2);
                 const int yq = plane_in * in.rpad + tl.rb * in.bn;
                 for (int kb = 0; kb < in.kblocks; ++kb) {
-                    const int ring = kb & 1;
+                    const int ring = a.single ? 0 : (kb & 1);
                     const uint32_t c = ring ? cnt1 : cnt0;
-                    const int s = 2 * (int)(c % HS) + ring;
-                    const uint32_t ph = (c / HS) & 1u;
+                    const int s = stage_of(c, ring);
+                    const uint32_t ph = phase_of(c);
                     if (!mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
                     if (ring) ++cnt1; else ++cnt0;
-                    const uint32_t dA = sbase + s * GR_STAGE;
+                    const uint32_t dA = sbase + s * a.stage_bytes;
                     mbar_arrive_expect_tx(full_bar(s), bytes);
                     tma_load_2d(dA, mJ, full_bar(s), kb * GR_BK, tl.mt * GR_BM);
                     tma_load_2d(dA + GR_A_BYTES, mQ, full_bar(s), kb * GR_BK, yq);
@@ -134,10 +141,11 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
             }
             for (int ring = 0; ring < 2; ++ring) {
                 const uint32_t cr = ring ? cnt1 : cnt0;
-                const uint32_t first = cr > (uint32_t)HS ? cr - HS : 0u;
+                const uint32_t depth = a.single ? (uint32_t)S : (uint32_t)HS;
+                const uint32_t first = cr > depth ? cr - depth : 0u;
                 for (uint32_t k = first; k < cr; ++k) {
                     const unsigned long long t0 = globaltimer_ns();
-                    while (!mbar_try_wait(full_bar(2 * (int)(k % HS) + ring), (k / HS) & 1u)) {
+                    while (!mbar_try_wait(full_bar(stage_of(k, ring)), phase_of(k))) {
                         if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
                             atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
                             break;
@@ -148,9 +156,10 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
         }
     } else if (warp <= 2) {
         // ---------------------------------------------- MMA issuers
-        constexpr int HS = GR_S / 2;
-        // Warp 1: even K blocks into acc0, warp 2: odd K blocks into acc1,
-        // of the TMEM slot (u & 1) of the CTA's u-th tile.
+        // Split mode: warp 1 takes even K blocks into acc0, warp 2 odd ones
+        // into acc1, of TMEM slot (u & 1).  Single mode: warp 1 issues every
+        // K block into one accumulator of up to 256 columns; warp 2 only keeps
+        // the per-tile handshake.
         if (lane == 0) {
             const int w = warp - 1;
             uint32_t c = 0;  // position in this warp's ring of stages
@@ -169,18 +178,34 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                 }
                 tc_fence_after();
                 const uint32_t idesc = idesc_bf16(GR_BM, in.bn);
-                const uint32_t d_tmem = tmem + (uint32_t)slot * 256u + (w == 0 ? 0u : 128u);
-                for (int kb = w; kb < in.kblocks; kb += 2, ++c) {
-                    const int s = 2 * (int)(c % HS) + w;
-                    const uint32_t ph = (c / HS) & 1u;
-                    if (!mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint64_t ad = sdesc_sw128(sbase + s * GR_STAGE);
-                    const uint64_t bd = ad + (uint64_t)(GR_A_BYTES >> 4);
+                if (a.single) {
+                    if (w == 0) {
+                        const uint32_t d_tmem = tmem + (uint32_t)slot * 256u;
+                        for (int kb = 0; kb < in.kblocks; ++kb, ++c) {
+                            const int s = stage_of(c, 0);
+                            if (!mbar_wait(full_bar(s), phase_of(c), a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                            tc_fence_after();
+                            const uint64_t ad = sdesc_sw128(sbase + s * a.stage_bytes);
+                            const uint64_t bd = ad + (uint64_t)(GR_A_BYTES >> 4);
 #pragma unroll
-                    for (int kk = 0; kk < GR_BK / 16; ++kk)
-                        mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb != w || kk != 0) ? 1u : 0u);
-                    mma_commit(empty_bar(s));
+                            for (int kk = 0; kk < GR_BK / 16; ++kk)
+                                mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb != 0 || kk != 0) ? 1u : 0u);
+                            mma_commit(empty_bar(s));
+                        }
+                    }
+                } else {
+                    const uint32_t d_tmem = tmem + (uint32_t)slot * 256u + (w == 0 ? 0u : 128u);
+                    for (int kb = w; kb < in.kblocks; kb += 2, ++c) {
+                        const int s = stage_of(c, w);
+                        if (!mbar_wait(full_bar(s), phase_of(c), a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint64_t ad = sdesc_sw128(sbase + s * a.stage_bytes);
+                        const uint64_t bd = ad + (uint64_t)(GR_A_BYTES >> 4);
+#pragma unroll
+                        for (int kk = 0; kk < GR_BK / 16; ++kk)
+                            mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb != w || kk != 0) ? 1u : 0u);
+                        mma_commit(empty_bar(s));
+                    }
                 }
                 if (ok) mma_commit(accf_bar(slot));
             }
@@ -195,6 +220,8 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
         }
     } else {
         // ---------------------------------------------- epilogue (8 warps)
+        // Warp w reads TMEM lanes 32*(w%4) .. +31 (one spin per thread) and
+        // half (w-3)/4 of the tile's 16-column chunks.
         const int quad = warp & 3;
         const int half = (warp - 3) >> 2;
         const int row = quad * 32 + lane;
@@ -214,19 +241,21 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
             const int i = tl.mt * GR_BM + row;
             const bool row_ok = i < in.n;
             const float hi = (in.h && row_ok) ? in.h[i] : 0.f;
-            const bool two_acc = in.kblocks > 1;
-            const int cph = in.bn / 64;
+            const bool two_acc = !a.single && in.kblocks > 1;
+            const int nch = in.bn / 16;
+            const int c0 = half == 0 ? 0 : (nch + 1) / 2;
+            const int c1 = half == 0 ? (nch + 1) / 2 : nch;
             const uint32_t tacc = tmem + lane_off + (uint32_t)slot * 256u;
             __nv_bfloat16 *qn = in.qop + (size_t)(plane_in ^ 1) * in.rpad * in.ldk;
-            for (int c = half * cph; c < (half + 1) * cph; ++c) {
-                uint32_t vf[32], vg[32];
-                tmem_ld32(tacc + c * 32, vf);
-                tmem_ld32(tacc + 128 + c * 32, vg);
+            for (int c = c0; c < c1; ++c) {
+                uint32_t vf[16], vg[16];
+                tmem_ld16(tacc + c * 16, vf);
+                if (two_acc) tmem_ld16(tacc + 128 + c * 16, vg);
                 tmem_wait_ld();
                 if (row_ok) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int r = tl.rb * in.bn + c * 32 + j;
+                    for (int j = 0; j < 16; ++j) {
+                        const int r = tl.rb * in.bn + c * 16 + j;
                         if (r >= in.R) continue;
                         float F = __uint_as_float(vf[j]);
                         if (two_acc) F += __uint_as_float(vg[j]);
@@ -250,7 +279,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
     __syncthreads();
     tc_fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(512) : "memory");
     }
 }
 
@@ -288,7 +317,8 @@ struct Group {
     GroupInst *d_inst = nullptr;
     GroupTile *d_tiles = nullptr;
     int ntiles = 0;
-    int pol_tiles_off[3] = {0, 0, 0}, pol_ntiles[3] = {0, 0, 0};
+    int pol_tiles_off[4] = {0, 0, 0, 0}, pol_ntiles[4] = {0, 0, 0, 0};
+    int pol_stages[4] = {0, 0, 0, 0}, pol_stage_bytes[4] = {0, 0, 0, 0};
     CUtensorMap *d_maps = nullptr;
     float *d_zeta = nullptr, *d_dt = nullptr;
     int *d_err = nullptr;
@@ -302,13 +332,31 @@ struct Group {
     int launches = 0;
 };
 
-static const char *kPolicyName[] = {"bn64-if-R<=64-else-128", "all-64", "all-128"};
-constexpr int kPolicies = 3;
+static const char *kPolicyName[] = {"bn64-if-R<=64-else-128", "all-64", "all-128", "whole-instance"};
+constexpr int kPolicies = 4;
+constexpr int kPolicyWhole = 3;
 
+// Replicas per tile of a member under a policy.  "whole-instance" covers all
+// R replicas of the member in one tile (R <= 256, a multiple of 16), so each
+// J slab is read once per step; it runs the single-accumulator mode.
 static int policy_bn(int policy, int R) {
     if (policy == 1) return 64;
     if (policy == 2) return 128;
+    if (policy == kPolicyWhole) return round_up(R, 16) <= 256 ? round_up(R, 16) : 128;
     return R <= 64 ? 64 : 128;
+}
+
+// Ring geometry of a policy: stage = A tile + the largest B tile (rounded to
+// 1024 bytes), as many even stages as fit the ring's shared memory.
+static void policy_ring(int policy, const std::vector<int> &bns, int *stages, int *stage_bytes) {
+    int bmax = 16;
+    for (int b : bns) bmax = std::max(bmax, b);
+    int sb = GR_BM * GR_BK * 2 + round_up(bmax * GR_BK * 2, 1024);
+    int st = std::min(GR_SMAX, GR_TILES / sb);
+    st &= ~1;
+    if (policy == kPolicyWhole) st = std::max(st, 2);
+    *stages = st;
+    *stage_bytes = sb;
 }
 
 static std::mutex g_tune_mu;
@@ -329,6 +377,9 @@ static si_status group_build_policies(Group *g) {
     std::vector<CUtensorMap> maps((size_t)kPolicies * 2 * c);
     std::vector<std::vector<GroupTile>> tiles(kPolicies);
     for (int pol = 0; pol < kPolicies; ++pol) {
+        std::vector<int> bns;
+        for (int i = 0; i < c; ++i) bns.push_back(policy_bn(pol, g->m[i].R));
+        policy_ring(pol, bns, &g->pol_stages[pol], &g->pol_stage_bytes[pol]);
         for (int i = 0; i < c; ++i) {
             GroupMember &x = g->m[i];
             GroupInst &d = inst[(size_t)pol * c + i];
@@ -405,6 +456,9 @@ static si_status group_launch_step(Group *g, int t, int steps) {
                       g->common.update_order, g->common.wall_zero_p};
     a.err = g->d_err;
     a.limit_ns = g->limit_ns;
+    a.single = g->policy == kPolicyWhole ? 1 : 0;
+    a.stages = g->pol_stages[g->policy];
+    a.stage_bytes = g->pol_stage_bytes[g->policy];
     k_group_step<<<g->grid, GR_THREADS, GR_SMEM, g->stream>>>(a);
     SI_CUDA_TRY(cudaGetLastError());
     return SI_OK;
@@ -472,6 +526,15 @@ static si_status group_time_policy(Group *g, int policy, int steps, float *ms) {
     return group_check_err(g);
 }
 
+// SI_GROUP_POLICY=<index> pins the tile policy (over the autotuner and its
+// cache); a negative value skips the timing and takes policy 0.
+static int forced_policy() {
+    const char *env = std::getenv("SI_GROUP_POLICY");
+    if (!env) return -1;
+    const int v = std::atoi(env);
+    return v < kPolicies ? v : -1;
+}
+
 static si_status group_autotune(Group *g) {
     const std::string key = group_key(g);
     {
@@ -535,7 +598,7 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
         x.R = prm[i].replicas;
         x.ldk = round_up(n, GR_BK);
         x.mpad = round_up(n, GR_BM);
-        x.rpad_max = round_up(x.R, 128);
+        x.rpad_max = std::max(round_up(x.R, 128), round_up(x.R, 16) <= 256 ? round_up(x.R, 16) : 0);
         const float *Jp = J[i];
         const float *hp = h ? h[i] : nullptr;
         void *Jtmp = nullptr, *htmp = nullptr;
@@ -731,8 +794,8 @@ si_status si_run_group(si_group *grp, const float *zeta, const float *dt, const 
     };
     si_status s;
     if (steps > 0) {
-        int cached = -1;
-        {
+        int cached = forced_policy();
+        if (cached < 0) {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             auto it = g_tune_cache.find(group_key(g));
             if (it != g_tune_cache.end()) cached = it->second;

@@ -24,7 +24,11 @@ def _build(members, seed=0):
     return Js, hs, qs
 
 
-def test_group_per_step_within_bf16_bound():
+@pytest.mark.parametrize("policy", [0, 1, 2, 3])
+def test_group_per_step_within_bf16_bound(policy, monkeypatch):
+    """Every tile policy (replica blocks of 64 / 128, whole-instance tiles in
+    one accumulator) takes the same step within the bf16 bound."""
+    monkeypatch.setenv("SI_GROUP_POLICY", str(policy))
     members = _members()
     Js, hs, qs = _build(members)
     ps = [np.zeros_like(q) for q in qs]
@@ -33,6 +37,7 @@ def test_group_per_step_within_bf16_bound():
     precs = ["j_fp8_q_bf16" if kind == "pm1" else "j_bf16_q_bf16" for (_, _, kind) in members]
     with b.Group(Js, hs, replicas=[R for (_, R, _) in members], steps=1, precs=precs) as g:
         assert "grouped" in g.describe()
+        names = ["bn64-if-R<=64-else-128", "all-64", "all-128", "whole-instance"]
         p0 = b.default_params()
         kw = dict(k=float(p0.k), m=float(p0.m), q0=float(p0.q0), q_max=float(np.float32(p0.q_max)),
                   p_max=float(p0.p_max))
@@ -45,9 +50,13 @@ def test_group_per_step_within_bf16_bound():
                 assert (np.abs(qg[k] - qo) <= eq).all(), (t, k)
                 assert (np.abs(pg[k] - po) <= ep).all(), (t, k)
             qs, ps = qg, pg
+        assert "policy=" + names[policy] in g.describe()
 
 
-def test_group_free_run_energies_and_determinism():
+@pytest.mark.parametrize("policy", [-1, 3])
+def test_group_free_run_energies_and_determinism(policy, monkeypatch):
+    if policy >= 0:
+        monkeypatch.setenv("SI_GROUP_POLICY", str(policy))
     members = _members()
     Js, hs, qs = _build(members, seed=5)
     T = 60
