@@ -386,6 +386,119 @@ def run_scale(args):
     return 0
 
 
+GRAD_N, GRAD_R, GRAD_T, GRAD_K = 2000, 64, 500, 50
+TUNE_KNOTS, TUNE_ITERS, TUNE_LR = 8, 10, 0.02
+
+
+def tuned_knots(b, T=GRAD_T, iters=TUNE_ITERS):
+    """Schedule tuned by the adjoint gradient on the differentiation workload
+    (N=2000 +-1, R=64, T=500): projected Adam on 8 zeta knots, starting from
+    the paper's linear ramp.  Returns (knots, TuneResult)."""
+    from paper_2305_07187_gb300 import schedule
+    J = inputs.pm1_coupling(GRAD_N, seed=1)
+    q0 = inputs.positions(GRAD_N, GRAD_R, seed0=100)
+    k0 = schedule.ramp_knots(TUNE_KNOTS, inputs.ZETA_START, inputs.ZETA_END)
+    with schedule.LibraryGrad(J, q0, inputs.dt_const(T), ckpt_every=GRAD_K) as fn:
+        res = schedule.tune_zeta(fn, k0, T, iters=iters, lr=TUNE_LR)
+    return res.knots, res
+
+
+def run_grad(args):
+    """Differentiation workload: si_grad of the relaxed final energy with
+    respect to the zeta and dt schedules and k, N=2000 +-1, R=64, T=500,
+    checkpoints every 50 steps (forward sweep, recompute, adjoint sweep).
+    Metric: replica-spin-updates/s of the forward trajectory differentiated
+    (R N T per si_grad call).  Then the schedule tuner runs on it."""
+    import torch
+
+    from paper_2305_07187_gb300 import _binding as b
+    from paper_2305_07187_gb300 import schedule
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    n, R, T = GRAD_N, GRAD_R, GRAD_T
+    J = inputs.pm1_coupling(n, seed=1)
+    q0 = inputs.positions(n, R, seed0=100)
+    zeta = inputs.zeta_ramp(T)
+    dt = inputs.dt_const(T)
+    ctx = b.Context(J, replicas=R, steps=T, prec="fp32", ckpt_every=GRAD_K, stream=stream.cuda_stream)
+    z_d, d_d, q_d = (torch.from_numpy(x).to(dev) for x in (zeta, dt, q0))
+    gz_d = torch.empty(T, dtype=torch.float32, device=dev)
+    gd_d = torch.empty(T, dtype=torch.float32, device=dev)
+    gk_d = torch.empty(1, dtype=torch.float32, device=dev)
+    ob_d = torch.empty(1, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        ctx.grad_into(z_d, d_d, q_d, None, gz_d, gd_d, gk_d, ob_d)
+        return ctx.last_launch_count()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(smi_index(0))
+    sampler.start()
+    time.sleep(0.3)
+    times, launches = [], 0
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        launches += step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        flush.zero_()
+    torch.cuda.synchronize()
+    # end to end: host inputs and outputs through the public call
+    e2e = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ctx.grad(zeta, dt, q0)
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    clocks = sampler.stop()
+    desc = ctx.describe()
+    ctx.close()
+    ms = sum(times) / len(times)
+    # schedule tuning on the same workload (untimed)
+    knots, res = tuned_knots(b)
+    cuts = {}
+    for name, z in (("linear", zeta), ("tuned", schedule.expand(knots, T))):
+        with b.Context(J, replicas=R, steps=T, prec="fp32") as c:
+            _, _, s = c.run(z, dt, q0)
+            _, cut, _ = c.energy(s)
+        cuts[name] = {"best": int(cut.max()), "median": float(np.median(cut))}
+    # roofline: FP32 CUDA cores.  Algorithmic work = forward GEMM + adjoint
+    # GEMM per step (2 x 2 n^2 R); the recompute GEMM of the checkpointing is
+    # executed work, not algorithmic.
+    flops = 2 * 2.0 * n * n * R * T
+    sm_mhz = float(clocks.get("sm_max_mhz") or 2070.0)
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = flops / (ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": R * n * T / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "differentiation: si_grad of the relaxed final energy w.r.t. zeta[T], dt[T], k; "
+                               "N=2000 +-1 complete graph, R=64, T=500, checkpoints every 50 steps, FP32",
+                   "kernel": desc, "l2": "256 MiB buffer written between timed steps"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "k_adj_gemm (forward, recompute, adjoint)",
+                     "peak_source": "derived: %d SMs x 128 FP32 FMA/clk x 2 x %.0f MHz" %
+                                    (props.multi_processor_count, sm_mhz),
+                     "algorithmic_flops": flops},
+        "e2e": {"value": R * n * T / (statistics.median(e2e) * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 4 * (2 * T + R * n), "d2h_bytes_per_step": 4 * (2 * T + 2)},
+        "gpu_launches": launches,
+        "schedule": {"knots": [round(float(x), 5) for x in knots], "objective_linear": res.initial,
+                     "objective_tuned": res.objective, "iters": TUNE_ITERS, "cuts_R64": cuts},
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def ncu_case_grouped(args):
     """Profiling case of the grouped path: the first --group-count instances
     of the uneven batch, autotuned, then one run of --time-steps steps."""
@@ -497,7 +610,7 @@ def main():
     ap.add_argument("--time-steps", type=int, default=T_STEPS)
     ap.add_argument("--group-count", type=int, default=256,
                     help="grouped workload: number of instances (profiling uses a prefix)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "grouped", "scale"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "grouped", "scale", "grad"],
                     help="batched: N=2000, R=1024, T=2000 (default); grouped: 256 uneven "
                          "instances, T=1000, one grouped launch per step")
     args = ap.parse_args()
@@ -515,6 +628,8 @@ def main():
         return run_grouped(args)
     if args.workload == "scale":
         return run_scale(args)
+    if args.workload == "grad":
+        return run_grad(args)
 
     import torch
     import torch.distributed as dist

@@ -157,6 +157,25 @@ si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt,
                   float *g_dt, float *g_k, float *objective);
 
 /*
+ * Hamiltonian of the spring system, evaluated in FP64 for drift monitoring:
+ *   H_r = sum_i p_ri^2/(2m) + k/2 sum_i (q_ri - q0)^2
+ *         + zeta * ( -1/2 q_r^T J q_r - h^T q_r )
+ * (kinetic energy and spring potential of Eqs. 2-3, coupling potential of
+ * Eq. 4 whose force is zeta (J q + h); the field term follows Eq. 1).  J and
+ * h are the context's working copies, so for SI_PREC_J_BF16_Q_BF16 J is the
+ * bf16-rounded matrix the kernels integrate.
+ *   q, p   [R][n] float, host or device (e.g. si_run's q_out, p_out)
+ *   zeta   the coupling coefficient of the stretch being monitored
+ *   H_out  [R] double, host or device
+ * Every product and sum is FP64 in a fixed order (deterministic).  R may
+ * differ from the context's replica count; R = 0 does nothing (the pointers
+ * may then be NULL).  Returns SI_ERR_INVALID_ARG for R < 0, or for NULL q, p
+ * or H_out when R > 0.
+ */
+si_status si_hamiltonian(si_ctx *ctx, const float *q, const float *p, int32_t R,
+                         double zeta, double *H_out);
+
+/*
  * Kernel timing.  With timing enabled, si_run records CUDA events on the
  * context's stream immediately before and after the launch(es) of the
  * time-step kernel (the coupling force fused with the integrator) and

@@ -35,7 +35,7 @@ PREC = {"fp32": 0, "fp64": 1, "j_fp8_q_bf16": 2, "j_bf16_q_bf16": 3}
 
 EXPORTS = ("si_default_params", "si_create", "si_run", "si_get_state", "si_energy", "si_grad",
            "si_enable_timing", "si_last_kernel_time", "si_describe", "si_last_launch_count",
-           "si_last_error", "si_destroy", "si_run_noalloc", "si_create_group", "si_run_group",
+           "si_last_error", "si_destroy", "si_run_noalloc", "si_hamiltonian", "si_create_group", "si_run_group",
            "si_group_energy", "si_group_enable_timing", "si_group_last_kernel_time",
            "si_group_describe", "si_group_last_launch_count", "si_destroy_group")
 
@@ -81,6 +81,8 @@ def load():
     lib.si_energy.restype = ctypes.c_int
     lib.si_grad.argtypes = [P, P, P, P, P, P, P, P, P]
     lib.si_grad.restype = ctypes.c_int
+    lib.si_hamiltonian.argtypes = [P, P, P, I32, ctypes.c_double, P]
+    lib.si_hamiltonian.restype = ctypes.c_int
     lib.si_enable_timing.argtypes = [P, I32]
     lib.si_enable_timing.restype = ctypes.c_int
     lib.si_last_kernel_time.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
@@ -279,6 +281,27 @@ class Context:
         f = np.empty(R, np.float64)
         self.energy_into(s, R, e, c, f)
         return e, c, f
+
+    def hamiltonian(self, q, p, zeta, out=None):
+        """si_hamiltonian: FP64 H per replica for the state (q, p) at coupling
+        coefficient zeta.  q, p: NumPy or CUDA tensors of R*n floats; returns
+        a NumPy float64 array, or fills `out` (NumPy or CUDA float64)."""
+        R = (int(q.numel()) if _is_torch(q) else np.asarray(q).size) // self.n
+        qa = _Arg(q, np.float32, R * self.n)
+        pa = _Arg(p, np.float32, R * self.n)
+        res = np.empty(R, np.float64) if out is None else out
+        oa = _Arg(res, np.float64, R, writable=True)
+        _check(load().si_hamiltonian(self.ctx, qa.ptr, pa.ptr, R, float(zeta), oa.ptr))
+        return res
+
+    def grad_into(self, zeta, dt, q_init, p_init=None, g_zeta=None, g_dt=None, g_k=None, objective=None):
+        """si_grad into caller buffers (NumPy or CUDA tensors; any output may be None)."""
+        nR = self.n * self.replicas
+        a = [_Arg(zeta, np.float32, self.steps), _Arg(dt, np.float32, self.steps),
+             _Arg(q_init, np.float32, nR), _Arg(p_init, np.float32, nR),
+             _Arg(g_zeta, np.float32, self.steps, writable=True), _Arg(g_dt, np.float32, self.steps, writable=True),
+             _Arg(g_k, np.float32, 1, writable=True), _Arg(objective, np.float32, 1, writable=True)]
+        _check(load().si_grad(self.ctx, *[x.ptr for x in a]))
 
     def grad(self, zeta, dt, q_init, p_init=None):
         """si_grad: returns (objective, g_zeta, g_dt, g_k) as NumPy/float."""

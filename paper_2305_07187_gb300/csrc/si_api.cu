@@ -447,6 +447,30 @@ si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy
     return SI_OK;
 }
 
+si_status si_hamiltonian(si_ctx *ctx, const float *q, const float *p, int32_t R, double zeta,
+                         double *H_out) {
+    set_error("");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || R < 0 || (R > 0 && (!q || !p || !H_out))) {
+        set_error("si_hamiltonian: ctx is required, R >= 0, and q, p, H_out when R > 0");
+        return SI_ERR_INVALID_ARG;
+    }
+    c->launches = 0;
+    if (R == 0) return SI_OK;
+    const size_t bytes = sizeof(float) * (size_t)R * c->n;
+    DevIn qd, pd;
+    si_status s = stage_in(qd, q, bytes, c->stream);
+    if (s != SI_OK) return s;
+    if ((s = stage_in(pd, p, bytes, c->stream)) != SI_OK) return s;
+    DevOut ho;
+    if ((s = stage_out(ho, H_out, sizeof(double) * R)) != SI_OK) return s;
+    s = monitor_hamiltonian(c, (const float *)qd.ptr, (const float *)pd.ptr, R, zeta, (double *)ho.ptr);
+    if (s != SI_OK) return s;
+    if ((s = finish_out(ho, c->stream)) != SI_OK) return s;
+    SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return SI_OK;
+}
+
 si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt, const float *q_init,
                   const float *p_init, float *g_zeta, float *g_dt, float *g_k,
                   float *objective) {

@@ -115,6 +115,9 @@ bool is_device_ptr(const void *p);
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 inline int round_up(int a, int b) { return cdiv(a, b) * b; }
 
+// FP64 Hamiltonian for drift monitoring, si_monitor.cu (device pointers).
+si_status monitor_hamiltonian(Ctx *c, const float *q, const float *p, int R, double zeta, double *H);
+
 // SIMT (FP32 / FP64) paths, si_simt.cu.
 si_status simt_run(Ctx *c, int steps, int8_t *spins_dev);
 si_status simt_energy(Ctx *c, const int8_t *spins_dev, int R, int ld,

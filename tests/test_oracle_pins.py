@@ -307,6 +307,55 @@ def test_relaxed_energy_and_hamiltonian():
     np.testing.assert_allclose(H, ref, rtol=1e-12)
 
 
+def test_hamiltonian_generates_the_oracle_step():
+    """Hamilton's equations pin H to the integrator (a different function of
+    the oracle): one kick-drift step of length dt from (q, p) moves p by
+    -dt dH/dq and then q by dt dH/dp at the new p.  dH/dq and dH/dp are taken
+    by FP64 central differences of the oracle's H, the step from or_run, with
+    walls far away; a dropped term, a wrong sign or a transposed J fails."""
+    n, R = 12, 2
+    J = inputs.gauss_coupling_bf16(n, seed=21).astype(np.float64)
+    h = inputs.field(n, seed=22).astype(np.float64)
+    g = np.random.Generator(np.random.PCG64(5))
+    q = g.uniform(-0.3, 0.3, (R, n))
+    p = g.uniform(-0.3, 0.3, (R, n))
+    kw = dict(zeta=0.37, k=0.6, m=1.7, q0=0.05)
+    eps = 1e-6
+    dHdq = np.empty_like(q)
+    dHdp1 = np.empty_like(p)
+    dt = 1e-3
+    q1, p1 = oracle.run(J, h, np.array([kw["zeta"]]), np.array([dt]), q, p, k=kw["k"], m=kw["m"],
+                        q0=kw["q0"], q_max=10.0, p_max=10.0)
+    for i in range(n):
+        e = np.zeros(n); e[i] = eps
+        dHdq[:, i] = (oracle.hamiltonian(J, h, q + e, p, **kw) - oracle.hamiltonian(J, h, q - e, p, **kw)) / (2 * eps)
+        dHdp1[:, i] = (oracle.hamiltonian(J, h, q, p1 + e, **kw) - oracle.hamiltonian(J, h, q, p1 - e, **kw)) / (2 * eps)
+    np.testing.assert_allclose((p1 - p) / dt, -dHdq, rtol=0, atol=1e-7)
+    np.testing.assert_allclose((q1 - q) / dt, dHdp1, rtol=0, atol=1e-7)
+
+
+def test_hamiltonian_nearly_conserved_at_constant_zeta():
+    """Symplectic Euler keeps H within O(dt) of its start with no secular
+    drift at constant zeta: over 4000 steps, the spread at dt = 0.01 is about
+    half that at dt = 0.02 and stays small (walls out of reach)."""
+    n, R = 10, 2
+    J = inputs.gauss_coupling_bf16(n, seed=23).astype(np.float64) * 0.05
+    q = inputs.positions(n, R, seed0=300).astype(np.float64)
+    spreads = []
+    for dt in (0.02, 0.01):
+        T = int(round(40.0 / dt))
+        qc, pc = q.copy(), np.zeros_like(q)
+        H0 = oracle.hamiltonian(J, None, qc, pc, zeta=0.2)
+        worst = 0.0
+        for _ in range(20):
+            qc, pc = oracle.run(J, None, np.full(T // 20, 0.2), np.full(T // 20, dt), qc, pc,
+                                q_max=10.0, p_max=10.0)
+            worst = max(worst, np.abs(oracle.hamiltonian(J, None, qc, pc, zeta=0.2) - H0).max())
+        spreads.append(worst / np.abs(H0).max())
+    assert spreads[0] < 0.05
+    assert 1.6 < spreads[0] / spreads[1] < 2.4
+
+
 def test_sign_readout():
     q = np.array([0.5, -0.5, 0.0, -0.0, 1e-300, -1e-300])
     np.testing.assert_array_equal(oracle.sign(q), [1, -1, 1, 1, 1, -1])
