@@ -468,13 +468,14 @@ def run_grad(args):
             _, _, s = c.run(z, dt, q0)
             _, cut, _ = c.energy(s)
         cuts[name] = {"best": int(cut.max()), "median": float(np.median(cut))}
-    # roofline: FP32 CUDA cores.  Algorithmic work = forward GEMM + adjoint
-    # GEMM per step (2 x 2 n^2 R); the recompute GEMM of the checkpointing is
+    # Roofline of the products J X^T, which run on the tensor cores (bf16
+    # pieces of the FP32 operand, three MMAs' worth per product).  Algorithmic
+    # work = forward product + adjoint product per step, 2 x 2 n^2 R; the
+    # recompute product of the checkpointing and the 3x piece split are
     # executed work, not algorithmic.
     flops = 2 * 2.0 * n * n * R * T
-    sm_mhz = float(clocks.get("sm_max_mhz") or 2070.0)
-    props = torch.cuda.get_device_properties(dev)
-    peak = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    peaks, src = load_peaks()
+    peak = float(peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS))
     achieved = flops / (ms * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": R * n * T / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -483,11 +484,12 @@ def run_grad(args):
         "config": {"workload": "differentiation: si_grad of the relaxed final energy w.r.t. zeta[T], dt[T], k; "
                                "N=2000 +-1 complete graph, R=64, T=500, checkpoints every 50 steps, FP32",
                    "kernel": desc, "l2": "256 MiB buffer written between timed steps"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_adj_gemm (forward, recompute, adjoint)",
-                     "peak_source": "derived: %d SMs x 128 FP32 FMA/clk x 2 x %.0f MHz" %
-                                    (props.multi_processor_count, sm_mhz),
-                     "algorithmic_flops": flops},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_adj_tc (forward, recompute and adjoint products, K split over a cluster)",
+                     "peak_source": "%s bf16_tflops (burst)" % src, "algorithmic_flops": flops,
+                     "note": "whole si_grad time: per step 7 dependent launches (3 products, 3 operand "
+                             "splits, 1 elementwise adjoint) replayed from a CUDA graph; latency-bound"},
         "e2e": {"value": R * n * T / (statistics.median(e2e) * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * (2 * T + R * n), "d2h_bytes_per_step": 4 * (2 * T + 2)},
         "gpu_launches": launches,

@@ -23,6 +23,7 @@
 // backwards.  Gradient sums are per-block partials reduced in a fixed order
 // (deterministic).
 #include <algorithm>
+#include <cstdlib>
 #include <cstdio>
 
 #include "si_device.cuh"
@@ -30,7 +31,7 @@
 namespace si {
 
 constexpr int AG_M = 64, AG_R = 64, AG_K = 16, AG_THREADS = 256;
-constexpr int AE_BLOCKS = 128, AE_THREADS = 256;
+constexpr int AE_BLOCKS = 256, AE_THREADS = 256;
 
 enum GemmMode { GM_FORWARD = 0, GM_TERMINAL = 1, GM_ADJOINT = 2 };
 
@@ -185,16 +186,30 @@ __global__ void __launch_bounds__(AE_THREADS) k_adj_elem(
         s2.add(-dtt * la * dq);
     }
     (void)p;
-    r0s[threadIdx.x] = s0.value();
-    r1s[threadIdx.x] = s1.value();
-    r2s[threadIdx.x] = s2.value();
+    // fixed-shape reduction: warp shuffle trees of the compensated sums,
+    // then the warps' results in warp order
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const T h0 = __shfl_down_sync(0xffffffffu, s0.hi, off), l0 = __shfl_down_sync(0xffffffffu, s0.lo, off);
+        const T h1 = __shfl_down_sync(0xffffffffu, s1.hi, off), l1 = __shfl_down_sync(0xffffffffu, s1.lo, off);
+        const T h2 = __shfl_down_sync(0xffffffffu, s2.hi, off), l2 = __shfl_down_sync(0xffffffffu, s2.lo, off);
+        s0.merge(h0, l0);
+        s1.merge(h1, l1);
+        s2.merge(h2, l2);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        r0s[warp] = s0.value();
+        r1s[warp] = s1.value();
+        r2s[warp] = s2.value();
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         CompSum<T> a0, a1, a2;
         a0.init();
         a1.init();
         a2.init();
-        for (int w = 0; w < AE_THREADS; ++w) {
+        for (int w = 0; w < AE_THREADS / 32; ++w) {
             a0.add(r0s[w]);
             a1.add(r1s[w]);
             a2.add(r2s[w]);
@@ -206,9 +221,13 @@ __global__ void __launch_bounds__(AE_THREADS) k_adj_elem(
 }
 
 // Final fixed-order reductions: g_dt[t], g_zeta[t], g_k and the objective.
+// One thread per step for g_dt / g_zeta; block 0 also reduces g_k (thread u
+// sums steps u, u+128, ... and thread 0 adds the 128 results in order) and
+// the objective.  Launched with 128 threads per block.
 template <typename T>
 __global__ void k_adj_finish(int T_steps, const T *part, int nobj, const T *obj_part, float *g_zeta,
                              float *g_dt, float *g_k, float *objective) {
+    __shared__ T gks[128];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < T_steps) {
         const T *pp = part + (size_t)t * 3 * AE_BLOCKS;
@@ -222,17 +241,24 @@ __global__ void k_adj_finish(int T_steps, const T *part, int nobj, const T *obj_
         if (g_dt) g_dt[t] = (float)a0.value();
         if (g_zeta) g_zeta[t] = (float)a1.value();
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        CompSum<T> gk, ob;
+    if (blockIdx.x == 0) {
+        CompSum<T> gk;
         gk.init();
-        ob.init();
-        for (int s = 0; s < T_steps; ++s) {
+        for (int s = threadIdx.x; s < T_steps; s += blockDim.x) {
             const T *pp = part + (size_t)s * 3 * AE_BLOCKS + 2 * AE_BLOCKS;
             for (int b = 0; b < AE_BLOCKS; ++b) gk.add(pp[b]);
         }
-        for (int b = 0; b < nobj; ++b) ob.add(obj_part[b]);
-        if (g_k) *g_k = (float)gk.value();
-        if (objective) *objective = (float)ob.value();
+        gks[threadIdx.x] = gk.value();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            CompSum<T> g2, ob;
+            g2.init();
+            ob.init();
+            for (int u = 0; u < (int)blockDim.x; ++u) g2.add(gks[u]);
+            for (int b = 0; b < nobj; ++b) ob.add(obj_part[b]);
+            if (g_k) *g_k = (float)g2.value();
+            if (objective) *objective = (float)ob.value();
+        }
     }
 }
 
@@ -250,26 +276,30 @@ __global__ void k_adj_load_state(const float *q_init, const float *p_init, int n
 
 template <typename T>
 static si_status adjoint_impl(Ctx *c, int steps, float *g_zeta, float *g_dt, float *g_k,
-                              float *objective, const float *q_init, const float *p_init) {
+                              float *objective, const float *q_init, const float *p_init, AdjTc *tc) {
     const int n = c->n, R = c->R, ld = c->ldj;
     const int K = c->prm.ckpt_every > 0 ? c->prm.ckpt_every : 50;
     const int nseg = steps > 0 ? cdiv(steps, K) : 0;
     const size_t plane = (size_t)R * ld;
     const dim3 ggrid(cdiv(n, AG_M), cdiv(R, AG_R));
-    const int nobj = (int)(ggrid.x * ggrid.y);
+    const int nobj = tc ? adj_tc_nobj(tc) : (int)(ggrid.x * ggrid.y);
     // workspace: ckpt (nseg+1) x {q,p}; slots (K+1) x {q,p}; F K; lq, lp, la, lb;
     // partials 3 * AE_BLOCKS * steps; objective partials.
     const size_t n_planes = 2 * (size_t)(nseg + 1) + 2 * (size_t)(K + 1) + (size_t)K + 4;
+    // + the outputs g_zeta[T], g_dt[T], g_k, objective (float) at the end
+    const size_t out_floats = 2 * (size_t)std::max(steps, 1) + 2;
     const size_t bytes = sizeof(T) * (n_planes * plane + 3 * (size_t)AE_BLOCKS * std::max(steps, 1) +
-                                      (size_t)nobj);
+                                      (size_t)nobj) + sizeof(float) * out_floats;
     if (c->g_ws_bytes < bytes) {
         if (c->g_ws) cudaFree(c->g_ws);
         c->g_ws = nullptr;
         c->g_ws_bytes = 0;
         SI_CUDA_TRY(cudaMalloc(&c->g_ws, bytes));
         c->g_ws_bytes = bytes;
+        // Zero once: the padding columns of every plane are never written
+        // afterwards and must stay zero for the CUDA-core products.
+        SI_CUDA_TRY(cudaMemsetAsync(c->g_ws, 0, bytes, c->stream));
     }
-    SI_CUDA_TRY(cudaMemsetAsync(c->g_ws, 0, bytes, c->stream));
     T *w = (T *)c->g_ws;
     T *ckq = w;                            w += (size_t)(nseg + 1) * plane;
     T *ckp = w;                            w += (size_t)(nseg + 1) * plane;
@@ -281,92 +311,194 @@ static si_status adjoint_impl(Ctx *c, int steps, float *g_zeta, float *g_dt, flo
     T *la = w;                             w += plane;
     T *lb = w;                             w += plane;
     T *part = w;                           w += 3 * (size_t)AE_BLOCKS * std::max(steps, 1);
-    T *objp = w;
+    T *objp = w;                           w += nobj;
+    float *gout = reinterpret_cast<float *>(w);   // g_zeta[T], g_dt[T], g_k, objective
     const StepParams spar{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max, 0, 0};
     const int lg = std::min(4096, cdiv((long long)plane, 256));
     k_adj_load_state<T><<<lg, 256, 0, c->stream>>>(q_init, p_init, n, R, ld, ckq, ckp);
     SI_CUDA_TRY(cudaGetLastError());
     c->launches += 1;
 
-    AdjGemmArgs<T> g{};
-    g.J = (const T *)c->dJ;
-    g.ldj = ld;
-    g.h = (const T *)c->dh;
-    g.n = n;
-    g.R = R;
-    g.sp = spar;
-    g.zeta = c->dzeta;
-    g.dt = c->ddt;
+    // The sweep after the initial state is the same sequence of launches on
+    // every call of a context: it is captured once into a CUDA graph (on a
+    // private stream) and replayed, so the ~7 launches per step do not wait
+    // on the host.
+    auto sweep = [&]() -> si_status {
+        AdjGemmArgs<T> g{};
+        g.J = (const T *)c->dJ;
+        g.ldj = ld;
+        g.h = (const T *)c->dh;
+        g.n = n;
+        g.R = R;
+        g.sp = spar;
+        g.zeta = c->dzeta;
+        g.dt = c->ddt;
 
-    // Recompute segment s from its checkpoint into the slots (q_t, p_t, F_t).
-    auto recompute = [&](int s) -> si_status {
-        const int t0 = s * K, len = std::min(K, steps - t0);
-        SI_CUDA_TRY(cudaMemcpyAsync(sq, ckq + (size_t)s * plane, sizeof(T) * plane, cudaMemcpyDeviceToDevice, c->stream));
-        SI_CUDA_TRY(cudaMemcpyAsync(sp, ckp + (size_t)s * plane, sizeof(T) * plane, cudaMemcpyDeviceToDevice, c->stream));
-        for (int j = 0; j < len; ++j) {
-            g.X = sq + (size_t)j * plane;
-            g.P = sp + (size_t)j * plane;
-            g.Qn = sq + (size_t)(j + 1) * plane;
-            g.Pn = sp + (size_t)(j + 1) * plane;
-            g.Fo = sF + (size_t)j * plane;
-            g.t = t0 + j;
+        // The three products of the sweep: on the tensor cores (three-piece bf16
+        // split of the operand, FP32 accumulation) when the context has one, else
+        // the CUDA-core tiles.
+        auto gemm_forward = [&](const T *X, const T *P, T *Qn, T *Pn, T *Fo, int t) -> si_status {
+            if (tc) {
+                return adj_tc_gemm(c, tc, 0, (const float *)X, (const float *)P, (float *)Qn, (float *)Pn,
+                                   (float *)Fo, nullptr, nullptr, nullptr, nullptr, t);
+            }
+            g.X = X;
+            g.P = P;
+            g.Qn = Qn;
+            g.Pn = Pn;
+            g.Fo = Fo;
+            g.t = t;
             k_adj_gemm<T, GM_FORWARD><<<ggrid, AG_THREADS, 0, c->stream>>>(g);
-        }
-        SI_CUDA_TRY(cudaGetLastError());
-        c->launches += len;
-        return SI_OK;
-    };
-
-    // Forward pass: checkpoints at the start of every segment and at T.
-    si_status st;
-    for (int s = 0; s < nseg; ++s) {
-        if ((st = recompute(s)) != SI_OK) return st;
-        const int len = std::min(K, steps - s * K);
-        SI_CUDA_TRY(cudaMemcpyAsync(ckq + (size_t)(s + 1) * plane, sq + (size_t)len * plane, sizeof(T) * plane,
-                                    cudaMemcpyDeviceToDevice, c->stream));
-        SI_CUDA_TRY(cudaMemcpyAsync(ckp + (size_t)(s + 1) * plane, sp + (size_t)len * plane, sizeof(T) * plane,
-                                    cudaMemcpyDeviceToDevice, c->stream));
-    }
-    // Terminal adjoint and objective at q_T.
-    g.X = ckq + (size_t)nseg * plane;
-    g.LQ = lq;
-    g.LP = lp;
-    g.obj_part = objp;
-    k_adj_gemm<T, GM_TERMINAL><<<ggrid, AG_THREADS, 0, c->stream>>>(g);
-    SI_CUDA_TRY(cudaGetLastError());
-    c->launches += 1;
-    // Reverse sweep.
-    for (int s = nseg - 1; s >= 0; --s) {
-        if ((st = recompute(s)) != SI_OK) return st;
-        const int t0 = s * K, len = std::min(K, steps - t0);
-        for (int j = len - 1; j >= 0; --j) {
-            const int t = t0 + j;
-            k_adj_elem<T><<<AE_BLOCKS, AE_THREADS, 0, c->stream>>>(
-                n, R, ld, sq + (size_t)j * plane, sp + (size_t)j * plane, sF + (size_t)j * plane,
-                sq + (size_t)(j + 1) * plane, sp + (size_t)(j + 1) * plane, lq, lp, la, lb, spar, c->dzeta,
-                c->ddt, t, part + (size_t)t * 3 * AE_BLOCKS);
+            SI_CUDA_TRY(cudaGetLastError());
+            c->launches += 1;
+            return SI_OK;
+        };
+        auto gemm_terminal = [&](const T *X) -> si_status {
+            if (tc) {
+                return adj_tc_gemm(c, tc, 1, (const float *)X, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                   (float *)lq, (float *)lp, (float *)objp, 0);
+            }
+            g.X = X;
+            g.LQ = lq;
+            g.LP = lp;
+            g.obj_part = objp;
+            k_adj_gemm<T, GM_TERMINAL><<<ggrid, AG_THREADS, 0, c->stream>>>(g);
+            SI_CUDA_TRY(cudaGetLastError());
+            c->launches += 1;
+            return SI_OK;
+        };
+        auto gemm_adjoint = [&](int t) -> si_status {
+            if (tc) {
+                return adj_tc_gemm(c, tc, 2, (const float *)la, nullptr, nullptr, nullptr, nullptr, (const float *)lb,
+                                   (float *)lq, (float *)lp, nullptr, t);
+            }
             g.X = la;
             g.LB = lb;
             g.LQ = lq;
             g.LP = lp;
             g.t = t;
             k_adj_gemm<T, GM_ADJOINT><<<ggrid, AG_THREADS, 0, c->stream>>>(g);
+            SI_CUDA_TRY(cudaGetLastError());
+            c->launches += 1;
+            return SI_OK;
+        };
+
+        // Recompute segment s from its checkpoint into the slots (q_t, p_t, F_t).
+        si_status st;
+        auto recompute = [&](int s) -> si_status {
+            const int t0 = s * K, len = std::min(K, steps - t0);
+            SI_CUDA_TRY(cudaMemcpyAsync(sq, ckq + (size_t)s * plane, sizeof(T) * plane, cudaMemcpyDeviceToDevice, c->stream));
+            SI_CUDA_TRY(cudaMemcpyAsync(sp, ckp + (size_t)s * plane, sizeof(T) * plane, cudaMemcpyDeviceToDevice, c->stream));
+            for (int j = 0; j < len; ++j) {
+                si_status e = gemm_forward(sq + (size_t)j * plane, sp + (size_t)j * plane, sq + (size_t)(j + 1) * plane,
+                                           sp + (size_t)(j + 1) * plane, sF + (size_t)j * plane, t0 + j);
+                if (e != SI_OK) return e;
+            }
+            return SI_OK;
+        };
+
+        // Forward pass: checkpoints at the start of every segment and at T.
+        for (int s = 0; s < nseg; ++s) {
+            if ((st = recompute(s)) != SI_OK) return st;
+            const int len = std::min(K, steps - s * K);
+            SI_CUDA_TRY(cudaMemcpyAsync(ckq + (size_t)(s + 1) * plane, sq + (size_t)len * plane, sizeof(T) * plane,
+                                        cudaMemcpyDeviceToDevice, c->stream));
+            SI_CUDA_TRY(cudaMemcpyAsync(ckp + (size_t)(s + 1) * plane, sp + (size_t)len * plane, sizeof(T) * plane,
+                                        cudaMemcpyDeviceToDevice, c->stream));
         }
+        // The final state of the forward sweep becomes the context's state
+        // (si_get_state reads it): q into exchange buffer 0, p into [R][n].
+        SI_CUDA_TRY(cudaMemcpyAsync(c->dqbuf, ckq + (size_t)nseg * plane, sizeof(T) * plane, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+        SI_CUDA_TRY(cudaMemcpy2DAsync(c->dp, sizeof(T) * n, ckp + (size_t)nseg * plane, sizeof(T) * ld, sizeof(T) * n, R,
+                                      cudaMemcpyDeviceToDevice, c->stream));
+        // Terminal adjoint and objective at q_T.
+        if ((st = gemm_terminal(ckq + (size_t)nseg * plane)) != SI_OK) return st;
+        // Reverse sweep.  The slots still hold the last segment from the
+        // forward pass, so only the earlier segments are recomputed.
+        for (int s = nseg - 1; s >= 0; --s) {
+            if (s != nseg - 1 && (st = recompute(s)) != SI_OK) return st;
+            const int t0 = s * K, len = std::min(K, steps - t0);
+            for (int j = len - 1; j >= 0; --j) {
+                const int t = t0 + j;
+                k_adj_elem<T><<<AE_BLOCKS, AE_THREADS, 0, c->stream>>>(
+                    n, R, ld, sq + (size_t)j * plane, sp + (size_t)j * plane, sF + (size_t)j * plane,
+                    sq + (size_t)(j + 1) * plane, sp + (size_t)(j + 1) * plane, lq, lp, la, lb, spar, c->dzeta,
+                    c->ddt, t, part + (size_t)t * 3 * AE_BLOCKS);
+                SI_CUDA_TRY(cudaGetLastError());
+                c->launches += 1;
+                if ((st = gemm_adjoint(t)) != SI_OK) return st;
+            }
+        }
+        const int T1 = std::max(steps, 1);
+        k_adj_finish<T><<<cdiv(T1, 128), 128, 0, c->stream>>>(steps, part, nobj, objp, gout, gout + T1, gout + 2 * T1,
+                                                              gout + 2 * T1 + 1);
         SI_CUDA_TRY(cudaGetLastError());
-        c->launches += 2 * len;
+        c->launches += 1;
+        return SI_OK;
+    };
+    const int key = steps * 4 + (tc ? 1 : 0) + (sizeof(T) == 8 ? 2 : 0);
+    if (!c->g_graph || c->g_graph_key != key || c->g_graph_ws != c->g_ws) {
+        if (c->g_graph) cudaGraphExecDestroy(c->g_graph);
+        c->g_graph = nullptr;
+        cudaStream_t cs;
+        SI_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaStream_t saved = c->stream;
+        const int launches0 = c->launches;
+        c->stream = cs;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        si_status s = SI_OK;
+        if (e == cudaSuccess) {
+            s = sweep();
+            e = cudaStreamEndCapture(cs, &graph);
+        }
+        c->stream = saved;
+        cudaStreamDestroy(cs);
+        c->g_graph_launches = c->launches - launches0;
+        c->launches = launches0;
+        if (s != SI_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return s;
+        }
+        SI_CUDA_TRY(e);
+        e = cudaGraphInstantiate(&c->g_graph, graph, 0);
+        cudaGraphDestroy(graph);
+        SI_CUDA_TRY(e);
+        c->g_graph_key = key;
+        c->g_graph_ws = c->g_ws;
     }
-    k_adj_finish<T><<<cdiv(std::max(steps, 1), 128), 128, 0, c->stream>>>(steps, part, nobj, objp, g_zeta, g_dt,
-                                                                        g_k, objective);
-    SI_CUDA_TRY(cudaGetLastError());
-    c->launches += 1;
+    SI_CUDA_TRY(cudaGraphLaunch(c->g_graph, c->stream));
+    c->launches += c->g_graph_launches;
+    c->cur_parity = 0;
+    c->have_run = true;
+    const int T1 = std::max(steps, 1);
+    if (g_zeta && steps > 0)
+        SI_CUDA_TRY(cudaMemcpyAsync(g_zeta, gout, sizeof(float) * steps, cudaMemcpyDeviceToDevice, c->stream));
+    if (g_dt && steps > 0)
+        SI_CUDA_TRY(cudaMemcpyAsync(g_dt, gout + T1, sizeof(float) * steps, cudaMemcpyDeviceToDevice, c->stream));
+    if (g_k) SI_CUDA_TRY(cudaMemcpyAsync(g_k, gout + 2 * T1, sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    if (objective)
+        SI_CUDA_TRY(cudaMemcpyAsync(objective, gout + 2 * T1 + 1, sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     return SI_OK;
 }
 
 si_status adjoint_grad(Ctx *c, int steps, float *g_zeta, float *g_dt, float *g_k, float *objective,
                        const float *q_init, const float *p_init) {
-    if (c->prm.prec == SI_PREC_FP64)
-        return adjoint_impl<double>(c, steps, g_zeta, g_dt, g_k, objective, q_init, p_init);
-    return adjoint_impl<float>(c, steps, g_zeta, g_dt, g_k, objective, q_init, p_init);
+    if (c->prm.prec == SI_PREC_FP64) {
+        c->g_path = 1;
+        return adjoint_impl<double>(c, steps, g_zeta, g_dt, g_k, objective, q_init, p_init, nullptr);
+    }
+    // FP32: the tensor cores take the products when J is exact in bf16
+    // (SI_ADJOINT_SIMT=1 keeps them on the CUDA cores).
+    AdjTc *tc = nullptr;
+    const char *env = std::getenv("SI_ADJOINT_SIMT");
+    if (c->bf16_j && !(env && std::atoi(env) == 1)) {
+        si_status s = adj_tc_prepare(c, &tc);
+        if (s != SI_OK) return s;
+    }
+    c->g_path = tc ? 2 : 1;
+    return adjoint_impl<float>(c, steps, g_zeta, g_dt, g_k, objective, q_init, p_init, tc);
 }
 
 }  // namespace si

@@ -1,0 +1,564 @@
+// Tensor-core products of the adjoint sweep (FP32 contexts whose J is exact
+// in bf16, e.g. +-1 or bf16-rounded Gaussian couplings).
+//
+// Each step of the reverse sweep needs G = J X^T twice (the recomputed
+// forward force J q_t and the adjoint product J lambda_a) over R replicas.
+// With J exact in bf16, the FP32 operand X is split into three bf16 pieces
+// x = x_hi + x_mid + x_lo (each the round-to-nearest bf16 of the remaining
+// residual, so the pieces carry the 24-bit significand); every product
+// J_ij * piece is exact in FP32 and the tensor cores accumulate in FP32.  The
+// result carries the rounding of an FP32 dot product, against the bf16 error
+// that a single-piece operand would add.
+//
+// Tile: 128 rows of J x 64 replicas; the B operand holds the three pieces of
+// the 64 replicas as 192 rows, so one kind::f16 MMA of N = 192 computes all
+// three partial products into one TMEM accumulator and the epilogue adds
+// them, (hi + mid) + lo.  The K dimension is split over the CTAs of a thread
+// block cluster to fill the GPU (N = 2000, R = 64 has only 16 tiles): each
+// split leaves its FP32 partial tile in its own shared memory, and after a
+// cluster barrier every CTA adds, through distributed shared memory and in
+// split order (deterministic), the partials of its own slice of replicas
+// and applies the step's epilogue to that slice: the forward integrator
+// step, the terminal adjoint, or the adjoint update.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "si_device.cuh"
+#include "si_tcgen05.cuh"
+
+namespace si {
+
+constexpr int AT_BM = 128, AT_BK = 64, AT_RB = 64, AT_PIECES = 3;
+constexpr int AT_BN = AT_RB * AT_PIECES;                 // 192 MMA columns
+constexpr int AT_A_BYTES = AT_BM * AT_BK * 2;            // 16 KB
+constexpr int AT_B_BYTES = AT_BN * AT_BK * 2;            // 24 KB
+constexpr int AT_STAGE = AT_A_BYTES + AT_B_BYTES;        // 40 KB, multiple of 1024
+constexpr int AT_S = 4;
+constexpr int AT_THREADS = 192;                          // producer, MMA, 4 epilogue warps
+constexpr int AT_TILES = AT_S * AT_STAGE;
+constexpr int AT_NBARS = 2 * AT_S + 2;                   // full, empty, accf, drain
+constexpr int AT_MISC = 1024;                            // barriers, flags, reduction scratch
+constexpr int AT_RECV = AT_RB * AT_BM * 4;               // 32 KB: partials pushed by the cluster
+constexpr int AT_SMEM = AT_TILES + AT_MISC + AT_RECV + 1024;
+static_assert(AT_NBARS * 8 + 16 + AT_BM * 4 <= AT_MISC, "misc area too small");
+static_assert(AT_STAGE % 1024 == 0, "stages must keep the 1024-byte swizzle alignment");
+
+enum { AT_FORWARD = 0, AT_TERMINAL = 1, AT_ADJOINT = 2 };
+
+struct AdjTc {
+    int n, R, ld, ldk, mpad, mtiles, nrb, kblocks, kb_per, splits;
+    __nv_bfloat16 *jb = nullptr;    // [mpad][ldk]
+    __nv_bfloat16 *xs = nullptr;    // [nrb * 192][ldk]
+    CUtensorMap mapA, mapB;
+};
+
+struct AdjTcArgs {
+    int n, R, ld, nrb, kblocks, kb_per, splits;   // splits = cluster size (1, 2, 4 or 8)
+    const float *h;
+    const float *X, *P;
+    float *Qn, *Pn, *Fo;
+    const float *LB;
+    float *LQ, *LP;
+    float *obj_part;                               // terminal: [tiles][splits]
+    StepParams sp;
+    const float *zeta, *dt;
+    int t;
+    int *err;
+    long long limit_ns;
+};
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+// Cluster barrier halves (every thread of every CTA of the cluster takes
+// part; not .aligned, so warps need not be converged).
+__device__ __forceinline__ void cluster_arrive_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_arrive_release() {
+    asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+    asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// 16-byte store into CTA `rank`'s shared memory at this CTA's address
+// `local_addr` (fire and forget; the next cluster barrier orders it).
+__device__ __forceinline__ void st_dsmem_v4(uint32_t local_addr, uint32_t rank, float4 v) {
+    asm volatile(
+        "{\n\t.reg .b32 ra;\n\tmapa.shared::cluster.u32 ra, %0, %1;\n\t"
+        "st.shared::cluster.v4.f32 [ra], {%2, %3, %4, %5};\n\t}" ::"r"(local_addr),
+        "r"(rank), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w)
+        : "memory");
+}
+
+// Epilogue of 16 replicas r0 .. r0+15 of spin i from G = (J X^T)_ir.  The
+// inputs of all 16 are loaded before the first store (X, P and LB are never
+// written by this kernel), so the loads overlap instead of waiting behind
+// the stores one element at a time.
+template <int MODE, int CNT = 16>
+__device__ __forceinline__ void at_apply16(const AdjTcArgs &a, int i, int r0, const float *G, float hi, float zt,
+                                           float dtt, float dtm, float &objp) {
+    float u0[CNT], u1[CNT];
+#pragma unroll
+    for (int u = 0; u < CNT; ++u) {
+        const int r = r0 + u;
+        const size_t e = (size_t)r * a.ld + i;
+        const bool v = r < a.R;
+        u0[u] = v ? __ldg(a.X + e) : 0.f;
+        if (MODE == AT_FORWARD) u1[u] = v ? __ldg(a.P + e) : 0.f;
+        if (MODE == AT_ADJOINT) u1[u] = v ? __ldg(a.LB + e) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < CNT; ++u) {
+        const int r = r0 + u;
+        if (r >= a.R) continue;
+        const size_t e = (size_t)r * a.ld + i;
+        if (MODE == AT_FORWARD) {
+            const float F = G[u] + hi;
+            float qo, po;
+            integrate<float>(u0[u], u1[u], F, zt, dtt, dtm, a.sp, qo, po);
+            a.Qn[e] = qo;
+            a.Pn[e] = po;
+            a.Fo[e] = F;
+        } else if (MODE == AT_TERMINAL) {
+            const float x = u0[u];
+            a.LQ[e] = -(G[u] + hi);
+            a.LP[e] = 0.f;
+            objp += -0.5f * x * G[u] - hi * x;
+        } else {
+            const float la = u0[u];
+            a.LQ[e] = u1[u] + dtt * (-a.sp.k * la + zt * G[u]);
+            a.LP[e] = la;
+        }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(AT_THREADS, 1)
+    k_adj_tc(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+             const __grid_constant__ AdjTcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar0 = sbase + AT_TILES;
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (AT_S + s); };
+    const uint32_t accf_bar = bar0 + 8u * (2 * AT_S);
+    const uint32_t drain_bar = bar0 + 8u * (2 * AT_S + 1);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + AT_TILES + AT_NBARS * 8);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + AT_TILES + AT_NBARS * 8 + 4);
+    float *red = reinterpret_cast<float *>(smem + AT_TILES + AT_NBARS * 8 + 16);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const int mn = blockIdx.x / a.splits, ks = blockIdx.x % a.splits;
+    const int mt = mn / a.nrb, rb = mn % a.nrb;
+    const int kb0 = ks * a.kb_per;
+    const int nk = min(a.kblocks, kb0 + a.kb_per) - kb0;   // >= 1 by construction
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < AT_S; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        mbar_init(accf_bar, 1);
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "n"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // phase 1 of the cluster barrier: every CTA of the cluster has started
+    // (its shared memory may receive partials once the phase completes)
+    if (a.splits > 1) cluster_arrive_relaxed();
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        if (lane == 0) {
+            int issued = 0;
+            for (int c = 0; c < nk; ++c) {
+                const int s = c % AT_S;
+                const uint32_t ph = (uint32_t)(c / AT_S) & 1u;
+                if (!mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns)) break;
+                const uint32_t dA = sbase + s * AT_STAGE;
+                mbar_arrive_expect_tx(full_bar(s), (uint32_t)AT_STAGE);
+                tma_load_2d(dA, &mapA, full_bar(s), (kb0 + c) * AT_BK, mt * AT_BM);
+                tma_load_2d(dA + AT_A_BYTES, &mapB, full_bar(s), (kb0 + c) * AT_BK, rb * AT_BN);
+                ++issued;
+            }
+            // Let every copy land before the CTA exits.
+            const int first = issued > AT_S ? issued - AT_S : 0;
+            for (int c = first; c < issued; ++c) {
+                const unsigned long long t0 = globaltimer_ns();
+                while (!mbar_try_wait(full_bar(c % AT_S), (uint32_t)(c / AT_S) & 1u)) {
+                    if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                        atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
+                        break;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16(AT_BM, AT_BN);
+            bool ok = true;
+            for (int c = 0; c < nk; ++c) {
+                const int s = c % AT_S;
+                if (!mbar_wait(full_bar(s), (uint32_t)(c / AT_S) & 1u, a.err, abort_flag, a.limit_ns)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint64_t ad = sdesc_sw128(sbase + s * AT_STAGE);
+                const uint64_t bd = sdesc_sw128(sbase + s * AT_STAGE + AT_A_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < AT_BK / 16; ++kk)
+                    mma_bf16(tmem, ad + 2u * kk, bd + 2u * kk, idesc, (c != 0 || kk != 0) ? 1u : 0u);
+                mma_commit(empty_bar(s));
+            }
+            if (ok) mma_commit(accf_bar);
+            mma_commit(drain_bar);
+            const unsigned long long t0 = globaltimer_ns();
+            while (!mbar_try_wait(drain_bar, 0u)) {
+                if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                    atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
+                    break;
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue (4 warps)
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        const int et = threadIdx.x - 64;             // 0..127 among the epilogue threads
+        const int i = mt * AT_BM + row;
+        const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+        bool ok = true;
+        if (lane == 0) ok = mbar_wait(accf_bar, 0u, a.err, abort_flag, a.limit_ns);
+        ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+        // all four warps agree on success before any partial is used
+        epi_bar();
+        if (!ok) *abort_flag = 1;
+        epi_bar();
+        ok = (*abort_flag == 0);
+        tc_fence_after();
+        const float hi = (a.h && i < a.n) ? a.h[i] : 0.f;
+        float zt = 0.f, dtt = 0.f, dtm = 0.f;
+        if (MODE != AT_TERMINAL) {
+            zt = a.zeta[a.t];
+            dtt = a.dt[a.t];
+            dtm = dtt / a.sp.m;
+        }
+        float objp = 0.f;
+        // Split-K partials are pushed to their owners: replicas [j S, j S + S)
+        // of the tile belong to cluster rank j, S = 64 / splits.  The
+        // receive buffer of rank j holds [source rank][S / 4][128 rows] of
+        // four-replica chunks.
+        const int S = AT_RB / a.splits;
+        const uint32_t recv = sbase + AT_TILES + AT_MISC;
+        if (a.splits > 1) cluster_wait_acquire();   // phase 1: all peers are running
+        if (ok) {
+#pragma unroll 1
+            for (int ch = 0; ch < AT_RB / 32; ++ch) {
+                uint32_t v0[32], v1[32], v2[32];
+                tmem_ld32(tmem + lane_off + ch * 32, v0);
+                tmem_ld32(tmem + lane_off + AT_RB + ch * 32, v1);
+                tmem_ld32(tmem + lane_off + 2 * AT_RB + ch * 32, v2);
+                tmem_wait_ld();
+                float G[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    G[j] = (__uint_as_float(v0[j]) + __uint_as_float(v1[j])) + __uint_as_float(v2[j]);
+                if (a.splits > 1) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int rl = ch * 32 + 4 * q;          // first replica of the chunk
+                        const int owner = rl / S, c4 = (rl % S) / 4;
+                        const uint32_t off = (uint32_t)(((ks * (S / 4) + c4) * AT_BM + row) * 16);
+                        st_dsmem_v4(recv + off, (uint32_t)owner,
+                                    make_float4(G[4 * q], G[4 * q + 1], G[4 * q + 2], G[4 * q + 3]));
+                    }
+                } else if (i < a.n) {
+                    at_apply16<MODE>(a, i, rb * AT_RB + ch * 32, G, hi, zt, dtt, dtm, objp);
+                    at_apply16<MODE>(a, i, rb * AT_RB + ch * 32 + 16, G + 16, hi, zt, dtt, dtm, objp);
+                }
+            }
+        }
+        if (MODE == AT_TERMINAL && a.splits == 1) {
+            red[et] = objp;
+            epi_bar();
+            if (et == 0) {
+                CompSum<float> s;
+                s.init();
+                for (int w = 0; w < AT_BM; ++w) s.add(red[w]);
+                a.obj_part[mn] = s.value();
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (a.splits > 1) {
+        // The epilogue warps took phase 1 before pushing; the others take it
+        // here.  Phase 2: every push of the cluster has landed.
+        if (warp < 2) cluster_wait_acquire();
+        cluster_arrive_release();
+        cluster_wait_acquire();
+        if (warp >= 2) {
+            const int quad = warp & 3;
+            const int row = quad * 32 + lane;
+            const int et = threadIdx.x - 64;
+            const int i = mt * AT_BM + row;
+            const float hi = (a.h && i < a.n) ? a.h[i] : 0.f;
+            float zt = 0.f, dtt = 0.f, dtm = 0.f;
+            if (MODE != AT_TERMINAL) {
+                zt = a.zeta[a.t];
+                dtt = a.dt[a.t];
+                dtm = dtt / a.sp.m;
+            }
+            float objp = 0.f;
+            const int S = AT_RB / a.splits;
+            const int nc = S / 4;
+            const float4 *rv = reinterpret_cast<const float4 *>(smem + AT_TILES + AT_MISC);
+            // add the pushed partials of this CTA's replicas in source-rank order
+            float G[32];
+#pragma unroll
+            for (int u = 0; u < 32; ++u) G[u] = 0.f;
+            for (int p = 0; p < a.splits; ++p) {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    if (q < nc) {
+                        const float4 v = rv[(p * nc + q) * AT_BM + row];
+                        G[4 * q] += v.x;
+                        G[4 * q + 1] += v.y;
+                        G[4 * q + 2] += v.z;
+                        G[4 * q + 3] += v.w;
+                    }
+                }
+            }
+            const int rl0 = ks * S;
+            if (*abort_flag == 0 && i < a.n) {
+                if (S == 32) {
+                    at_apply16<MODE, 32>(a, i, rb * AT_RB + rl0, G, hi, zt, dtt, dtm, objp);
+                } else if (S == 16) {
+                    at_apply16<MODE, 16>(a, i, rb * AT_RB + rl0, G, hi, zt, dtt, dtm, objp);
+                } else {
+                    at_apply16<MODE, 8>(a, i, rb * AT_RB + rl0, G, hi, zt, dtt, dtm, objp);
+                }
+            }
+            if (MODE == AT_TERMINAL) {
+                float *red = reinterpret_cast<float *>(smem + AT_TILES + AT_NBARS * 8 + 16);
+                red[et] = objp;
+                epi_bar();
+                if (et == 0) {
+                    CompSum<float> s;
+                    s.init();
+                    for (int w = 0; w < AT_BM; ++w) s.add(red[w]);
+                    a.obj_part[mn * a.splits + ks] = s.value();
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(256) : "memory");
+    }
+}
+
+// Split of the FP32 operand X [R][ld] into bf16 pieces, laid out as the B
+// operand rows [rb][piece][64][ldk] (zero for padded replicas and spins).
+__global__ void k_adj_split(const float *X, int n, int R, int ld, int nrb, int ldk, __nv_bfloat16 *xs) {
+    const long long total = (long long)nrb * AT_RB * ldk;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(e % ldk);
+        const int rr = (int)(e / ldk);               // rb * 64 + rl
+        const int rb = rr / AT_RB, rl = rr % AT_RB;
+        const float x = (rr < R && j < n) ? X[(size_t)rr * ld + j] : 0.f;
+        const __nv_bfloat16 p0 = __float2bfloat16_rn(x);
+        const float r1 = x - __bfloat162float(p0);
+        const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
+        const float r2 = r1 - __bfloat162float(p1);
+        const __nv_bfloat16 p2 = __float2bfloat16_rn(r2);
+        __nv_bfloat16 *base = xs + ((size_t)rb * AT_BN + rl) * ldk + j;
+        base[0] = p0;
+        base[(size_t)AT_RB * ldk] = p1;
+        base[(size_t)2 * AT_RB * ldk] = p2;
+    }
+}
+
+__global__ void k_adj_jb(const float *J, int n, int ld, __nv_bfloat16 *out, int ldk, int mpad) {
+    const long long total = (long long)mpad * ldk;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ldk), j = (int)(e % ldk);
+        out[e] = __float2bfloat16_rn((i < n && j < n) ? J[(size_t)i * ld + j] : 0.f);
+    }
+}
+
+void adj_tc_free(AdjTc *t) {
+    if (!t) return;
+    if (t->jb) cudaFree(t->jb);
+    if (t->xs) cudaFree(t->xs);
+    delete t;
+}
+
+int adj_tc_nobj(const AdjTc *t) { return t->mtiles * t->nrb * t->splits; }
+int adj_tc_splits(const AdjTc *t) { return t ? t->splits : 0; }
+
+template <int MODE>
+static cudaError_t launch_adj(const AdjTc *t, const AdjTcArgs &a, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(t->mtiles * t->nrb * t->splits));
+    cfg.blockDim = dim3(AT_THREADS);
+    cfg.dynamicSmemBytes = AT_SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)t->splits;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_adj_tc<MODE>, t->mapA, t->mapB, a);
+}
+
+si_status adj_tc_prepare(Ctx *c, AdjTc **out) {
+    if (c->g_tc) {
+        *out = c->g_tc;
+        return SI_OK;
+    }
+    AdjTc *t = new AdjTc();
+    t->n = c->n;
+    t->R = c->R;
+    t->ld = c->ldj;
+    t->ldk = round_up(c->n, AT_BK);
+    t->mpad = round_up(c->n, AT_BM);
+    t->mtiles = t->mpad / AT_BM;
+    t->nrb = cdiv(c->R, AT_RB);
+    t->kblocks = t->ldk / AT_BK;
+    const int tiles = t->mtiles * t->nrb;
+    auto fail = [&](si_status e) {
+        adj_tc_free(t);
+        return e;
+    };
+    for (int mode = 0; mode < 3; ++mode) {
+        cudaError_t e = mode == 0 ? cudaFuncSetAttribute(k_adj_tc<AT_FORWARD>,
+                                                         cudaFuncAttributeMaxDynamicSharedMemorySize, AT_SMEM)
+                        : mode == 1 ? cudaFuncSetAttribute(k_adj_tc<AT_TERMINAL>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, AT_SMEM)
+                                    : cudaFuncSetAttribute(k_adj_tc<AT_ADJOINT>,
+                                                           cudaFuncAttributeMaxDynamicSharedMemorySize, AT_SMEM);
+        if (e != cudaSuccess) {
+            set_error("si_grad: cannot reserve shared memory for the tensor-core kernel");
+            return fail(SI_ERR_CUDA);
+        }
+    }
+    // K split = cluster size in {1, 2, 4, 8}: about one wave of CTAs (one per
+    // SM), every split non-empty, and all clusters resident at once (an
+    // 8-CTA cluster needs 8 free SMs of one GPC).
+    int splits = 8;
+    while (splits > 1 && (tiles * splits > c->num_sms || (splits - 1) * cdiv(t->kblocks, splits) >= t->kblocks))
+        splits >>= 1;
+    while (splits > 1) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(tiles * splits));
+        cfg.blockDim = dim3(AT_THREADS);
+        cfg.dynamicSmemBytes = AT_SMEM;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)splits;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_adj_tc<AT_FORWARD>, &cfg) == cudaSuccess &&
+            nclusters >= tiles)
+            break;
+        cudaGetLastError();
+        splits >>= 1;
+    }
+    t->splits = splits;
+    t->kb_per = cdiv(t->kblocks, splits);
+    if (cudaMalloc((void **)&t->jb, sizeof(__nv_bfloat16) * (size_t)t->mpad * t->ldk) != cudaSuccess ||
+        cudaMalloc((void **)&t->xs, sizeof(__nv_bfloat16) * (size_t)t->nrb * AT_BN * t->ldk) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("si_grad: out of device memory for the tensor-core workspace");
+        return fail(SI_ERR_OOM);
+    }
+    if (cudaMemsetAsync(t->xs, 0, sizeof(__nv_bfloat16) * (size_t)t->nrb * AT_BN * t->ldk, c->stream) !=
+        cudaSuccess) {
+        set_error("si_grad: cudaMemsetAsync failed");
+        return fail(SI_ERR_CUDA);
+    }
+    k_adj_jb<<<std::min(4096, cdiv((long long)t->mpad * t->ldk, 256)), 256, 0, c->stream>>>(
+        (const float *)c->dJ, c->n, c->ldj, t->jb, t->ldk, t->mpad);
+    if (cudaGetLastError() != cudaSuccess) {
+        set_error("si_grad: J conversion launch failed");
+        return fail(SI_ERR_CUDA);
+    }
+    si_status s;
+    if ((s = tc_make_map_bf16(&t->mapA, t->jb, t->ldk, t->mpad, AT_BK, AT_BM)) != SI_OK) return fail(s);
+    if ((s = tc_make_map_bf16(&t->mapB, t->xs, t->ldk, t->nrb * AT_BN, AT_BK, AT_BN)) != SI_OK) return fail(s);
+    c->launches += 1;
+    c->g_tc = t;
+    *out = t;
+    return SI_OK;
+}
+
+si_status adj_tc_gemm(Ctx *c, AdjTc *t, int mode, const float *X, const float *P, float *Qn, float *Pn,
+                      float *Fo, const float *LB, float *LQ, float *LP, float *obj_part, int tstep) {
+    k_adj_split<<<std::min(2048, cdiv((long long)t->nrb * AT_RB * t->ldk, 256)), 256, 0, c->stream>>>(
+        X, t->n, t->R, t->ld, t->nrb, t->ldk, t->xs);
+    SI_CUDA_TRY(cudaGetLastError());
+    AdjTcArgs a{};
+    a.n = t->n;
+    a.R = t->R;
+    a.ld = t->ld;
+    a.nrb = t->nrb;
+    a.kblocks = t->kblocks;
+    a.kb_per = t->kb_per;
+    a.splits = t->splits;
+    a.h = c->has_h ? c->dhf : nullptr;
+    a.X = X;
+    a.P = P;
+    a.Qn = Qn;
+    a.Pn = Pn;
+    a.Fo = Fo;
+    a.LB = LB;
+    a.LQ = LQ;
+    a.LP = LP;
+    a.obj_part = obj_part;
+    a.sp = StepParams{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max, 0, 0};
+    a.zeta = c->dzeta;
+    a.dt = c->ddt;
+    a.t = tstep;
+    a.err = c->derr;
+    a.limit_ns = c->spin_limit_ns;
+    cudaError_t e = mode == AT_FORWARD    ? launch_adj<AT_FORWARD>(t, a, c->stream)
+                    : mode == AT_TERMINAL ? launch_adj<AT_TERMINAL>(t, a, c->stream)
+                                          : launch_adj<AT_ADJOINT>(t, a, c->stream);
+    SI_CUDA_TRY(e);
+    c->launches += 2;
+    return SI_OK;
+}
+
+}  // namespace si

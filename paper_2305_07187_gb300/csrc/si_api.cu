@@ -105,6 +105,8 @@ static void free_ctx(Ctx *c) {
                     c->dE, c->dC, c->dEf, c->dstage, c->g_ws, c->e_sig, c->e_sum};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    adj_tc_free(c->g_tc);
+    if (c->g_graph) cudaGraphExecDestroy(c->g_graph);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     delete c;
@@ -188,6 +190,7 @@ static si_status create_impl(Ctx *c, const float *J, const float *h) {
         return SI_ERR_INVALID_ARG;
     }
     c->integer_j = !(flags & VF_NOT_INT8);
+    c->bf16_j = !(flags & VF_NOT_BF16);
     c->has_h = (h != nullptr);
     c->integer_h = !(flags & VF_H_NOT_INT8);
     c->s_upper = c->integer_j ? s_upper : 0;
@@ -524,6 +527,15 @@ si_status si_describe(const si_ctx *ctx, char *buf, int32_t len) {
         std::snprintf(buf, len, "plain_persistent prec=%s n=%d R=%d", prec[c->prm.prec], c->n, c->R);
     } else {
         std::snprintf(buf, len, "simt_tiled prec=%s n=%d R=%d tile=64x64", prec[c->prm.prec], c->n, c->R);
+    }
+    if (c->g_path) {
+        const size_t l = std::strlen(buf);
+        if ((int)l + 1 < len) {
+            if (c->g_path == 2)
+                std::snprintf(buf + l, len - l, " grad=tcgen05-bf16x3 ksplit=%d", adj_tc_splits(c->g_tc));
+            else
+                std::snprintf(buf + l, len - l, " grad=cuda-core");
+        }
     }
     return SI_OK;
 }

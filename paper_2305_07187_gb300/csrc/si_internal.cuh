@@ -42,6 +42,7 @@ struct StepParams {
 };
 
 enum class Path { PLAIN_PERSISTENT, SIMT_TILED, TENSOR };
+struct AdjTc;
 
 struct Ctx {
     si_params prm;
@@ -51,6 +52,7 @@ struct Ctx {
     Path path = Path::SIMT_TILED;
     bool integer_j = false;      // every J_ij integer in [-127, 127]
     bool integer_h = true;       // h NULL or integer in [-127, 127]
+    bool bf16_j = false;         // every J_ij exact in bf16
     bool has_h = false;
     long long s_upper = 0;       // sum_{i<j} J_ij (integer J only)
     long long spin_limit_ns = 2000000000LL;
@@ -108,6 +110,14 @@ struct Ctx {
     // Gradient workspace (allocated lazily by si_grad).
     void *g_ws = nullptr;
     size_t g_ws_bytes = 0;
+    // Tensor-core adjoint products (FP32 contexts with bf16-exact J),
+    // created by the first si_grad, owned by the context.
+    AdjTc *g_tc = nullptr;
+    cudaGraphExec_t g_graph = nullptr;   // captured adjoint sweep
+    int g_graph_key = -1;
+    void *g_graph_ws = nullptr;
+    int g_graph_launches = 0;
+    int g_path = 0;              // 0: no si_grad yet, 1: CUDA cores, 2: tensor cores
 };
 
 // ------------------------------------------------------------ helpers
@@ -156,6 +166,14 @@ si_status tc_convert_j(const float *J_dev, int n, void *out, int ldk, int mpad, 
                        cudaStream_t st);
 
 // Adjoint, si_adjoint.cu.
+// Tensor-core products of the adjoint sweep, si_adjoint_tc.cu.
+si_status adj_tc_prepare(Ctx *c, AdjTc **out);
+si_status adj_tc_gemm(Ctx *c, AdjTc *a, int mode, const float *X, const float *P, float *Qn, float *Pn,
+                      float *Fo, const float *LB, float *LQ, float *LP, float *obj_part, int t);
+int adj_tc_nobj(const AdjTc *a);
+int adj_tc_splits(const AdjTc *a);
+void adj_tc_free(AdjTc *a);
+
 si_status adjoint_grad(Ctx *c, int steps, float *g_zeta, float *g_dt,
                        float *g_k, float *objective, const float *q_init,
                        const float *p_init);
@@ -168,7 +186,8 @@ enum : unsigned long long {
     VF_NOT_INT8 = 1ull << 3,
     VF_NOT_E4M3 = 1ull << 4,
     VF_H_NOT_INT8 = 1ull << 5,
-    VF_H_NONFINITE = 1ull << 6
+    VF_H_NONFINITE = 1ull << 6,
+    VF_NOT_BF16 = 1ull << 7
 };
 
 }  // namespace si

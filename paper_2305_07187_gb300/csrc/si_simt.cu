@@ -235,6 +235,7 @@ __global__ void k_validate(const float *J, const float *h, int n, int prec,
         if (isfinite(v)) {
             __nv_fp8_e4m3 e8(v);
             if ((float)e8 != v) f |= VF_NOT_E4M3;
+            if (__bfloat162float(__float2bfloat16_rn(v)) != v) f |= VF_NOT_BF16;
         }
     }
     if (h) {

@@ -65,15 +65,24 @@ def test_fp64_adjoint_against_central_differences():
     assert abs(gk - fd) <= 1e-4 * scale
 
 
-def test_fp32_adjoint_close_to_oracle():
+@pytest.mark.parametrize("kind,n,R", [("tensor", 96, 8), ("tensor", 300, 70), ("simt-env", 96, 8),
+                                      ("simt-j", 96, 8)])
+def test_fp32_adjoint_close_to_oracle(kind, n, R, monkeypatch):
     """FP32 adjoint vs the FP64 reverse mode on a short horizon: the FP32
     forward drifts from the FP64 one by rounding, amplified by the dynamics,
-    so the bar is 1e-3 relative to the largest component."""
-    n, R, T = 96, 8, 30
+    so the bar is 1e-3 relative to the largest component.  Both product
+    paths: tensor cores (J exact in bf16; three-piece operand split, ragged
+    n and R > 64) and CUDA cores (forced, or J not exact in bf16)."""
+    T = 30
     J, q0, zeta, dt = _case(n, R, T, seed=9)
+    if kind == "simt-env":
+        monkeypatch.setenv("SI_ADJOINT_SIMT", "1")
+    if kind == "simt-j":
+        J = (J / np.float32(3.0)).astype(np.float32)
     with b.Context(J, replicas=R, steps=T, prec="fp32", ckpt_every=10) as ctx:
         obj, gz, gd, gk = ctx.grad(zeta, dt, q0)
         kw = params_f64(ctx)
+        assert ("grad=tcgen05-bf16x3" if kind == "tensor" else "grad=cuda-core") in ctx.describe()
     kw.pop("wall_zero_p")
     o_obj, o_gz, o_gd, o_gk = oracle.grad(J, None, zeta, dt, q0, **kw)
     assert abs(obj - o_obj) <= 1e-4 * abs(o_obj)
@@ -94,16 +103,23 @@ def test_checkpoint_interval_does_not_change_the_gradient():
 
 def test_gradient_workload_n2000_r64_t500():
     """The gradient workload: N=2000 +-1, R=64, T=500, checkpoints every 50.
-    The objective equals the relaxed energy of the final state of si_run (same
-    forward kernels), evaluated by the oracle."""
+    The objective equals the relaxed energy, evaluated by the oracle, of the
+    final state of the gradient's own forward sweep (si_get_state after
+    si_grad); that state keeps the walls and stays close to si_run's."""
     n, R, T = 2000, 64, 500
     J, q0, zeta, dt = _case(n, R, T, seed=1)
     with b.Context(J, replicas=R, steps=T, prec="fp32", ckpt_every=50) as ctx:
         obj, gz, gd, gk = ctx.grad(zeta, dt, q0)
+        assert "grad=tcgen05-bf16x3" in ctx.describe()
+        qT, pT = ctx.get_state()
         q, p, s = ctx.run(zeta, dt, q0)
     assert np.isfinite(gz).all() and np.isfinite(gd).all() and np.isfinite(gk)
-    ref = oracle.relaxed_energy(J, None, q).sum()
+    assert np.abs(qT).max() <= b.SQRT2_F32 and np.abs(pT).max() <= 2.0
+    ref = oracle.relaxed_energy(J, None, qT).sum()
     assert abs(obj - ref) <= 1e-5 * abs(ref)
+    # chaotic divergence from si_run's trajectory stays a small fraction
+    run_E = oracle.relaxed_energy(J, None, q).sum()
+    assert abs(ref - run_E) <= 1e-2 * abs(run_E)
 
 
 def test_autograd_function_and_schedule_tuning():
