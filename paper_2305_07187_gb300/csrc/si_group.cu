@@ -253,6 +253,16 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                 if (two_acc) tmem_ld16(tacc + 128 + c * 16, vg);
                 tmem_wait_ld();
                 if (row_ok) {
+                    // load the 16 replicas' state before the first store, so
+                    // the loads overlap instead of queueing behind the stores
+                    float qv[16], pv[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int r = tl.rb * in.bn + c * 16 + j;
+                        const size_t e = (size_t)r * in.n + i;
+                        qv[j] = r < in.R ? in.q_state[e] : 0.f;
+                        pv[j] = r < in.R ? in.p_state[e] : 0.f;
+                    }
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const int r = tl.rb * in.bn + c * 16 + j;
@@ -261,7 +271,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                         if (two_acc) F += __uint_as_float(vg[j]);
                         const size_t e = (size_t)r * in.n + i;
                         float qo, po;
-                        integrate<float>(in.q_state[e], in.p_state[e], F + hi, zt, dtt, dtm, a.sp, qo, po);
+                        integrate<float>(qv[j], pv[j], F + hi, zt, dtt, dtm, a.sp, qo, po);
                         in.q_state[e] = qo;
                         in.p_state[e] = po;
                         if (!a.last) qn[(size_t)r * in.ldk + i] = __float2bfloat16_rn(qo);
