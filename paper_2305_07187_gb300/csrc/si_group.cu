@@ -113,11 +113,17 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
     auto phase_of = [&](uint32_t c) -> uint32_t {
         return a.single ? (c / (uint32_t)S) & 1u : (c / (uint32_t)HS) & 1u;
     };
+    // The hot loops track (index within the ring, phase) incrementally; the
+    // divisions above are only for the drain at the end.
+    const int ring_len = a.single ? S : HS;
+    auto ring_stage = [&](int k, int ring) -> int { return a.single ? k : 2 * k + ring; };
 
     if (warp == 0) {
         // ---------------------------------------------- TMA producer
         if (lane == 0) {
             uint32_t cnt0 = 0u, cnt1 = 0u;   // stages armed in ring 0 / ring 1
+            int rk0 = 0, rk1 = 0;            // next index within ring 0 / 1
+            uint32_t rph0 = 0u, rph1 = 0u;   // and its phase parity
             bool ok = true;
             for (int k = blockIdx.x; k < a.ntiles && ok; k += gridDim.x) {
                 const GroupTile tl = a.tiles[k];
@@ -128,11 +134,16 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                 const int yq = plane_in * in.rpad + tl.rb * in.bn;
                 for (int kb = 0; kb < in.kblocks; ++kb) {
                     const int ring = a.single ? 0 : (kb & 1);
-                    const uint32_t c = ring ? cnt1 : cnt0;
-                    const int s = stage_of(c, ring);
-                    const uint32_t ph = phase_of(c);
+                    int &rk = ring ? rk1 : rk0;
+                    uint32_t &rph = ring ? rph1 : rph0;
+                    const int s = ring_stage(rk, ring);
+                    const uint32_t ph = rph;
                     if (!mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
                     if (ring) ++cnt1; else ++cnt0;
+                    if (++rk == ring_len) {
+                        rk = 0;
+                        rph ^= 1u;
+                    }
                     const uint32_t dA = sbase + s * a.stage_bytes;
                     mbar_arrive_expect_tx(full_bar(s), bytes);
                     tma_load_2d(dA, mJ, full_bar(s), kb * GR_BK, tl.mt * GR_BM);
@@ -162,7 +173,8 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
         // the per-tile handshake.
         if (lane == 0) {
             const int w = warp - 1;
-            uint32_t c = 0;  // position in this warp's ring of stages
+            int rk = 0;          // index within this warp's ring of stages
+            uint32_t rph = 0u;   // and its phase parity
             bool ok = true;
             int u = 0;
             for (int k = blockIdx.x; k < a.ntiles && ok; k += gridDim.x, ++u) {
@@ -181,9 +193,13 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                 if (a.single) {
                     if (w == 0) {
                         const uint32_t d_tmem = tmem + (uint32_t)slot * 256u;
-                        for (int kb = 0; kb < in.kblocks; ++kb, ++c) {
-                            const int s = stage_of(c, 0);
-                            if (!mbar_wait(full_bar(s), phase_of(c), a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                        for (int kb = 0; kb < in.kblocks; ++kb) {
+                            const int s = ring_stage(rk, 0);
+                            if (!mbar_wait(full_bar(s), rph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                            if (++rk == ring_len) {
+                                rk = 0;
+                                rph ^= 1u;
+                            }
                             tc_fence_after();
                             const uint64_t ad = sdesc_sw128(sbase + s * a.stage_bytes);
                             const uint64_t bd = ad + (uint64_t)(GR_A_BYTES >> 4);
@@ -195,9 +211,13 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                     }
                 } else {
                     const uint32_t d_tmem = tmem + (uint32_t)slot * 256u + (w == 0 ? 0u : 128u);
-                    for (int kb = w; kb < in.kblocks; kb += 2, ++c) {
-                        const int s = stage_of(c, w);
-                        if (!mbar_wait(full_bar(s), phase_of(c), a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                    for (int kb = w; kb < in.kblocks; kb += 2) {
+                        const int s = ring_stage(rk, w);
+                        if (!mbar_wait(full_bar(s), rph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                        if (++rk == ring_len) {
+                            rk = 0;
+                            rph ^= 1u;
+                        }
                         tc_fence_after();
                         const uint64_t ad = sdesc_sw128(sbase + s * a.stage_bytes);
                         const uint64_t bd = ad + (uint64_t)(GR_A_BYTES >> 4);
