@@ -511,6 +511,21 @@ def run_grad(args):
     return 0
 
 
+def ncu_case_grad(args):
+    """Profiling case of the differentiation workload: N=2000 +-1, R=64,
+    --time-steps steps (checkpoints every 10), one warm-up and one profiled
+    si_grad."""
+    from paper_2305_07187_gb300 import _binding as b
+    T = args.time_steps
+    J = inputs.pm1_coupling(GRAD_N, seed=1)
+    q0 = inputs.positions(GRAD_N, GRAD_R, seed0=100)
+    with b.Context(J, replicas=GRAD_R, steps=T, prec="fp32", ckpt_every=10) as ctx:
+        for _ in range(2):
+            ctx.grad(inputs.zeta_ramp(T), inputs.dt_const(T), q0)
+        print(ctx.describe())
+    return 0
+
+
 def ncu_case_grouped(args):
     """Profiling case of the grouped path: the first --group-count instances
     of the uneven batch, autotuned, then one run of --time-steps steps."""
@@ -634,6 +649,8 @@ def main():
         _build.build()
     if args.ncu_case and args.workload == "grouped":
         return ncu_case_grouped(args)
+    if args.ncu_case and args.workload == "grad":
+        return ncu_case_grad(args)
     if args.ncu_case:
         return ncu_case(args)
     if args.workload == "grouped":
