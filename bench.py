@@ -511,6 +511,47 @@ def run_grad(args):
     return 0
 
 
+def run_study(args):
+    """Synthetic studies on the batched workload (N=2000 +-1, R=1024,
+    T=2000): final-cut distributions of the zeta strategies (fixed 0.8 zeta0,
+    fixed 10 zeta0, ramps with plateaus of 1, 200 and 1000 steps, the
+    gradient-tuned schedule) and of the update-order / wall variants, plus the
+    energy trajectory of the linear ramp read out every 100 steps."""
+    from paper_2305_07187_gb300 import _binding as b
+    from paper_2305_07187_gb300 import study
+    n, R, T = N_SPINS, REPLICAS, T_STEPS
+    J = inputs.pm1_coupling(n, seed=1)
+    q0 = inputs.positions(n, R, seed0=100)
+    dt = inputs.dt_const(T)
+    knots, _ = tuned_knots(b)
+    t0 = time.perf_counter()
+    strategies = {}
+    for name, z in study.zeta_strategies(T, tuned_knots=knots).items():
+        cuts, _ = study.final_cuts(J, q0, z, dt)
+        strategies[name] = study.summarize(cuts)
+    variants = {}
+    for name, kw in (("literal-eq5", {"update_order": 1}), ("wall-zero-p", {"wall_zero_p": 1}),
+                     ("wall-at-1", {"q_max": 1.0})):
+        cuts, _ = study.final_cuts(J, q0, inputs.zeta_ramp(T), dt, **kw)
+        variants[name] = study.summarize(cuts)
+    steps, E, _ = study.energy_trajectory(J, q0, inputs.zeta_ramp(T), dt, 100)
+    wall = time.perf_counter() - t0
+    line = {
+        "metric": "median final cut (linear ramp)", "value": strategies["ramp-L1"]["median"], "unit": "cut",
+        "higher_is_better": True, "n_gpus": 1, "data": "synthetic",
+        "config": {"workload": "study: N=2000 +-1 complete graph (seed 1), R=1024 (seeds 100..1123), T=2000, "
+                               "dt=0.2, J e4m3-exact / q bf16 tensor path; tuned = 8 zeta knots from 10 Adam "
+                               "steps of si_grad at R=64, T=500, stretched to T=2000"},
+        "strategies": strategies, "variants_linear_ramp": variants,
+        "trajectory_linear_ramp": {"steps": [int(x) for x in steps],
+                                   "mean_energy": [float(x) for x in E.mean(axis=1)],
+                                   "min_energy": [int(x) for x in E.min(axis=1)]},
+        "wall_s": wall,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def ncu_case_grad(args):
     """Profiling case of the differentiation workload: N=2000 +-1, R=64,
     --time-steps steps (checkpoints every 10), one warm-up and one profiled
@@ -637,7 +678,7 @@ def main():
     ap.add_argument("--time-steps", type=int, default=T_STEPS)
     ap.add_argument("--group-count", type=int, default=256,
                     help="grouped workload: number of instances (profiling uses a prefix)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "grouped", "scale", "grad"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "grouped", "scale", "grad", "study"],
                     help="batched: N=2000, R=1024, T=2000 (default); grouped: 256 uneven "
                          "instances, T=1000, one grouped launch per step")
     args = ap.parse_args()
@@ -659,6 +700,8 @@ def main():
         return run_scale(args)
     if args.workload == "grad":
         return run_grad(args)
+    if args.workload == "study":
+        return run_study(args)
 
     import torch
     import torch.distributed as dist
