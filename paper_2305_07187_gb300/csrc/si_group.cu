@@ -46,6 +46,7 @@ struct GroupInst {
 
 struct GroupTile {
     int inst, mt, rb, cost;
+    int kb_off, kb_cnt;        // the M tile's non-zero K blocks: kbl[kb_off .. kb_off + kb_cnt)
 };
 
 struct GroupArgs {
@@ -53,6 +54,7 @@ struct GroupArgs {
     const GroupTile *tiles;
     int ntiles;
     const CUtensorMap *maps;   // [2*count]: J map, q map of each instance
+    const int *kbl;            // K-block lists of all (instance, M tile)
     const float *zeta, *dt;
     int t, last;
     StepParams sp;
@@ -132,8 +134,9 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                 const CUtensorMap *mQ = mJ + 1;
                 const uint32_t bytes = (uint32_t)(GR_A_BYTES + in.bn * GR_BK * 2);
                 const int yq = plane_in * in.rpad + tl.rb * in.bn;
-                for (int kb = 0; kb < in.kblocks; ++kb) {
-                    const int ring = a.single ? 0 : (kb & 1);
+                for (int j = 0; j < tl.kb_cnt; ++j) {
+                    const int kb = a.kbl[tl.kb_off + j];
+                    const int ring = a.single ? 0 : (j & 1);
                     int &rk = ring ? rk1 : rk0;
                     uint32_t &rph = ring ? rph1 : rph0;
                     const int s = ring_stage(rk, ring);
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                 if (a.single) {
                     if (w == 0) {
                         const uint32_t d_tmem = tmem + (uint32_t)slot * 256u;
-                        for (int kb = 0; kb < in.kblocks; ++kb) {
+                        for (int kb = 0; kb < tl.kb_cnt; ++kb) {
                             const int s = ring_stage(rk, 0);
                             if (!mbar_wait(full_bar(s), rph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
                             if (++rk == ring_len) {
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                     }
                 } else {
                     const uint32_t d_tmem = tmem + (uint32_t)slot * 256u + (w == 0 ? 0u : 128u);
-                    for (int kb = w; kb < in.kblocks; kb += 2) {
+                    for (int kb = w; kb < tl.kb_cnt; kb += 2) {
                         const int s = ring_stage(rk, w);
                         if (!mbar_wait(full_bar(s), rph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
                         if (++rk == ring_len) {
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
             const int i = tl.mt * GR_BM + row;
             const bool row_ok = i < in.n;
             const float hi = (in.h && row_ok) ? in.h[i] : 0.f;
-            const bool two_acc = !a.single && in.kblocks > 1;
+            const bool two_acc = !a.single && tl.kb_cnt > 1;
             const int nch = in.bn / 16;
             const int c0 = half == 0 ? 0 : (nch + 1) / 2;
             const int c1 = half == 0 ? (nch + 1) / 2 : nch;
@@ -335,6 +338,7 @@ struct GroupMember {
     int rpad_max = 0;
     int8_t *spins = nullptr;
     Ctx energy;                 // readout view (int8 J, h copies)
+    std::vector<int> kb_off, kb_cnt;   // per M tile: its non-zero K blocks in Group::kbl
 };
 
 struct Group {
@@ -350,6 +354,8 @@ struct Group {
     int pol_tiles_off[4] = {0, 0, 0, 0}, pol_ntiles[4] = {0, 0, 0, 0};
     int pol_stages[4] = {0, 0, 0, 0}, pol_stage_bytes[4] = {0, 0, 0, 0};
     CUtensorMap *d_maps = nullptr;
+    std::vector<int> kbl;       // K-block lists of every (member, M tile), host copy
+    int *d_kbl = nullptr;
     float *d_zeta = nullptr, *d_dt = nullptr;
     int *d_err = nullptr;
     int policy = -1;            // chosen tile policy
@@ -394,8 +400,53 @@ static std::map<std::string, int> g_tune_cache;
 
 static std::string group_key(const Group *g) {
     std::string k = std::to_string(g->sms) + ":";
-    for (const auto &x : g->m) k += std::to_string(x.n) + "x" + std::to_string(x.R) + ",";
+    for (const auto &x : g->m) {
+        long long nb = 0;
+        for (int v : x.kb_cnt) nb += v;
+        k += std::to_string(x.n) + "x" + std::to_string(x.R) + "b" + std::to_string(nb) + ",";
+    }
     return k;
+}
+
+// Which 128 x 64 blocks of the bf16 J hold a non-zero coupling: one CTA per
+// block, mask[mt * kblocks + kb].
+__global__ void k_block_nonzero(const __nv_bfloat16 *J, int ldk, int kblocks, unsigned char *mask) {
+    const int mt = blockIdx.y, kb = blockIdx.x;
+    const unsigned short *Jb = reinterpret_cast<const unsigned short *>(J);
+    int nz = 0;
+    for (int e = threadIdx.x; e < GR_BM * GR_BK; e += blockDim.x) {
+        const int r = e / GR_BK, cidx = e % GR_BK;
+        const unsigned short v = Jb[(size_t)(mt * GR_BM + r) * ldk + kb * GR_BK + cidx];
+        nz |= (v & 0x7FFFu) != 0u;   // +0 and -0 count as zero
+    }
+    nz = __syncthreads_or(nz);
+    if (threadIdx.x == 0) mask[(size_t)mt * kblocks + kb] = nz ? 1 : 0;
+}
+
+// K-block lists of a member from its block mask; an M tile without any
+// non-zero block keeps block 0 (all zero) so that its accumulator is written.
+static si_status member_block_lists(Group *g, GroupMember &x) {
+    const int mtiles = x.mpad / GR_BM, kblocks = x.ldk / GR_BK;
+    unsigned char *d_mask = nullptr;
+    SI_CUDA_TRY(cudaMalloc((void **)&d_mask, (size_t)mtiles * kblocks));
+    k_block_nonzero<<<dim3(kblocks, mtiles), 256, 0, g->stream>>>((const __nv_bfloat16 *)x.J, x.ldk, kblocks, d_mask);
+    cudaError_t e = cudaGetLastError();
+    std::vector<unsigned char> mask((size_t)mtiles * kblocks);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(mask.data(), d_mask, mask.size(), cudaMemcpyDeviceToHost, g->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    cudaFree(d_mask);
+    SI_CUDA_TRY(e);
+    x.kb_off.assign(mtiles, 0);
+    x.kb_cnt.assign(mtiles, 0);
+    for (int mt = 0; mt < mtiles; ++mt) {
+        x.kb_off[mt] = (int)g->kbl.size();
+        for (int kb = 0; kb < kblocks; ++kb)
+            if (mask[(size_t)mt * kblocks + kb]) g->kbl.push_back(kb);
+        if ((int)g->kbl.size() == x.kb_off[mt]) g->kbl.push_back(0);
+        x.kb_cnt[mt] = (int)g->kbl.size() - x.kb_off[mt];
+    }
+    return SI_OK;
 }
 
 // Build, once at creation, the instance table, tensor maps and tile list of
@@ -433,7 +484,7 @@ static si_status group_build_policies(Group *g) {
             if (s != SI_OK) return s;
             for (int mt = 0; mt < d.mtiles; ++mt)
                 for (int rb = 0; rb < d.rblocks; ++rb)
-                    tiles[pol].push_back(GroupTile{i, mt, rb, d.kblocks * (d.bn + 64)});
+                    tiles[pol].push_back(GroupTile{i, mt, rb, x.kb_cnt[mt] * (d.bn + 64), x.kb_off[mt], x.kb_cnt[mt]});
         }
         // Longest first; tiles of one M slab stay adjacent so that concurrent
         // replica blocks share the J slab through L2.
@@ -445,6 +496,9 @@ static si_status group_build_policies(Group *g) {
     SI_CUDA_TRY(cudaMalloc((void **)&g->d_inst, sizeof(GroupInst) * inst.size()));
     SI_CUDA_TRY(cudaMalloc((void **)&g->d_maps, sizeof(CUtensorMap) * maps.size()));
     SI_CUDA_TRY(cudaMalloc((void **)&g->d_tiles, sizeof(GroupTile) * ntot));
+    SI_CUDA_TRY(cudaMalloc((void **)&g->d_kbl, sizeof(int) * std::max<size_t>(1, g->kbl.size())));
+    SI_CUDA_TRY(cudaMemcpyAsync(g->d_kbl, g->kbl.data(), sizeof(int) * g->kbl.size(), cudaMemcpyHostToDevice,
+                                g->stream));
     SI_CUDA_TRY(cudaMemcpyAsync(g->d_inst, inst.data(), sizeof(GroupInst) * inst.size(), cudaMemcpyHostToDevice,
                                 g->stream));
     SI_CUDA_TRY(cudaMemcpyAsync(g->d_maps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice,
@@ -478,6 +532,7 @@ static si_status group_launch_step(Group *g, int t, int steps) {
     a.tiles = g->d_tiles + g->pol_tiles_off[g->policy];
     a.ntiles = g->ntiles;
     a.maps = g->d_maps + (size_t)g->policy * 2 * g->count;
+    a.kbl = g->d_kbl;
     a.zeta = g->d_zeta;
     a.dt = g->d_dt;
     a.t = t;
@@ -603,7 +658,7 @@ static void free_group(Group *g) {
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
-    void *ptrs[] = {g->d_inst, g->d_tiles, g->d_maps, g->d_zeta, g->d_dt, g->d_err};
+    void *ptrs[] = {g->d_inst, g->d_tiles, g->d_maps, g->d_kbl, g->d_zeta, g->d_dt, g->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (g->graph) cudaGraphExecDestroy(g->graph);
@@ -667,6 +722,9 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
         }
         SI_CUDA_TRY(cudaMalloc(&x.J, (size_t)x.mpad * x.ldk * 2));
         s = tc_convert_j(Jp, n, x.J, x.ldk, x.mpad, g->sms, g->stream);
+        if (s != SI_OK) { cleanup(); return s; }
+        // block sparsity: all-zero 128 x 64 blocks of J are never loaded
+        s = member_block_lists(g, x);
         if (s != SI_OK) { cleanup(); return s; }
         SI_CUDA_TRY(cudaMalloc((void **)&x.q, sizeof(float) * (size_t)x.R * n));
         SI_CUDA_TRY(cudaMalloc((void **)&x.p, sizeof(float) * (size_t)x.R * n));
@@ -907,7 +965,9 @@ si_status si_group_describe(const si_group *grp, char *buf, int32_t len) {
     for (const auto &x : g->m) {
         const int bn = policy_bn(g->policy, x.R);
         macs += (long long)x.n * x.n * x.R;
-        jbytes += (long long)x.mpad * x.ldk * 2 * cdiv(x.R, bn);
+        long long nb = 0;
+        for (int v : x.kb_cnt) nb += v;
+        jbytes += nb * GR_BM * GR_BK * 2 * cdiv(x.R, bn);
     }
     std::snprintf(buf, len, "grouped tcgen05 count=%d tiles=%d grid=%d policy=%s graph-steps=%d macs/step=%lld jbytes/step=%lld",
                   g->count, g->ntiles, g->grid, g->policy >= 0 ? kPolicyName[g->policy] : "none", g->graph_steps,

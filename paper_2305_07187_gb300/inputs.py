@@ -42,6 +42,28 @@ def pm1_coupling(n: int, seed: int = 1) -> np.ndarray:
     return J
 
 
+def king_graph_coupling(L: int, seed: int = 5) -> np.ndarray:
+    """King graph on an L x L grid with open boundaries (spin index
+    i = row * L + col; each spin coupled to its up to 8 neighbours),
+    J_ij = +-1 iid on the edges, zero elsewhere (float32, symmetric)."""
+    g = _rng(seed)
+    n = L * L
+    J = np.zeros((n, n), dtype=np.float32)
+    rows, cols = [], []
+    for r in range(L):
+        for c in range(L):
+            i = r * L + c
+            for dr, dc in ((0, 1), (1, -1), (1, 0), (1, 1)):
+                rr, cc = r + dr, c + dc
+                if 0 <= rr < L and 0 <= cc < L:
+                    rows.append(i)
+                    cols.append(rr * L + cc)
+    v = g.choice(np.array([-1.0, 1.0], dtype=np.float32), size=len(rows))
+    J[rows, cols] = v
+    J[cols, rows] = v
+    return J
+
+
 def round_to_bf16(x: np.ndarray) -> np.ndarray:
     """Round float32 values to the nearest bfloat16 (ties to even), as float32."""
     x = np.ascontiguousarray(x, dtype=np.float32)
@@ -142,6 +164,25 @@ def pm1_coupling_torch(n: int, seed: int, device="cuda"):
     u = torch.randint(0, 2, (n, n), generator=g, device=device, dtype=torch.int8)
     J = (2 * u.to(torch.float32) - 1).triu(1)
     return J + J.T
+
+
+def king_graph_coupling_torch(L: int, seed: int, device="cuda"):
+    """King graph as in king_graph_coupling, drawn on the device (torch
+    Philox stream, so not the NumPy graph of the same seed)."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(int(seed))
+    n = L * L
+    idx = torch.arange(n, device=device)
+    r, c = idx // L, idx % L
+    J = torch.zeros((n, n), dtype=torch.float32, device=device)
+    for dr, dc in ((0, 1), (1, -1), (1, 0), (1, 1)):
+        ok = (r + dr < L) & (c + dc >= 0) & (c + dc < L)
+        i = idx[ok]
+        j = (r[ok] + dr) * L + (c[ok] + dc)
+        v = 2 * torch.randint(0, 2, (i.numel(),), generator=g, device=device, dtype=torch.int8).to(torch.float32) - 1
+        J[i, j] = v
+        J[j, i] = v
+    return J
 
 
 def gauss_coupling_bf16_torch(n: int, seed: int, device="cuda"):

@@ -108,3 +108,39 @@ def test_group_rejects_mismatched_parameters():
     J = inputs.pm1_coupling(32, seed=1)
     with pytest.raises(b.SpringIsingError):
         b.Group([J, J], replicas=[4, 4], steps=5, precs=["fp32", "fp32"])
+
+
+def test_group_block_sparse_king_graphs():
+    """King graphs (banded J) in a group with a dense member: all-zero
+    128 x 64 blocks of J are skipped, the step stays within the bf16 bound,
+    energies are exact, and the J bytes per step drop."""
+    import re
+    members = [("king", 32, 64), ("king", 13, 16), ("dense", 300, 32)]
+    Js = [inputs.king_graph_coupling(a, seed=70 + k) if kind == "king" else inputs.pm1_coupling(a, seed=70 + k)
+          for k, (kind, a, _) in enumerate(members)]
+    Rs = [R for (_, _, R) in members]
+    qs = [inputs.positions(J.shape[0], R, seed0=7000 + 100 * k) * 4 for k, (J, R) in enumerate(zip(Js, Rs))]
+    ps = [np.zeros_like(q) for q in qs]
+    T = 5
+    zeta, dt = inputs.zeta_ramp(T, start=0.3, end=0.5), inputs.dt_const(T)
+    p0 = b.default_params()
+    kw = dict(k=float(p0.k), m=float(p0.m), q0=float(p0.q0), q_max=float(np.float32(p0.q_max)), p_max=float(p0.p_max))
+    with b.Group(Js, None, replicas=Rs, steps=1, precs="j_fp8_q_bf16") as g:
+        for t in range(T):
+            qg, pg, _ = g.run(zeta[t:t + 1], dt[t:t + 1], qs, ps)
+            for k in range(len(members)):
+                qo, po = oracle.run(Js[k], None, zeta[t:t + 1], dt[t:t + 1], qs[k], ps[k], **kw)
+                eq, ep = bf16_step_bound(Js[k], qs[k].astype(np.float64), ps[k].astype(np.float64),
+                                         float(zeta[t]), float(dt[t]), kw)
+                assert (np.abs(qg[k] - qo) <= eq).all() and (np.abs(pg[k] - po) <= ep).all(), (t, k)
+            qs, ps = qg, pg
+        jbytes = int(re.search(r"jbytes/step=(\d+)", g.describe()).group(1))
+    dense = sum(-(-J.shape[0] // 128) * 128 * -(-J.shape[0] // 64) * 64 * 2 * -(-R // 64)
+                for J, R in zip(Js, Rs))
+    assert jbytes < 0.6 * dense
+    with b.Group(Js, None, replicas=Rs, steps=30, precs="j_fp8_q_bf16") as g:
+        _, _, s = g.run(inputs.zeta_ramp(30), inputs.dt_const(30), qs)
+        for k in range(len(members)):
+            e, c, _ = g.energy(k, s[k])
+            np.testing.assert_array_equal(e, oracle.energy(Js[k], None, s[k]).astype(np.int64))
+            np.testing.assert_array_equal(c, oracle.cut(Js[k], s[k]).astype(np.int64))

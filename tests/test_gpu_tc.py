@@ -2,8 +2,8 @@
 as the MMA operand, FP32 accumulation and state) against the FP64 oracle.
 
 Tolerance, derived from the arithmetic: the operand rounding changes each
-force by at most 2^-9 * S_i with S_i = sum_j |J_ij| |q_j| (round to nearest
-bf16), FP32 accumulation of n products adds at most n * 2^-24 * S_i, the
+force by at most 2^-8 * S_i with S_i = sum_j |J_ij| |q_j| (round to nearest
+bf16: 8 significant bits, unit roundoff 2^-8), FP32 accumulation of n products adds at most n * 2^-24 * S_i, the
 update itself rounds a handful of FP32 operations, and the walls are
 1-Lipschitz.  Every element must fall inside that bound; with bf16-exact
 positions only the accumulation term remains.

@@ -28,3 +28,15 @@ def test_empirical_cdf_and_summary():
     s = study.summarize(np.arange(1, 102))
     assert s["best"] == 101 and s["median"] == 51 and s["count"] == 101
     assert s["p10"] == 11 and s["p90"] == 91
+
+
+def test_king_graph_generator():
+    L = 7
+    J = inputs.king_graph_coupling(L, seed=3)
+    assert np.array_equal(J, J.T) and not np.diag(J).any()
+    assert set(np.unique(J)) <= {-1.0, 0.0, 1.0}
+    deg = (J != 0).sum(1).reshape(L, L)
+    assert deg[0, 0] == 3 and deg[0, 3] == 5 and deg[3, 3] == 8
+    # couplings only between king-move neighbours
+    i, j = np.nonzero(J)
+    assert (np.maximum(np.abs(i // L - j // L), np.abs(i % L - j % L)) == 1).all()
