@@ -374,11 +374,12 @@ constexpr int kPolicyWhole = 3;
 
 // Replicas per tile of a member under a policy.  "whole-instance" covers all
 // R replicas of the member in one tile (R <= 256, a multiple of 16), so each
-// J slab is read once per step; it runs the single-accumulator mode.
+// J slab is read once per step, and larger R in tiles of 256; it runs the
+// single-accumulator mode (one MMA of N up to 256 per K step).
 static int policy_bn(int policy, int R) {
     if (policy == 1) return 64;
     if (policy == 2) return 128;
-    if (policy == kPolicyWhole) return round_up(R, 16) <= 256 ? round_up(R, 16) : 128;
+    if (policy == kPolicyWhole) return round_up(R, 16) <= 256 ? round_up(R, 16) : 256;
     return R <= 64 ? 64 : 128;
 }
 
@@ -683,7 +684,7 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
         x.R = prm[i].replicas;
         x.ldk = round_up(n, GR_BK);
         x.mpad = round_up(n, GR_BM);
-        x.rpad_max = std::max(round_up(x.R, 128), round_up(x.R, 16) <= 256 ? round_up(x.R, 16) : 0);
+        x.rpad_max = std::max(round_up(x.R, 128), round_up(x.R, 16) <= 256 ? round_up(x.R, 16) : round_up(x.R, 256));
         const float *Jp = J[i];
         const float *hp = h ? h[i] : nullptr;
         void *Jtmp = nullptr, *htmp = nullptr;

@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 def _members():
     # (n, R, kind): ragged sizes, both tile widths, +-1 and Gaussian couplings
     return [(17, 16, "pm1"), (128, 48, "gauss"), (300, 64, "pm1"), (513, 130, "gauss"),
-            (1000, 200, "pm1"), (64, 1, "pm1"), (257, 96, "gauss")]
+            (1000, 200, "pm1"), (64, 1, "pm1"), (257, 96, "gauss"), (130, 300, "pm1")]
 
 
 def _build(members, seed=0):
