@@ -159,8 +159,11 @@ template <typename T>
 __global__ void __launch_bounds__(AE_THREADS) k_adj_elem(
     int n, int R, int ld, const T *q, const T *p, const T *F, const T *qn, const T *pn,
     const T *lq, const T *lp, T *la_out, T *lb_out, StepParams sp, const float *zeta,
-    const float *dt, int t, T *part /* [3][AE_BLOCKS] of step t */) {
+    const float *dt, int t, T *part /* [3][AE_BLOCKS] of step t */,
+    __nv_bfloat16 *xs_la /* tensor-core operand pieces of la, or null */, int ldk) {
     __shared__ T r0s[AE_THREADS], r1s[AE_THREADS], r2s[AE_THREADS];
+    grid_dep_wait();
+    grid_dep_launch();
     const T k = (T)sp.k, q0 = (T)sp.q0, qmax = (T)sp.q_max, pmax = (T)sp.p_max, m = (T)sp.m;
     const T zt = (T)zeta[t], dtt = (T)dt[t];
     const T dtm = dtt / m;
@@ -179,6 +182,14 @@ __global__ void __launch_bounds__(AE_THREADS) k_adj_elem(
         const T la = Dp * (lp[x] + dtm * lb);
         la_out[x] = la;
         lb_out[x] = lb;
+        if (xs_la) {
+            __nv_bfloat16 p0, p1, p2;
+            bf16_split3((float)la, p0, p1, p2);
+            __nv_bfloat16 *xb = xs_la + ((size_t)(r / ADJ_TC_RB) * ADJ_TC_BN + (r % ADJ_TC_RB)) * ldk + i;
+            xb[0] = p0;
+            xb[(size_t)ADJ_TC_RB * ldk] = p1;
+            xb[(size_t)2 * ADJ_TC_RB * ldk] = p2;
+        }
         const T dq = q[x] - q0;
         const T force = -k * dq + zt * F[x];
         s0.add(lb * pn[x] / m + la * force);
@@ -336,11 +347,15 @@ static si_status adjoint_impl(Ctx *c, int steps, float *g_zeta, float *g_dt, flo
 
         // The three products of the sweep: on the tensor cores (three-piece bf16
         // split of the operand, FP32 accumulation) when the context has one, else
-        // the CUDA-core tiles.
-        auto gemm_forward = [&](const T *X, const T *P, T *Qn, T *Pn, T *Fo, int t) -> si_status {
+        // the CUDA-core tiles.  On the tensor cores the operand pieces of a
+        // segment's forward chain alternate between buffers 0 and 1 (each
+        // forward product writes the pieces of q_{t+1} for the next one; only a
+        // segment's first product splits its checkpoint), and lambda_a's pieces,
+        // written by the elementwise adjoint kernel, sit in buffer 2.
+        auto gemm_forward = [&](const T *X, const T *P, T *Qn, T *Pn, T *Fo, int t, int j) -> si_status {
             if (tc) {
                 return adj_tc_gemm(c, tc, 0, (const float *)X, (const float *)P, (float *)Qn, (float *)Pn,
-                                   (float *)Fo, nullptr, nullptr, nullptr, nullptr, t);
+                                   (float *)Fo, nullptr, nullptr, nullptr, nullptr, t, j & 1, j == 0, (j + 1) & 1);
             }
             g.X = X;
             g.P = P;
@@ -356,7 +371,7 @@ static si_status adjoint_impl(Ctx *c, int steps, float *g_zeta, float *g_dt, flo
         auto gemm_terminal = [&](const T *X) -> si_status {
             if (tc) {
                 return adj_tc_gemm(c, tc, 1, (const float *)X, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                   (float *)lq, (float *)lp, (float *)objp, 0);
+                                   (float *)lq, (float *)lp, (float *)objp, 0, 2, true, -1);
             }
             g.X = X;
             g.LQ = lq;
@@ -370,7 +385,7 @@ static si_status adjoint_impl(Ctx *c, int steps, float *g_zeta, float *g_dt, flo
         auto gemm_adjoint = [&](int t) -> si_status {
             if (tc) {
                 return adj_tc_gemm(c, tc, 2, (const float *)la, nullptr, nullptr, nullptr, nullptr, (const float *)lb,
-                                   (float *)lq, (float *)lp, nullptr, t);
+                                   (float *)lq, (float *)lp, nullptr, t, 2, false, -1);
             }
             g.X = la;
             g.LB = lb;
@@ -391,7 +406,7 @@ static si_status adjoint_impl(Ctx *c, int steps, float *g_zeta, float *g_dt, flo
             SI_CUDA_TRY(cudaMemcpyAsync(sp, ckp + (size_t)s * plane, sizeof(T) * plane, cudaMemcpyDeviceToDevice, c->stream));
             for (int j = 0; j < len; ++j) {
                 si_status e = gemm_forward(sq + (size_t)j * plane, sp + (size_t)j * plane, sq + (size_t)(j + 1) * plane,
-                                           sp + (size_t)(j + 1) * plane, sF + (size_t)j * plane, t0 + j);
+                                           sp + (size_t)(j + 1) * plane, sF + (size_t)j * plane, t0 + j, j);
                 if (e != SI_OK) return e;
             }
             return SI_OK;
@@ -421,11 +436,26 @@ static si_status adjoint_impl(Ctx *c, int steps, float *g_zeta, float *g_dt, flo
             const int t0 = s * K, len = std::min(K, steps - t0);
             for (int j = len - 1; j >= 0; --j) {
                 const int t = t0 + j;
-                k_adj_elem<T><<<AE_BLOCKS, AE_THREADS, 0, c->stream>>>(
-                    n, R, ld, sq + (size_t)j * plane, sp + (size_t)j * plane, sF + (size_t)j * plane,
-                    sq + (size_t)(j + 1) * plane, sp + (size_t)(j + 1) * plane, lq, lp, la, lb, spar, c->dzeta,
-                    c->ddt, t, part + (size_t)t * 3 * AE_BLOCKS);
-                SI_CUDA_TRY(cudaGetLastError());
+                {
+                    // programmatic dependent launch: the prologue overlaps the
+                    // previous product; the kernel waits before reading it
+                    cudaLaunchConfig_t cfg = {};
+                    cfg.gridDim = dim3(AE_BLOCKS);
+                    cfg.blockDim = dim3(AE_THREADS);
+                    cfg.stream = c->stream;
+                    cudaLaunchAttribute attr[1];
+                    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                    attr[0].val.programmaticStreamSerializationAllowed = 1;
+                    cfg.attrs = attr;
+                    cfg.numAttrs = 1;
+                    SI_CUDA_TRY(cudaLaunchKernelEx(
+                        &cfg, k_adj_elem<T>, n, R, ld, (const T *)(sq + (size_t)j * plane),
+                        (const T *)(sp + (size_t)j * plane), (const T *)(sF + (size_t)j * plane),
+                        (const T *)(sq + (size_t)(j + 1) * plane), (const T *)(sp + (size_t)(j + 1) * plane),
+                        (const T *)lq, (const T *)lp, la, lb, spar, (const float *)c->dzeta, (const float *)c->ddt, t,
+                        part + (size_t)t * 3 * AE_BLOCKS, tc ? adj_tc_xs(tc, 2) : (__nv_bfloat16 *)nullptr,
+                        tc ? adj_tc_ldk(tc) : 0));
+                }
                 c->launches += 1;
                 if ((st = gemm_adjoint(t)) != SI_OK) return st;
             }

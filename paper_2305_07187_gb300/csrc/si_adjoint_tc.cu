@@ -30,8 +30,8 @@
 
 namespace si {
 
-constexpr int AT_BM = 128, AT_BK = 64, AT_RB = 64, AT_PIECES = 3;
-constexpr int AT_BN = AT_RB * AT_PIECES;                 // 192 MMA columns
+constexpr int AT_BM = 128, AT_BK = 64, AT_RB = ADJ_TC_RB;
+constexpr int AT_BN = ADJ_TC_BN;                         // 192 MMA columns: 64 replicas x 3 pieces
 constexpr int AT_A_BYTES = AT_BM * AT_BK * 2;            // 16 KB
 constexpr int AT_B_BYTES = AT_BN * AT_BK * 2;            // 24 KB
 constexpr int AT_STAGE = AT_A_BYTES + AT_B_BYTES;        // 40 KB, multiple of 1024
@@ -50,12 +50,15 @@ enum { AT_FORWARD = 0, AT_TERMINAL = 1, AT_ADJOINT = 2 };
 struct AdjTc {
     int n, R, ld, ldk, mpad, mtiles, nrb, kblocks, kb_per, splits;
     __nv_bfloat16 *jb = nullptr;    // [mpad][ldk]
-    __nv_bfloat16 *xs = nullptr;    // [nrb * 192][ldk]
+    __nv_bfloat16 *xs = nullptr;    // [3][nrb * 192][ldk]: forward chain (two buffers), lambda_a
     CUtensorMap mapA, mapB;
 };
 
 struct AdjTcArgs {
     int n, R, ld, nrb, kblocks, kb_per, splits;   // splits = cluster size (1, 2, 4 or 8)
+    int xin;                                       // operand buffer of X (0, 1 or 2)
+    int ldk;
+    __nv_bfloat16 *xs_out;                         // forward: pieces of q_{t+1} for the next product, or null
     const float *h;
     const float *X, *P;
     float *Qn, *Pn, *Fo;
@@ -122,6 +125,14 @@ __device__ __forceinline__ void at_apply16(const AdjTcArgs &a, int i, int r0, co
             a.Qn[e] = qo;
             a.Pn[e] = po;
             a.Fo[e] = F;
+            if (a.xs_out) {
+                __nv_bfloat16 p0, p1, p2;
+                bf16_split3(qo, p0, p1, p2);
+                __nv_bfloat16 *xb = a.xs_out + ((size_t)(r / AT_RB) * AT_BN + (r % AT_RB)) * a.ldk + i;
+                xb[0] = p0;
+                xb[(size_t)AT_RB * a.ldk] = p1;
+                xb[(size_t)2 * AT_RB * a.ldk] = p2;
+            }
         } else if (MODE == AT_TERMINAL) {
             const float x = u0[u];
             a.LQ[e] = -(G[u] + hi);
@@ -180,6 +191,10 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // The setup above overlaps the previous kernel of the sweep; every read of
+    // its results comes after this wait.
+    grid_dep_wait();
+    grid_dep_launch();
     // phase 1 of the cluster barrier: every CTA of the cluster has started
     // (its shared memory may receive partials once the phase completes)
     if (a.splits > 1) cluster_arrive_relaxed();
@@ -195,7 +210,7 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
                 const uint32_t dA = sbase + s * AT_STAGE;
                 mbar_arrive_expect_tx(full_bar(s), (uint32_t)AT_STAGE);
                 tma_load_2d(dA, &mapA, full_bar(s), (kb0 + c) * AT_BK, mt * AT_BM);
-                tma_load_2d(dA + AT_A_BYTES, &mapB, full_bar(s), (kb0 + c) * AT_BK, rb * AT_BN);
+                tma_load_2d(dA + AT_A_BYTES, &mapB, full_bar(s), (kb0 + c) * AT_BK, (a.xin * a.nrb + rb) * AT_BN);
                 ++issued;
             }
             // Let every copy land before the CTA exits.
@@ -385,6 +400,8 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
 // Split of the FP32 operand X [R][ld] into bf16 pieces, laid out as the B
 // operand rows [rb][piece][64][ldk] (zero for padded replicas and spins).
 __global__ void k_adj_split(const float *X, int n, int R, int ld, int nrb, int ldk, __nv_bfloat16 *xs) {
+    grid_dep_wait();
+    grid_dep_launch();
     const long long total = (long long)nrb * AT_RB * ldk;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
@@ -392,11 +409,8 @@ __global__ void k_adj_split(const float *X, int n, int R, int ld, int nrb, int l
         const int rr = (int)(e / ldk);               // rb * 64 + rl
         const int rb = rr / AT_RB, rl = rr % AT_RB;
         const float x = (rr < R && j < n) ? X[(size_t)rr * ld + j] : 0.f;
-        const __nv_bfloat16 p0 = __float2bfloat16_rn(x);
-        const float r1 = x - __bfloat162float(p0);
-        const __nv_bfloat16 p1 = __float2bfloat16_rn(r1);
-        const float r2 = r1 - __bfloat162float(p1);
-        const __nv_bfloat16 p2 = __float2bfloat16_rn(r2);
+        __nv_bfloat16 p0, p1, p2;
+        bf16_split3(x, p0, p1, p2);
         __nv_bfloat16 *base = xs + ((size_t)rb * AT_BN + rl) * ldk + j;
         base[0] = p0;
         base[(size_t)AT_RB * ldk] = p1;
@@ -430,13 +444,15 @@ static cudaError_t launch_adj(const AdjTc *t, const AdjTcArgs &a, cudaStream_t s
     cfg.blockDim = dim3(AT_THREADS);
     cfg.dynamicSmemBytes = AT_SMEM;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)t->splits;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, k_adj_tc<MODE>, t->mapA, t->mapB, a);
 }
 
@@ -499,12 +515,12 @@ si_status adj_tc_prepare(Ctx *c, AdjTc **out) {
     t->splits = splits;
     t->kb_per = cdiv(t->kblocks, splits);
     if (cudaMalloc((void **)&t->jb, sizeof(__nv_bfloat16) * (size_t)t->mpad * t->ldk) != cudaSuccess ||
-        cudaMalloc((void **)&t->xs, sizeof(__nv_bfloat16) * (size_t)t->nrb * AT_BN * t->ldk) != cudaSuccess) {
+        cudaMalloc((void **)&t->xs, sizeof(__nv_bfloat16) * 3 * (size_t)t->nrb * AT_BN * t->ldk) != cudaSuccess) {
         cudaGetLastError();
         set_error("si_grad: out of device memory for the tensor-core workspace");
         return fail(SI_ERR_OOM);
     }
-    if (cudaMemsetAsync(t->xs, 0, sizeof(__nv_bfloat16) * (size_t)t->nrb * AT_BN * t->ldk, c->stream) !=
+    if (cudaMemsetAsync(t->xs, 0, sizeof(__nv_bfloat16) * 3 * (size_t)t->nrb * AT_BN * t->ldk, c->stream) !=
         cudaSuccess) {
         set_error("si_grad: cudaMemsetAsync failed");
         return fail(SI_ERR_CUDA);
@@ -517,18 +533,34 @@ si_status adj_tc_prepare(Ctx *c, AdjTc **out) {
     }
     si_status s;
     if ((s = tc_make_map_bf16(&t->mapA, t->jb, t->ldk, t->mpad, AT_BK, AT_BM)) != SI_OK) return fail(s);
-    if ((s = tc_make_map_bf16(&t->mapB, t->xs, t->ldk, t->nrb * AT_BN, AT_BK, AT_BN)) != SI_OK) return fail(s);
+    if ((s = tc_make_map_bf16(&t->mapB, t->xs, t->ldk, 3 * t->nrb * AT_BN, AT_BK, AT_BN)) != SI_OK) return fail(s);
     c->launches += 1;
     c->g_tc = t;
     *out = t;
     return SI_OK;
 }
 
+__nv_bfloat16 *adj_tc_xs(const AdjTc *t, int buf) {
+    return t->xs + (size_t)buf * t->nrb * AT_BN * t->ldk;
+}
+int adj_tc_ldk(const AdjTc *t) { return t->ldk; }
+
 si_status adj_tc_gemm(Ctx *c, AdjTc *t, int mode, const float *X, const float *P, float *Qn, float *Pn,
-                      float *Fo, const float *LB, float *LQ, float *LP, float *obj_part, int tstep) {
-    k_adj_split<<<std::min(2048, cdiv((long long)t->nrb * AT_RB * t->ldk, 256)), 256, 0, c->stream>>>(
-        X, t->n, t->R, t->ld, t->nrb, t->ldk, t->xs);
-    SI_CUDA_TRY(cudaGetLastError());
+                      float *Fo, const float *LB, float *LQ, float *LP, float *obj_part, int tstep, int xin,
+                      bool split, int xout) {
+    if (split) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)std::min(2048, cdiv((long long)t->nrb * AT_RB * t->ldk, 256)));
+        cfg.blockDim = dim3(256);
+        cfg.stream = c->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        SI_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_adj_split, X, t->n, t->R, t->ld, t->nrb, t->ldk, adj_tc_xs(t, xin)));
+        c->launches += 1;
+    }
     AdjTcArgs a{};
     a.n = t->n;
     a.R = t->R;
@@ -537,6 +569,9 @@ si_status adj_tc_gemm(Ctx *c, AdjTc *t, int mode, const float *X, const float *P
     a.kblocks = t->kblocks;
     a.kb_per = t->kb_per;
     a.splits = t->splits;
+    a.xin = xin;
+    a.ldk = t->ldk;
+    a.xs_out = (mode == AT_FORWARD && xout >= 0) ? adj_tc_xs(t, xout) : nullptr;
     a.h = c->has_h ? c->dhf : nullptr;
     a.X = X;
     a.P = P;
@@ -557,7 +592,7 @@ si_status adj_tc_gemm(Ctx *c, AdjTc *t, int mode, const float *X, const float *P
                     : mode == AT_TERMINAL ? launch_adj<AT_TERMINAL>(t, a, c->stream)
                                           : launch_adj<AT_ADJOINT>(t, a, c->stream);
     SI_CUDA_TRY(e);
-    c->launches += 2;
+    c->launches += 1;
     return SI_OK;
 }
 

@@ -108,6 +108,24 @@ struct CompSum {
     __device__ __forceinline__ T value() const { return hi + lo; }
 };
 
+// Three-piece bf16 split of an FP32 value: x = p0 + p1 + p2 up to the last
+// bits of the significand, each piece the round-to-nearest bf16 of the
+// residual left by the previous ones (the residuals are exact in FP32).
+__device__ __forceinline__ void bf16_split3(float x, __nv_bfloat16 &p0, __nv_bfloat16 &p1, __nv_bfloat16 &p2) {
+    p0 = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(p0);
+    p1 = __float2bfloat16_rn(r1);
+    const float r2 = r1 - __bfloat162float(p1);
+    p2 = __float2bfloat16_rn(r2);
+}
+
+// Programmatic dependent launch: wait until the grids this one depends on
+// have completed and their writes are visible (returns at once when the
+// launch had no programmatic dependency), and let the next grid in the
+// stream start its prologue.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <typename T>
 __device__ __forceinline__ int8_t spin_of(T q) {
     return q >= (T)0 ? (int8_t)1 : (int8_t)-1;

@@ -168,8 +168,17 @@ si_status tc_convert_j(const float *J_dev, int n, void *out, int ldk, int mpad, 
 // Adjoint, si_adjoint.cu.
 // Tensor-core products of the adjoint sweep, si_adjoint_tc.cu.
 si_status adj_tc_prepare(Ctx *c, AdjTc **out);
+// Operand layout of the tensor-core adjoint: replica blocks of 64, each as
+// three bf16 pieces (rows [rb][piece][64][ldk]).
+constexpr int ADJ_TC_RB = 64, ADJ_TC_BN = 3 * ADJ_TC_RB;
+// Product J X^T of the sweep: X's pieces are read from operand buffer xin
+// (split from X first when `split`); a forward product writes the pieces of
+// q_{t+1} into buffer xout (>= 0).
 si_status adj_tc_gemm(Ctx *c, AdjTc *a, int mode, const float *X, const float *P, float *Qn, float *Pn,
-                      float *Fo, const float *LB, float *LQ, float *LP, float *obj_part, int t);
+                      float *Fo, const float *LB, float *LQ, float *LP, float *obj_part, int t, int xin,
+                      bool split, int xout);
+__nv_bfloat16 *adj_tc_xs(const AdjTc *a, int buf);
+int adj_tc_ldk(const AdjTc *a);
 int adj_tc_nobj(const AdjTc *a);
 int adj_tc_splits(const AdjTc *a);
 void adj_tc_free(AdjTc *a);
