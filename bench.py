@@ -498,8 +498,9 @@ def run_grad(args):
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "k_adj_tc (forward, recompute and adjoint products, K split over a cluster)",
                      "peak_source": "%s bf16_tflops (burst)" % src, "algorithmic_flops": flops,
-                     "note": "whole si_grad time: per step 7 dependent launches (3 products, 3 operand "
-                             "splits, 1 elementwise adjoint) replayed from a CUDA graph; latency-bound"},
+                     "note": "whole si_grad time: per step 3 products (forward, recompute, adjoint) and 1 "
+                             "elementwise adjoint kernel, dependent launches replayed from a CUDA graph; "
+                             "latency-bound"},
         "e2e": {"value": R * n * T / (statistics.median(e2e) * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * (2 * T + R * n), "d2h_bytes_per_step": 4 * (2 * T + 2)},
         "gpu_launches": launches,
