@@ -148,9 +148,18 @@ si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R,
  * that integrates the equation of motion backwards (checkpoints every
  * prm.ckpt_every steps, recomputation in between).  The derivative of each
  * wall clamp is taken as 1 strictly inside and 0 on or beyond the wall.
- *   g_zeta [steps], g_dt [steps], g_k [1], objective [1]; any may be NULL.
- * Supported for SI_PREC_FP32 and SI_PREC_FP64, kick-drift order, without
- * wall_zero_p (else SI_ERR_UNSUPPORTED).
+ *   zeta, dt  [steps] float, host or device
+ *   q_init    [R][n] float; p_init [R][n] float or NULL (zero momenta)
+ *   g_zeta [steps], g_dt [steps], g_k [1], objective [1] float, host or
+ *   device; any may be NULL.
+ * FP32 contexts whose J is exact in bf16 compute the products J X^T on the
+ * tensor cores from a three-piece bf16 split of the FP32 operand (exact
+ * products, FP32 accumulation); otherwise, and for SI_PREC_FP64, on CUDA
+ * cores.  SI_ADJOINT_SIMT=1 in the environment forces the CUDA cores.  After
+ * the call si_get_state returns the final state of the forward sweep.
+ * Deterministic: repeated calls give bit-identical results, whatever
+ * ckpt_every is.  Supported for SI_PREC_FP32 and SI_PREC_FP64, kick-drift
+ * order, without wall_zero_p (else SI_ERR_UNSUPPORTED).
  */
 si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt,
                   const float *q_init, const float *p_init, float *g_zeta,
