@@ -29,7 +29,9 @@
 
 namespace si {
 
-constexpr int GR_BM = 128, GR_BK = 64, GR_THREADS = 352;
+constexpr int GR_BM = 128, GR_BK = 64;
+constexpr int GR_EPI = 12;                       // epilogue warps: 3 per TMEM lane quadrant
+constexpr int GR_THREADS = 32 * (3 + GR_EPI);
 constexpr int GR_A_BYTES = GR_BM * GR_BK * 2;
 constexpr int GR_SMAX = 8;                       // most ring stages of any policy
 constexpr int GR_TILES = 196608;                 // shared memory for the ring
@@ -88,7 +90,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
         }
         for (int k = 0; k < 2; ++k) {
             mbar_init(accf_bar(k), 2);
-            mbar_init(tmem_empty_bar(k), 8);
+            mbar_init(tmem_empty_bar(k), GR_EPI);
         }
         mbar_init(drain_bar, 2);
         *abort_flag = 0;
@@ -242,11 +244,11 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
             }
         }
     } else {
-        // ---------------------------------------------- epilogue (8 warps)
+        // ---------------------------------------------- epilogue (GR_EPI warps)
         // Warp w reads TMEM lanes 32*(w%4) .. +31 (one spin per thread) and
-        // half (w-3)/4 of the tile's 16-column chunks.
+        // share (w-3)/4 of the tile's 16-column chunks.
         const int quad = warp & 3;
-        const int half = (warp - 3) >> 2;
+        const int half = (warp - 3) >> 2;   // which share of the chunks (0 .. GR_EPI/4 - 1)
         const int row = quad * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
         const float zt = a.zeta[a.t], dtt = a.dt[a.t];
@@ -266,8 +268,9 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
             const float hi = (in.h && row_ok) ? in.h[i] : 0.f;
             const bool two_acc = !a.single && tl.kb_cnt > 1;
             const int nch = in.bn / 16;
-            const int c0 = half == 0 ? 0 : (nch + 1) / 2;
-            const int c1 = half == 0 ? (nch + 1) / 2 : nch;
+            constexpr int NPART = GR_EPI / 4;
+            const int c0 = (nch * half + NPART - 1) / NPART;
+            const int c1 = (nch * (half + 1) + NPART - 1) / NPART;
             const uint32_t tacc = tmem + lane_off + (uint32_t)slot * 256u;
             __nv_bfloat16 *qn = in.qop + (size_t)(plane_in ^ 1) * in.rpad * in.ldk;
             for (int c = c0; c < c1; ++c) {
