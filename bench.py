@@ -536,6 +536,14 @@ def run_study(args):
         cuts, _ = study.final_cuts(J, q0, inputs.zeta_ramp(T), dt, **kw)
         variants[name] = study.summarize(cuts)
     steps, E, _ = study.energy_trajectory(J, q0, inputs.zeta_ramp(T), dt, 100)
+    # Hamiltonian drift at constant zeta below the instability (zeta 2 sqrt(N)
+    # < k), 10 x 100 steps: FP32 plain path and bf16-operand tensor path
+    from paper_2305_07187_gb300 import monitor
+    drift = {}
+    for name, prec, Rm in (("fp32", "fp32", 64), ("tensor_bf16", "j_fp8_q_bf16", R)):
+        with b.Context(J, replicas=Rm, steps=100, prec=prec) as c:
+            _, d = monitor.hamiltonian_drift(c, 0.002, 0.2, q0[:Rm], segments=10)
+        drift[name] = {"replicas": Rm, "max_rel_drift": float(d.max()), "median_rel_drift": float(np.median(d))}
     wall = time.perf_counter() - t0
     line = {
         "metric": "median final cut (linear ramp)", "value": strategies["ramp-L1"]["median"], "unit": "cut",
@@ -547,6 +555,7 @@ def run_study(args):
         "trajectory_linear_ramp": {"steps": [int(x) for x in steps],
                                    "mean_energy": [float(x) for x in E.mean(axis=1)],
                                    "min_energy": [int(x) for x in E.min(axis=1)]},
+        "hamiltonian_drift_zeta0.002_dt0.2_1000steps": drift,
         "wall_s": wall,
     }
     print(json.dumps(line))

@@ -106,8 +106,7 @@ __global__ void __launch_bounds__(TE_THREADS, 1)
                     mma_bf16(tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb | kk) != 0 ? 1u : 0u);
                 mma_commit(empty_bar(s));
             }
-            mma_commit(accf_bar);
-            (void)ok;
+            if (ok) mma_commit(accf_bar);   // on abort the epilogue sees the abort flag instead
         }
     } else {
         // epilogue: warps 2..5, TMEM lane quadrant warp%4, one spin per thread
