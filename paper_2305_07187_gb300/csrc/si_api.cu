@@ -290,6 +290,7 @@ void si_default_params(si_params *p) {
 
 si_status si_create(si_ctx **out, const si_params *prm, const float *J, const float *h,
                     void *stream) {
+    NvtxRange nvtx_range("si_create");
     set_error("");
     if (!out || !J) {
         set_error("si_create: out and J are required");
@@ -313,6 +314,7 @@ si_status si_create(si_ctx **out, const si_params *prm, const float *J, const fl
 
 si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q_init,
                  const float *p_init, float *q_out, float *p_out, int8_t *spins_out) {
+    NvtxRange nvtx_range("si_run");
     set_error("");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !q_init || (c->prm.steps > 0 && (!zeta || !dt))) {
@@ -383,6 +385,7 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
 }
 
 si_status si_get_state(si_ctx *ctx, double *q_out, double *p_out) {
+    NvtxRange nvtx_range("si_get_state");
     set_error("");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !c->have_run) {
@@ -405,6 +408,7 @@ si_status si_get_state(si_ctx *ctx, double *q_out, double *p_out) {
 
 si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy_out,
                     int32_t *cut_out, double *energy_f) {
+    NvtxRange nvtx_range("si_energy");
     set_error("");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !spins || R < 0) {
@@ -452,6 +456,7 @@ si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy
 
 si_status si_hamiltonian(si_ctx *ctx, const float *q, const float *p, int32_t R, double zeta,
                          double *H_out) {
+    NvtxRange nvtx_range("si_hamiltonian");
     set_error("");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || R < 0 || (R > 0 && (!q || !p || !H_out))) {
@@ -477,6 +482,7 @@ si_status si_hamiltonian(si_ctx *ctx, const float *q, const float *p, int32_t R,
 si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt, const float *q_init,
                   const float *p_init, float *g_zeta, float *g_dt, float *g_k,
                   float *objective) {
+    NvtxRange nvtx_range("si_grad");
     set_error("");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
     if (!c || !q_init || (c->prm.steps > 0 && (!zeta || !dt))) {

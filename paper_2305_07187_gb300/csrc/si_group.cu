@@ -401,9 +401,52 @@ static void policy_ring(int policy, const std::vector<int> &bns, int *stages, in
 
 static std::mutex g_tune_mu;
 static std::map<std::string, int> g_tune_cache;
+static bool g_tune_file_loaded = false;
+
+// Autotuner results persist across processes in the text file named by
+// SI_TUNE_CACHE (one "key policy" line per group shape; later lines win).
+// Without the variable the cache lives in the process only.  Callers hold
+// g_tune_mu.
+static void tune_file_load_locked() {
+    if (g_tune_file_loaded) return;
+    g_tune_file_loaded = true;
+    const char *path = std::getenv("SI_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return;
+    char line[8192];
+    while (std::fgets(line, sizeof line, f)) {
+        char *sp = std::strrchr(line, ' ');
+        if (!sp) continue;
+        const int pol = std::atoi(sp + 1);
+        *sp = '\0';
+        if (pol >= 0 && pol < kPolicies && line[0]) g_tune_cache[line] = pol;
+    }
+    std::fclose(f);
+}
+
+static void tune_file_store_locked(const std::string &key, int pol) {
+    const char *path = std::getenv("SI_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE *f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%s %d\n", key.c_str(), pol);
+    std::fclose(f);
+}
+
+static bool tune_cache_find(const std::string &key, int *pol) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_file_load_locked();
+    auto it = g_tune_cache.find(key);
+    if (it == g_tune_cache.end()) return false;
+    *pol = it->second;
+    return true;
+}
 
 static std::string group_key(const Group *g) {
-    std::string k = std::to_string(g->sms) + ":";
+    int drv = 0;
+    cudaDriverGetVersion(&drv);
+    std::string k = "sm" + std::to_string(g->sms) + "-drv" + std::to_string(drv) + ":";
     for (const auto &x : g->m) {
         long long nb = 0;
         for (int v : x.kb_cnt) nb += v;
@@ -627,9 +670,8 @@ static int forced_policy() {
 static si_status group_autotune(Group *g) {
     const std::string key = group_key(g);
     {
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(key);
-        if (it != g_tune_cache.end()) return group_apply_policy(g, it->second);
+        int cached = -1;
+        if (tune_cache_find(key, &cached)) return group_apply_policy(g, cached);
     }
     int best = 0;
     const char *env = std::getenv("SI_GROUP_POLICY");
@@ -650,6 +692,7 @@ static si_status group_autotune(Group *g) {
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune_cache[key] = best;
+        if (!env) tune_file_store_locked(key, best);
     }
     return group_apply_policy(g, best);
 }
@@ -804,6 +847,7 @@ extern "C" {
 
 si_status si_create_group(si_group **out, int32_t count, const si_params *prm, const float *const *J,
                           const float *const *h, void *stream) {
+    NvtxRange nvtx_range("si_create_group");
     set_error("");
     if (!out || count < 1 || !prm || !J) {
         set_error("si_create_group: out, count >= 1, prm[count] and J[count] are required");
@@ -849,6 +893,7 @@ si_status si_create_group(si_group **out, int32_t count, const si_params *prm, c
 si_status si_run_group(si_group *grp, const float *zeta, const float *dt, const float *const *q_init,
                        const float *const *p_init, float *const *q_out, float *const *p_out,
                        int8_t *const *spins_out) {
+    NvtxRange nvtx_range("si_run_group");
     set_error("");
     Group *g = reinterpret_cast<Group *>(grp);
     if (!g || !q_init || (g->steps > 0 && (!zeta || !dt))) {
@@ -888,9 +933,7 @@ si_status si_run_group(si_group *grp, const float *zeta, const float *dt, const 
     if (steps > 0) {
         int cached = forced_policy();
         if (cached < 0) {
-            std::lock_guard<std::mutex> lk(g_tune_mu);
-            auto it = g_tune_cache.find(group_key(g));
-            if (it != g_tune_cache.end()) cached = it->second;
+            tune_cache_find(group_key(g), &cached);
         }
         if (cached < 0) {
             // autotune once per group shape, on the real data as scratch state
@@ -932,6 +975,7 @@ si_status si_run_group(si_group *grp, const float *zeta, const float *dt, const 
 
 si_status si_group_energy(si_group *grp, int32_t index, const int8_t *spins, int32_t R, int32_t *energy_out,
                           int32_t *cut_out, double *energy_f) {
+    NvtxRange nvtx_range("si_group_energy");
     Group *g = reinterpret_cast<Group *>(grp);
     if (!g || index < 0 || index >= g->count) {
         set_error("si_group_energy: bad group or index");

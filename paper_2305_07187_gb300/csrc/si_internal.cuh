@@ -11,6 +11,7 @@
 #include <string>
 
 #include "spring_ising.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace si {
 
@@ -118,6 +119,15 @@ struct Ctx {
     void *g_graph_ws = nullptr;
     int g_graph_launches = 0;
     int g_path = 0;              // 0: no si_grad yet, 1: CUDA cores, 2: tensor cores
+};
+
+// NVTX range over one public call (header-only NVTX 3: free unless a
+// profiler is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
 };
 
 // ------------------------------------------------------------ helpers

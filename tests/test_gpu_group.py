@@ -144,3 +144,38 @@ def test_group_block_sparse_king_graphs():
             e, c, _ = g.energy(k, s[k])
             np.testing.assert_array_equal(e, oracle.energy(Js[k], None, s[k]).astype(np.int64))
             np.testing.assert_array_equal(c, oracle.cut(Js[k], s[k]).astype(np.int64))
+
+
+def test_autotune_cache_persists_across_processes(tmp_path):
+    """SI_TUNE_CACHE: the autotuner's choice is written to the file and a
+    later process takes the policy from it without timing (here a policy
+    edited into the file, which the second process must use)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    code = (
+        "import sys, numpy as np\n"
+        "sys.path.insert(0, %r)\n"
+        "from paper_2305_07187_gb300 import _binding as b, inputs\n"
+        "Js = [inputs.pm1_coupling(n, seed=5) for n in (96, 160)]\n"
+        "with b.Group(Js, None, replicas=[48, 80], steps=4, precs='j_fp8_q_bf16') as g:\n"
+        "    g.run(inputs.zeta_ramp(4), inputs.dt_const(4), [inputs.positions(96, 48), inputs.positions(160, 80)])\n"
+        "    print(g.describe())\n" % root)
+    env = dict(os.environ, SI_TUNE_CACHE=str(cache))
+    env.pop("SI_GROUP_POLICY", None)
+    out1 = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert out1.returncode == 0, out1.stderr
+    lines = cache.read_text().strip().splitlines()
+    assert len(lines) == 1
+    key, pol = lines[0].rsplit(" ", 1)
+    assert "96x48" in key and "160x80" in key
+    names = ["bn64-if-R<=64-else-128", "all-64", "all-128", "whole-instance"]
+    assert "policy=" + names[int(pol)] in out1.stdout
+    other = (int(pol) + 1) % 4
+    cache.write_text("%s %d\n" % (key, other))
+    out2 = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert out2.returncode == 0, out2.stderr
+    assert "policy=" + names[other] in out2.stdout
+    assert cache.read_text().strip().splitlines() == ["%s %d" % (key, other)]
