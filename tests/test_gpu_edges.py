@@ -1,0 +1,49 @@
+"""Degenerate and boundary cases of the newer entry points: a gradient over
+zero steps, a one-spin group member, a group of a single replica, and a
+Hamiltonian of an all-zero state."""
+import numpy as np
+import pytest
+
+from _helpers import b, inputs, oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_grad_over_zero_steps(prec):
+    n, R = 50, 3
+    J = inputs.pm1_coupling(n, seed=31)
+    q0 = inputs.positions(n, R, seed0=3100)
+    with b.Context(J, replicas=R, steps=0, prec=prec) as c:
+        obj, gz, gd, gk = c.grad(np.zeros(0, np.float32), np.zeros(0, np.float32), q0)
+    assert gz.size == 0 and gd.size == 0 and gk == 0.0
+    ref = oracle.relaxed_energy(J, None, q0.astype(np.float64)).sum()
+    assert abs(obj - ref) <= 1e-5 * abs(ref)
+
+
+def test_group_with_one_spin_and_one_replica_members():
+    Js = [np.zeros((1, 1), np.float32), inputs.pm1_coupling(40, seed=32), inputs.pm1_coupling(3, seed=33)]
+    Rs = [5, 1, 16]
+    qs = [inputs.positions(J.shape[0], R, seed0=3200 + k) for k, (J, R) in enumerate(zip(Js, Rs))]
+    T = 3
+    zeta, dt = inputs.zeta_ramp(T), inputs.dt_const(T)
+    p0 = b.default_params()
+    kw = dict(k=float(p0.k), m=float(p0.m), q0=float(p0.q0), q_max=float(np.float32(p0.q_max)), p_max=float(p0.p_max))
+    with b.Group(Js, None, replicas=Rs, steps=T, precs="j_fp8_q_bf16") as g:
+        qg, pg, sg = g.run(zeta, dt, qs)
+        for k in range(len(Js)):
+            qo, po = oracle.run(Js[k], None, zeta, dt, qs[k], **kw)
+            np.testing.assert_allclose(qg[k], qo, rtol=0, atol=1e-3)
+            np.testing.assert_array_equal(sg[k], oracle.sign(qg[k]))
+            e, c, _ = g.energy(k, sg[k])
+            np.testing.assert_array_equal(e, oracle.energy(Js[k], None, sg[k]).astype(np.int64))
+    # the one-spin member is a free spring: q follows the oracle closely
+    np.testing.assert_allclose(qg[0], oracle.run(Js[0], None, zeta, dt, qs[0], **kw)[0], rtol=0, atol=1e-6)
+
+
+def test_hamiltonian_of_zero_state_is_zero():
+    n, R = 33, 4
+    J = inputs.gauss_coupling_bf16(n, seed=34)
+    with b.Context(J, replicas=R, steps=1, prec="fp32", q0=0.0) as c:
+        H = c.hamiltonian(np.zeros((R, n), np.float32), np.zeros((R, n), np.float32), 0.7)
+    assert (H == 0.0).all()
