@@ -305,7 +305,7 @@ static si_status adjoint_impl(Ctx *c, int steps, float *g_zeta, float *g_dt, flo
         if (c->g_ws) cudaFree(c->g_ws);
         c->g_ws = nullptr;
         c->g_ws_bytes = 0;
-        SI_CUDA_TRY(cudaMalloc(&c->g_ws, bytes));
+        SI_CUDA_TRY(si_dev_malloc(&c->g_ws, bytes));
         c->g_ws_bytes = bytes;
         // Zero once: the padding columns of every plane are never written
         // afterwards and must stay zero for the CUDA-core products.

@@ -514,8 +514,8 @@ si_status adj_tc_prepare(Ctx *c, AdjTc **out) {
     }
     t->splits = splits;
     t->kb_per = cdiv(t->kblocks, splits);
-    if (cudaMalloc((void **)&t->jb, sizeof(__nv_bfloat16) * (size_t)t->mpad * t->ldk) != cudaSuccess ||
-        cudaMalloc((void **)&t->xs, sizeof(__nv_bfloat16) * 3 * (size_t)t->nrb * AT_BN * t->ldk) != cudaSuccess) {
+    if (si_dev_malloc((void **)&t->jb, sizeof(__nv_bfloat16) * (size_t)t->mpad * t->ldk) != cudaSuccess ||
+        si_dev_malloc((void **)&t->xs, sizeof(__nv_bfloat16) * 3 * (size_t)t->nrb * AT_BN * t->ldk) != cudaSuccess) {
         cudaGetLastError();
         set_error("si_grad: out of device memory for the tensor-core workspace");
         return fail(SI_ERR_OOM);

@@ -1,6 +1,7 @@
 // C ABI of the Spring-Ising hot path: context life cycle, argument checks,
 // host/device staging and dispatch to the kernel families.
 #include <cmath>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -43,7 +44,7 @@ static si_status stage_in(DevIn &d, const void *src, size_t bytes, cudaStream_t 
         d.ptr = src;
         return SI_OK;
     }
-    SI_CUDA_TRY(cudaMalloc(&d.owned, bytes));
+    SI_CUDA_TRY(si_dev_malloc(&d.owned, bytes));
     SI_CUDA_TRY(cudaMemcpyAsync(d.owned, src, bytes, cudaMemcpyHostToDevice, st));
     d.ptr = d.owned;
     return SI_OK;
@@ -68,7 +69,7 @@ static si_status stage_out(DevOut &d, void *dst, size_t bytes) {
         d.ptr = dst;
         return SI_OK;
     }
-    SI_CUDA_TRY(cudaMalloc(&d.owned, bytes));
+    SI_CUDA_TRY(si_dev_malloc(&d.owned, bytes));
     d.ptr = d.owned;
     d.host = dst;
     return SI_OK;
@@ -97,6 +98,21 @@ static si_status check_device_error(Ctx *c) {
     }
     return SI_OK;
 }
+
+static std::atomic<long> g_alloc_count{0};
+
+cudaError_t dev_malloc_raw(void **p, size_t bytes) {
+    if (const char *e = std::getenv("SI_DEBUG_FAIL_ALLOC")) {
+        const long k = std::atol(e);
+        if (k > 0 && g_alloc_count.fetch_add(1) + 1 == k) {
+            *p = nullptr;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
+void alloc_fault_reset() { g_alloc_count = 0; }
 
 static void free_ctx(Ctx *c) {
     if (!c) return;
@@ -210,21 +226,21 @@ static si_status create_impl(Ctx *c, const float *J, const float *h) {
         c->path = (c->R <= 4) ? Path::PLAIN_PERSISTENT : Path::SIMT_TILED;
         s = simt_convert_j(c, (const float *)Jd.ptr, n);
         if (s != SI_OK) return s;
-        SI_CUDA_TRY(cudaMalloc(&c->dp, (size_t)c->R * n * es));
+        SI_CUDA_TRY(si_dev_malloc(&c->dp, (size_t)c->R * n * es));
         c->qbuf_bytes = 2 * (size_t)c->R * c->ldj * es;
-        SI_CUDA_TRY(cudaMalloc(&c->dqbuf, c->qbuf_bytes));
+        SI_CUDA_TRY(si_dev_malloc(&c->dqbuf, c->qbuf_bytes));
         SI_CUDA_TRY(cudaMemsetAsync(c->dqbuf, 0, c->qbuf_bytes, c->stream));
     }
-    if (c->integer_j) SI_CUDA_TRY(cudaMalloc((void **)&c->dJ8, (size_t)n * c->ld8));
+    if (c->integer_j) SI_CUDA_TRY(si_dev_malloc((void **)&c->dJ8, (size_t)n * c->ld8));
     // h copies.
-    SI_CUDA_TRY(cudaMalloc((void **)&c->dhf, sizeof(float) * n));
-    if (c->integer_h && c->has_h) SI_CUDA_TRY(cudaMalloc((void **)&c->dh8, n));
+    SI_CUDA_TRY(si_dev_malloc((void **)&c->dhf, sizeof(float) * n));
+    if (c->integer_h && c->has_h) SI_CUDA_TRY(si_dev_malloc((void **)&c->dh8, n));
     if (f64) {
-        SI_CUDA_TRY(cudaMalloc(&c->dh, sizeof(double) * n));
+        SI_CUDA_TRY(si_dev_malloc(&c->dh, sizeof(double) * n));
         k_copy_h<double><<<std::min(1024, cdiv(n, 256)), 256, 0, c->stream>>>(
             (const float *)hd.ptr, n, (double *)c->dh, c->dhf, c->dh8);
     } else {
-        SI_CUDA_TRY(cudaMalloc(&c->dh, sizeof(float) * n));
+        SI_CUDA_TRY(si_dev_malloc(&c->dh, sizeof(float) * n));
         k_copy_h<float><<<std::min(1024, cdiv(n, 256)), 256, 0, c->stream>>>(
             (const float *)hd.ptr, n, (float *)c->dh, c->dhf, c->dh8);
     }
@@ -235,13 +251,13 @@ static si_status create_impl(Ctx *c, const float *J, const float *h) {
         c->dh = nullptr;
     }
     const int sched = std::max(1, p.steps);
-    SI_CUDA_TRY(cudaMalloc((void **)&c->dzeta, sizeof(float) * sched));
-    SI_CUDA_TRY(cudaMalloc((void **)&c->ddt, sizeof(float) * sched));
+    SI_CUDA_TRY(si_dev_malloc((void **)&c->dzeta, sizeof(float) * sched));
+    SI_CUDA_TRY(si_dev_malloc((void **)&c->ddt, sizeof(float) * sched));
     c->nbar = 4096;
-    SI_CUDA_TRY(cudaMalloc((void **)&c->dbar, sizeof(unsigned) * c->nbar));
-    SI_CUDA_TRY(cudaMalloc((void **)&c->derr, sizeof(int)));
+    SI_CUDA_TRY(si_dev_malloc((void **)&c->dbar, sizeof(unsigned) * c->nbar));
+    SI_CUDA_TRY(si_dev_malloc((void **)&c->derr, sizeof(int)));
     SI_CUDA_TRY(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
-    SI_CUDA_TRY(cudaMalloc((void **)&c->dspins, (size_t)c->R * c->ld8));
+    SI_CUDA_TRY(si_dev_malloc((void **)&c->dspins, (size_t)c->R * c->ld8));
     SI_CUDA_TRY(cudaMemsetAsync(c->dspins, 0, (size_t)c->R * c->ld8, c->stream));
     if (c->integer_j) {
         si_status s8 = convert_j8(c, (const float *)Jd.ptr);
@@ -292,6 +308,7 @@ si_status si_create(si_ctx **out, const si_params *prm, const float *J, const fl
                     void *stream) {
     NvtxRange nvtx_range("si_create");
     set_error("");
+    alloc_fault_reset();
     if (!out || !J) {
         set_error("si_create: out and J are required");
         return SI_ERR_INVALID_ARG;
@@ -433,7 +450,7 @@ si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy
         if (c->dspins_in) cudaFree(c->dspins_in);
         c->dspins_in = nullptr;
         c->spins_in_cap = 0;
-        SI_CUDA_TRY(cudaMalloc((void **)&c->dspins_in, (size_t)R * c->ld8));
+        SI_CUDA_TRY(si_dev_malloc((void **)&c->dspins_in, (size_t)R * c->ld8));
         c->spins_in_cap = R;
     }
     k_pad_spins<<<std::min(4096, cdiv((long long)R * c->ld8, 256)), 256, 0, c->stream>>>(

@@ -184,14 +184,14 @@ si_status tc_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E, 
         if (c->e_sig) cudaFree(c->e_sig);
         c->e_sig = nullptr;
         c->e_sig_bytes = 0;
-        SI_CUDA_TRY(cudaMalloc(&c->e_sig, bytes));
+        SI_CUDA_TRY(si_dev_malloc(&c->e_sig, bytes));
         c->e_sig_bytes = bytes;
     }
     if (R > c->e_sum_cap) {
         if (c->e_sum) cudaFree(c->e_sum);
         c->e_sum = nullptr;
         c->e_sum_cap = 0;
-        SI_CUDA_TRY(cudaMalloc((void **)&c->e_sum, sizeof(unsigned long long) * R));
+        SI_CUDA_TRY(si_dev_malloc((void **)&c->e_sum, sizeof(unsigned long long) * R));
         c->e_sum_cap = R;
     }
     const int grid1 = std::min(8 * c->num_sms, cdiv((long long)rpad * c->ldk, 256));

@@ -475,7 +475,7 @@ __global__ void k_block_nonzero(const __nv_bfloat16 *J, int ldk, int kblocks, un
 static si_status member_block_lists(Group *g, GroupMember &x) {
     const int mtiles = x.mpad / GR_BM, kblocks = x.ldk / GR_BK;
     unsigned char *d_mask = nullptr;
-    SI_CUDA_TRY(cudaMalloc((void **)&d_mask, (size_t)mtiles * kblocks));
+    SI_CUDA_TRY(si_dev_malloc((void **)&d_mask, (size_t)mtiles * kblocks));
     k_block_nonzero<<<dim3(kblocks, mtiles), 256, 0, g->stream>>>((const __nv_bfloat16 *)x.J, x.ldk, kblocks, d_mask);
     cudaError_t e = cudaGetLastError();
     std::vector<unsigned char> mask((size_t)mtiles * kblocks);
@@ -540,10 +540,10 @@ static si_status group_build_policies(Group *g) {
     }
     size_t ntot = 0;
     for (auto &v : tiles) ntot += v.size();
-    SI_CUDA_TRY(cudaMalloc((void **)&g->d_inst, sizeof(GroupInst) * inst.size()));
-    SI_CUDA_TRY(cudaMalloc((void **)&g->d_maps, sizeof(CUtensorMap) * maps.size()));
-    SI_CUDA_TRY(cudaMalloc((void **)&g->d_tiles, sizeof(GroupTile) * ntot));
-    SI_CUDA_TRY(cudaMalloc((void **)&g->d_kbl, sizeof(int) * std::max<size_t>(1, g->kbl.size())));
+    SI_CUDA_TRY(si_dev_malloc((void **)&g->d_inst, sizeof(GroupInst) * inst.size()));
+    SI_CUDA_TRY(si_dev_malloc((void **)&g->d_maps, sizeof(CUtensorMap) * maps.size()));
+    SI_CUDA_TRY(si_dev_malloc((void **)&g->d_tiles, sizeof(GroupTile) * ntot));
+    SI_CUDA_TRY(si_dev_malloc((void **)&g->d_kbl, sizeof(int) * std::max<size_t>(1, g->kbl.size())));
     SI_CUDA_TRY(cudaMemcpyAsync(g->d_kbl, g->kbl.data(), sizeof(int) * g->kbl.size(), cudaMemcpyHostToDevice,
                                 g->stream));
     SI_CUDA_TRY(cudaMemcpyAsync(g->d_inst, inst.data(), sizeof(GroupInst) * inst.size(), cudaMemcpyHostToDevice,
@@ -733,51 +733,50 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
         x.rpad_max = std::max(round_up(x.R, 128), round_up(x.R, 16) <= 256 ? round_up(x.R, 16) : round_up(x.R, 256));
         const float *Jp = J[i];
         const float *hp = h ? h[i] : nullptr;
-        void *Jtmp = nullptr, *htmp = nullptr;
+        // device copies of host J / h for this member, freed on every exit
+        struct DevTmp {
+            void *p = nullptr;
+            ~DevTmp() {
+                if (p) cudaFree(p);
+            }
+        } Jtmp, htmp;
         if (!is_device_ptr(Jp)) {
-            SI_CUDA_TRY(cudaMalloc(&Jtmp, sizeof(float) * (size_t)n * n));
-            SI_CUDA_TRY(cudaMemcpyAsync(Jtmp, Jp, sizeof(float) * (size_t)n * n, cudaMemcpyHostToDevice, g->stream));
-            Jp = (const float *)Jtmp;
+            SI_CUDA_TRY(si_dev_malloc(&Jtmp.p, sizeof(float) * (size_t)n * n));
+            SI_CUDA_TRY(cudaMemcpyAsync(Jtmp.p, Jp, sizeof(float) * (size_t)n * n, cudaMemcpyHostToDevice, g->stream));
+            Jp = (const float *)Jtmp.p;
         }
         if (hp && !is_device_ptr(hp)) {
-            SI_CUDA_TRY(cudaMalloc(&htmp, sizeof(float) * n));
-            SI_CUDA_TRY(cudaMemcpyAsync(htmp, hp, sizeof(float) * n, cudaMemcpyHostToDevice, g->stream));
-            hp = (const float *)htmp;
+            SI_CUDA_TRY(si_dev_malloc(&htmp.p, sizeof(float) * n));
+            SI_CUDA_TRY(cudaMemcpyAsync(htmp.p, hp, sizeof(float) * n, cudaMemcpyHostToDevice, g->stream));
+            hp = (const float *)htmp.p;
         }
         unsigned long long flags = 0;
         long long s_upper = 0;
         si_status s = simt_validate(Jp, hp, n, prm[i].prec, &flags, &s_upper, g->stream);
-        auto cleanup = [&]() {
-            if (Jtmp) cudaFree(Jtmp);
-            if (htmp) cudaFree(htmp);
-        };
-        if (s != SI_OK) { cleanup(); return s; }
+        if (s != SI_OK) return s;
         if (flags & (VF_NONFINITE | VF_H_NONFINITE)) {
-            cleanup();
             set_error("group member " + std::to_string(i) + ": J or h holds a non-finite value");
             return SI_ERR_INVALID_ARG;
         }
         if (flags & (VF_ASYM | VF_DIAG)) {
-            cleanup();
             set_error("group member " + std::to_string(i) + ": J must be symmetric with a zero diagonal");
             return SI_ERR_NOT_SYMMETRIC;
         }
         if (prm[i].prec == SI_PREC_J_FP8_Q_BF16 && (flags & VF_NOT_E4M3)) {
-            cleanup();
             set_error("group member " + std::to_string(i) + ": SI_PREC_J_FP8_Q_BF16 needs J exact in e4m3");
             return SI_ERR_INVALID_ARG;
         }
-        SI_CUDA_TRY(cudaMalloc(&x.J, (size_t)x.mpad * x.ldk * 2));
+        SI_CUDA_TRY(si_dev_malloc(&x.J, (size_t)x.mpad * x.ldk * 2));
         s = tc_convert_j(Jp, n, x.J, x.ldk, x.mpad, g->sms, g->stream);
-        if (s != SI_OK) { cleanup(); return s; }
+        if (s != SI_OK) return s;
         // block sparsity: all-zero 128 x 64 blocks of J are never loaded
         s = member_block_lists(g, x);
-        if (s != SI_OK) { cleanup(); return s; }
-        SI_CUDA_TRY(cudaMalloc((void **)&x.q, sizeof(float) * (size_t)x.R * n));
-        SI_CUDA_TRY(cudaMalloc((void **)&x.p, sizeof(float) * (size_t)x.R * n));
-        SI_CUDA_TRY(cudaMalloc((void **)&x.spins, (size_t)x.R * n));
+        if (s != SI_OK) return s;
+        SI_CUDA_TRY(si_dev_malloc((void **)&x.q, sizeof(float) * (size_t)x.R * n));
+        SI_CUDA_TRY(si_dev_malloc((void **)&x.p, sizeof(float) * (size_t)x.R * n));
+        SI_CUDA_TRY(si_dev_malloc((void **)&x.spins, (size_t)x.R * n));
         const size_t qb = 2ull * x.rpad_max * x.ldk * 2;
-        SI_CUDA_TRY(cudaMalloc((void **)&x.qop, qb));
+        SI_CUDA_TRY(si_dev_malloc((void **)&x.qop, qb));
         SI_CUDA_TRY(cudaMemsetAsync(x.qop, 0, qb, g->stream));
         // readout view for si_group_energy
         Ctx &c = x.energy;
@@ -796,19 +795,19 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
         c.dJ = x.J;
         c.ldk = x.ldk;
         c.mpad = x.mpad;
-        SI_CUDA_TRY(cudaMalloc((void **)&x.h, sizeof(float) * n));
+        SI_CUDA_TRY(si_dev_malloc((void **)&x.h, sizeof(float) * n));
         if (hp) SI_CUDA_TRY(cudaMemcpyAsync(x.h, hp, sizeof(float) * n, cudaMemcpyDeviceToDevice, g->stream));
         else SI_CUDA_TRY(cudaMemsetAsync(x.h, 0, sizeof(float) * n, g->stream));
         c.dhf = x.h;
         if (c.integer_j) {
-            SI_CUDA_TRY(cudaMalloc((void **)&c.dJ8, (size_t)n * c.ld8));
+            SI_CUDA_TRY(si_dev_malloc((void **)&c.dJ8, (size_t)n * c.ld8));
             s = convert_j8(&c, Jp);
-            if (s != SI_OK) { cleanup(); return s; }
+            if (s != SI_OK) return s;
         }
         if (c.has_h && c.integer_h) {
-            SI_CUDA_TRY(cudaMalloc((void **)&c.dh8, n));
+            SI_CUDA_TRY(si_dev_malloc((void **)&c.dh8, n));
             s = h_to_int8(hp, n, c.dh8, g->stream);
-            if (s != SI_OK) { cleanup(); return s; }
+            if (s != SI_OK) return s;
         }
         SI_CUDA_TRY(cudaStreamSynchronize(g->stream));
         if (!hp) {
@@ -816,13 +815,12 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
             x.h = nullptr;
             c.dhf = nullptr;
         }
-        cleanup();
     }
     si_status sb = group_build_policies(g);
     if (sb != SI_OK) return sb;
-    SI_CUDA_TRY(cudaMalloc((void **)&g->d_zeta, sizeof(float) * std::max(1, g->steps)));
-    SI_CUDA_TRY(cudaMalloc((void **)&g->d_dt, sizeof(float) * std::max(1, g->steps)));
-    SI_CUDA_TRY(cudaMalloc((void **)&g->d_err, sizeof(int)));
+    SI_CUDA_TRY(si_dev_malloc((void **)&g->d_zeta, sizeof(float) * std::max(1, g->steps)));
+    SI_CUDA_TRY(si_dev_malloc((void **)&g->d_dt, sizeof(float) * std::max(1, g->steps)));
+    SI_CUDA_TRY(si_dev_malloc((void **)&g->d_err, sizeof(int)));
     SI_CUDA_TRY(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream));
     for (auto &x : g->m) {            // readout views share the group's error word
         x.energy.derr = g->d_err;
@@ -848,6 +846,7 @@ extern "C" {
 si_status si_create_group(si_group **out, int32_t count, const si_params *prm, const float *const *J,
                           const float *const *h, void *stream) {
     NvtxRange nvtx_range("si_create_group");
+    alloc_fault_reset();
     set_error("");
     if (!out || count < 1 || !prm || !J) {
         set_error("si_create_group: out, count >= 1, prm[count] and J[count] are required");

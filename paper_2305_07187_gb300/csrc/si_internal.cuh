@@ -27,6 +27,18 @@ void set_error(const std::string &msg);
         }                                                                      \
     } while (0)
 
+// Every device allocation of the library goes through si_dev_malloc.  With
+// SI_DEBUG_FAIL_ALLOC=k in the environment the k-th allocation after the
+// last si_create / si_create_group entry fails with
+// cudaErrorMemoryAllocation (fault injection for the error paths; host-side
+// only, nothing reaches the GPU).
+cudaError_t dev_malloc_raw(void **p, size_t bytes);
+void alloc_fault_reset();
+template <typename P>
+inline cudaError_t si_dev_malloc(P **p, size_t bytes) {
+    return dev_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+
 // Device error word values (written by kernels, read by the host).
 enum : int {
     DEV_OK = 0,

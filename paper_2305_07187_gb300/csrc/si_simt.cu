@@ -439,7 +439,7 @@ si_status simt_convert_j(Ctx *c, const float *J_dev, int n) {
     const bool f64 = c->prm.prec == SI_PREC_FP64;
     const size_t es = f64 ? 8 : 4;
     c->ldj = round_up(n, 16);
-    SI_CUDA_TRY(cudaMalloc(&c->dJ, (size_t)n * c->ldj * es));
+    SI_CUDA_TRY(si_dev_malloc(&c->dJ, (size_t)n * c->ldj * es));
     const int g = grid_for((long long)n * c->ldj, 256, c->num_sms);
     if (f64) k_convert_j<double><<<g, 256, 0, c->stream>>>(J_dev, n, (double *)c->dJ, c->ldj);
     else k_convert_j<float><<<g, 256, 0, c->stream>>>(J_dev, n, (float *)c->dJ, c->ldj);
@@ -605,7 +605,7 @@ si_status simt_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E
             if (c->dE) cudaFree(c->dE);
             c->dE = nullptr;
             c->e_cap = 0;
-            SI_CUDA_TRY(cudaMalloc((void **)&c->dE, sizeof(int32_t) * R));
+            SI_CUDA_TRY(si_dev_malloc((void **)&c->dE, sizeof(int32_t) * R));
             c->e_cap = R;
         }
         Euse = c->dE;

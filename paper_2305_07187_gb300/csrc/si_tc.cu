@@ -593,15 +593,15 @@ si_status tc_prepare(Ctx *c, const float *J_dev) {
     int per_sm = 0;
     c->tile_n = choose_tile(c, &per_sm);
     c->rpad = round_up(c->R, c->tile_n);
-    SI_CUDA_TRY(cudaMalloc(&c->dJ, (size_t)c->mpad * c->ldk * 2));
+    SI_CUDA_TRY(si_dev_malloc(&c->dJ, (size_t)c->mpad * c->ldk * 2));
     k_convert_j_bf16<<<std::min(8 * c->num_sms, cdiv((long long)c->mpad * c->ldk, 256)), 256, 0, c->stream>>>(
         J_dev, n, (__nv_bfloat16 *)c->dJ, c->ldk, c->mpad);
     SI_CUDA_TRY(cudaGetLastError());
     c->qbuf_bytes = 2ull * c->rpad * c->ldk * 2;
-    SI_CUDA_TRY(cudaMalloc(&c->dqbuf, c->qbuf_bytes));
+    SI_CUDA_TRY(si_dev_malloc(&c->dqbuf, c->qbuf_bytes));
     SI_CUDA_TRY(cudaMemsetAsync(c->dqbuf, 0, c->qbuf_bytes, c->stream));
-    SI_CUDA_TRY(cudaMalloc(&c->dq, sizeof(float) * (size_t)c->R * n));
-    SI_CUDA_TRY(cudaMalloc(&c->dp, sizeof(float) * (size_t)c->R * n));
+    SI_CUDA_TRY(si_dev_malloc(&c->dq, sizeof(float) * (size_t)c->R * n));
+    SI_CUDA_TRY(si_dev_malloc(&c->dp, sizeof(float) * (size_t)c->R * n));
     si_status s = tc_make_map_bf16(&c->mapA, c->dJ, c->ldk, c->mpad, TC_BK, TC_BM);
     if (s != SI_OK) return s;
     s = tc_make_map_bf16(&c->mapB, c->dqbuf, c->ldk, 2 * c->rpad, TC_BK, c->tile_n);
