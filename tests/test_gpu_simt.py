@@ -12,7 +12,8 @@ TOL_FP64_100 = 1e-10     # FP64 debug path, 100 free-running steps
 
 
 @pytest.mark.parametrize("n,R", [(1, 1), (17, 1), (127, 2), (129, 3), (300, 4),
-                                 (2000, 1), (5, 5), (70, 17), (130, 64), (257, 100)])
+                                 (2000, 1), (2001, 1), (5, 5), (70, 17), (130, 64), (257, 100),
+                                 (2001, 15), (2001, 16)])
 def test_fp32_per_step_teacher_forced(n, R):
     J = inputs.pm1_coupling(n, seed=n)
     T = 40

@@ -44,7 +44,7 @@ def _teacher_forced_tc(J, R, T, prec="j_fp8_q_bf16", bf16_exact=False, h=None, s
 
 
 @pytest.mark.parametrize("n,R", [(1, 1), (17, 3), (128, 16), (129, 17), (300, 64), (640, 100),
-                                 (2000, 130)])
+                                 (2000, 130), (2001, 15), (2001, 17)])
 def test_tc_per_step_within_bf16_bound(n, R):
     J = inputs.pm1_coupling(n, seed=n)
     assert _teacher_forced_tc(J, R, T=12) <= 1.0
