@@ -47,7 +47,8 @@ struct GroupInst {
 };
 
 struct GroupTile {
-    int inst, mt, rb, cost;
+    int inst, mt, r0, bn;      // replicas r0 .. r0 + bn - 1 (bn: the instance's width or half of it)
+    int cost;
     int kb_off, kb_cnt;        // the M tile's non-zero K blocks: kbl[kb_off .. kb_off + kb_cnt)
 };
 
@@ -55,7 +56,7 @@ struct GroupArgs {
     const GroupInst *inst;
     const GroupTile *tiles;
     int ntiles;
-    const CUtensorMap *maps;   // [2*count]: J map, q map of each instance
+    const CUtensorMap *maps;   // [3*count]: J map, q map (width bn), q map (width bn/2) of each instance
     const int *kbl;            // K-block lists of all (instance, M tile)
     const float *zeta, *dt;
     int t, last;
@@ -132,10 +133,10 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
             for (int k = blockIdx.x; k < a.ntiles && ok; k += gridDim.x) {
                 const GroupTile tl = a.tiles[k];
                 const GroupInst &in = a.inst[tl.inst];
-                const CUtensorMap *mJ = a.maps + 2 * tl.inst;
-                const CUtensorMap *mQ = mJ + 1;
-                const uint32_t bytes = (uint32_t)(GR_A_BYTES + in.bn * GR_BK * 2);
-                const int yq = plane_in * in.rpad + tl.rb * in.bn;
+                const CUtensorMap *mJ = a.maps + 3 * tl.inst;
+                const CUtensorMap *mQ = mJ + (tl.bn == in.bn ? 1 : 2);
+                const uint32_t bytes = (uint32_t)(GR_A_BYTES + tl.bn * GR_BK * 2);
+                const int yq = plane_in * in.rpad + tl.r0;
                 for (int j = 0; j < tl.kb_cnt; ++j) {
                     const int kb = a.kbl[tl.kb_off + j];
                     const int ring = a.single ? 0 : (j & 1);
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                     }
                 }
                 tc_fence_after();
-                const uint32_t idesc = idesc_bf16(GR_BM, in.bn);
+                const uint32_t idesc = idesc_bf16(GR_BM, tl.bn);
                 if (a.single) {
                     if (w == 0) {
                         const uint32_t d_tmem = tmem + (uint32_t)slot * 256u;
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
             const bool row_ok = i < in.n;
             const float hi = (in.h && row_ok) ? in.h[i] : 0.f;
             const bool two_acc = !a.single && tl.kb_cnt > 1;
-            const int nch = in.bn / 16;
+            const int nch = tl.bn / 16;
             constexpr int NPART = GR_EPI / 4;
             const int c0 = (nch * half + NPART - 1) / NPART;
             const int c1 = (nch * (half + 1) + NPART - 1) / NPART;
@@ -284,14 +285,14 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                     float qv[16], pv[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const int r = tl.rb * in.bn + c * 16 + j;
+                        const int r = tl.r0 + c * 16 + j;
                         const size_t e = (size_t)r * in.n + i;
                         qv[j] = r < in.R ? in.q_state[e] : 0.f;
                         pv[j] = r < in.R ? in.p_state[e] : 0.f;
                     }
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const int r = tl.rb * in.bn + c * 16 + j;
+                        const int r = tl.r0 + c * 16 + j;
                         if (r >= in.R) continue;
                         float F = __uint_as_float(vf[j]);
                         if (two_acc) F += __uint_as_float(vg[j]);
@@ -496,13 +497,71 @@ static si_status member_block_lists(Group *g, GroupMember &x) {
     return SI_OK;
 }
 
+// Tile cost model: a K block moves its J tile and bn replica rows through
+// shared memory twice (TMA write, MMA read), 16 KB + bn * 128 B each way.
+static int tile_cost(int kb_cnt, int bn) { return kb_cnt * (128 + bn); }
+static bool half_width(int bn) { return bn % 32 == 0 && bn >= 32; }
+
+// Round-robin makespan of a cost-sorted tile list on `grid` CTAs (the kernel
+// walks the list with stride gridDim.x).
+static long long rr_makespan(const std::vector<GroupTile> &t, int grid) {
+    std::vector<long long> load((size_t)grid, 0);
+    for (size_t k = 0; k < t.size(); ++k) load[k % grid] += t[k].cost;
+    return *std::max_element(load.begin(), load.end());
+}
+
+static void sort_tiles(std::vector<GroupTile> &t) {
+    // Longest first; tiles of one M slab stay adjacent so that concurrent
+    // replica blocks share the J slab through L2.
+    std::stable_sort(t.begin(), t.end(), [](const GroupTile &x, const GroupTile &y) { return x.cost > y.cost; });
+}
+
+// The last wave of equal tiles leaves most CTAs idle (N=32768, R=512: 512
+// tiles on 152 CTAs, 4 waves for some, 3 for the rest).  Splitting the
+// cheapest s tiles into two tiles of half the replicas fills it: try a range
+// of s and keep the list with the smallest round-robin makespan.
+static void balance_tiles(std::vector<GroupTile> &tiles, int grid) {
+    sort_tiles(tiles);
+    if (grid <= 0 || tiles.size() <= (size_t)grid) return;
+    std::vector<GroupTile> best = tiles;
+    long long best_ms = rr_makespan(tiles, grid);
+    const int T = (int)tiles.size();
+    const int step = std::max(1, T / 128);
+    for (int sidx = step; sidx <= T; sidx += step) {
+        std::vector<GroupTile> cand;
+        cand.reserve((size_t)T + sidx);
+        int split = 0;
+        for (int k = T - 1; k >= 0; --k) {
+            const GroupTile &x = tiles[k];
+            if (split < sidx && half_width(x.bn)) {
+                GroupTile a = x, b = x;
+                a.bn = b.bn = x.bn / 2;
+                b.r0 = x.r0 + a.bn;
+                a.cost = b.cost = tile_cost(x.kb_cnt, a.bn);
+                cand.push_back(a);
+                cand.push_back(b);
+                ++split;
+            } else {
+                cand.push_back(x);
+            }
+        }
+        sort_tiles(cand);
+        const long long ms = rr_makespan(cand, grid);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = cand;
+        }
+    }
+    tiles.swap(best);
+}
+
 // Build, once at creation, the instance table, tensor maps and tile list of
 // every tile policy (device tables are never rewritten after a launch used
 // them); group_apply_policy only selects one.
 static si_status group_build_policies(Group *g) {
     const int c = g->count;
     std::vector<GroupInst> inst((size_t)kPolicies * c);
-    std::vector<CUtensorMap> maps((size_t)kPolicies * 2 * c);
+    std::vector<CUtensorMap> maps((size_t)kPolicies * 3 * c);
     std::vector<std::vector<GroupTile>> tiles(kPolicies);
     for (int pol = 0; pol < kPolicies; ++pol) {
         std::vector<int> bns;
@@ -524,19 +583,19 @@ static si_status group_build_policies(Group *g) {
             d.p_state = x.p;
             d.qop = x.qop;
             d.spins = x.spins;
-            CUtensorMap *mp = &maps[((size_t)pol * c + i) * 2];
+            CUtensorMap *mp = &maps[((size_t)pol * c + i) * 3];
             si_status s = tc_make_map_bf16(mp, x.J, x.ldk, x.mpad, GR_BK, GR_BM);
             if (s != SI_OK) return s;
             s = tc_make_map_bf16(mp + 1, x.qop, x.ldk, 2 * x.rpad_max, GR_BK, d.bn);
             if (s != SI_OK) return s;
+            s = tc_make_map_bf16(mp + 2, x.qop, x.ldk, 2 * x.rpad_max, GR_BK, half_width(d.bn) ? d.bn / 2 : d.bn);
+            if (s != SI_OK) return s;
             for (int mt = 0; mt < d.mtiles; ++mt)
                 for (int rb = 0; rb < d.rblocks; ++rb)
-                    tiles[pol].push_back(GroupTile{i, mt, rb, x.kb_cnt[mt] * (d.bn + 64), x.kb_off[mt], x.kb_cnt[mt]});
+                    tiles[pol].push_back(GroupTile{i, mt, rb * d.bn, d.bn, tile_cost(x.kb_cnt[mt], d.bn),
+                                                   x.kb_off[mt], x.kb_cnt[mt]});
         }
-        // Longest first; tiles of one M slab stay adjacent so that concurrent
-        // replica blocks share the J slab through L2.
-        std::stable_sort(tiles[pol].begin(), tiles[pol].end(),
-                         [](const GroupTile &x, const GroupTile &y) { return x.cost > y.cost; });
+        balance_tiles(tiles[pol], g->sms);
     }
     size_t ntot = 0;
     for (auto &v : tiles) ntot += v.size();
@@ -578,7 +637,7 @@ static si_status group_launch_step(Group *g, int t, int steps) {
     a.inst = g->d_inst + (size_t)g->policy * g->count;
     a.tiles = g->d_tiles + g->pol_tiles_off[g->policy];
     a.ntiles = g->ntiles;
-    a.maps = g->d_maps + (size_t)g->policy * 2 * g->count;
+    a.maps = g->d_maps + (size_t)g->policy * 3 * g->count;
     a.kbl = g->d_kbl;
     a.zeta = g->d_zeta;
     a.dt = g->d_dt;
