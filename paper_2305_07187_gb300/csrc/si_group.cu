@@ -517,12 +517,13 @@ static void sort_tiles(std::vector<GroupTile> &t) {
 }
 
 // The last wave of equal tiles leaves most CTAs idle (N=32768, R=512: 512
-// tiles on 152 CTAs, 4 waves for some, 3 for the rest).  Splitting the
-// cheapest s tiles into two tiles of half the replicas fills it: try a range
-// of s and keep the list with the smallest round-robin makespan.
+// tiles on 152 CTAs, 4 waves for some, 3 for the rest), and a list shorter
+// than the grid leaves CTAs without work.  Splitting the cheapest s tiles
+// into two tiles of half the replicas fills them: try a range of s and keep
+// the list with the smallest round-robin makespan.
 static void balance_tiles(std::vector<GroupTile> &tiles, int grid) {
     sort_tiles(tiles);
-    if (grid <= 0 || tiles.size() <= (size_t)grid) return;
+    if (grid <= 0 || tiles.empty()) return;
     std::vector<GroupTile> best = tiles;
     long long best_ms = rr_makespan(tiles, grid);
     const int T = (int)tiles.size();

@@ -179,3 +179,37 @@ def test_autotune_cache_persists_across_processes(tmp_path):
     assert out2.returncode == 0, out2.stderr
     assert "policy=" + names[other] in out2.stdout
     assert cache.read_text().strip().splitlines() == ["%s %d" % (key, other)]
+
+
+@pytest.mark.parametrize("policy,n,R", [(1, 3072, 512), (2, 1280, 256), (3, 12288, 512)])
+def test_group_split_tiles_per_step(policy, n, R, monkeypatch):
+    """Tile lists with more tiles than CTAs: some tiles are split into two of
+    half the replicas (the describe string's tile count exceeds the plain
+    count).  One step from the same state, checked against the oracle on a
+    sample of replicas spread over every tile (replicas are independent)."""
+    import re
+    import torch
+    monkeypatch.setenv("SI_GROUP_POLICY", str(policy))
+    J = inputs.pm1_coupling_torch(n, seed=60 + policy, device="cuda")
+    q = inputs.positions_torch(n, R, seed=6000 + policy, device="cuda")
+    z = torch.tensor([0.3], device="cuda")
+    d = torch.tensor([0.2], device="cuda")
+    with b.Group([J], None, replicas=[R], steps=1, precs="j_fp8_q_bf16") as g:
+        qo_d = torch.empty_like(q)
+        po_d = torch.empty_like(q)
+        g.run_into(z, d, [q], None, [qo_d], [po_d], None)
+        torch.cuda.synchronize()
+        desc = g.describe()
+    bn = {1: 64, 2: 128, 3: 256}[policy]
+    plain_tiles = (-(-n // 128)) * (-(-R // bn))
+    assert int(re.search(r"tiles=(\d+)", desc).group(1)) > plain_tiles, desc
+    sample = np.arange(3, R, 37)
+    Jh = J.cpu().numpy().astype(np.float64)
+    qh = q.cpu().numpy()[sample].astype(np.float64)
+    p0 = b.default_params()
+    kw = dict(k=float(p0.k), m=float(p0.m), q0=float(p0.q0), q_max=float(np.float32(p0.q_max)), p_max=float(p0.p_max))
+    qo, po = oracle.run(Jh, None, np.array([0.3]), np.array([0.2]), qh, None, **kw)
+    eq, ep = bf16_step_bound(Jh, qh, np.zeros_like(qh), 0.3, 0.2, kw)
+    qg = qo_d.cpu().numpy()[sample]
+    pg = po_d.cpu().numpy()[sample]
+    assert (np.abs(qg - qo) <= eq).all() and (np.abs(pg - po) <= ep).all()
