@@ -235,7 +235,7 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
         qb = torch.empty_like(qa)
         pb = torch.empty_like(qa)
         sp = torch.empty((R, n), dtype=torch.int8, device=dev)
-        cut_d = torch.empty(R, dtype=torch.int32, device=dev)
+        cut_h = np.empty(R, dtype=np.int32)
         for seed in range(seeds + 1):
             q_init = torch.from_numpy(inputs.positions(n, R, seed0=200000 + 4096 * seed)).to(dev)
             torch.cuda.synchronize()
@@ -246,8 +246,8 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
             for seg in range(T_STEPS // every):
                 sl = slice(seg * every, (seg + 1) * every)
                 cb.run_into(zb[sl], db[sl], qa, pa, qb, pb, sp)
-                cb.energy_into(sp, R, None, cut_d, None)
-                if int(cut_d.max().item()) >= c_star:
+                cb.energy_into(sp, R, None, cut_h, None)   # cuts to host within the call
+                if int(cut_h.max()) >= c_star:
                     hit = (seg + 1) * every
                     break
                 qa, qb = qb, qa

@@ -14,9 +14,10 @@
  * General conventions
  *   - Every pointer argument may be host or device memory; the library tells
  *     them apart with cudaPointerGetAttributes.  Host inputs are copied in on
- *     the context's stream; host outputs are copied out and the stream is
- *     synchronised before the call returns.  With device pointers only, calls
- *     are asynchronous with respect to the host except where stated.
+ *     the context's stream; host outputs are copied out.  The computing
+ *     calls (si_run, si_energy, si_grad, si_hamiltonian, si_run_group,
+ *     si_group_energy) return after their work has finished: they end by
+ *     reading the device error word or synchronising the context's stream.
  *   - The caller owns every buffer it passes.  The context owns its device
  *     copy of J, the integrator state, the operand buffers and the
  *     checkpoints, all allocated in si_create and freed in si_destroy.
@@ -25,7 +26,8 @@
  *   - No call aborts the process.  Each returns an si_status; si_last_error()
  *     gives a message for the last failure on the calling thread.  A device
  *     wait that exceeds its time limit ends the kernel cooperatively and is
- *     reported as SI_ERR_TIMEOUT; the context stays usable.
+ *     reported as SI_ERR_TIMEOUT; the context stays usable.  After an
+ *     error status the contents of the call's outputs are unspecified.
  */
 #ifndef SPRING_ISING_H
 #define SPRING_ISING_H

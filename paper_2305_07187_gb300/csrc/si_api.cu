@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 
 #include "si_internal.cuh"
@@ -81,6 +82,20 @@ static si_status finish_out(DevOut &d, cudaStream_t st) {
 }
 
 // Read and clear the device error word; synchronises the stream.
+static si_status check_device_error(Ctx *c);
+
+// End of a call: enqueue the copies to host outputs, then one synchronising
+// read of the device error word covers them and every launch before.
+static si_status finish_call(Ctx *c, std::initializer_list<DevOut *> outs) {
+    for (DevOut *d : outs) {
+        si_status s = finish_out(*d, c->stream);
+        if (s != SI_OK) return s;
+    }
+    if (c->derr) return check_device_error(c);
+    SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return SI_OK;
+}
+
 static si_status check_device_error(Ctx *c) {
     int herr = 0;
     SI_CUDA_TRY(cudaMemcpyAsync(&herr, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -373,8 +388,6 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
         SI_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
         c->ev_valid = true;
     }
-    if ((s = check_device_error(c)) != SI_OK) return s;
-    c->have_run = true;
     if (q_out || p_out) {
         if (c->path == Path::TENSOR) s = tc_copy_state(c, (float *)qo.ptr, (float *)po.ptr);
         else s = simt_copy_state(c, (float *)qo.ptr, (float *)po.ptr);
@@ -394,10 +407,8 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
         SI_CUDA_TRY(cudaGetLastError());
         c->launches += 1;
     }
-    if ((s = finish_out(qo, c->stream)) != SI_OK) return s;
-    if ((s = finish_out(po, c->stream)) != SI_OK) return s;
-    if ((s = finish_out(so, c->stream)) != SI_OK) return s;
-    SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if ((s = finish_call(c, {&qo, &po, &so})) != SI_OK) return s;
+    c->have_run = true;
     return SI_OK;
 }
 
@@ -463,12 +474,7 @@ si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy
     if ((s = stage_out(fo, energy_f, sizeof(double) * R)) != SI_OK) return s;
     s = simt_energy(c, c->dspins_in, R, c->ld8, (int32_t *)eo.ptr, (int32_t *)co.ptr, (double *)fo.ptr);
     if (s != SI_OK) return s;
-    if (c->derr && (s = check_device_error(c)) != SI_OK) return s;
-    if ((s = finish_out(eo, c->stream)) != SI_OK) return s;
-    if ((s = finish_out(co, c->stream)) != SI_OK) return s;
-    if ((s = finish_out(fo, c->stream)) != SI_OK) return s;
-    SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    return SI_OK;
+    return finish_call(c, {&eo, &co, &fo});
 }
 
 si_status si_hamiltonian(si_ctx *ctx, const float *q, const float *p, int32_t R, double zeta,
@@ -531,13 +537,7 @@ si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt, const float *
     s = adjoint_grad(c, steps, (float *)gz.ptr, (float *)gd.ptr, (float *)gk.ptr, (float *)ob.ptr,
                      (const float *)qi.ptr, (const float *)pi.ptr);
     if (s != SI_OK) return s;
-    if ((s = check_device_error(c)) != SI_OK) return s;
-    if ((s = finish_out(gz, c->stream)) != SI_OK) return s;
-    if ((s = finish_out(gd, c->stream)) != SI_OK) return s;
-    if ((s = finish_out(gk, c->stream)) != SI_OK) return s;
-    if ((s = finish_out(ob, c->stream)) != SI_OK) return s;
-    SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    return SI_OK;
+    return finish_call(c, {&gz, &gd, &gk, &ob});
 }
 
 si_status si_describe(const si_ctx *ctx, char *buf, int32_t len) {

@@ -110,6 +110,7 @@ struct Ctx {
 
     // Tensor path configuration.
     int tile_n = 0;                      // replicas per CTA
+    int tc_per_sm = 0;                   // co-resident CTAs per SM of the step kernel (0: not yet queried)
     int stages = 0;
     int rpad = 0;                        // R rounded up to tile_n
     CUtensorMap mapA, mapB;              // J tiles, q operand tiles

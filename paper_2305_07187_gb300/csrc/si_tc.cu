@@ -527,16 +527,23 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
     }
     const int smem = L::TOTAL + (EPI == 4 ? 256 : 1024);
     a.smem_bytes = smem;
-    SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S, EPI>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                     (int)cudaSharedmemCarveoutMaxShared));
-    int per_sm = 0;
-    SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_run<BN, S, EPI>, tc_threads<EPI>(), smem));
+    // launch attributes and the co-residency check once per context (its
+    // device and tile are fixed)
+    if (c->tc_per_sm <= 0) {
+        SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S, EPI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         (int)cudaSharedmemCarveoutMaxShared));
+        int per_sm = 0;
+        SI_CUDA_TRY(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_run<BN, S, EPI>, tc_threads<EPI>(), smem));
+        c->tc_per_sm = per_sm;
+    }
+    const int per_sm = c->tc_per_sm;
     if (per_sm * c->num_sms < grid) {
         set_error("tensor path: grid cannot be co-resident (reduce replicas per context)");
         return SI_ERR_UNSUPPORTED;
     }
-    SI_CUDA_TRY(cudaMemsetAsync(c->dbar, 0, sizeof(unsigned) * c->nbar, c->stream));
+    SI_CUDA_TRY(cudaMemsetAsync(c->dbar, 0, sizeof(unsigned) * grid, c->stream));
     void *args[] = {(void *)&c->mapA, (void *)&c->mapB, (void *)&a};
     SI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_tc_run<BN, S, EPI>, dim3(grid), dim3(tc_threads<EPI>()),
                                             args, smem, c->stream));
