@@ -23,7 +23,12 @@ bool is_device_ptr(const void *p) {
         cudaGetLastError();  // clear the sticky-free error of a failed query
         return false;
     }
-    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    if (attr.type == cudaMemoryTypeManaged) return true;
+    if (attr.type != cudaMemoryTypeDevice) return false;
+    // memory of another GPU is staged like host memory (copied with
+    // cudaMemcpyDefault), so no kernel here dereferences a peer address
+    int dev = 0;
+    return cudaGetDevice(&dev) == cudaSuccess && attr.device == dev;
 }
 
 // A pointer argument staged on the device: either the caller's device
@@ -46,7 +51,7 @@ static si_status stage_in(DevIn &d, const void *src, size_t bytes, cudaStream_t 
         return SI_OK;
     }
     SI_CUDA_TRY(si_dev_malloc(&d.owned, bytes));
-    SI_CUDA_TRY(cudaMemcpyAsync(d.owned, src, bytes, cudaMemcpyHostToDevice, st));
+    SI_CUDA_TRY(cudaMemcpyAsync(d.owned, src, bytes, cudaMemcpyDefault, st));
     d.ptr = d.owned;
     return SI_OK;
 }
@@ -77,7 +82,7 @@ static si_status stage_out(DevOut &d, void *dst, size_t bytes) {
 }
 
 static si_status finish_out(DevOut &d, cudaStream_t st) {
-    if (d.host) SI_CUDA_TRY(cudaMemcpyAsync(d.host, d.ptr, d.bytes, cudaMemcpyDeviceToHost, st));
+    if (d.host) SI_CUDA_TRY(cudaMemcpyAsync(d.host, d.ptr, d.bytes, cudaMemcpyDefault, st));
     return SI_OK;
 }
 
@@ -357,8 +362,7 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
     const int steps = c->prm.steps, n = c->n, R = c->R;
     const size_t sb = sizeof(float) * std::max(steps, 1);
     if (steps > 0) {
-        const cudaMemcpyKind kz = is_device_ptr(zeta) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        const cudaMemcpyKind kd = is_device_ptr(dt) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        const cudaMemcpyKind kz = cudaMemcpyDefault, kd = cudaMemcpyDefault;
         SI_CUDA_TRY(cudaMemcpyAsync(c->dzeta, zeta, sizeof(float) * steps, kz, c->stream));
         SI_CUDA_TRY(cudaMemcpyAsync(c->ddt, dt, sizeof(float) * steps, kd, c->stream));
     }
@@ -519,8 +523,7 @@ si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt, const float *
     c->launches = 0;
     const int steps = c->prm.steps, n = c->n, R = c->R;
     if (steps > 0) {
-        const cudaMemcpyKind kz = is_device_ptr(zeta) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-        const cudaMemcpyKind kd = is_device_ptr(dt) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        const cudaMemcpyKind kz = cudaMemcpyDefault, kd = cudaMemcpyDefault;
         SI_CUDA_TRY(cudaMemcpyAsync(c->dzeta, zeta, sizeof(float) * steps, kz, c->stream));
         SI_CUDA_TRY(cudaMemcpyAsync(c->ddt, dt, sizeof(float) * steps, kd, c->stream));
     }

@@ -802,12 +802,12 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
         } Jtmp, htmp;
         if (!is_device_ptr(Jp)) {
             SI_CUDA_TRY(si_dev_malloc(&Jtmp.p, sizeof(float) * (size_t)n * n));
-            SI_CUDA_TRY(cudaMemcpyAsync(Jtmp.p, Jp, sizeof(float) * (size_t)n * n, cudaMemcpyHostToDevice, g->stream));
+            SI_CUDA_TRY(cudaMemcpyAsync(Jtmp.p, Jp, sizeof(float) * (size_t)n * n, cudaMemcpyDefault, g->stream));
             Jp = (const float *)Jtmp.p;
         }
         if (hp && !is_device_ptr(hp)) {
             SI_CUDA_TRY(si_dev_malloc(&htmp.p, sizeof(float) * n));
-            SI_CUDA_TRY(cudaMemcpyAsync(htmp.p, hp, sizeof(float) * n, cudaMemcpyHostToDevice, g->stream));
+            SI_CUDA_TRY(cudaMemcpyAsync(htmp.p, hp, sizeof(float) * n, cudaMemcpyDefault, g->stream));
             hp = (const float *)htmp.p;
         }
         unsigned long long flags = 0;
@@ -967,10 +967,8 @@ si_status si_run_group(si_group *grp, const float *zeta, const float *dt, const 
     g->launches = 0;
     const int steps = g->steps;
     if (steps > 0) {
-        SI_CUDA_TRY(cudaMemcpyAsync(g->d_zeta, zeta, sizeof(float) * steps,
-                                    is_device_ptr(zeta) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
-        SI_CUDA_TRY(cudaMemcpyAsync(g->d_dt, dt, sizeof(float) * steps,
-                                    is_device_ptr(dt) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->stream));
+        SI_CUDA_TRY(cudaMemcpyAsync(g->d_zeta, zeta, sizeof(float) * steps, cudaMemcpyDefault, g->stream));
+        SI_CUDA_TRY(cudaMemcpyAsync(g->d_dt, dt, sizeof(float) * steps, cudaMemcpyDefault, g->stream));
     }
     auto load_state = [&]() -> si_status {
         for (int i = 0; i < g->count; ++i) {
