@@ -249,7 +249,6 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
         pa = torch.zeros_like(qa)
         qb = torch.empty_like(qa)
         pb = torch.empty_like(qa)
-        sp = torch.empty((R, n), dtype=torch.int8, device=dev)
         cut_h = np.empty(R, dtype=np.int32)
         for seed in range(seeds + 1):
             q_init = torch.from_numpy(inputs.positions(n, R, seed0=200000 + 4096 * seed)).to(dev)
@@ -260,8 +259,8 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
             hit = None
             for seg in range(T_STEPS // every):
                 sl = slice(seg * every, (seg + 1) * every)
-                cb.run_into(zb[sl], db[sl], qa, pa, qb, pb, sp)
-                cb.energy_into(sp, R, None, cut_h, None)   # cuts to host within the call
+                cb.run_into(zb[sl], db[sl], qa, pa, qb, pb, None)
+                cb.energy_into(None, R, None, cut_h, None)   # the run's own spins; cuts to host in the call
                 if int(cut_h.max()) >= c_star:
                     hit = (seg + 1) * every
                     break

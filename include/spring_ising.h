@@ -130,7 +130,10 @@ si_status si_get_state(si_ctx *ctx, double *q_out, double *p_out);
 
 /*
  * Ising energy of Eq. 1 and cut value for R spin vectors.
- *   spins      [R][n] int8 in {-1,+1}
+ *   spins      [R][n] int8 in {-1,+1}; or NULL for the sign readout of the
+ *              final state of the last si_run on this context (R must then
+ *              equal the context's replica count; SI_ERR_INVALID_ARG if no
+ *              si_run has completed since creation or since the last si_grad)
  *   energy_out [R] exact int32 energy; requires J and h integer-valued with
  *              |J_ij|, |h_i| <= 127 (else SI_ERR_UNSUPPORTED); or NULL
  *   cut_out    [R] exact int32 cut of the MAX-CUT instance with weights

@@ -273,9 +273,13 @@ class Context:
         _check(load().si_energy(self.ctx, sp.ptr, int(R), eo.ptr, co.ptr, fo.ptr))
 
     def energy(self, spins, exact=True):
-        """Host convenience: returns (energy_int32 or None, cut or None, energy_f)."""
-        s = spins if _is_torch(spins) else np.ascontiguousarray(spins, dtype=np.int8)
-        R = int(s.numel() // self.n) if _is_torch(s) else s.size // self.n
+        """Host convenience: returns (energy_int32 or None, cut or None, energy_f).
+        spins=None reads the spins of the last run() on this context."""
+        if spins is None:
+            s, R = None, self.replicas
+        else:
+            s = spins if _is_torch(spins) else np.ascontiguousarray(spins, dtype=np.int8)
+            R = int(s.numel() // self.n) if _is_torch(s) else s.size // self.n
         e = np.empty(R, np.int32) if exact else None
         c = np.empty(R, np.int32) if exact else None
         f = np.empty(R, np.float64)

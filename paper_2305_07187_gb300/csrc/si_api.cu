@@ -397,15 +397,16 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
         else s = simt_copy_state(c, (float *)qo.ptr, (float *)po.ptr);
         if (s != SI_OK) return s;
     }
-    if (spins_out) {
-        if (steps == 0) {
-            // no step ran: spins of the initial positions
-            if (c->path == Path::TENSOR) {
-                if ((s = tc_spins(c, c->dspins, c->ld8)) != SI_OK) return s;
-            } else if ((s = simt_spins(c, c->dspins, c->ld8)) != SI_OK) {
-                return s;
-            }
+    if (steps == 0) {
+        // no step ran: spins of the initial positions
+        if (c->path == Path::TENSOR) {
+            if ((s = tc_spins(c, c->dspins, c->ld8)) != SI_OK) return s;
+        } else if ((s = simt_spins(c, c->dspins, c->ld8)) != SI_OK) {
+            return s;
         }
+    }
+    c->run_spins_valid = false;
+    if (spins_out) {
         k_unpad_spins<<<std::min(4096, cdiv((long long)R * n, 256)), 256, 0, c->stream>>>(
             c->dspins, c->ld8, n, R, (int8_t *)so.ptr);
         SI_CUDA_TRY(cudaGetLastError());
@@ -413,6 +414,7 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
     }
     if ((s = finish_call(c, {&qo, &po, &so})) != SI_OK) return s;
     c->have_run = true;
+    c->run_spins_valid = true;
     return SI_OK;
 }
 
@@ -443,8 +445,12 @@ si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy
     NvtxRange nvtx_range("si_energy");
     set_error("");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
-    if (!c || !spins || R < 0) {
-        set_error("si_energy: ctx and spins are required, R >= 0");
+    if (!c || R < 0) {
+        set_error("si_energy: ctx is required, R >= 0");
+        return SI_ERR_INVALID_ARG;
+    }
+    if (!spins && (!c->run_spins_valid || R != c->R)) {
+        set_error("si_energy: spins NULL reads the last si_run's spins: needs a completed si_run and R = replicas");
         return SI_ERR_INVALID_ARG;
     }
     c->launches = 0;
@@ -458,8 +464,19 @@ si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy
         return SI_ERR_UNSUPPORTED;
     }
     const int n = c->n;
+    si_status s;
+    DevOut eo, co, fo;
+    if ((s = stage_out(eo, energy_out, sizeof(int32_t) * R)) != SI_OK) return s;
+    if ((s = stage_out(co, cut_out, sizeof(int32_t) * R)) != SI_OK) return s;
+    if ((s = stage_out(fo, energy_f, sizeof(double) * R)) != SI_OK) return s;
+    if (!spins) {
+        // the last run's spins, already in the padded layout
+        s = simt_energy(c, c->dspins, R, c->ld8, (int32_t *)eo.ptr, (int32_t *)co.ptr, (double *)fo.ptr);
+        if (s != SI_OK) return s;
+        return finish_call(c, {&eo, &co, &fo});
+    }
     DevIn sd;
-    si_status s = stage_in(sd, spins, (size_t)R * n, c->stream);
+    s = stage_in(sd, spins, (size_t)R * n, c->stream);
     if (s != SI_OK) return s;
     if (R > c->spins_in_cap) {
         if (c->dspins_in) cudaFree(c->dspins_in);
@@ -472,10 +489,6 @@ si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy
         (const int8_t *)sd.ptr, n, R, c->dspins_in, c->ld8);
     SI_CUDA_TRY(cudaGetLastError());
     c->launches += 1;
-    DevOut eo, co, fo;
-    if ((s = stage_out(eo, energy_out, sizeof(int32_t) * R)) != SI_OK) return s;
-    if ((s = stage_out(co, cut_out, sizeof(int32_t) * R)) != SI_OK) return s;
-    if ((s = stage_out(fo, energy_f, sizeof(double) * R)) != SI_OK) return s;
     s = simt_energy(c, c->dspins_in, R, c->ld8, (int32_t *)eo.ptr, (int32_t *)co.ptr, (double *)fo.ptr);
     if (s != SI_OK) return s;
     return finish_call(c, {&eo, &co, &fo});
@@ -537,6 +550,7 @@ si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt, const float *
     if ((s = stage_out(gd, g_dt, sizeof(float) * std::max(steps, 1))) != SI_OK) return s;
     if ((s = stage_out(gk, g_k, sizeof(float))) != SI_OK) return s;
     if ((s = stage_out(ob, objective, sizeof(float))) != SI_OK) return s;
+    c->run_spins_valid = false;   // the sweep replaces the context's state
     s = adjoint_grad(c, steps, (float *)gz.ptr, (float *)gd.ptr, (float *)gk.ptr, (float *)ob.ptr,
                      (const float *)qi.ptr, (const float *)pi.ptr);
     if (s != SI_OK) return s;

@@ -104,6 +104,7 @@ struct Ctx {
     int launches = 0;
     int cur_parity = 0;                  // q exchange buffer holding q(t_T)
     bool have_run = false;               // a run completed since creation
+    bool run_spins_valid = false;        // dspins holds the sign readout of the last si_run
     bool timing = false;                 // record events around the step kernel
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool ev_valid = false;

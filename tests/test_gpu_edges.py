@@ -47,3 +47,26 @@ def test_hamiltonian_of_zero_state_is_zero():
     with b.Context(J, replicas=R, steps=1, prec="fp32", q0=0.0) as c:
         H = c.hamiltonian(np.zeros((R, n), np.float32), np.zeros((R, n), np.float32), 0.7)
     assert (H == 0.0).all()
+
+
+@pytest.mark.parametrize("prec,n,R", [("fp32", 130, 3), ("fp32", 77, 9), ("j_fp8_q_bf16", 300, 70)])
+def test_energy_of_the_last_run_without_passing_spins(prec, n, R):
+    """si_energy with spins NULL reads the sign readout of the last si_run
+    (also for a run of zero steps); it is refused before any run and after a
+    gradient sweep, which replaces the state."""
+    J = inputs.pm1_coupling(n, seed=35)
+    q0 = inputs.positions(n, R, seed0=3500)
+    for T in (5, 0):
+        with b.Context(J, replicas=R, steps=T, prec=prec) as c:
+            with pytest.raises(b.SpringIsingError):
+                c.energy(None)
+            _, _, s = c.run(inputs.zeta_ramp(T), inputs.dt_const(T), q0)
+            e0, c0, f0 = c.energy(s)
+            e1, c1, f1 = c.energy(None)
+            np.testing.assert_array_equal(e1, e0)
+            np.testing.assert_array_equal(c1, c0)
+            np.testing.assert_array_equal(e1, oracle.energy(J, None, s).astype(np.int64))
+            if prec == "fp32" and T > 0:
+                c.grad(inputs.zeta_ramp(T), inputs.dt_const(T), q0)
+                with pytest.raises(b.SpringIsingError):
+                    c.energy(None)
