@@ -65,6 +65,48 @@ def test_fp64_adjoint_against_central_differences():
     assert abs(gk - fd) <= 1e-4 * scale
 
 
+def test_fp64_adjoint_against_gpu_central_differences():
+    """The same check with the differences taken on the GPU: FP64 forward
+    runs of the library at perturbed schedules (and spring constants), the
+    relaxed energy of their FP64 final states (si_get_state), against the
+    FP64 adjoint.  The perturbation is the one the float32 schedule entries
+    actually received."""
+    n, R, T = 64, 4, 60
+    J, q0, zeta, dt = _case(n, R, T, seed=5)
+    J64 = J.astype(np.float64)
+    eps = 1e-5
+    with b.Context(J, replicas=R, steps=T, prec="fp64") as ctx:
+        obj, gz, gd, gk = ctx.grad(zeta, dt, q0)
+
+        def L(z, d):
+            ctx.run(z, d, q0)
+            q, _ = ctx.get_state()
+            return float(oracle.relaxed_energy(J64, None, q).sum())
+
+        scale = max(np.abs(gz).max(), np.abs(gd).max(), abs(gk))
+        for t in (0, 7, 19, 33, 48, 59):
+            zp, zm = zeta.copy(), zeta.copy()
+            zp[t] = np.float32(zeta[t] + eps)
+            zm[t] = np.float32(zeta[t] - eps)
+            fd = (L(zp, dt) - L(zm, dt)) / (float(zp[t]) - float(zm[t]))
+            assert abs(gz[t] - fd) <= 1e-4 * scale, (t, gz[t], fd)
+            dp, dm = dt.copy(), dt.copy()
+            dp[t] = np.float32(dt[t] + eps)
+            dm[t] = np.float32(dt[t] - eps)
+            fd = (L(zeta, dp) - L(zeta, dm)) / (float(dp[t]) - float(dm[t]))
+            assert abs(gd[t] - fd) <= 1e-4 * scale, (t, gd[t], fd)
+    k0 = float(b.default_params().k)
+    kp, km = np.float32(k0 + eps), np.float32(k0 - eps)
+    Ls = []
+    for kk in (kp, km):
+        with b.Context(J, replicas=R, steps=T, prec="fp64", k=float(kk)) as ck:
+            ck.run(zeta, dt, q0)
+            q, _ = ck.get_state()
+            Ls.append(float(oracle.relaxed_energy(J64, None, q).sum()))
+    fd = (Ls[0] - Ls[1]) / (float(kp) - float(km))
+    assert abs(gk - fd) <= 1e-4 * scale
+
+
 @pytest.mark.parametrize("kind,n,R", [("tensor", 96, 8), ("tensor", 300, 70), ("simt-env", 96, 8),
                                       ("simt-j", 96, 8)])
 def test_fp32_adjoint_close_to_oracle(kind, n, R, monkeypatch):
