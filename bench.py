@@ -83,6 +83,33 @@ def tc_kernel_sha():
     return h.hexdigest()[:16]
 
 
+def plain_kernel_sha():
+    """Hash of the device source of the plain persistent kernel (its section of
+    si_simt.cu) and of the device helper header it includes; same use as
+    tc_kernel_sha."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2305_07187_gb300", "csrc")
+    src = open(os.path.join(csrc, "si_simt.cu"), "rb").read()
+    a = src.find(b"// ====================================================================== K1")
+    b_ = src.find(b"// ====================================================================== tiled")
+    h = hashlib.sha256(src[a:b_] if 0 <= a < b_ else src)
+    h.update(open(os.path.join(csrc, "si_device.cuh"), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(fname, desc, sha):
+    """DRAM bytes per launch from an ncu capture stored under profiles/, or
+    None when the kernel configuration or its device source has changed."""
+    try:
+        with open(os.path.join(ROOT, "profiles", fname)) as f:
+            tj = json.load(f)
+        if tj.get("kernel_desc") == desc and tj.get("source_sha") == sha:
+            return tj.get("bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
 def load_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -767,6 +794,144 @@ def run_sparse(args):
     return 0
 
 
+PLAIN_T = 1000
+
+
+def run_plain(args):
+    """Plain FP32 path: N=2000 +-1 complete graph (seed 1), R=1, T=1000,
+    linear zeta ramp, FP32 J and state.  One bench step = si_run (k_plain, all
+    T steps in one persistent launch) plus the exact energy / cut readout of
+    its spins.  Roofline on the matvec's bytes: J in FP32 once per step over
+    the kernel's event time.  J stays in shared memory across the steps, so
+    this is an effective bandwidth; the step itself waits on the grid barrier."""
+    import torch
+
+    from paper_2305_07187_gb300 import _binding as b
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    n, T = N_SPINS, PLAIN_T
+    J = inputs.pm1_coupling(n, seed=1)
+    q0 = inputs.positions(n, 1, seed0=100)
+    zeta, dt = inputs.zeta_ramp(T), inputs.dt_const(T)
+    ctx = b.Context(J, replicas=1, steps=T, prec="fp32", stream=stream.cuda_stream)
+    desc = ctx.describe()
+    z_d, d_d, q_d = (torch.from_numpy(x).to(dev) for x in (zeta, dt, q0))
+    s_d = torch.empty((1, n), dtype=torch.int8, device=dev)
+    e_d = torch.empty(1, dtype=torch.int32, device=dev)
+    c_d = torch.empty(1, dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ctx.enable_timing(True)
+
+    def step():
+        ctx.run_into(z_d, d_d, q_d, None, None, None, s_d)
+        n_l = ctx.last_launch_count()
+        k_ms = ctx.last_kernel_ms()
+        ctx.energy_into(s_d, 1, e_d, c_d, None)
+        return n_l + ctx.last_launch_count(), k_ms
+
+    for _ in range(max(3, args.warmup)):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(smi_index(0))
+    sampler.start()
+    time.sleep(0.3)
+    step_ms, kern_ms, launches = [], [], 0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        nl, km = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        kern_ms.append(km)
+        launches += nl
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    # end to end through the C ABI with pinned host buffers
+    q_h = torch.from_numpy(q0).pin_memory()
+    z_h = torch.from_numpy(zeta).pin_memory()
+    d_h = torch.from_numpy(dt).pin_memory()
+    s_h = torch.empty((1, n), dtype=torch.int8).pin_memory()
+    e_h = torch.empty(1, dtype=torch.int32).pin_memory()
+    c_h = torch.empty(1, dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for it in range(args.steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.run_into(z_h, d_h, q_h, None, None, None, s_h)
+        ctx.energy_into(s_h, 1, e_h, c_h, None)
+        el = (time.perf_counter() - t0) * 1e3
+        if it > 0:
+            e2e_ms.append(el)
+    assert torch.equal(s_h, s_d.cpu()) and torch.equal(c_h, c_d.cpu())
+    ctx.close()
+    ms = sum(step_ms) / len(step_ms)
+    k_avg = sum(kern_ms) / len(kern_ms)
+    units = n * T
+    bytes_launch = 4.0 * n * n * T
+    peaks, src = load_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = bytes_launch / (k_avg * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "plain FP32: N=2000 +-1 complete graph (seed 1), h=0, R=1, q0~U[-0.1,0.1] "
+                               "(seed 100), p0=0, T=1000, zeta linear ramp, dt=0.2; sign spins and exact "
+                               "int32 cut of the final state",
+                   "kernel": desc, "l2": "flushed (256 MiB write) between timed steps, outside the events"},
+        "e2e": {"value": units / (statistics.median(e2e_ms) * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(q0.nbytes + zeta.nbytes + dt.nbytes),
+                "d2h_bytes_per_step": int(s_h.numel() + 8)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": stored_traffic("traffic_k_plain.json", desc, plain_kernel_sha()),
+                     "kernel": "k_plain (persistent matvec, J resident in shared memory, q exchanged as "
+                               "step-tagged words)",
+                     "kernel_ms": k_avg, "peak_source": "%s hbm_gbs" % src,
+                     "algorithmic_bytes_per_launch": bytes_launch,
+                     "note": "J (FP32, 4 n^2 B) once per step; it is read from shared memory, so DRAM "
+                             "traffic is J once per launch and the step is bound by the cross-SM exchange "
+                             "of q"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        Jd = J.astype(np.float64)
+        qd = q0.astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.run(Jd, None, zeta[:5], dt[:5], qd)
+        per = (time.perf_counter() - t0) / 5
+        T_s = int(max(5, min(T, 12.0 / max(per, 1e-6))))
+        t0 = time.perf_counter()
+        oracle.run(Jd, None, zeta[:T_s], dt[:T_s], qd)
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": n * T_s / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "N=2000, R=1, first %d of the 1000 steps (FP64; one replica, so "
+                                          "one thread), %.1f s" % (T_s, el)}
+    print(json.dumps(line))
+    return 0
+
+
+def ncu_case_plain(args):
+    """Profiling case of the plain path: N=2000, R=1, FP32, --time-steps
+    steps; one warm-up and one profiled si_run."""
+    from paper_2305_07187_gb300 import _binding as b
+    T = args.time_steps
+    J = inputs.pm1_coupling(N_SPINS, seed=1)
+    q0 = inputs.positions(N_SPINS, 1, seed0=100)
+    with b.Context(J, replicas=1, steps=T, prec="fp32") as ctx:
+        for _ in range(2):
+            ctx.run(inputs.zeta_ramp(T), inputs.dt_const(T), q0)
+        print(ctx.describe())
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -782,9 +947,9 @@ def main():
     ap.add_argument("--time-steps", type=int, default=T_STEPS)
     ap.add_argument("--group-count", type=int, default=256,
                     help="grouped workload: number of instances (profiling uses a prefix)")
-    ap.add_argument("--workload", default="batched", choices=["batched", "grouped", "scale", "grad", "study", "sparse"],
-                    help="batched: N=2000, R=1024, T=2000 (default); grouped: 256 uneven "
-                         "instances, T=1000, one grouped launch per step")
+    ap.add_argument("--workload", default="batched", choices=["batched", "plain", "grouped", "scale", "grad", "study", "sparse"],
+                    help="batched: N=2000, R=1024, T=2000 (default); plain: FP32, N=2000, R=1, "
+                         "T=1000; grouped: 256 uneven instances, T=1000, one grouped launch per step")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -796,8 +961,12 @@ def main():
         return ncu_case_grouped(args)
     if args.ncu_case and args.workload == "grad":
         return ncu_case_grad(args)
+    if args.ncu_case and args.workload == "plain":
+        return ncu_case_plain(args)
     if args.ncu_case:
         return ncu_case(args)
+    if args.workload == "plain":
+        return run_plain(args)
     if args.workload == "grouped":
         return run_grouped(args)
     if args.workload == "scale":
@@ -902,16 +1071,7 @@ def main():
     k_avg = sum(kern_ms) / len(kern_ms)
     achieved = flops / (k_avg * 1e-3) / 1e12
     peak = float(peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS))
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            with open(tfile) as f:
-                tj = json.load(f)
-            if tj.get("kernel_desc") == desc and tj.get("source_sha") == tc_kernel_sha():
-                traffic = tj.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = stored_traffic("traffic.json", desc, tc_kernel_sha())
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms_max, "higher_is_better": True,

@@ -138,7 +138,7 @@ static void free_ctx(Ctx *c) {
     if (!c) return;
     void *ptrs[] = {c->dJ, c->dJ8, c->dh, c->dhf, c->dh8, c->dq, c->dp, c->dqbuf,
                     c->dzeta, c->ddt, c->dbar, c->derr, c->dspins, c->dspins_in,
-                    c->dE, c->dC, c->dEf, c->dstage, c->g_ws, c->e_sig, c->e_sum};
+                    c->dE, c->dC, c->dEf, c->dstage, c->g_ws, c->e_sig, c->e_sum, c->dxch};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     adj_tc_free(c->g_tc);
@@ -250,6 +250,10 @@ static si_status create_impl(Ctx *c, const float *J, const float *h) {
         c->qbuf_bytes = 2 * (size_t)c->R * c->ldj * es;
         SI_CUDA_TRY(si_dev_malloc(&c->dqbuf, c->qbuf_bytes));
         SI_CUDA_TRY(cudaMemsetAsync(c->dqbuf, 0, c->qbuf_bytes, c->stream));
+        if (c->path == Path::PLAIN_PERSISTENT && !f64) {
+            c->xch_bytes = 2 * (size_t)c->R * c->ldj * sizeof(unsigned long long);
+            SI_CUDA_TRY(si_dev_malloc((void **)&c->dxch, c->xch_bytes));
+        }
     }
     if (c->integer_j) SI_CUDA_TRY(si_dev_malloc((void **)&c->dJ8, (size_t)n * c->ld8));
     // h copies.

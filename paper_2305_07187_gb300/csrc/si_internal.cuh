@@ -90,6 +90,10 @@ struct Ctx {
     void *dq = nullptr, *dp = nullptr;   // [R][n] state precision
     void *dqbuf = nullptr;               // q exchange / operand double buffer
     size_t qbuf_bytes = 0;
+    // FP32 plain path: q exchanged between CTAs as (value bits, step tag)
+    // words, [2][R][ldj] x 8 bytes
+    unsigned long long *dxch = nullptr;
+    size_t xch_bytes = 0;
     float *dzeta = nullptr, *ddt = nullptr;  // schedules [steps]
     unsigned *dbar = nullptr;            // inter-CTA barrier counters
     int nbar = 0;
@@ -180,6 +184,10 @@ si_status tc_init_state(Ctx *c, const float *q_init, const float *p_init);
 si_status tc_spins(Ctx *c, int8_t *spins, int ld);
 // Exact energy/cut on the tensor cores (integer J, tensor-path contexts);
 // SI_ERR_UNSUPPORTED when it does not apply.
+// E and cut from per-replica totals s_r = sigma^T J sigma (64-bit), with the
+// integer field term, one CTA of 128 threads per replica.
+__global__ void k_energy_finish(const unsigned long long *sum, const int8_t *h8, const int8_t *s, int lds, int n,
+                                int R, long long s_upper, int32_t *E, int32_t *C);
 si_status tc_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E, int32_t *C);
 const char *tc_describe(const Ctx *c, char *buf, int len);
 // 2D bf16 tensor map with the 128-byte swizzle (inner dimension contiguous).

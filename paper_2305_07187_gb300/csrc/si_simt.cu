@@ -5,7 +5,11 @@
 //    CTA owns a contiguous block of rows of J, keeps them resident in shared
 //    memory when they fit (else streams them from L2 with 128-bit loads),
 //    computes F_i = sum_j J_ij q_j with warp-shuffle reductions and applies
-//    the integrator of Eq. 8 in place; a bounded grid barrier separates steps.
+//    the integrator of Eq. 8 in place.  FP32: every CTA publishes its new q_i
+//    as one 8-byte word (value bits, step tag) and the next step polls the
+//    words it reads until their tags show that step, so the data exchange is
+//    the synchronisation.  FP64 (no 8-byte room for a tag): a bounded grid
+//    barrier separates the steps.
 //  * k_tiled_step: one launch per step, 64x64 output tiles of F = J Q^T for
 //    many replicas with the integrator fused into the epilogue.
 //  * k_energy_i8: exact int32 Ising energy (Eq. 1) and cut with dp4a.
@@ -31,7 +35,8 @@ struct PlainArgs {
     const T *h;            // [n] or null
     int n, R, steps;
     const float *zeta, *dt;
-    T *qbuf;               // [2][R][ldj]; step t reads buffer t&1
+    T *qbuf;               // [2][R][ldj]; step t reads buffer t&1 (FP64); FP32: q(0) in buffer 0, q(T) written to buffer T&1
+    unsigned long long *xch;   // FP32: [2][R][ldj] words (tag << 32 | value bits), tags zero at launch; else null
     T *p;                  // [R][n]
     int8_t *spins;         // [R][lds] or null (written after the last step)
     int lds;
@@ -44,12 +49,29 @@ struct PlainArgs {
     int stall_step;        // failure-detection test hook (-1: off)
 };
 
+// Two 64-bit words, each read as one single-copy-atomic access (the memory
+// model treats a vector access as its elements; each element here is a
+// naturally aligned 8-byte scalar).  p must be 16-byte aligned.
+__device__ __forceinline__ void ld_relaxed_gpu_v2_u64(const unsigned long long *p, unsigned long long &a,
+                                                      unsigned long long &b) {
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0,%1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
+}
+
+__device__ __forceinline__ void st_relaxed_gpu_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Words of q(t) each thread of the FP32 exchange polls at once.
+constexpr int PLAIN_POLL = 8;
+
 template <typename T>
 __global__ void __launch_bounds__(PLAIN_THREADS, 1) k_plain(PlainArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int VEC = 16 / sizeof(T);
     T *sq = reinterpret_cast<T *>(smem_raw);            // [R][ldj]
-    T *sJ = sq + (size_t)a.R * a.ldj;                    // [rows][ldj]
+    T *sJ = sq + (size_t)a.R * a.ldj;                    // [rows][ldj] when resident
+    T *sp = sJ + (a.j_resident ? (size_t)a.rows_per_block * a.ldj : 0);   // [R][rows]: this CTA's p
+    T *sh = sp + (size_t)a.R * a.rows_per_block;                          // [rows]: its h
     const int row0 = blockIdx.x * a.rows_per_block;
     const int nrows = max(0, min(a.rows_per_block, a.n - row0));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -61,18 +83,77 @@ __global__ void __launch_bounds__(PLAIN_THREADS, 1) k_plain(PlainArgs<T> a) {
         const int total = nrows * a.ldj / VEC;
         for (int e = threadIdx.x; e < total; e += blockDim.x) dst[e] = src[e];
     }
+    // p and h of the CTA's rows stay in shared memory for the whole run
+    // (p is never read by another CTA); p goes back to global memory at the end.
+    for (int e = threadIdx.x; e < a.R * nrows; e += blockDim.x) {
+        const int r = e / nrows, rr = e - r * nrows;
+        sp[r * a.rows_per_block + rr] = a.p[(size_t)r * a.n + row0 + rr];
+    }
+    for (int rr = threadIdx.x; rr < nrows; rr += blockDim.x) sh[rr] = a.h ? a.h[row0 + rr] : (T)0;
+    const bool tagged = a.xch != nullptr;   // FP32 contexts only
+    const bool pads = blockIdx.x == gridDim.x - 1;   // this CTA also publishes the padding columns
     for (int t = 0; t < a.steps; ++t) {
         const T *qc = a.qbuf + (size_t)(t & 1) * a.R * a.ldj;
         T *qn = a.qbuf + (size_t)((t + 1) & 1) * a.R * a.ldj;
-        {
+        const T zt = (T)a.zeta[t], dtt = (T)a.dt[t];
+        const T dtm = dtt / (T)a.sp.m;
+        if (!tagged || t == 0) {
+            // q(0) (written before the launch), or the FP64 exchange buffer
             const uint4 *src = reinterpret_cast<const uint4 *>(qc);
             uint4 *dst = reinterpret_cast<uint4 *>(sq);
             const int total = a.R * a.ldj / VEC;
             for (int e = threadIdx.x; e < total; e += blockDim.x) dst[e] = __ldcg(src + e);
+            __syncthreads();
+        } else {
+            // Poll the words of q(t), padding included, until each carries
+            // tag t; a word with that tag was written in one access together
+            // with its value.  A thread keeps up to PLAIN_POLL pairs of words
+            // in flight and re-reads only those not yet tagged.
+            bool fail = false;
+            const unsigned tag = (unsigned)t;
+            const unsigned long long *src = a.xch + (size_t)(t & 1) * a.R * a.ldj;
+            float *sqf = reinterpret_cast<float *>(sq);
+            const int npairs = a.R * a.ldj / 2;
+            for (int base = threadIdx.x; base < npairs && !fail; base += PLAIN_POLL * blockDim.x) {
+                unsigned long long w0[PLAIN_POLL], w1[PLAIN_POLL];
+                unsigned pending = 0;
+#pragma unroll
+                for (int k = 0; k < PLAIN_POLL; ++k)
+                    if (base + k * (int)blockDim.x < npairs) pending |= 1u << k;
+                unsigned long long t0 = 0;
+                for (unsigned it = 0; pending != 0; ++it) {
+#pragma unroll
+                    for (int k = 0; k < PLAIN_POLL; ++k)
+                        if (pending & (1u << k)) ld_relaxed_gpu_v2_u64(src + 2 * (base + k * blockDim.x), w0[k], w1[k]);
+#pragma unroll
+                    for (int k = 0; k < PLAIN_POLL; ++k)
+                        if ((pending & (1u << k)) && (unsigned)(w0[k] >> 32) == tag && (unsigned)(w1[k] >> 32) == tag)
+                            pending &= ~(1u << k);
+                    if (pending == 0) break;
+                    if (it == 0) {
+                        t0 = globaltimer_ns();
+                    } else if ((it & 63u) == 0) {
+                        if (ld_volatile_int(a.err) != 0) {
+                            fail = true;
+                        } else if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                            atomicCAS(a.err, 0, DEV_TIMEOUT_BARRIER);
+                            fail = true;
+                        }
+                        if (fail) break;
+                    }
+                }
+                if (fail) break;
+#pragma unroll
+                for (int k = 0; k < PLAIN_POLL; ++k) {
+                    const int e = base + k * blockDim.x;
+                    if (e < npairs) {
+                        sqf[2 * e] = __uint_as_float((unsigned)w0[k]);
+                        sqf[2 * e + 1] = __uint_as_float((unsigned)w1[k]);
+                    }
+                }
+            }
+            if (__syncthreads_or(fail ? 1 : 0)) break;
         }
-        __syncthreads();
-        const T zt = (T)a.zeta[t], dtt = (T)a.dt[t];
-        const T dtm = dtt / (T)a.sp.m;
         for (int rr = warp; rr < nrows; rr += nwarps) {
             const int i = row0 + rr;
             const T *Jrow = a.j_resident ? sJ + (size_t)rr * a.ldj : a.J + (size_t)i * a.ldj;
@@ -81,6 +162,9 @@ __global__ void __launch_bounds__(PLAIN_THREADS, 1) k_plain(PlainArgs<T> a) {
             CompSum<T> acc[PLAIN_RMAX];
 #pragma unroll
             for (int r = 0; r < PLAIN_RMAX; ++r) acc[r].init();
+            // unrolled so that the loads and FMA chains of later chunks issue
+            // ahead; only the compensated add carries a dependency (same order)
+#pragma unroll 4
             for (int j = lane * VEC; j < a.ldj; j += 32 * VEC) {
                 uint4 jv;
                 if (a.j_resident) jv = *reinterpret_cast<const uint4 *>(Jrow + j);
@@ -100,6 +184,7 @@ __global__ void __launch_bounds__(PLAIN_THREADS, 1) k_plain(PlainArgs<T> a) {
             }
 #pragma unroll
             for (int r = 0; r < PLAIN_RMAX; ++r) {
+                if (r >= a.R) break;   // uniform over the warp
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) {
                     const T oh = __shfl_down_sync(0xffffffffu, acc[r].hi, off);
@@ -108,20 +193,44 @@ __global__ void __launch_bounds__(PLAIN_THREADS, 1) k_plain(PlainArgs<T> a) {
                 }
             }
             if (lane == 0) {
-                const T hi = a.h ? a.h[i] : (T)0;
-                for (int r = 0; r < a.R; ++r) {
-                    T q = sq[(size_t)r * a.ldj + i];
-                    T p = a.p[(size_t)r * a.n + i];
+                const T hi = sh[rr];
+#pragma unroll
+                for (int r = 0; r < PLAIN_RMAX; ++r) {
+                    if (r >= a.R) break;
+                    const T q = sq[(size_t)r * a.ldj + i];
+                    const T p = sp[r * a.rows_per_block + rr];
                     T qo, po;
                     integrate<T>(q, p, acc[r].value() + hi, zt, dtt, dtm, a.sp, qo, po);
-                    qn[(size_t)r * a.ldj + i] = qo;
-                    a.p[(size_t)r * a.n + i] = po;
+                    if (!tagged || t == a.steps - 1) qn[(size_t)r * a.ldj + i] = qo;
+                    if (tagged && !(t == a.stall_step && blockIdx.x == 0)) {
+                        const unsigned bits = __float_as_uint((float)qo);
+                        st_relaxed_gpu_u64(a.xch + ((size_t)((t + 1) & 1) * a.R + r) * a.ldj + i,
+                                           ((unsigned long long)(unsigned)(t + 1) << 32) | bits);
+                    }
+                    sp[r * a.rows_per_block + rr] = po;
                     if (a.spins && t == a.steps - 1) a.spins[(size_t)r * a.lds + i] = spin_of(qo);
                 }
             }
         }
-        const unsigned target = (unsigned)(t + 1) * gridDim.x + (t == a.stall_step ? 1u : 0u);
-        if (!grid_barrier(a.bar, target, a.err, a.limit_ns)) break;
+        if (tagged && pads && warp == nwarps - 1) {
+            // padding columns [n, ldj): value 0 with this step's tag
+            for (int e = lane; e < a.R * (a.ldj - a.n); e += 32) {
+                const int r = e / (a.ldj - a.n), i = a.n + (e - r * (a.ldj - a.n));
+                st_relaxed_gpu_u64(a.xch + ((size_t)((t + 1) & 1) * a.R + r) * a.ldj + i,
+                                   (unsigned long long)(unsigned)(t + 1) << 32);
+            }
+        }
+        if (tagged) {
+            __syncthreads();   // every warp is done with sq before the next step refills it
+        } else {
+            const unsigned target = (unsigned)(t + 1) * gridDim.x + (t == a.stall_step ? 1u : 0u);
+            if (!grid_barrier(a.bar, target, a.err, a.limit_ns)) break;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < a.R * nrows; e += blockDim.x) {
+        const int r = e / nrows, rr = e - r * nrows;
+        a.p[(size_t)r * a.n + row0 + rr] = sp[r * a.rows_per_block + rr];
     }
 }
 
@@ -314,11 +423,15 @@ constexpr int EN_THREADS = 256;
 // s_r = sum_ij J_ij s_i s_j exactly in int32 (|s_r| <= 127 n^2 < 2^31 for
 // n <= 4096; larger n uses a 64-bit block sum), E = -s/2 - sum h_i s_i,
 // cut = (s - 2 S_upper) / 4 with S_upper = sum_{i<j} J_ij.
+// Rows split over blockIdx.y (rows_per_split each) when sum_out is given:
+// every CTA adds its partial s_r to sum_out[r] (64-bit integer atomics,
+// exact in any order) and k_energy_finish forms E and the cut.
 __global__ void __launch_bounds__(EN_THREADS) k_energy_i8(const int8_t *J8, int ld8,
                                                          const int8_t *h8, int n, int R,
                                                          const int8_t *s, int lds,
                                                          long long s_upper, int32_t *E,
-                                                         int32_t *C) {
+                                                         int32_t *C, int rows_per_split,
+                                                         unsigned long long *sum_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     int8_t *ss = reinterpret_cast<int8_t *>(smem_raw);   // [EN_RB][ld8]
     __shared__ long long red[EN_RB];
@@ -335,7 +448,8 @@ __global__ void __launch_bounds__(EN_THREADS) k_energy_i8(const int8_t *J8, int 
     long long part[EN_RB];
 #pragma unroll
     for (int r = 0; r < EN_RB; ++r) part[r] = 0;
-    for (int i = warp; i < n; i += nwarps) {
+    const int i0 = blockIdx.y * rows_per_split, i1 = min(n, i0 + rows_per_split);
+    for (int i = i0 + warp; i < i1; i += nwarps) {
         int dot[EN_RB];
 #pragma unroll
         for (int r = 0; r < EN_RB; ++r) dot[r] = 0;
@@ -361,6 +475,11 @@ __global__ void __launch_bounds__(EN_THREADS) k_energy_i8(const int8_t *J8, int 
     if (lane == 0) {
 #pragma unroll
         for (int r = 0; r < EN_RB; ++r) atomicAdd(reinterpret_cast<unsigned long long *>(&red[r]), (unsigned long long)part[r]);
+    }
+    if (sum_out) {
+        __syncthreads();
+        if (threadIdx.x < nr) atomicAdd(sum_out + r0 + threadIdx.x, (unsigned long long)red[threadIdx.x]);
+        return;
     }
     if (h8) {
         for (int e = threadIdx.x; e < EN_RB * n; e += blockDim.x) {
@@ -476,6 +595,7 @@ static si_status plain_launch(Ctx *c, int steps, int8_t *spins_dev) {
     a.zeta = c->dzeta;
     a.dt = c->ddt;
     a.qbuf = (T *)c->dqbuf;
+    a.xch = sizeof(T) == 4 ? c->dxch : nullptr;
     a.p = (T *)c->dp;
     a.spins = spins_dev;
     a.lds = c->ld8;
@@ -492,8 +612,9 @@ static si_status plain_launch(Ctx *c, int steps, int8_t *spins_dev) {
     a.rows_per_block = cdiv(c->n, grid);
     grid = cdiv(c->n, a.rows_per_block);
     const size_t sj_bytes = (size_t)a.rows_per_block * c->ldj * sizeof(T);
-    a.j_resident = (sq_bytes + sj_bytes + 1024 <= (size_t)max_smem) ? 1 : 0;
-    const size_t smem = sq_bytes + (a.j_resident ? sj_bytes : 0);
+    const size_t sph_bytes = (size_t)(c->R + 1) * a.rows_per_block * sizeof(T);   // p and h of the CTA's rows
+    a.j_resident = (sq_bytes + sj_bytes + sph_bytes + 1024 <= (size_t)max_smem) ? 1 : 0;
+    const size_t smem = sq_bytes + (a.j_resident ? sj_bytes : 0) + sph_bytes;
     if (smem > (size_t)max_smem) {
         set_error("plain path: q vectors do not fit in shared memory");
         return SI_ERR_UNSUPPORTED;
@@ -505,7 +626,12 @@ static si_status plain_launch(Ctx *c, int steps, int8_t *spins_dev) {
         set_error("plain path: grid cannot be co-resident");
         return SI_ERR_UNSUPPORTED;
     }
-    SI_CUDA_TRY(cudaMemsetAsync(c->dbar, 0, sizeof(unsigned) * c->nbar, c->stream));
+    if (a.xch) {
+        // tags of an earlier run must not match this run's steps
+        SI_CUDA_TRY(cudaMemsetAsync(a.xch, 0, c->xch_bytes, c->stream));
+    } else {
+        SI_CUDA_TRY(cudaMemsetAsync(c->dbar, 0, sizeof(unsigned) * c->nbar, c->stream));
+    }
     void *args[] = {&a};
     SI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_plain<T>, dim3(grid), dim3(PLAIN_THREADS),
                                             args, smem, c->stream));
@@ -621,10 +747,33 @@ si_status simt_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E
             return SI_ERR_UNSUPPORTED;
         }
         SI_CUDA_TRY(cudaFuncSetAttribute(k_energy_i8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        k_energy_i8<<<cdiv(R, EN_RB), EN_THREADS, smem, c->stream>>>(
-            c->dJ8, c->ld8, c->dh8, c->n, R, spins_dev, ld, c->s_upper, Euse, C);
-        SI_CUDA_TRY(cudaGetLastError());
-        c->launches += 1;
+        // Few replica blocks (small R) leave most SMs idle while one CTA
+        // streams all of J: split the rows too, at least 32 per CTA.
+        const int bx = cdiv(R, EN_RB);
+        const int nsplit = bx >= c->num_sms ? 1 : std::max(1, std::min(cdiv(c->n, 32), cdiv(2 * c->num_sms, bx)));
+        if (nsplit > 1) {
+            if (R > c->e_sum_cap) {
+                if (c->e_sum) cudaFree(c->e_sum);
+                c->e_sum = nullptr;
+                c->e_sum_cap = 0;
+                SI_CUDA_TRY(si_dev_malloc((void **)&c->e_sum, sizeof(unsigned long long) * R));
+                c->e_sum_cap = R;
+            }
+            SI_CUDA_TRY(cudaMemsetAsync(c->e_sum, 0, sizeof(unsigned long long) * R, c->stream));
+            const int rps = cdiv(c->n, nsplit);
+            k_energy_i8<<<dim3(bx, cdiv(c->n, rps)), EN_THREADS, smem, c->stream>>>(
+                c->dJ8, c->ld8, nullptr, c->n, R, spins_dev, ld, c->s_upper, nullptr, nullptr, rps, c->e_sum);
+            SI_CUDA_TRY(cudaGetLastError());
+            k_energy_finish<<<R, 128, 0, c->stream>>>(c->e_sum, c->has_h ? c->dh8 : nullptr, spins_dev, ld, c->n,
+                                                      R, c->s_upper, Euse, C);
+            SI_CUDA_TRY(cudaGetLastError());
+            c->launches += 2;
+        } else {
+            k_energy_i8<<<bx, EN_THREADS, smem, c->stream>>>(c->dJ8, c->ld8, c->dh8, c->n, R, spins_dev, ld,
+                                                             c->s_upper, Euse, C, c->n, nullptr);
+            SI_CUDA_TRY(cudaGetLastError());
+            c->launches += 1;
+        }
     }
     if (Ef && exact_ok) {
         k_energy_int_to_f<<<cdiv(R, 256), 256, 0, c->stream>>>(Euse, R, Ef);

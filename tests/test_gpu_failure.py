@@ -1,7 +1,9 @@
-"""Failure detection on the GPU without a GPU fault: a step wait is pointed at
-a count that no CTA will ever publish (SI_DEBUG_STALL_STEP), so the bounded
-wait must run out; the call returns SI_ERR_TIMEOUT, the kernel ends on its
-own, and the device stays usable for the next context."""
+"""Failure detection on the GPU without a GPU fault: at step
+SI_DEBUG_STALL_STEP a step wait is left without its producer (the FP32 plain
+path: the first CTA does not publish its tagged q words; the tensor path: the
+wait is pointed at a count no CTA will publish), so the bounded wait must run
+out; the call returns SI_ERR_TIMEOUT, the kernel ends on its own, and the
+device stays usable for the next context."""
 import numpy as np
 import pytest
 
