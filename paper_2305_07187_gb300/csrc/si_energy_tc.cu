@@ -109,30 +109,47 @@ __global__ void __launch_bounds__(TE_THREADS, 1)
             if (ok) mma_commit(accf_bar);   // on abort the epilogue sees the abort flag instead
         }
     } else {
-        // epilogue: warps 2..5, TMEM lane quadrant warp%4, one spin per thread
+        // epilogue: warps 2..5, TMEM lane quadrant warp%4, one spin per
+        // thread.  The products G_ir sigma_ir go to shared memory as
+        // [replica][row] (the operand ring is free once the accumulator is
+        // complete: every stage has been loaded and read by the MMAs); after
+        // a barrier of the four warps, thread t adds the 128 rows of replica
+        // column t and issues one 64-bit add for the tile.  Integer sums:
+        // exact in any order.
         const int quad = warp & 3;
-        const int i = m0 + quad * 32 + lane;
+        const int row = quad * 32 + lane;
+        const int i = m0 + row;
+        int *prod = reinterpret_cast<int *>(smem);   // [TE_BN][TE_BM + 1]
         bool ok = true;
         if (lane == 0) ok = mbar_wait(accf_bar, 0u, a.err, abort_flag, a.limit_ns);
         ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
         if (ok) {
             tc_fence_after();
             const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+#pragma unroll 1
             for (int c = 0; c < TE_BN / 32; ++c) {
                 uint32_t v[32];
-                tmem_ld32(tl + c * 32, v);
-                tmem_wait_ld();
+                int sg[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                     const int r = r0 + c * 32 + j;
-                    int x = 0;
-                    if (i < a.n && r < a.R) x = (int)__uint_as_float(v[j]) * (int)a.spins[(size_t)r * a.lds + i];
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
-                    if (lane == 0 && r < a.R && x != 0)
-                        atomicAdd(a.sum + r, (unsigned long long)(long long)x);
+                    sg[j] = (i < a.n && r < a.R) ? (int)a.spins[(size_t)r * a.lds + i] : 0;
                 }
+                tmem_ld32(tl + c * 32, v);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) prod[(c * 32 + j) * (TE_BM + 1) + row] = (int)__uint_as_float(v[j]) * sg[j];
             }
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");   // the four epilogue warps
+        if (ok) {
+            const int rl = row;                  // replica column of this thread
+            const int r = r0 + rl;
+            long long x = 0;
+            const int *col = prod + rl * (TE_BM + 1);
+#pragma unroll 8
+            for (int w = 0; w < TE_BM; ++w) x += col[w];
+            if (r < a.R && x != 0) atomicAdd(a.sum + r, (unsigned long long)x);
         }
     }
     tc_fence_before();
