@@ -185,7 +185,6 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
             int u = 0;
             for (int k = blockIdx.x; k < a.ntiles && ok; k += gridDim.x, ++u) {
                 const GroupTile tl = a.tiles[k];
-                const GroupInst &in = a.inst[tl.inst];
                 const int slot = u & 1;
                 if (u >= 2) {
                     if (!mbar_wait(tmem_empty_bar(slot), (uint32_t)(((u >> 1) - 1) & 1), a.err, abort_flag,
