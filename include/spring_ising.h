@@ -108,7 +108,13 @@ si_status si_create(si_ctx **out, const si_params *prm, const float *J,
  *   zeta    [steps]  coupling coefficient zeta(t_n) (the dynamic-equilibrium
  *                    ramp of the paper is a host-built schedule)
  *   dt      [steps]  time step Delta_n
- *   q_init  [R][n]   initial positions (required)
+ *   q_init  [R][n]   initial positions; or NULL to continue from the
+ *                    context's state at its working precision (the final
+ *                    state of the last successful si_run, or of the forward
+ *                    sweep of the last si_grad), with p_init NULL too;
+ *                    SI_ERR_INVALID_ARG if there is no such state.  A
+ *                    segmented run continued this way equals one run over the
+ *                    concatenated schedules.
  *   p_init  [R][n]   initial momenta, or NULL for zero
  *   q_out   [R][n]   final positions, or NULL
  *   p_out   [R][n]   final momenta, or NULL

@@ -237,7 +237,8 @@ class Context:
         return int(load().si_last_launch_count(self.ctx))
 
     def run_into(self, zeta, dt, q_init, p_init=None, q_out=None, p_out=None, spins_out=None):
-        """si_run with caller-provided outputs (numpy or torch, host or device)."""
+        """si_run with caller-provided outputs (numpy or torch, host or device).
+        q_init None (with p_init None) continues from the context's state."""
         nR = self.n * self.replicas
         z = _Arg(zeta, np.float32, self.steps)
         d = _Arg(dt, np.float32, self.steps)

@@ -358,8 +358,14 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
     NvtxRange nvtx_range("si_run");
     set_error("");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
-    if (!c || !q_init || (c->prm.steps > 0 && (!zeta || !dt))) {
-        set_error("si_run: ctx, q_init, zeta and dt are required");
+    if (!c || (c->prm.steps > 0 && (!zeta || !dt))) {
+        set_error("si_run: ctx, zeta and dt are required");
+        return SI_ERR_INVALID_ARG;
+    }
+    const bool cont = (q_init == nullptr);
+    if (cont && (p_init || !c->have_run)) {
+        set_error("si_run: q_init NULL continues from the context's state: needs a completed si_run or si_grad, "
+                  "and p_init NULL");
         return SI_ERR_INVALID_ARG;
     }
     c->launches = 0;
@@ -382,12 +388,17 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
     if ((s = stage_out(so, spins_out, (size_t)R * n)) != SI_OK) return s;
 
     c->ev_valid = false;
+    // the state is rewritten from here on: only a successful run leaves one
+    // to continue from or to read back
+    c->have_run = false;
     if (c->path == Path::TENSOR) {
-        if ((s = tc_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr)) != SI_OK) return s;
+        s = cont ? tc_continue_state(c) : tc_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr);
+        if (s != SI_OK) return s;
         if (c->timing) SI_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
         if ((s = tc_run(c, steps, c->dspins)) != SI_OK) return s;
     } else {
-        if ((s = simt_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr)) != SI_OK) return s;
+        s = cont ? simt_continue_state(c) : simt_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr);
+        if (s != SI_OK) return s;
         if (c->timing) SI_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
         if ((s = simt_run(c, steps, c->dspins)) != SI_OK) return s;
         c->cur_parity = steps & 1;

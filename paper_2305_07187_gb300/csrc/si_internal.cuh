@@ -167,6 +167,9 @@ si_status simt_validate(const float *J_dev, const float *h_dev, int n,
 // Writes sign(q) for R replicas of the state into spins [R][ld].
 si_status simt_spins(Ctx *c, int8_t *spins, int ld);
 si_status simt_init_state(Ctx *c, const float *q_init, const float *p_init);
+// Start the next run from the state the last one left (exchange buffer of
+// parity cur_parity, p in place).
+si_status simt_continue_state(Ctx *c);
 // int8 copy of J for the exact energy.
 si_status convert_j8(Ctx *c, const float *J_dev);
 // int8 copy of an integer-valued field.
@@ -181,6 +184,9 @@ si_status tc_run(Ctx *c, int steps, int8_t *spins_dev);
 si_status tc_copy_state(Ctx *c, float *q_out, float *p_out);
 si_status tc_copy_state_f64(Ctx *c, double *q_out, double *p_out);
 si_status tc_init_state(Ctx *c, const float *q_init, const float *p_init);
+// Start the next run from the FP32 state in place: rebuild the bf16 operand
+// plane of step 0 from it.
+si_status tc_continue_state(Ctx *c);
 si_status tc_spins(Ctx *c, int8_t *spins, int ld);
 // Exact energy/cut on the tensor cores (integer J, tensor-path contexts);
 // SI_ERR_UNSUPPORTED when it does not apply.

@@ -683,6 +683,17 @@ si_status simt_init_state(Ctx *c, const float *q_init, const float *p_init) {
     return SI_OK;
 }
 
+si_status simt_continue_state(Ctx *c) {
+    // every run reads q(0) from exchange buffer 0
+    if (c->cur_parity == 1) {
+        const size_t plane = (size_t)c->R * c->ldj * (c->prm.prec == SI_PREC_FP64 ? sizeof(double) : sizeof(float));
+        SI_CUDA_TRY(cudaMemcpyAsync(c->dqbuf, (const char *)c->dqbuf + plane, plane, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+        c->cur_parity = 0;
+    }
+    return SI_OK;
+}
+
 template <typename O>
 static si_status copy_state_impl(Ctx *c, O *q_out, O *p_out) {
     const int parity = c->cur_parity;

@@ -475,6 +475,16 @@ __global__ void k_tc_init(const float *q_init, const float *p_init, int n, int R
     }
 }
 
+// bf16 operand plane of step 0 from the FP32 positions in place.
+__global__ void k_tc_operand(const float *q_state, int n, int R, __nv_bfloat16 *qop, int ldk) {
+    const long long total = (long long)R * n;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n), i = (int)(e % n);
+        qop[(size_t)r * ldk + i] = __float2bfloat16_rn(q_state[e]);
+    }
+}
+
 template <typename O>
 __global__ void k_tc_copy(const float *q_state, const float *p_state, long long total, O *q_out,
                           O *p_out) {
@@ -626,6 +636,15 @@ si_status tc_init_state(Ctx *c, const float *q_init, const float *p_init) {
     const long long total = (long long)c->R * c->n;
     k_tc_init<<<std::min(8 * c->num_sms, cdiv(total, 256)), 256, 0, c->stream>>>(
         q_init, p_init, c->n, c->R, (float *)c->dq, (float *)c->dp, (__nv_bfloat16 *)c->dqbuf, c->ldk);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    return SI_OK;
+}
+
+si_status tc_continue_state(Ctx *c) {
+    const long long total = (long long)c->R * c->n;
+    k_tc_operand<<<std::min(8 * c->num_sms, cdiv(total, 256)), 256, 0, c->stream>>>(
+        (const float *)c->dq, c->n, c->R, (__nv_bfloat16 *)c->dqbuf, c->ldk);
     SI_CUDA_TRY(cudaGetLastError());
     c->launches += 1;
     return SI_OK;

@@ -6,6 +6,7 @@ from paper_2305_07187_gb300 import _binding as b
 from paper_2305_07187_gb300 import inputs
 
 SQ2F = b.SQRT2_F32  # the float32 wall the library uses by default
+TOL_FP64_100 = 1e-10  # FP64 debug path, 100 free-running steps (normwise relative)
 
 
 def params_f64(ctx):

@@ -3,12 +3,11 @@ against the FP64 oracle, through the C ABI."""
 import numpy as np
 import pytest
 
-from _helpers import b, inputs, normwise_rel, oracle, params_f64, random_spins, teacher_forced
+from _helpers import TOL_FP64_100, b, inputs, normwise_rel, oracle, params_f64, random_spins, teacher_forced
 
 pytestmark = pytest.mark.gpu
 
 TOL_FP32_STEP = 1e-6     # per-step normwise relative, FP32 plain path
-TOL_FP64_100 = 1e-10     # FP64 debug path, 100 free-running steps
 
 
 @pytest.mark.parametrize("n,R", [(1, 1), (17, 1), (127, 2), (129, 3), (300, 4),
