@@ -4,7 +4,7 @@ Hamiltonian of an all-zero state."""
 import numpy as np
 import pytest
 
-from _helpers import b, inputs, oracle
+from _helpers import b, inputs, oracle, random_spins
 
 pytestmark = pytest.mark.gpu
 
@@ -70,3 +70,31 @@ def test_energy_of_the_last_run_without_passing_spins(prec, n, R):
                 c.grad(inputs.zeta_ramp(T), inputs.dt_const(T), q0)
                 with pytest.raises(b.SpringIsingError):
                     c.energy(None)
+
+
+def test_energy_of_the_last_run_around_other_readouts():
+    """On the tensor path the last run's step kernel also leaves its sign
+    readout as the exact readout's bf16 operand.  Readouts of other spins in
+    between (more replicas than the context's too) and continued runs must
+    not disturb si_energy with spins NULL."""
+    n, R, T = 300, 70, 6
+    J = inputs.pm1_coupling(n, seed=36)
+    q0 = inputs.positions(n, R, seed0=3600)
+    z, d = inputs.zeta_ramp(T), inputs.dt_const(T)
+    with b.Context(J, replicas=R, steps=T, prec="j_fp8_q_bf16") as c:
+        _, _, s1 = c.run(z, d, q0)
+        e1, c1, _ = c.energy(None)                     # straight after the run
+        other = random_spins(2 * R + 7, n, seed=37)
+        eo, co, _ = c.energy(other)
+        e2, c2, _ = c.energy(None)                     # after a readout of other spins
+        _, _, s3 = c.run(z, d, None)
+        e3, c3, _ = c.energy(None)
+    ref1 = oracle.energy(J, None, s1).astype(np.int64)
+    np.testing.assert_array_equal(e1, ref1)
+    np.testing.assert_array_equal(e2, ref1)
+    np.testing.assert_array_equal(c1, oracle.cut(J, s1).astype(np.int64))
+    np.testing.assert_array_equal(c2, c1)
+    np.testing.assert_array_equal(eo, oracle.energy(J, None, other).astype(np.int64))
+    np.testing.assert_array_equal(co, oracle.cut(J, other).astype(np.int64))
+    np.testing.assert_array_equal(e3, oracle.energy(J, None, s3).astype(np.int64))
+    np.testing.assert_array_equal(c3, oracle.cut(J, s3).astype(np.int64))
