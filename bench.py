@@ -688,6 +688,12 @@ def run_grouped(args):
     achieved = bytes_step * GROUP_T / (k_ms * 1e-3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
     flops = sum(2.0 * sp.n * sp.n * sp.replicas for sp in specs) * GROUP_T
+    # mixed roofline: each instance bound by its own bytes or flops
+    bf16 = float(peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS)) * 1e12
+    mixed_s = sum(max((sp.n * sp.n * (1 if sp.kind == "pm1" else 2) + sp.replicas * sp.n * 20) / (peak * 1e9),
+                      2.0 * sp.n * sp.n * sp.replicas / bf16) for sp in specs)
+    n_tensor = sum(1 for sp in specs if 2.0 * sp.n * sp.n * sp.replicas / bf16 >
+                   (sp.n * sp.n * (1 if sp.kind == "pm1" else 2) + sp.replicas * sp.n * 20) / (peak * 1e9))
     line = {
         "metric": METRIC, "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -700,6 +706,8 @@ def run_grouped(args):
                      "frac": achieved / peak, "traffic": None, "kernel": "k_group_step",
                      "kernel_ms": k_ms, "algorithmic_bytes_per_step": bytes_step,
                      "tensor_tflops": flops / (k_ms * 1e-3) / 1e12,
+                     "mixed_roofline_ms_per_step": mixed_s * 1e3,
+                     "frac_of_mixed": mixed_s * 1e3 * GROUP_T / k_ms, "tensor_bound_instances": n_tensor,
                      "peak_source": "%s hbm_gbs" % src},
         "gpu_launches": launches, "clocks": clocks,
     }
