@@ -878,7 +878,6 @@ def run_plain(args):
     peaks, src = load_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = bytes_launch / (k_avg * 1e-3) / 1e9
-    l2 = l2_reread_gbs(torch, dev, stream)
     line = {
         "metric": METRIC, "value": units / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -896,9 +895,6 @@ def run_plain(args):
                                "step-tagged words)",
                      "kernel_ms": k_avg, "peak_source": "%s hbm_gbs" % src,
                      "algorithmic_bytes_per_launch": bytes_launch,
-                     "l2_reread_gbs_measured": l2, "frac_of_l2_reread": achieved / l2,
-                     "l2_method": "torch copy between two 16 MiB L2-resident buffers, read + write bytes, "
-                                  "best of 5 x 50 copies, CUDA events",
                      "note": "J (FP32, 4 n^2 B) once per step; it is read from shared memory, so DRAM "
                              "traffic is J once per launch and the step is bound by the cross-SM exchange "
                              "of q"},
@@ -922,29 +918,6 @@ def run_plain(args):
                                           "one thread), %.1f s" % (T_s, el)}
     print(json.dumps(line))
     return 0
-
-
-def l2_reread_gbs(torch, dev, stream, mib=16, iters=50):
-    """L2 re-read bandwidth of this GPU, measured here (read + write bytes of
-    a device copy between two buffers that together stay L2-resident, best of
-    5 CUDA-event timings of `iters` copies on the current stream)."""
-    a = torch.empty(mib * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    bb = torch.empty_like(a)
-    a.fill_(1.0)
-    for _ in range(10):
-        bb.copy_(a)
-    best = None
-    for _ in range(5):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(iters):
-            bb.copy_(a)
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        best = ms if best is None else min(best, ms)
-    return 2.0 * a.numel() * 4 * iters / (best * 1e-3) / 1e9
 
 
 def ncu_case_plain(args):
