@@ -65,22 +65,25 @@ def final_cuts(J, q0, zeta, dt, prec="j_fp8_q_bf16", stream=None, **params):
 
 def energy_trajectory(J, q0, zeta, dt, every: int, prec="j_fp8_q_bf16", stream=None, **params):
     """Exact Ising energy of every replica's sign readout after every `every`
-    steps (segments resumed from the full FP32 state).  Returns
-    (steps [S], energies int64 [S][R], final spins)."""
+    steps: segments of `every` steps that continue from the context's own
+    state (si_run with q_init NULL), each followed by the readout of the
+    run's spins in place.  Returns (steps [S], energies int64 [S][R], final
+    spins)."""
     from . import _binding as b
     T = len(zeta)
     if every <= 0 or T % every:
         raise ValueError("the run length must be a multiple of the readout interval")
     q = np.ascontiguousarray(q0, dtype=np.float32)
-    p = np.zeros_like(q)
-    R = q.shape[0]
+    R, n = q.shape
+    nseg = T // every
+    s = np.empty((R, n), np.int8)
     steps, energies = [], []
     with b.Context(J, replicas=R, steps=every, prec=prec, stream=stream, **params) as ctx:
-        s = None
-        for seg in range(T // every):
+        for seg in range(nseg):
             sl = slice(seg * every, (seg + 1) * every)
-            q, p, s = ctx.run(zeta[sl], dt[sl], q, p)
-            e, _, _ = ctx.energy(s)
+            ctx.run_into(zeta[sl], dt[sl], q if seg == 0 else None, None, None, None,
+                         s if seg == nseg - 1 else None)
+            e, _, _ = ctx.energy(None)
             steps.append((seg + 1) * every)
             energies.append(e.astype(np.int64))
     return np.asarray(steps), np.stack(energies), s
