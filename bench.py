@@ -423,7 +423,8 @@ def run_scale(args):
                      "frac": achieved / peak, "traffic": None, "kernel": "k_group_step (one member)",
                      "kernel_ms": kern_ms, "peak_source": "%s bf16_tflops (burst)" % src},
         "fp32_plain": {"ms_per_step": fp32_ms_step, "extrapolated_run_ms": fp32_ms_step * T,
-                       "note": "k_tiled_step (CUDA cores), 3 steps timed, extrapolated to T=5000",
+                       "note": "k_tiled_f32 (register-tiled FP32 on CUDA cores), 3 steps timed, "
+                               "extrapolated to T=5000",
                        "speedup": fp32_ms_step * T / run_ms},
         "clocks": clocks,
     }

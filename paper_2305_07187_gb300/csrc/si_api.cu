@@ -138,7 +138,7 @@ static void free_ctx(Ctx *c) {
     if (!c) return;
     void *ptrs[] = {c->dJ, c->dJ8, c->dh, c->dhf, c->dh8, c->dq, c->dp, c->dqbuf,
                     c->dzeta, c->ddt, c->dbar, c->derr, c->dspins, c->dspins_in,
-                    c->dE, c->dC, c->dEf, c->dstage, c->g_ws, c->e_sig, c->e_sum, c->dxch};
+                    c->dE, c->dC, c->dEf, c->dstage, c->g_ws, c->e_sig, c->e_sum, c->dxch, c->dqT};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     adj_tc_free(c->g_tc);
@@ -253,6 +253,11 @@ static si_status create_impl(Ctx *c, const float *J, const float *h) {
         if (c->path == Path::PLAIN_PERSISTENT && !f64) {
             c->xch_bytes = 2 * (size_t)c->R * c->ldj * sizeof(unsigned long long);
             SI_CUDA_TRY(si_dev_malloc((void **)&c->dxch, c->xch_bytes));
+        }
+        if (c->path == Path::SIMT_TILED && !f64) {
+            const size_t bytes = 3 * (size_t)c->ldj * round_up(c->R, 128) * sizeof(float);
+            SI_CUDA_TRY(si_dev_malloc((void **)&c->dqT, bytes));
+            SI_CUDA_TRY(cudaMemsetAsync(c->dqT, 0, bytes, c->stream));
         }
     }
     if (c->integer_j) SI_CUDA_TRY(si_dev_malloc((void **)&c->dJ8, (size_t)n * c->ld8));

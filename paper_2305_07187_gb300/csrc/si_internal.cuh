@@ -94,6 +94,9 @@ struct Ctx {
     // words, [2][R][ldj] x 8 bytes
     unsigned long long *dxch = nullptr;
     size_t xch_bytes = 0;
+    // FP32 tiled path (R > 4): spin-major q (two planes) and p during a run,
+    // [3][ldj][round_up(R, 128)]
+    float *dqT = nullptr;
     float *dzeta = nullptr, *ddt = nullptr;  // schedules [steps]
     unsigned *dbar = nullptr;            // inter-CTA barrier counters
     int nbar = 0;

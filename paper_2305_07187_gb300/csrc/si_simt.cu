@@ -325,6 +325,161 @@ __global__ void __launch_bounds__(TB_THREADS) k_tiled_step(TiledArgs<T> a, const
     }
 }
 
+// ------------------------------------------------------------ tiled, FP32
+// Register-tiled FP32 step for many replicas: 128 spins x 128 replicas per
+// CTA, 8 x 8 outputs per thread, 16-wide K chunks double-buffered in shared
+// memory by cp.async.  Both operands are K-major: the J tile is read as rows
+// of J (J is symmetric, so row k holds column k), and the positions are kept
+// during a run as qT [ldj][Rp] (spin-major), written by each step's
+// epilogue for the next.  p stays spin-major (pT) for the run; the
+// replica-major q, p and the spins are written at the last step only.  The
+// arithmetic is that of k_tiled_step: 16-term FMA chains per chunk, chunk
+// sums added with compensation in K order.
+constexpr int TF_M = 128, TF_R = 128, TF_K = 16, TF_THREADS = 256;
+
+struct TiledF32Args {
+    const float *J;
+    int ldj;
+    const float *h;
+    int n, R, Rp;
+    const float *qTc;   // [ldj][Rp] q(t_n), spin-major
+    float *qTn;         // [ldj][Rp] q(t_{n+1})
+    float *pT;          // [ldj][Rp] p, updated in place
+    int last;           // also write the replica-major state and spins
+    float *qn;          // [R][ldj] q(t_{n+1}) (last step)
+    float *p;           // [R][n] p (last step)
+    int8_t *spins;      // [R][lds] or null (last step)
+    int lds;
+    StepParams sp;
+};
+
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *src, int src_bytes) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
+
+__global__ void __launch_bounds__(TF_THREADS, 1) k_tiled_f32(TiledF32Args a, const float *zeta, const float *dt,
+                                                            int t) {
+    __shared__ __align__(16) float Js[2][TF_K][TF_M];
+    __shared__ __align__(16) float Qs[2][TF_K][TF_R];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int i0 = blockIdx.x * TF_M, r0 = blockIdx.y * TF_R;
+    // thread outputs: rows i0 + 8 ty + u, replicas r0 + 4 tx + v and
+    // r0 + 64 + 4 tx + v (two groups of 4, so the 128-bit reads of a quarter
+    // warp fall in distinct bank groups)
+    auto load = [&](int buf, int k0) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int e = tid + TF_THREADS * j;
+            const int kk = e >> 5, c4 = (e & 31) * 4;
+            const int k = k0 + kk;
+            const int col = i0 + c4;
+            const bool in = k < a.n && col < a.ldj;
+            cp_async16(&Js[buf][kk][c4], in ? (const void *)(a.J + (size_t)k * a.ldj + col) : (const void *)a.J,
+                       in ? 16 : 0);
+            cp_async16(&Qs[buf][kk][c4], a.qTc + (size_t)k * a.Rp + r0 + c4, 16);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    CompSum<float> acc[8][8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[u][v].init();
+    const int nk = a.ldj / TF_K;
+    load(0, 0);
+    for (int c = 0; c < nk; ++c) {
+        const int buf = c & 1;
+        if (c + 1 < nk) {
+            load(buf ^ 1, (c + 1) * TF_K);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        float part[8][8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) part[u][v] = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < TF_K; ++kk) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&Js[buf][kk][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&Js[buf][kk][ty * 8 + 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Qs[buf][kk][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Qs[buf][kk][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int v = 0; v < 8; ++v) part[u][v] = fmaf(av[u], bv[v], part[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) acc[u][v].add(part[u][v]);
+        __syncthreads();   // the next iteration's load overwrites this buffer
+    }
+    const float zt = zeta[t], dtt = dt[t], dtm = dtt / a.sp.m;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const int i = i0 + ty * 8 + u;
+        if (i >= a.n) continue;
+        const float hi = a.h ? a.h[i] : 0.f;
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            const int rb = r0 + g * 64 + tx * 4;
+            const size_t e = (size_t)i * a.Rp + rb;
+            const float4 q4 = *reinterpret_cast<const float4 *>(a.qTc + e);
+            const float4 p4 = *reinterpret_cast<const float4 *>(a.pT + e);
+            const float qv[4] = {q4.x, q4.y, q4.z, q4.w}, pv[4] = {p4.x, p4.y, p4.z, p4.w};
+            float qo[4], po[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                integrate<float>(qv[v], pv[v], acc[u][g * 4 + v].value() + hi, zt, dtt, dtm, a.sp, qo[v], po[v]);
+                if (rb + v >= a.R) qo[v] = po[v] = 0.f;   // padding replicas stay zero
+            }
+            *reinterpret_cast<float4 *>(a.qTn + e) = make_float4(qo[0], qo[1], qo[2], qo[3]);
+            *reinterpret_cast<float4 *>(a.pT + e) = make_float4(po[0], po[1], po[2], po[3]);
+            if (a.last) {
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    const int r = rb + v;
+                    if (r >= a.R) continue;
+                    a.qn[(size_t)r * a.ldj + i] = qo[v];
+                    a.p[(size_t)r * a.n + i] = po[v];
+                    if (a.spins) a.spins[(size_t)r * a.lds + i] = spin_of(qo[v]);
+                }
+            }
+        }
+    }
+}
+
+// q(0) [R][ldj] and p [R][n] -> spin-major qT, pT [ldj][Rp] (zero padding),
+// through 32 x 32 shared-memory tiles so that both sides are coalesced.
+__global__ void k_tiled_f32_begin(const float *q, const float *p, int n, int R, int ldj, int Rp, float *qT,
+                                  float *pT) {
+    __shared__ float tq[32][33], tp[32][33];
+    const int i0 = blockIdx.x * 32, rb0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+    for (int y = ty; y < 32; y += 8) {
+        const int r = rb0 + y, i = i0 + tx;
+        const bool ok = r < R && i < n;
+        tq[y][tx] = ok ? q[(size_t)r * ldj + i] : 0.f;
+        tp[y][tx] = ok ? p[(size_t)r * n + i] : 0.f;
+    }
+    __syncthreads();
+    for (int y = ty; y < 32; y += 8) {
+        const int i = i0 + y, r = rb0 + tx;
+        if (i < ldj && r < Rp) {
+            qT[(size_t)i * Rp + r] = tq[tx][y];
+            pT[(size_t)i * Rp + r] = tp[tx][y];
+        }
+    }
+}
+
 // ====================================================================== misc
 __global__ void k_validate(const float *J, const float *h, int n, int prec,
                            unsigned long long *flags, long long *s_upper) {
@@ -639,6 +794,40 @@ static si_status plain_launch(Ctx *c, int steps, int8_t *spins_dev) {
     return SI_OK;
 }
 
+static si_status tiled_f32_launch(Ctx *c, int steps, int8_t *spins_dev) {
+    const int Rp = round_up(c->R, TF_R);
+    const size_t plane = (size_t)c->ldj * Rp;
+    float *qT = c->dqT, *pT = c->dqT + 2 * plane;
+    float *qb = (float *)c->dqbuf;
+    k_tiled_f32_begin<<<dim3(cdiv(c->ldj, 32), cdiv(Rp, 32)), 256, 0, c->stream>>>(
+        qb, (const float *)c->dp, c->n, c->R, c->ldj, Rp, qT, pT);
+    SI_CUDA_TRY(cudaGetLastError());
+    TiledF32Args a;
+    a.J = (const float *)c->dJ;
+    a.ldj = c->ldj;
+    a.h = (const float *)c->dh;
+    a.n = c->n;
+    a.R = c->R;
+    a.Rp = Rp;
+    a.pT = pT;
+    a.p = (float *)c->dp;
+    a.lds = c->ld8;
+    a.sp = StepParams{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max,
+                      c->prm.update_order, c->prm.wall_zero_p};
+    const dim3 grid(cdiv(c->n, TF_M), Rp / TF_R);
+    for (int t = 0; t < steps; ++t) {
+        a.qTc = qT + (size_t)(t & 1) * plane;
+        a.qTn = qT + (size_t)((t + 1) & 1) * plane;
+        a.last = t == steps - 1;
+        a.qn = qb + (size_t)((t + 1) & 1) * c->R * c->ldj;
+        a.spins = a.last ? spins_dev : nullptr;
+        k_tiled_f32<<<grid, TF_THREADS, 0, c->stream>>>(a, c->dzeta, c->ddt, t);
+    }
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += steps + 1;
+    return SI_OK;
+}
+
 template <typename T>
 static si_status tiled_launch(Ctx *c, int steps, int8_t *spins_dev) {
     TiledArgs<T> a;
@@ -669,7 +858,9 @@ si_status simt_run(Ctx *c, int steps, int8_t *spins_dev) {
     const bool f64 = c->prm.prec == SI_PREC_FP64;
     if (c->path == Path::PLAIN_PERSISTENT)
         return f64 ? plain_launch<double>(c, steps, spins_dev) : plain_launch<float>(c, steps, spins_dev);
-    return f64 ? tiled_launch<double>(c, steps, spins_dev) : tiled_launch<float>(c, steps, spins_dev);
+    if (f64) return tiled_launch<double>(c, steps, spins_dev);
+    if (steps > 0 && c->dqT) return tiled_f32_launch(c, steps, spins_dev);
+    return tiled_launch<float>(c, steps, spins_dev);
 }
 
 si_status simt_init_state(Ctx *c, const float *q_init, const float *p_init) {
