@@ -613,6 +613,22 @@ def ncu_case_grad(args):
     return 0
 
 
+def ncu_case_scale(args):
+    """Profiling case of the FP32 CUDA-core path of the scale comparison at a
+    capture-sized N=8192 (J 256 MB in FP32, above L2), R=512, --time-steps
+    steps: one warm-up and one profiled si_run."""
+    from paper_2305_07187_gb300 import _binding as b
+    n, R, T = 8192, SCALE_R, args.time_steps
+    J = inputs.pm1_coupling(n, seed=1)
+    q0 = inputs.positions(n, R, seed0=100)
+    with b.Context(J, replicas=R, steps=T, prec="fp32") as ctx:
+        del J
+        for _ in range(2):
+            ctx.run(inputs.zeta_ramp(T), inputs.dt_const(T), q0)
+        print(ctx.describe())
+    return 0
+
+
 def ncu_case_grouped(args):
     """Profiling case of the grouped path: the first --group-count instances
     of the uneven batch, autotuned, then one run of --time-steps steps."""
@@ -966,6 +982,8 @@ def main():
         return ncu_case_grad(args)
     if args.ncu_case and args.workload == "plain":
         return ncu_case_plain(args)
+    if args.ncu_case and args.workload == "scale":
+        return ncu_case_scale(args)
     if args.ncu_case:
         return ncu_case(args)
     if args.workload == "plain":
