@@ -102,9 +102,11 @@ static si_status finish_call(Ctx *c, std::initializer_list<DevOut *> outs) {
 }
 
 static si_status check_device_error(Ctx *c) {
-    int herr = 0;
-    SI_CUDA_TRY(cudaMemcpyAsync(&herr, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    int local = 0;
+    int *dst = c->herr ? c->herr : &local;
+    SI_CUDA_TRY(cudaMemcpyAsync(dst, c->derr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const int herr = *dst;
     if (herr != DEV_OK) {
         SI_CUDA_TRY(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
         SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -141,6 +143,7 @@ static void free_ctx(Ctx *c) {
                     c->dE, c->dC, c->dEf, c->dstage, c->g_ws, c->e_sig, c->e_sum, c->dxch, c->dqT};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (c->herr) cudaFreeHost(c->herr);
     adj_tc_free(c->g_tc);
     if (c->g_graph) cudaGraphExecDestroy(c->g_graph);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -286,6 +289,10 @@ static si_status create_impl(Ctx *c, const float *J, const float *h) {
     SI_CUDA_TRY(si_dev_malloc((void **)&c->dbar, sizeof(unsigned) * c->nbar));
     SI_CUDA_TRY(si_dev_malloc((void **)&c->derr, sizeof(int)));
     SI_CUDA_TRY(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
+    if (cudaHostAlloc((void **)&c->herr, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();   // optional: the read then goes through pageable memory
+        c->herr = nullptr;
+    }
     SI_CUDA_TRY(si_dev_malloc((void **)&c->dspins, (size_t)c->R * c->ld8));
     SI_CUDA_TRY(cudaMemsetAsync(c->dspins, 0, (size_t)c->R * c->ld8, c->stream));
     if (c->integer_j) {

@@ -361,6 +361,7 @@ struct Group {
     int *d_kbl = nullptr;
     float *d_zeta = nullptr, *d_dt = nullptr;
     int *d_err = nullptr;
+    int *h_err = nullptr;   // pinned host copy of the error word
     int policy = -1;            // chosen tile policy
     int grid = 0;
     cudaGraphExec_t graph = nullptr;
@@ -685,9 +686,11 @@ static si_status group_graph(Group *g, int steps) {
 }
 
 static si_status group_check_err(Group *g) {
-    int herr = 0;
-    SI_CUDA_TRY(cudaMemcpyAsync(&herr, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
+    int local = 0;
+    int *dst = g->h_err ? g->h_err : &local;
+    SI_CUDA_TRY(cudaMemcpyAsync(dst, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
     SI_CUDA_TRY(cudaStreamSynchronize(g->stream));
+    const int herr = *dst;
     if (herr != DEV_OK) {
         SI_CUDA_TRY(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream));
         SI_CUDA_TRY(cudaStreamSynchronize(g->stream));
@@ -767,6 +770,7 @@ static void free_group(Group *g) {
     void *ptrs[] = {g->d_inst, g->d_tiles, g->d_maps, g->d_kbl, g->d_zeta, g->d_dt, g->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (g->h_err) cudaFreeHost(g->h_err);
     if (g->graph) cudaGraphExecDestroy(g->graph);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
@@ -881,6 +885,10 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
     SI_CUDA_TRY(si_dev_malloc((void **)&g->d_dt, sizeof(float) * std::max(1, g->steps)));
     SI_CUDA_TRY(si_dev_malloc((void **)&g->d_err, sizeof(int)));
     SI_CUDA_TRY(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream));
+    if (cudaHostAlloc((void **)&g->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();   // optional: the read then goes through pageable memory
+        g->h_err = nullptr;
+    }
     for (auto &x : g->m) {            // readout views share the group's error word
         x.energy.derr = g->d_err;
         x.energy.spin_limit_ns = g->limit_ns;

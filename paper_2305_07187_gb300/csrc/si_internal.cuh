@@ -101,6 +101,7 @@ struct Ctx {
     unsigned *dbar = nullptr;            // inter-CTA barrier counters
     int nbar = 0;
     int *derr = nullptr;                 // device error word
+    int *herr = nullptr;                 // pinned host copy of it (the read at the end of a call is a DMA)
     int8_t *dspins = nullptr;            // [R][ld8]
     int8_t *dspins_in = nullptr;         // staging for si_energy
     int spins_in_cap = 0;                // replicas the staging holds
