@@ -329,7 +329,8 @@ __global__ void __launch_bounds__(TB_THREADS) k_tiled_step(TiledArgs<T> a, const
 // Register-tiled FP32 step for many replicas: 128 spins x 128 replicas per
 // CTA, 8 x 8 outputs per thread, 16-wide K chunks double-buffered in shared
 // memory by cp.async.  Both operands are K-major: the J tile is read as rows
-// of J (J is symmetric, so row k holds column k), and the positions are kept
+// of J (J is symmetric, so row k holds column k; si_create rejects any J
+// whose transpose differs by a single value), and the positions are kept
 // during a run as qT [ldj][Rp] (spin-major), written by each step's
 // epilogue for the next.  p stays spin-major (pT) for the run; the
 // replica-major q, p and the spins are written at the last step only.  The
