@@ -14,10 +14,17 @@
  * General conventions
  *   - Every pointer argument may be host or device memory; the library tells
  *     them apart with cudaPointerGetAttributes.  Host inputs are copied in on
- *     the context's stream; host outputs are copied out.  The computing
- *     calls (si_run, si_energy, si_grad, si_hamiltonian, si_run_group,
- *     si_group_energy) return after their work has finished: they end by
- *     reading the device error word or synchronising the context's stream.
+ *     the context's stream; host outputs are copied out.  si_run and
+ *     si_energy are asynchronous with respect to the host when none of
+ *     their outputs is host memory (device outputs, or none): they return
+ *     once their work is enqueued on the context's stream, and a device-side
+ *     error of that work (a timed-out wait) is reported by the next call
+ *     that synchronises, which also drops the run's state (no continuing,
+ *     no readout of its spins).  With a host output, and for the other
+ *     computing calls (si_grad, si_hamiltonian, si_get_state, si_run_group,
+ *     si_group_energy), the call returns after its work has finished: it
+ *     ends by reading the device error word.  si_synchronize waits for a
+ *     context's work and reports its pending device error.
  *   - The caller owns every buffer it passes.  The context owns its device
  *     copy of J, the integrator state, the operand buffers and the
  *     checkpoints, all allocated in si_create and freed in si_destroy.
@@ -204,6 +211,13 @@ si_status si_hamiltonian(si_ctx *ctx, const float *q, const float *p, int32_t R,
  */
 si_status si_enable_timing(si_ctx *ctx, int32_t on);
 si_status si_last_kernel_time(const si_ctx *ctx, float *ms);
+
+/*
+ * Wait until all work enqueued by this context has finished and report a
+ * pending device-side error of it (SI_ERR_TIMEOUT for a wait that ran out;
+ * the run's state is then dropped), else SI_OK.
+ */
+si_status si_synchronize(si_ctx *ctx);
 
 /*
  * Allocation-free single-replica run.  The paper has no counterpart: this

@@ -34,7 +34,7 @@ SI_PREC_J_BF16_Q_BF16 = 3
 PREC = {"fp32": 0, "fp64": 1, "j_fp8_q_bf16": 2, "j_bf16_q_bf16": 3}
 
 EXPORTS = ("si_default_params", "si_create", "si_run", "si_get_state", "si_energy", "si_grad",
-           "si_enable_timing", "si_last_kernel_time", "si_describe", "si_last_launch_count",
+           "si_enable_timing", "si_last_kernel_time", "si_synchronize", "si_describe", "si_last_launch_count",
            "si_last_error", "si_destroy", "si_run_noalloc", "si_hamiltonian", "si_create_group", "si_run_group",
            "si_group_energy", "si_group_enable_timing", "si_group_last_kernel_time",
            "si_group_describe", "si_group_last_launch_count", "si_destroy_group")
@@ -87,6 +87,8 @@ def load():
     lib.si_enable_timing.restype = ctypes.c_int
     lib.si_last_kernel_time.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
     lib.si_last_kernel_time.restype = ctypes.c_int
+    lib.si_synchronize.argtypes = [P]
+    lib.si_synchronize.restype = ctypes.c_int
     lib.si_run_noalloc.argtypes = [ctypes.POINTER(SiParams), P, P, P, P, P, P, P, P]
     lib.si_run_noalloc.restype = ctypes.c_int
     PP = ctypes.POINTER(ctypes.c_void_p)
@@ -227,6 +229,11 @@ class Context:
 
     def enable_timing(self, on=True):
         _check(load().si_enable_timing(self.ctx, 1 if on else 0))
+
+    def synchronize(self):
+        """si_synchronize: wait for this context's work; raises a pending
+        device error of an earlier call that returned early."""
+        _check(load().si_synchronize(self.ctx))
 
     def last_kernel_ms(self) -> float:
         v = ctypes.c_float(0.0)

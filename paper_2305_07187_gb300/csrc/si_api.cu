@@ -90,12 +90,18 @@ static si_status finish_out(DevOut &d, cudaStream_t st) {
 static si_status check_device_error(Ctx *c);
 
 // End of a call: enqueue the copies to host outputs, then one synchronising
-// read of the device error word covers them and every launch before.
-static si_status finish_call(Ctx *c, std::initializer_list<DevOut *> outs) {
+// read of the device error word covers them and every launch before.  A call
+// that may return early (si_run, si_energy) and has no host output returns
+// once its work is enqueued: a device error of its kernels is reported by
+// the next synchronising call.
+static si_status finish_call(Ctx *c, std::initializer_list<DevOut *> outs, bool may_return_early = false) {
+    bool host_out = false;
     for (DevOut *d : outs) {
         si_status s = finish_out(*d, c->stream);
         if (s != SI_OK) return s;
+        host_out = host_out || d->host != nullptr;
     }
+    if (may_return_early && !host_out) return SI_OK;
     if (c->derr) return check_device_error(c);
     SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
     return SI_OK;
@@ -108,6 +114,10 @@ static si_status check_device_error(Ctx *c) {
     SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
     const int herr = *dst;
     if (herr != DEV_OK) {
+        // the error may come from an earlier call that returned early: no
+        // state of a run is left to continue from or to read back
+        c->have_run = false;
+        c->run_spins_valid = false;
         SI_CUDA_TRY(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
         SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
         if (herr == DEV_BAD_CONFIG) {
@@ -439,7 +449,7 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
         SI_CUDA_TRY(cudaGetLastError());
         c->launches += 1;
     }
-    if ((s = finish_call(c, {&qo, &po, &so})) != SI_OK) return s;
+    if ((s = finish_call(c, {&qo, &po, &so}, true)) != SI_OK) return s;
     c->have_run = true;
     c->run_spins_valid = true;
     return SI_OK;
@@ -500,7 +510,7 @@ si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy
         // the last run's spins, already in the padded layout
         s = simt_energy(c, c->dspins, R, c->ld8, (int32_t *)eo.ptr, (int32_t *)co.ptr, (double *)fo.ptr);
         if (s != SI_OK) return s;
-        return finish_call(c, {&eo, &co, &fo});
+        return finish_call(c, {&eo, &co, &fo}, true);
     }
     DevIn sd;
     s = stage_in(sd, spins, (size_t)R * n, c->stream);
@@ -518,7 +528,7 @@ si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy
     c->launches += 1;
     s = simt_energy(c, c->dspins_in, R, c->ld8, (int32_t *)eo.ptr, (int32_t *)co.ptr, (double *)fo.ptr);
     if (s != SI_OK) return s;
-    return finish_call(c, {&eo, &co, &fo});
+    return finish_call(c, {&eo, &co, &fo}, true);
 }
 
 si_status si_hamiltonian(si_ctx *ctx, const float *q, const float *p, int32_t R, double zeta,
@@ -616,6 +626,19 @@ si_status si_enable_timing(si_ctx *ctx, int32_t on) {
     }
     c->timing = on != 0;
     c->ev_valid = false;
+    return SI_OK;
+}
+
+si_status si_synchronize(si_ctx *ctx) {
+    NvtxRange nvtx_range("si_synchronize");
+    set_error("");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) {
+        set_error("si_synchronize: ctx is required");
+        return SI_ERR_INVALID_ARG;
+    }
+    if (c->derr) return check_device_error(c);
+    SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
     return SI_OK;
 }
 

@@ -98,3 +98,30 @@ def test_energy_of_the_last_run_around_other_readouts():
     np.testing.assert_array_equal(co, oracle.cut(J, other).astype(np.int64))
     np.testing.assert_array_equal(e3, oracle.energy(J, None, s3).astype(np.int64))
     np.testing.assert_array_equal(c3, oracle.cut(J, s3).astype(np.int64))
+
+
+@pytest.mark.parametrize("prec,n,R", [("fp32", 130, 3), ("fp32", 77, 9), ("j_fp8_q_bf16", 300, 70)])
+def test_early_returning_calls_give_the_synchronous_results(prec, n, R):
+    """si_run and si_energy with device data only return before their work
+    has finished; after si_synchronize their outputs equal those of the same
+    calls with host outputs."""
+    import torch
+    T = 7
+    J = inputs.pm1_coupling(n, seed=38)
+    z, d = inputs.zeta_ramp(T), inputs.dt_const(T)
+    q0 = inputs.positions(n, R, seed0=3800)
+    with b.Context(J, replicas=R, steps=T, prec=prec) as c:
+        zd, dd, qd = (torch.from_numpy(x).cuda() for x in (z, d, q0))
+        qo = torch.empty((R, n), dtype=torch.float32, device="cuda")
+        so = torch.empty((R, n), dtype=torch.int8, device="cuda")
+        eo = torch.empty(R, dtype=torch.int32, device="cuda")
+        co = torch.empty(R, dtype=torch.int32, device="cuda")
+        c.run_into(zd, dd, qd, None, qo, None, so)
+        c.energy_into(None, R, eo, co, None)
+        c.synchronize()
+        q_h, _, s_h = c.run(z, d, q0)
+        e_h, c_h, _ = c.energy(s_h)
+    np.testing.assert_array_equal(qo.cpu().numpy(), q_h)
+    np.testing.assert_array_equal(so.cpu().numpy(), s_h)
+    np.testing.assert_array_equal(eo.cpu().numpy(), e_h)
+    np.testing.assert_array_equal(co.cpu().numpy(), c_h)

@@ -32,3 +32,27 @@ def test_stalled_wait_times_out_and_device_recovers(prec, R, monkeypatch):
         e, _, _ = ctx.energy(s)
     assert np.abs(q).max() <= b.SQRT2_F32 and np.abs(p).max() <= 2.0
     np.testing.assert_array_equal(e, oracle.energy(J, None, s).astype(np.int64))
+
+
+@pytest.mark.parametrize("prec,R", [("fp32", 1), ("j_fp8_q_bf16", 256)])
+def test_error_of_an_early_returning_run_surfaces_at_the_next_synchronising_call(prec, R, monkeypatch):
+    """si_run with device inputs and no host output returns once its work is
+    enqueued; the timed-out wait is then reported by si_synchronize, and the
+    failed run leaves no spins to read out."""
+    import torch
+    n, T = 300, 12
+    J = inputs.pm1_coupling(n, seed=5)
+    z = torch.from_numpy(inputs.zeta_ramp(T)).cuda()
+    d = torch.from_numpy(inputs.dt_const(T)).cuda()
+    q = torch.from_numpy(inputs.positions(n, R, seed0=50)).cuda()
+    monkeypatch.setenv("SI_DEBUG_STALL_STEP", "3")
+    monkeypatch.setenv("SI_SPIN_LIMIT_NS", "200000000")
+    with b.Context(J, replicas=R, steps=T, prec=prec) as ctx:
+        ctx.run_into(z, d, q)
+        with pytest.raises(b.SpringIsingError) as ei:
+            ctx.synchronize()
+        assert ei.value.status == b.SI_ERR_TIMEOUT
+        with pytest.raises(b.SpringIsingError) as ei:
+            ctx.energy(None)
+        assert ei.value.status == b.SI_ERR_INVALID_ARG
+        ctx.synchronize()   # nothing pending any more
