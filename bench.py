@@ -241,10 +241,14 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
 
     Target C*: median final cut of the plain FP32 path over 1000 replicas
     (T=1000, linear zeta ramp, seeds 100..1099).  Batched path (tensor cores,
-    R=1024, the T=2000 schedule): wall time from the first launch to the first
-    readout (every `every` steps; exact int32 cuts of all replicas, readout
-    included) at which any replica reaches C*; the run is advanced segment by
-    segment from its own FP32 state.  Median over `seeds` initial-position
+    R=1024, the T=2000 schedule): wall time from the first launch to the host
+    seeing the first readout (every `every` steps; exact int32 cuts of all
+    replicas, readout included) at which any replica reaches C*; the run is
+    advanced segment by segment from its own FP32 state.  The loop is
+    pipelined: segment s (run, readout into device memory, cuts copied to
+    pinned host memory) is queued before the cuts of segment s-1 are checked,
+    so the GPU never waits for the host; at most one segment runs past the
+    hit, after the clock has stopped.  Median over `seeds` initial-position
     seeds.  FP32 plain (R=1): TTS99 = t_run ln(0.01)/ln(1 - p_s), p_s the
     fraction of the 1000 FP32 replicas that reach C*."""
     n = N_SPINS
@@ -271,23 +275,34 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
     zb = torch.from_numpy(inputs.zeta_ramp(T_STEPS)).to(dev)
     db = torch.from_numpy(inputs.dt_const(T_STEPS)).to(dev)
     ttts, hit_steps = [], []
+    nseg = T_STEPS // every
     with b.Context(J, replicas=R, steps=every, prec="j_fp8_q_bf16", stream=stream.cuda_stream) as cb:
-        cut_h = torch.empty(R, dtype=torch.int32).pin_memory().numpy()   # pinned: the cuts' D2H copy
+        cut_d = torch.empty((nseg, R), dtype=torch.int32, device=dev)
+        cut_p = torch.empty((nseg, R), dtype=torch.int32).pin_memory()
+        ready = [torch.cuda.Event() for _ in range(nseg)]
         for seed in range(seeds + 1):
             q_init = torch.from_numpy(inputs.positions(n, R, seed0=200000 + 4096 * seed)).to(dev)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             hit = None
-            for seg in range(T_STEPS // every):
-                sl = slice(seg * every, (seg + 1) * every)
-                # the first segment starts from q_init (zero momenta), the
-                # others continue from the context's FP32 state
-                cb.run_into(zb[sl], db[sl], q_init if seg == 0 else None, None, None, None, None)
-                cb.energy_into(None, R, None, cut_h, None)   # the run's own spins; cuts to host in the call
-                if int(cut_h.max()) >= c_star:
-                    hit = (seg + 1) * every
-                    break
+            for seg in range(nseg + 1):
+                if seg < nseg:
+                    sl = slice(seg * every, (seg + 1) * every)
+                    # the first segment starts from q_init (zero momenta), the
+                    # others continue from the context's FP32 state; both
+                    # calls return once queued (device data only)
+                    cb.run_into(zb[sl], db[sl], q_init if seg == 0 else None, None, None, None, None)
+                    cb.energy_into(None, R, None, cut_d[seg], None)
+                    cut_p[seg].copy_(cut_d[seg], non_blocking=True)
+                    ready[seg].record(stream)
+                if seg >= 1:
+                    # the previous segment's cuts, while this one runs
+                    ready[seg - 1].synchronize()
+                    if int(cut_p[seg - 1].numpy().max()) >= c_star:
+                        hit = seg * every
+                        break
             el = time.perf_counter() - t0
+            cb.synchronize()   # the segment queued past the hit, and any pending device error
             if seed == 0:
                 continue          # warm-up
             ttts.append(el if hit is not None else float("inf"))
