@@ -459,6 +459,11 @@ si_status si_get_state(si_ctx *ctx, double *q_out, double *p_out) {
     NvtxRange nvtx_range("si_get_state");
     set_error("");
     Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (c && c->derr && c->have_run) {
+        // a run that returned early may have failed since: report it first
+        const si_status e = check_device_error(c);
+        if (e != SI_OK) return e;
+    }
     if (!c || !c->have_run) {
         set_error("si_get_state: no completed run");
         return SI_ERR_INVALID_ARG;

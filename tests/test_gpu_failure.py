@@ -52,6 +52,10 @@ def test_error_of_an_early_returning_run_surfaces_at_the_next_synchronising_call
         with pytest.raises(b.SpringIsingError) as ei:
             ctx.synchronize()
         assert ei.value.status == b.SI_ERR_TIMEOUT
+        ctx.run_into(z, d, q)
+        with pytest.raises(b.SpringIsingError) as ei:
+            ctx.get_state()                 # reports the pending error, not a half-written state
+        assert ei.value.status == b.SI_ERR_TIMEOUT
         with pytest.raises(b.SpringIsingError) as ei:
             ctx.energy(None)
         assert ei.value.status == b.SI_ERR_INVALID_ARG
