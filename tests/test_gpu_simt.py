@@ -12,7 +12,7 @@ TOL_FP32_STEP = 1e-6     # per-step normwise relative, FP32 plain path
 
 @pytest.mark.parametrize("n,R", [(1, 1), (17, 1), (127, 2), (129, 3), (300, 4),
                                  (2000, 1), (2001, 1), (5, 5), (70, 17), (130, 64), (257, 100),
-                                 (2001, 15), (2001, 16)])
+                                 (2001, 15), (2001, 16), (300, 130), (129, 257)])
 def test_fp32_per_step_teacher_forced(n, R):
     J = inputs.pm1_coupling(n, seed=n)
     T = 40
