@@ -221,7 +221,9 @@ extern "C" si_status si_run_noalloc(const si_params *prm, const float *J, const 
         set_error("si_run_noalloc: spins_out needs steps >= 1");
         return SI_ERR_INVALID_ARG;
     }
-    SI_CUDA_TRY(cudaMemcpyAsync(q, a.qbuf + (size_t)(a.steps & 1) * n, sq_bytes, cudaMemcpyDeviceToDevice, st));
+    // Read the error word before the positions go back to the caller: a run
+    // that timed out leaves q as it came in (p is updated in place and is
+    // then unspecified).
     int herr = 0;
     SI_CUDA_TRY(cudaMemcpyAsync(&herr, a.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     SI_CUDA_TRY(cudaStreamSynchronize(st));
@@ -229,5 +231,7 @@ extern "C" si_status si_run_noalloc(const si_params *prm, const float *J, const 
         set_error("si_run_noalloc: inter-CTA step barrier timed out");
         return SI_ERR_TIMEOUT;
     }
+    SI_CUDA_TRY(cudaMemcpyAsync(q, a.qbuf + (size_t)(a.steps & 1) * n, sq_bytes, cudaMemcpyDeviceToDevice, st));
+    SI_CUDA_TRY(cudaStreamSynchronize(st));
     return SI_OK;
 }

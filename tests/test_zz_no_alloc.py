@@ -9,7 +9,7 @@ shown to start clean each time.  Collected last on purpose.
 import numpy as np
 import pytest
 
-from _helpers import b, inputs, normwise_rel
+from _helpers import b, inputs, normwise_rel, oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -36,6 +36,38 @@ def test_noalloc_matches_context_run_twice(n, T, exact):
             assert np.array_equal(s, s_ref[0]), call
         else:
             assert normwise_rel(q, p, q_ref[0], p_ref[0]) <= 1e-6, call
+
+
+@pytest.mark.parametrize("n", [8192, b.NOALLOC_MAX_N])
+def test_noalloc_global_coupling_rows_against_oracle(n):
+    """Sizes whose rows of J no longer fit in a CTA's shared memory, so the
+    kernel reads J from global memory every step (the largest allowed n
+    included): per step from an identical state against the FP64 oracle
+    (1e-6 normwise, the FP32 bar), and a three-step call equal bit for bit to
+    three one-step calls."""
+    import torch
+    dev = torch.device("cuda")
+    T = 3
+    J = inputs.pm1_coupling(n, seed=n + 11)
+    zeta = inputs.zeta_ramp(2000)[1500:1500 + T]
+    dt = inputs.dt_const(T)
+    q = (inputs.positions(n, 1, seed0=91) * 8).astype(np.float32)
+    p = np.zeros_like(q)
+    Jd = torch.from_numpy(J).to(dev)
+    zd, dd = torch.from_numpy(zeta).to(dev), torch.from_numpy(dt).to(dev)
+    kw = dict(k=0.5, m=1.0, q0=0.0, q_max=float(np.float32(b.SQRT2_F32)), p_max=2.0)
+    qd = torch.from_numpy(q[0].copy()).to(dev)
+    pd = torch.from_numpy(p[0].copy()).to(dev)
+    for t in range(T):
+        b.run_noalloc(Jd, None, zd[t:t + 1], dd[t:t + 1], qd, pd)
+        qg, pg = qd.cpu().numpy()[None, :], pd.cpu().numpy()[None, :]
+        qo, po = oracle.run(J, None, zeta[t:t + 1], dt[t:t + 1], q, p, **kw)
+        assert normwise_rel(qg, pg, qo, po) <= 1e-6, t
+        q, p = qg, pg
+    q3 = torch.from_numpy((inputs.positions(n, 1, seed0=91) * 8).astype(np.float32)[0]).to(dev)
+    p3 = torch.zeros(n, dtype=torch.float32, device=dev)
+    b.run_noalloc(Jd, None, zd, dd, q3, p3)
+    assert np.array_equal(q3.cpu().numpy(), q[0]) and np.array_equal(p3.cpu().numpy(), p[0])
 
 
 def test_noalloc_rejects_too_large_n():
