@@ -350,12 +350,15 @@ SCALE_N, SCALE_R, SCALE_T, SCALE_EVERY = 32768, 512, 5000, 100
 
 
 def run_scale(args):
-    """Scale workload: N=32768 +-1 complete graph (J e4m3-exact, 1 GiB as
-    e4m3), R=512, T=5000, exact int32 energy of all replicas every 100 steps.
-    Runs as a one-member group (J streamed from HBM every step) in segments
-    of 100 steps resumed from the FP32 state, with the tensor-core readout in
-    between.  The FP32 plain path on the same GPU is timed on 3 steps and
-    extrapolated to T (stated in the line)."""
+    """Scale workload: N=32768 +-1 complete graph (J stored as e4m3, 1 GiB),
+    R=512, T=5000, exact int32 energy of all replicas every 100 steps.  Runs
+    through si_create / si_run: the context's persistent grid would not be
+    co-resident, so the library serves it with the grouped per-step kernel (J
+    streamed from HBM every step).  Segments of 100 steps continue from the
+    context's own state (q_init NULL, no state copy) and each is followed by
+    the tensor-core readout of the run's spins (si_energy with spins NULL).
+    The FP32 plain path on the same GPU is timed on 3 steps and extrapolated
+    to T (stated in the line)."""
     import torch
 
     from paper_2305_07187_gb300 import _binding as b
@@ -372,27 +375,20 @@ def run_scale(args):
     J = inputs.pm1_coupling_torch(n, seed=11, device=dev)
     q0 = inputs.positions_torch(n, R, seed=12, device=dev)
     dt = torch.from_numpy(inputs.dt_const(T)).to(dev)
-    g = b.Group([J], None, replicas=[R], steps=every, precs=["j_fp8_q_bf16"], stream=stream.cuda_stream)
-    qa, pa = q0.clone(), torch.zeros_like(q0)
-    qb, pb = torch.empty_like(q0), torch.empty_like(q0)
-    sp = torch.empty((R, n), dtype=torch.int8, device=dev)
-    g.enable_timing(True)
+    ctx = b.Context(J, replicas=R, steps=every, prec="j_fp8_q_bf16", stream=stream.cuda_stream)
+    ctx.enable_timing(True)
+    cuts = torch.empty(R, dtype=torch.int32, device=dev)
 
     def one_run(z=zeta):
-        nonlocal qa, pa, qb, pb
-        qa.copy_(q0)
-        pa.zero_()
-        best = None
+        best = torch.full((1,), -2 ** 31, dtype=torch.int64, device=dev)
         kern = 0.0
         for seg in range(T // every):
             sl = slice(seg * every, (seg + 1) * every)
-            g.run_into(z[sl], dt[sl], [qa], [pa], [qb], [pb], [sp])
-            kern += g.last_kernel_ms()
-            e, c, _ = g.energy(0, sp)
-            best = int(c.max()) if best is None else max(best, int(c.max()))
-            qa, qb = qb, qa
-            pa, pb = pb, pa
-        return kern, best
+            ctx.run_into(z[sl], dt[sl], q0 if seg == 0 else None)   # later segments continue in place
+            kern += ctx.last_kernel_ms()
+            ctx.energy_into(None, R, None, cuts, None)               # the run's own spins, on the device
+            best = torch.maximum(best, cuts.max().to(torch.int64))
+        return kern, int(best.item())
 
     one_run()                                   # warm-up (autotune, graph capture)
     torch.cuda.synchronize()
@@ -408,8 +404,8 @@ def run_scale(args):
     run_ms = e0.elapsed_time(e1)
     clocks = sampler.stop()
     _, best_cut_linear = one_run(zeta_lin)    # untimed: the paper's linear ramp, same inputs
-    desc = g.describe()
-    g.close()
+    desc = ctx.describe()
+    ctx.close()
     # FP32 plain path on the same GPU, 3 steps, extrapolated to T
     Jc = J.cpu().numpy()
     del J
@@ -428,14 +424,16 @@ def run_scale(args):
         "metric": METRIC, "value": R * n * T / (run_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": 1,
         "warmup": 1, "ms_per_step": run_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": "N=32768 +-1 complete graph (J e4m3-exact, bf16 working copy 2 GiB), R=512, "
+        "config": {"workload": "N=32768 +-1 complete graph (J stored as e4m3, 1 GiB), R=512, "
                                "T=5000, zeta schedule tuned by the adjoint gradient at N=2000 (8 knots, "
-                               "scaled by sqrt(2000/N)), exact int32 energy+cut of all replicas every 100 steps",
+                               "scaled by sqrt(2000/N)), exact int32 energy+cut of all replicas every 100 steps; "
+                               "si_create/si_run continued in place, si_energy of the run's spins",
                    "kernel": desc, "best_cut": best_cut, "best_cut_linear_ramp": best_cut_linear,
                    "tuned_knots_n32768": [round(float(x), 5) for x in knots_n],
                    "tune_objective": [tune.initial, tune.objective]},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "k_group_step (one member)",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k_group_step (the grouped per-step kernel serving the si_create context)",
                      "kernel_ms": kern_ms, "peak_source": "%s bf16_tflops (burst)" % src},
         "fp32_plain": {"ms_per_step": fp32_ms_step, "extrapolated_run_ms": fp32_ms_step * T,
                        "note": "k_tiled_f32 (register-tiled FP32 on CUDA cores), 3 steps timed, "
@@ -1099,6 +1097,11 @@ def main():
     # results agree between the two paths (same inputs, deterministic kernels)
     assert torch.equal(s_h, s_d.cpu()) and torch.equal(e_h, e_d.cpu())
 
+    # end-of-run gather over ranks (host side, outside every timed region):
+    # the job's best replica, the merged cut histogram
+    from paper_2305_07187_gb300 import replicas
+    gathered = replicas.gather_best(c_h.numpy(), e_h.numpy(), s_h.numpy(), dist if world > 1 else None)
+
     units = REPLICAS * N_SPINS * T_STEPS
     value = whole_job_value(units, world, ms_max)
     e2e_value = whole_job_value(units, world, e2e_max)
@@ -1127,6 +1130,10 @@ def main():
                      "algorithmic_flop_per_launch": flops},
         "gpu_launches": launches,
         "clocks": clocks,
+        "gather": {"best_cut": gathered["best"]["cut"], "best_energy": gathered["best"]["energy"],
+                   "best_rank": gathered["best"]["rank"], "best_replica": gathered["best"]["replica"],
+                   "replicas": gathered["replicas"], "median_cut": float(np.median(c_h.numpy())) if world == 1
+                   else None},
     }
     if rank == 0 and world == 1 and not args.no_ttt:
         line["ttt"] = time_to_target(b, torch, dev, stream)

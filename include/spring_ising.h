@@ -15,16 +15,18 @@
  *   - Every pointer argument may be host or device memory; the library tells
  *     them apart with cudaPointerGetAttributes.  Host inputs are copied in on
  *     the context's stream; host outputs are copied out.  si_run and
- *     si_energy are asynchronous with respect to the host when none of
- *     their outputs is host memory (device outputs, or none): they return
- *     once their work is enqueued on the context's stream, and a device-side
- *     error of that work (a timed-out wait) is reported by the next call
- *     that synchronises, which also drops the run's state (no continuing,
- *     no readout of its spins).  With a host output, and for the other
- *     computing calls (si_grad, si_hamiltonian, si_get_state, si_run_group,
- *     si_group_energy), the call returns after its work has finished: it
- *     ends by reading the device error word.  si_synchronize waits for a
- *     context's work and reports its pending device error.
+ *     si_energy are asynchronous with respect to the host when all of their
+ *     array arguments are device memory (or NULL): they return once their
+ *     work is enqueued on the context's stream, and a device-side error of
+ *     that work (a timed-out wait) is reported by the next call that
+ *     synchronises, which also drops the run's state (no continuing, no
+ *     readout of its spins).  A call with any host input or host output
+ *     returns only after its work has finished, so the caller may reuse or
+ *     free its host buffers (pinned ones included) as soon as it returns.
+ *     The other computing calls (si_grad, si_hamiltonian, si_get_state,
+ *     si_run_group, si_group_energy) always return after their work has
+ *     finished: they end by reading the device error word.  si_synchronize
+ *     waits for a context's work and reports its pending device error.
  *   - The caller owns every buffer it passes.  The context owns its device
  *     copy of J, the integrator state, the operand buffers and the
  *     checkpoints, all allocated in si_create and freed in si_destroy.
@@ -134,6 +136,18 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt,
                  float *p_out, int8_t *spins_out);
 
 /*
+ * Change the integrator parameters of an existing context without copying J
+ * again: k, m, q0, q_max, p_max, update_order, wall_zero_p and ckpt_every
+ * take the values in *prm for every later call (e.g. the spring constant
+ * being tuned by gradient descent).  n, replicas, steps, prec and tile_n
+ * must equal the context's (else SI_ERR_INVALID_ARG); the other fields are
+ * checked as in si_create.  The context's state, J and h are kept, so a
+ * run may continue (q_init NULL) under the new parameters.  Work already
+ * enqueued keeps the values it was launched with.
+ */
+si_status si_set_params(si_ctx *ctx, const si_params *prm);
+
+/*
  * Copy the state after the last si_run at the context's working precision,
  * widened to double: q_out, p_out [R][n] (either may be NULL).  Used by the
  * FP64 debug mode, whose state would lose digits through si_run's float
@@ -207,7 +221,9 @@ si_status si_hamiltonian(si_ctx *ctx, const float *q, const float *p, int32_t R,
  * context's stream immediately before and after the launch(es) of the
  * time-step kernel (the coupling force fused with the integrator) and
  * si_last_kernel_time returns their elapsed time in milliseconds.  Off by
- * default; the events cost two records per si_run.
+ * default; the events cost two records per si_run.  si_last_kernel_time
+ * waits for the run; if that run ended on a device error (a timed-out wait)
+ * it returns that error, as si_synchronize would, instead of a time.
  */
 si_status si_enable_timing(si_ctx *ctx, int32_t on);
 si_status si_last_kernel_time(const si_ctx *ctx, float *ms);
@@ -237,7 +253,9 @@ si_status si_synchronize(si_ctx *ctx);
  *   q, p       device, [n], initial state in, final state out
  *   spins_out  device, [n] int8 sign(q) after the last step, or NULL
  *   stream     cudaStream_t as void*
- * n > SI_NOALLOC_MAX_N is rejected with SI_ERR_INVALID_ARG.  The first call
+ * n > SI_NOALLOC_MAX_N is rejected with SI_ERR_INVALID_ARG.  On
+ * SI_ERR_TIMEOUT (an inter-CTA step wait ran out) q still holds its input
+ * positions, but p, which the kernel updates in place, is unspecified.  The first call
  * on a device looks up the scratch array's device address (once per device),
  * so make that first call before any stream capture.  All calls share the
  * one scratch array and it keeps the last call's contents (the call clears

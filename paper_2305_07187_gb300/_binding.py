@@ -33,7 +33,7 @@ SI_PREC_J_FP8_Q_BF16 = 2
 SI_PREC_J_BF16_Q_BF16 = 3
 PREC = {"fp32": 0, "fp64": 1, "j_fp8_q_bf16": 2, "j_bf16_q_bf16": 3}
 
-EXPORTS = ("si_default_params", "si_create", "si_run", "si_get_state", "si_energy", "si_grad",
+EXPORTS = ("si_default_params", "si_create", "si_set_params", "si_run", "si_get_state", "si_energy", "si_grad",
            "si_enable_timing", "si_last_kernel_time", "si_synchronize", "si_describe", "si_last_launch_count",
            "si_last_error", "si_destroy", "si_run_noalloc", "si_hamiltonian", "si_create_group", "si_run_group",
            "si_group_energy", "si_group_enable_timing", "si_group_last_kernel_time",
@@ -73,6 +73,8 @@ def load():
     lib.si_default_params.restype = None
     lib.si_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(SiParams), P, P, P]
     lib.si_create.restype = ctypes.c_int
+    lib.si_set_params.argtypes = [P, ctypes.POINTER(SiParams)]
+    lib.si_set_params.restype = ctypes.c_int
     lib.si_run.argtypes = [P, P, P, P, P, P, P, P]
     lib.si_run.restype = ctypes.c_int
     lib.si_get_state.argtypes = [P, P, P]
@@ -229,6 +231,16 @@ class Context:
 
     def enable_timing(self, on=True):
         _check(load().si_enable_timing(self.ctx, 1 if on else 0))
+
+    def set_params(self, **params):
+        """si_set_params: change integrator fields (k, m, q0, q_max, p_max,
+        update_order, wall_zero_p, ckpt_every) of this context in place."""
+        p = SiParams()
+        ctypes.memmove(ctypes.byref(p), ctypes.byref(self.params), ctypes.sizeof(SiParams))
+        for key, v in params.items():
+            setattr(p, key, v)
+        _check(load().si_set_params(self.ctx, ctypes.byref(p)))
+        self.params = p
 
     def synchronize(self):
         """si_synchronize: wait for this context's work; raises a pending

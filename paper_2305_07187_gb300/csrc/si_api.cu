@@ -91,17 +91,21 @@ static si_status check_device_error(Ctx *c);
 
 // End of a call: enqueue the copies to host outputs, then one synchronising
 // read of the device error word covers them and every launch before.  A call
-// that may return early (si_run, si_energy) and has no host output returns
-// once its work is enqueued: a device error of its kernels is reported by
-// the next synchronising call.
-static si_status finish_call(Ctx *c, std::initializer_list<DevOut *> outs, bool may_return_early = false) {
+// that may return early (si_run, si_energy) and has neither a host output nor
+// a host input returns once its work is enqueued: a device error of its
+// kernels is reported by the next synchronising call.
+// A call with a host input never returns early either: its copies from the
+// caller's memory (pinned memory is read asynchronously) must have finished
+// before the caller may reuse that memory.
+static si_status finish_call(Ctx *c, std::initializer_list<DevOut *> outs, bool may_return_early = false,
+                             bool host_in = false) {
     bool host_out = false;
     for (DevOut *d : outs) {
         si_status s = finish_out(*d, c->stream);
         if (s != SI_OK) return s;
         host_out = host_out || d->host != nullptr;
     }
-    if (may_return_early && !host_out) return SI_OK;
+    if (may_return_early && !host_out && !host_in) return SI_OK;
     if (c->derr) return check_device_error(c);
     SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
     return SI_OK;
@@ -148,6 +152,10 @@ void alloc_fault_reset() { g_alloc_count = 0; }
 
 static void free_ctx(Ctx *c) {
     if (!c) return;
+    if (c->grp) {
+        cudaStreamSynchronize(c->stream);
+        group_ctx_free(c);   // also clears the pointers that alias its buffers
+    }
     void *ptrs[] = {c->dJ, c->dJ8, c->dh, c->dhf, c->dh8, c->dq, c->dp, c->dqbuf,
                     c->dzeta, c->ddt, c->dbar, c->derr, c->dspins, c->dspins_in,
                     c->dE, c->dC, c->dEf, c->dstage, c->g_ws, c->e_sig, c->e_sum, c->dxch, c->dqT};
@@ -247,13 +255,27 @@ static si_status create_impl(Ctx *c, const float *J, const float *h) {
     c->R = p.replicas;
     c->ld8 = round_up(n, 16);
 
+    // Error word and spin readout buffer (the grouped service of a tensor
+    // context writes both).
+    SI_CUDA_TRY(si_dev_malloc((void **)&c->derr, sizeof(int)));
+    SI_CUDA_TRY(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
+    if (cudaHostAlloc((void **)&c->herr, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();   // optional: the read then goes through pageable memory
+        c->herr = nullptr;
+    }
+    SI_CUDA_TRY(si_dev_malloc((void **)&c->dspins, (size_t)c->R * c->ld8));
+    SI_CUDA_TRY(cudaMemsetAsync(c->dspins, 0, (size_t)c->R * c->ld8, c->stream));
+
     // Coupling storage.
     const bool tensor = p.prec == SI_PREC_J_FP8_Q_BF16 || p.prec == SI_PREC_J_BF16_Q_BF16;
     const bool f64 = p.prec == SI_PREC_FP64;
     const size_t es = f64 ? 8 : 4;
     if (tensor) {
         c->path = Path::TENSOR;
-        s = tc_prepare(c, (const float *)Jd.ptr);
+        // one persistent launch for all steps when its grid is co-resident,
+        // else one grouped launch per step
+        s = tc_persistent_fits(c) ? tc_prepare(c, (const float *)Jd.ptr)
+                                  : group_ctx_create(c, (const float *)Jd.ptr, (const float *)hd.ptr);
         if (s != SI_OK) return s;
     } else {
         c->path = (c->R <= 4) ? Path::PLAIN_PERSISTENT : Path::SIMT_TILED;
@@ -273,7 +295,9 @@ static si_status create_impl(Ctx *c, const float *J, const float *h) {
             SI_CUDA_TRY(cudaMemsetAsync(c->dqT, 0, bytes, c->stream));
         }
     }
-    if (c->integer_j) SI_CUDA_TRY(si_dev_malloc((void **)&c->dJ8, (size_t)n * c->ld8));
+    // int8 copy of J for the dp4a readout (tensor contexts read out on the
+    // tensor cores and build it only if ever needed)
+    if (c->integer_j && !tensor) SI_CUDA_TRY(si_dev_malloc((void **)&c->dJ8, (size_t)n * c->ld8));
     // h copies.
     SI_CUDA_TRY(si_dev_malloc((void **)&c->dhf, sizeof(float) * n));
     if (c->integer_h && c->has_h) SI_CUDA_TRY(si_dev_malloc((void **)&c->dh8, n));
@@ -297,15 +321,7 @@ static si_status create_impl(Ctx *c, const float *J, const float *h) {
     SI_CUDA_TRY(si_dev_malloc((void **)&c->ddt, sizeof(float) * sched));
     c->nbar = 4096;
     SI_CUDA_TRY(si_dev_malloc((void **)&c->dbar, sizeof(unsigned) * c->nbar));
-    SI_CUDA_TRY(si_dev_malloc((void **)&c->derr, sizeof(int)));
-    SI_CUDA_TRY(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
-    if (cudaHostAlloc((void **)&c->herr, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
-        cudaGetLastError();   // optional: the read then goes through pageable memory
-        c->herr = nullptr;
-    }
-    SI_CUDA_TRY(si_dev_malloc((void **)&c->dspins, (size_t)c->R * c->ld8));
-    SI_CUDA_TRY(cudaMemsetAsync(c->dspins, 0, (size_t)c->R * c->ld8, c->stream));
-    if (c->integer_j) {
+    if (c->dJ8) {
         si_status s8 = convert_j8(c, (const float *)Jd.ptr);
         if (s8 != SI_OK) return s8;
     }
@@ -393,6 +409,8 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
     c->launches = 0;
     const int steps = c->prm.steps, n = c->n, R = c->R;
     const size_t sb = sizeof(float) * std::max(steps, 1);
+    const bool host_in = (steps > 0 && (!is_device_ptr(zeta) || !is_device_ptr(dt))) ||
+                         (q_init && !is_device_ptr(q_init)) || (p_init && !is_device_ptr(p_init));
     if (steps > 0) {
         const cudaMemcpyKind kz = cudaMemcpyDefault, kd = cudaMemcpyDefault;
         SI_CUDA_TRY(cudaMemcpyAsync(c->dzeta, zeta, sizeof(float) * steps, kz, c->stream));
@@ -413,7 +431,17 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
     // the state is rewritten from here on: only a successful run leaves one
     // to continue from or to read back
     c->have_run = false;
-    if (c->path == Path::TENSOR) {
+    if (c->path == Path::TENSOR && c->grp) {
+        if (!cont) {
+            const size_t bytes = sizeof(float) * (size_t)R * n;
+            SI_CUDA_TRY(cudaMemcpyAsync(c->dq, qi.ptr, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            if (pi.ptr) SI_CUDA_TRY(cudaMemcpyAsync(c->dp, pi.ptr, bytes, cudaMemcpyDeviceToDevice, c->stream));
+            else SI_CUDA_TRY(cudaMemsetAsync(c->dp, 0, bytes, c->stream));
+        }
+        if ((s = group_ctx_prepare(c, steps)) != SI_OK) return s;
+        if (c->timing) SI_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+        if ((s = group_ctx_run(c, steps)) != SI_OK) return s;
+    } else if (c->path == Path::TENSOR) {
         s = cont ? tc_continue_state(c) : tc_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr);
         if (s != SI_OK) return s;
         if (c->timing) SI_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
@@ -449,7 +477,7 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
         SI_CUDA_TRY(cudaGetLastError());
         c->launches += 1;
     }
-    if ((s = finish_call(c, {&qo, &po, &so}, true)) != SI_OK) return s;
+    if ((s = finish_call(c, {&qo, &po, &so}, true, host_in)) != SI_OK) return s;
     c->have_run = true;
     c->run_spins_valid = true;
     return SI_OK;
@@ -533,7 +561,7 @@ si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy
     c->launches += 1;
     s = simt_energy(c, c->dspins_in, R, c->ld8, (int32_t *)eo.ptr, (int32_t *)co.ptr, (double *)fo.ptr);
     if (s != SI_OK) return s;
-    return finish_call(c, {&eo, &co, &fo}, true);
+    return finish_call(c, {&eo, &co, &fo}, true, sd.owned != nullptr);
 }
 
 si_status si_hamiltonian(si_ctx *ctx, const float *q, const float *p, int32_t R, double zeta,
@@ -599,11 +627,42 @@ si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt, const float *
     return finish_call(c, {&gz, &gd, &gk, &ob});
 }
 
+si_status si_set_params(si_ctx *ctx, const si_params *prm) {
+    NvtxRange nvtx_range("si_set_params");
+    set_error("");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c) {
+        set_error("si_set_params: ctx is required");
+        return SI_ERR_INVALID_ARG;
+    }
+    si_status s = check_params(prm);
+    if (s != SI_OK) return s;
+    const si_params &o = c->prm;
+    if (prm->n != o.n || prm->replicas != o.replicas || prm->steps != o.steps || prm->prec != o.prec ||
+        prm->tile_n != o.tile_n) {
+        set_error("si_set_params: n, replicas, steps, prec and tile_n are fixed at si_create");
+        return SI_ERR_INVALID_ARG;
+    }
+    // Work already enqueued read the old values at launch; only the captured
+    // gradient sweep holds them, so it is captured again on the next si_grad.
+    c->prm = *prm;
+    if (c->grp) group_ctx_params(c);
+    if (c->g_graph) {
+        SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        cudaGraphExecDestroy(c->g_graph);
+        c->g_graph = nullptr;
+    }
+    c->g_graph_key = -1;
+    return SI_OK;
+}
+
 si_status si_describe(const si_ctx *ctx, char *buf, int32_t len) {
     const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
     if (!c || !buf || len <= 0) return SI_ERR_INVALID_ARG;
     const char *prec[] = {"fp32", "fp64", "j_fp8_q_bf16", "j_bf16_q_bf16"};
-    if (c->path == Path::TENSOR) {
+    if (c->path == Path::TENSOR && c->grp) {
+        group_ctx_describe(c, buf, len);
+    } else if (c->path == Path::TENSOR) {
         tc_describe(c, buf, len);
     } else if (c->path == Path::PLAIN_PERSISTENT) {
         std::snprintf(buf, len, "plain_persistent prec=%s n=%d R=%d", prec[c->prm.prec], c->n, c->R);
@@ -648,13 +707,22 @@ si_status si_synchronize(si_ctx *ctx) {
 }
 
 si_status si_last_kernel_time(const si_ctx *ctx, float *ms) {
-    const Ctx *c = reinterpret_cast<const Ctx *>(ctx);
+    Ctx *c = const_cast<Ctx *>(reinterpret_cast<const Ctx *>(ctx));
     if (!c || !ms) return SI_ERR_INVALID_ARG;
     if (!c->ev_valid) {
         set_error("no timed run (enable timing before si_run)");
         return SI_ERR_INVALID_ARG;
     }
     SI_CUDA_TRY(cudaEventSynchronize(c->ev1));
+    if (c->derr && c->have_run) {
+        // a run that returned early may have ended on a timed-out wait: its
+        // events then bracket an aborted kernel, so report the error instead
+        const si_status e = check_device_error(c);
+        if (e != SI_OK) {
+            c->ev_valid = false;
+            return e;
+        }
+    }
     SI_CUDA_TRY(cudaEventElapsedTime(ms, c->ev0, c->ev1));
     return SI_OK;
 }

@@ -7,6 +7,8 @@
 // G_ir by sigma_ir, reduces the 128 rows of the tile per replica and adds the
 // tile's integer sum into a 64-bit per-replica total; a finishing kernel
 // forms E = -s/2 - h.sigma and cut = (s - 2 S_upper)/4 (weights w = -J).
+// When the context stores J as e4m3, the four epilogue warps, idle during the
+// mainloop, first widen each J tile to bf16 in shared memory (exactly).
 #include <algorithm>
 #include <cstdio>
 
@@ -18,7 +20,8 @@ constexpr int TE_BM = 128, TE_BN = 128, TE_BK = 64, TE_S = 4, TE_THREADS = 192;
 constexpr int TE_A_BYTES = TE_BM * TE_BK * 2, TE_B_BYTES = TE_BN * TE_BK * 2;
 constexpr int TE_STAGE = TE_A_BYTES + TE_B_BYTES;
 constexpr int TE_BARS = TE_S * TE_STAGE;
-constexpr int TE_SMEM = TE_BARS + (2 * TE_S + 1) * 8 + 16 + 1024;
+constexpr int TE_NBARS = 3 * TE_S + 1;   // full[S], empty[S], accf, conv[S]
+constexpr int TE_SMEM = TE_BARS + TE_NBARS * 8 + 16 + 1024;
 
 struct TeArgs {
     int n, R, kblocks;
@@ -29,6 +32,7 @@ struct TeArgs {
     long long limit_ns;
 };
 
+template <bool E4>
 __global__ void __launch_bounds__(TE_THREADS, 1)
     k_tc_sigma_j_sigma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapS,
                        TeArgs a) {
@@ -40,8 +44,9 @@ __global__ void __launch_bounds__(TE_THREADS, 1)
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (TE_S + s); };
     const uint32_t accf_bar = bar0 + 8u * (2 * TE_S);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + TE_BARS + (2 * TE_S + 1) * 8);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + TE_BARS + (2 * TE_S + 1) * 8 + 4);
+    auto conv_bar = [&](int s) { return bar0 + 8u * (2 * TE_S + 1 + s); };
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + TE_BARS + TE_NBARS * 8);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + TE_BARS + TE_NBARS * 8 + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * TE_BM, r0 = blockIdx.y * TE_BN;
 
@@ -49,6 +54,7 @@ __global__ void __launch_bounds__(TE_THREADS, 1)
         for (int s = 0; s < TE_S; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
+            mbar_init(conv_bar(s), 4);
         }
         mbar_init(accf_bar, 1);
         *abort_flag = 0;
@@ -75,8 +81,8 @@ __global__ void __launch_bounds__(TE_THREADS, 1)
                 const uint32_t ph = (it / TE_S) & 1u;
                 if (!mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns)) break;
                 const uint32_t d = sbase + s * TE_STAGE;
-                mbar_arrive_expect_tx(full_bar(s), (uint32_t)TE_STAGE);
-                tma_load_2d(d, &mapA, full_bar(s), kb * TE_BK, m0);
+                mbar_arrive_expect_tx(full_bar(s), (uint32_t)(E4 ? TE_BM * TE_BK + TE_B_BYTES : TE_STAGE));
+                tma_load_2d(E4 ? d + (uint32_t)E4M3_TILE_OFFSET : d, &mapA, full_bar(s), kb * TE_BK, m0);
                 tma_load_2d(d + TE_A_BYTES, &mapS, full_bar(s), kb * TE_BK, r0);
             }
             const uint32_t first = it > (uint32_t)TE_S ? it - TE_S : 0u;
@@ -98,6 +104,7 @@ __global__ void __launch_bounds__(TE_THREADS, 1)
                 const int s = kb % TE_S;
                 const uint32_t ph = (kb / TE_S) & 1u;
                 if (!mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                if (E4 && !mbar_wait(conv_bar(s), ph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
                 tc_fence_after();
                 const uint64_t ad = sdesc_sw128(sbase + s * TE_STAGE);
                 const uint64_t bd = ad + (uint64_t)(TE_A_BYTES >> 4);
@@ -121,6 +128,20 @@ __global__ void __launch_bounds__(TE_THREADS, 1)
         const int i = m0 + row;
         int *prod = reinterpret_cast<int *>(smem);   // [TE_BN][TE_BM + 1]
         bool ok = true;
+        if (E4) {
+            // widen the e4m3 J tiles in place, in the order they arrive (thread
+            // (warp - 2) * 32 + lane converts that row of every tile)
+            const int crow = (warp - 2) * 32 + lane;
+            for (int kb = 0; kb < a.kblocks; ++kb) {
+                const int s = kb % TE_S;
+                const uint32_t ph = (kb / TE_S) & 1u;
+                const int okw = mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns) ? 1 : 0;
+                if (!named_barrier_and(2, 128, okw)) break;
+                widen_e4m3_tile(sbase + s * TE_STAGE, crow, 2);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(conv_bar(s));
+            }
+        }
         if (lane == 0) ok = mbar_wait(accf_bar, 0u, a.err, abort_flag, a.limit_ns);
         ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
         if (ok) {
@@ -218,7 +239,8 @@ si_status tc_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E, 
     si_status s = tc_make_map_bf16(&mapS, c->e_sig, c->ldk, rpad, TE_BK, TE_BN);
     if (s != SI_OK) return s;
     CUtensorMap mapA;
-    s = tc_make_map_bf16(&mapA, c->dJ, c->ldk, c->mpad, TE_BK, TE_BM);
+    s = c->j_e4m3 ? tc_make_map_e4m3(&mapA, c->dJ, c->ldk, c->mpad, TE_BM)
+                  : tc_make_map_bf16(&mapA, c->dJ, c->ldk, c->mpad, TE_BK, TE_BM);
     if (s != SI_OK) return s;
     SI_CUDA_TRY(cudaMemsetAsync(c->e_sum, 0, sizeof(unsigned long long) * R, c->stream));
     TeArgs a;
@@ -230,9 +252,16 @@ si_status tc_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E, 
     a.sum = c->e_sum;
     a.err = c->derr;
     a.limit_ns = c->spin_limit_ns;
-    SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_sigma_j_sigma, cudaFuncAttributeMaxDynamicSharedMemorySize, TE_SMEM));
     dim3 grid(c->mpad / TE_BM, rpad / TE_BN);
-    k_tc_sigma_j_sigma<<<grid, TE_THREADS, TE_SMEM, c->stream>>>(mapA, mapS, a);
+    if (c->j_e4m3) {
+        SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_sigma_j_sigma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TE_SMEM));
+        k_tc_sigma_j_sigma<true><<<grid, TE_THREADS, TE_SMEM, c->stream>>>(mapA, mapS, a);
+    } else {
+        SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_sigma_j_sigma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TE_SMEM));
+        k_tc_sigma_j_sigma<false><<<grid, TE_THREADS, TE_SMEM, c->stream>>>(mapA, mapS, a);
+    }
     SI_CUDA_TRY(cudaGetLastError());
     k_energy_finish<<<R, 128, 0, c->stream>>>(c->e_sum, c->has_h ? c->dh8 : nullptr, spins_dev, ld, c->n, R,
                                               c->s_upper, E, C);

@@ -16,6 +16,11 @@
 // Tile width (64 or 128 replicas per tile, per instance) is chosen by an
 // autotuner that times a few steps of each candidate policy on the actual
 // group and caches the winner by group shape.
+//
+// Members of precision SI_PREC_J_FP8_Q_BF16 keep J in HBM as 1-byte e4m3
+// (validated exact); four converter warps widen each of their J tiles to bf16
+// in shared memory before the MMAs read it, so the step streams half the J
+// bytes of a bf16 member.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -30,20 +35,25 @@
 namespace si {
 
 constexpr int GR_BM = 128, GR_BK = 64;
-constexpr int GR_EPI = 12;                       // epilogue warps: 3 per TMEM lane quadrant
-constexpr int GR_THREADS = 32 * (3 + GR_EPI);
+// Warps: producer, 2 MMA issuers, EPI epilogue warps (EPI / 4 per TMEM lane
+// quadrant), then 4 converter warps (e4m3 J tiles).
+template <int EPI>
+constexpr int gr_threads() { return 32 * (3 + EPI + 4); }
+constexpr int GR_EPI_DEFAULT = 12;
 constexpr int GR_A_BYTES = GR_BM * GR_BK * 2;
 constexpr int GR_SMAX = 8;                       // most ring stages of any policy
 constexpr int GR_TILES = 196608;                 // shared memory for the ring
-constexpr int GR_NBARS = 2 * GR_SMAX + 2 + 2 + 1;  // full, empty, accf[2], tmem_empty[2], drain
+constexpr int GR_NBARS = 3 * GR_SMAX + 2 + 2 + 1;  // full, empty, accf[2], tmem_empty[2], drain, conv
 constexpr int GR_SMEM = GR_TILES + GR_NBARS * 8 + 16 + 1024;
 
 struct GroupInst {
     int n, R, ldk, rpad, mtiles, rblocks, kblocks, bn;
+    int e4m3;                  // J stored as e4m3 bytes (else bf16)
+    int lds;                   // row stride of spins
     const float *h;            // [n] or null
     float *q_state, *p_state;  // [R][n]
     __nv_bfloat16 *qop;        // [2][rpad][ldk]
-    int8_t *spins;             // [R][n]
+    int8_t *spins;             // [R][lds]
 };
 
 struct GroupTile {
@@ -68,7 +78,9 @@ struct GroupArgs {
     int stage_bytes;           // A tile + largest B tile of the policy (multiple of 1024)
 };
 
-__global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_constant__ GroupArgs a) {
+template <int GR_EPI>
+__global__ void __launch_bounds__(gr_threads<GR_EPI>(), 1) k_group_step(const __grid_constant__ GroupArgs a) {
+    constexpr int GR_CONV_WARP0 = 3 + GR_EPI;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -79,6 +91,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
     auto accf_bar = [&](int k) { return bar0 + 8u * (2 * GR_SMAX + k); };
     auto tmem_empty_bar = [&](int k) { return bar0 + 8u * (2 * GR_SMAX + 2 + k); };
     const uint32_t drain_bar = bar0 + 8u * (2 * GR_SMAX + 4);
+    auto conv_bar = [&](int s) { return bar0 + 8u * (2 * GR_SMAX + 5 + s); };
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + GR_TILES + GR_NBARS * 8);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + GR_TILES + GR_NBARS * 8 + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -88,6 +101,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
         for (int s = 0; s < GR_SMAX; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
+            mbar_init(conv_bar(s), 4);
         }
         for (int k = 0; k < 2; ++k) {
             mbar_init(accf_bar(k), 2);
@@ -135,7 +149,8 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                 const GroupInst &in = a.inst[tl.inst];
                 const CUtensorMap *mJ = a.maps + 3 * tl.inst;
                 const CUtensorMap *mQ = mJ + (tl.bn == in.bn ? 1 : 2);
-                const uint32_t bytes = (uint32_t)(GR_A_BYTES + tl.bn * GR_BK * 2);
+                const uint32_t bytes = (uint32_t)((in.e4m3 ? GR_BM * GR_BK : GR_A_BYTES) + tl.bn * GR_BK * 2);
+                const uint32_t a_off = in.e4m3 ? (uint32_t)E4M3_TILE_OFFSET : 0u;
                 const int yq = plane_in * in.rpad + tl.r0;
                 for (int j = 0; j < tl.kb_cnt; ++j) {
                     const int kb = a.kbl[tl.kb_off + j];
@@ -152,7 +167,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                     }
                     const uint32_t dA = sbase + s * a.stage_bytes;
                     mbar_arrive_expect_tx(full_bar(s), bytes);
-                    tma_load_2d(dA, mJ, full_bar(s), kb * GR_BK, tl.mt * GR_BM);
+                    tma_load_2d(dA + a_off, mJ, full_bar(s), kb * GR_BK, tl.mt * GR_BM);
                     tma_load_2d(dA + GR_A_BYTES, mQ, full_bar(s), kb * GR_BK, yq);
                 }
             }
@@ -200,7 +215,11 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                         const uint32_t d_tmem = tmem + (uint32_t)slot * 256u;
                         for (int kb = 0; kb < tl.kb_cnt; ++kb) {
                             const int s = ring_stage(rk, 0);
-                            if (!mbar_wait(full_bar(s), rph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                            if (!mbar_wait(full_bar(s), rph, a.err, abort_flag, a.limit_ns) ||
+                                !mbar_wait(conv_bar(s), rph, a.err, abort_flag, a.limit_ns)) {
+                                ok = false;
+                                break;
+                            }
                             if (++rk == ring_len) {
                                 rk = 0;
                                 rph ^= 1u;
@@ -218,7 +237,11 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                     const uint32_t d_tmem = tmem + (uint32_t)slot * 256u + (w == 0 ? 0u : 128u);
                     for (int kb = w; kb < tl.kb_cnt; kb += 2) {
                         const int s = ring_stage(rk, w);
-                        if (!mbar_wait(full_bar(s), rph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                        if (!mbar_wait(full_bar(s), rph, a.err, abort_flag, a.limit_ns) ||
+                            !mbar_wait(conv_bar(s), rph, a.err, abort_flag, a.limit_ns)) {
+                            ok = false;
+                            break;
+                        }
                         if (++rk == ring_len) {
                             rk = 0;
                             rph ^= 1u;
@@ -243,7 +266,7 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                 }
             }
         }
-    } else {
+    } else if (warp < GR_CONV_WARP0) {
         // ---------------------------------------------- epilogue (GR_EPI warps)
         // Warp w reads TMEM lanes 32*(w%4) .. +31 (one spin per thread) and
         // share (w-3)/4 of the tile's 16-column chunks.
@@ -301,13 +324,46 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_group_step(const __grid_const
                         in.q_state[e] = qo;
                         in.p_state[e] = po;
                         if (!a.last) qn[(size_t)r * in.ldk + i] = __float2bfloat16_rn(qo);
-                        else if (in.spins) in.spins[e] = spin_of(qo);
+                        else if (in.spins) in.spins[(size_t)r * in.lds + i] = spin_of(qo);
                     }
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tmem_empty_bar(slot));
+        }
+    } else {
+        // ---------------------------------------------- converters (4 warps)
+        // Walk the stages in the producer's order.  Every use of a stage is
+        // released to the MMA warp through conv_bar, after its e4m3 J tile
+        // (if the member stores J as e4m3) has been widened in place; bf16
+        // tiles pass straight through.  Waiting for the stage's TMA first
+        // keeps conv_bar one phase behind full_bar, so no waiter can see a
+        // phase two ahead.  Every thread waits itself; the four warps agree
+        // on success through one reducing barrier.
+        const int row = (warp - GR_CONV_WARP0) * 32 + lane;
+        int rk0 = 0, rk1 = 0;
+        uint32_t rph0 = 0u, rph1 = 0u;
+        bool ok = true;
+        for (int k = blockIdx.x; k < a.ntiles && ok; k += gridDim.x) {
+            const GroupTile tl = a.tiles[k];
+            const int e4 = a.inst[tl.inst].e4m3;
+            for (int j = 0; j < tl.kb_cnt; ++j) {
+                const int ring = a.single ? 0 : (j & 1);
+                int &rk = ring ? rk1 : rk0;
+                uint32_t &rph = ring ? rph1 : rph0;
+                const int s = ring_stage(rk, ring);
+                const uint32_t ph = rph;
+                const int okw = mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns) ? 1 : 0;
+                if (!named_barrier_and(2, 128, okw)) { ok = false; break; }
+                if (++rk == ring_len) {
+                    rk = 0;
+                    rph ^= 1u;
+                }
+                if (e4) widen_e4m3_tile(sbase + s * a.stage_bytes, row, 2);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(conv_bar(s));
+            }
         }
     }
 
@@ -333,19 +389,26 @@ __global__ void k_group_init(const GroupInst *inst) {
 // ============================================================ host side
 struct GroupMember {
     int n, R;
-    void *J = nullptr;          // bf16 [mpad][ldk]
+    bool e4m3 = false;          // J stored as e4m3 bytes (SI_PREC_J_FP8_Q_BF16), else bf16
+    void *J = nullptr;          // [mpad][ldk], e4m3 or bf16
     int ldk = 0, mpad = 0;
     float *h = nullptr;
     float *q = nullptr, *p = nullptr;
     __nv_bfloat16 *qop = nullptr;
     int rpad_max = 0;
     int8_t *spins = nullptr;
+    int lds = 0;                // row stride of spins (n, or the serving context's padded stride)
+    bool own_spins = true;
     Ctx energy;                 // readout view (int8 J, h copies)
     std::vector<int> kb_off, kb_cnt;   // per M tile: its non-zero K blocks in Group::kbl
 };
 
 struct Group {
     int count = 0, steps = 0;
+    // Set when the group serves one si_create context whose persistent grid
+    // would not be co-resident: the member then writes the context's spin
+    // buffer and error word, and the context does the readouts.
+    Ctx *host = nullptr;
     si_params common;
     cudaStream_t stream = nullptr;
     int device = 0, sms = 0;
@@ -363,6 +426,7 @@ struct Group {
     int *d_err = nullptr;
     int *h_err = nullptr;   // pinned host copy of the error word
     int policy = -1;            // chosen tile policy
+    int epi = 12;               // epilogue warps of the step kernel (8 or 12)
     int grid = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_steps = -1;
@@ -456,16 +520,18 @@ static std::string group_key(const Group *g) {
     return k;
 }
 
-// Which 128 x 64 blocks of the bf16 J hold a non-zero coupling: one CTA per
-// block, mask[mt * kblocks + kb].
-__global__ void k_block_nonzero(const __nv_bfloat16 *J, int ldk, int kblocks, unsigned char *mask) {
+// Which 128 x 64 blocks of J (bf16 when E is unsigned short, e4m3 when it is
+// unsigned char) hold a non-zero coupling: one CTA per block,
+// mask[mt * kblocks + kb].
+template <typename E>
+__global__ void k_block_nonzero(const E *J, int ldk, int kblocks, unsigned char *mask) {
     const int mt = blockIdx.y, kb = blockIdx.x;
-    const unsigned short *Jb = reinterpret_cast<const unsigned short *>(J);
+    const unsigned absmask = sizeof(E) == 1 ? 0x7Fu : 0x7FFFu;   // +0 and -0 count as zero
     int nz = 0;
     for (int e = threadIdx.x; e < GR_BM * GR_BK; e += blockDim.x) {
         const int r = e / GR_BK, cidx = e % GR_BK;
-        const unsigned short v = Jb[(size_t)(mt * GR_BM + r) * ldk + kb * GR_BK + cidx];
-        nz |= (v & 0x7FFFu) != 0u;   // +0 and -0 count as zero
+        const unsigned v = J[(size_t)(mt * GR_BM + r) * ldk + kb * GR_BK + cidx];
+        nz |= (v & absmask) != 0u;
     }
     nz = __syncthreads_or(nz);
     if (threadIdx.x == 0) mask[(size_t)mt * kblocks + kb] = nz ? 1 : 0;
@@ -477,7 +543,12 @@ static si_status member_block_lists(Group *g, GroupMember &x) {
     const int mtiles = x.mpad / GR_BM, kblocks = x.ldk / GR_BK;
     unsigned char *d_mask = nullptr;
     SI_CUDA_TRY(si_dev_malloc((void **)&d_mask, (size_t)mtiles * kblocks));
-    k_block_nonzero<<<dim3(kblocks, mtiles), 256, 0, g->stream>>>((const __nv_bfloat16 *)x.J, x.ldk, kblocks, d_mask);
+    if (x.e4m3)
+        k_block_nonzero<unsigned char><<<dim3(kblocks, mtiles), 256, 0, g->stream>>>(
+            (const unsigned char *)x.J, x.ldk, kblocks, d_mask);
+    else
+        k_block_nonzero<unsigned short><<<dim3(kblocks, mtiles), 256, 0, g->stream>>>(
+            (const unsigned short *)x.J, x.ldk, kblocks, d_mask);
     cudaError_t e = cudaGetLastError();
     std::vector<unsigned char> mask((size_t)mtiles * kblocks);
     if (e == cudaSuccess)
@@ -579,13 +650,16 @@ static si_status group_build_policies(Group *g) {
             d.mtiles = x.mpad / GR_BM;
             d.rblocks = cdiv(x.R, d.bn);
             d.kblocks = x.ldk / GR_BK;
+            d.e4m3 = x.e4m3 ? 1 : 0;
             d.h = x.h;
             d.q_state = x.q;
             d.p_state = x.p;
             d.qop = x.qop;
             d.spins = x.spins;
+            d.lds = x.lds;
             CUtensorMap *mp = &maps[((size_t)pol * c + i) * 3];
-            si_status s = tc_make_map_bf16(mp, x.J, x.ldk, x.mpad, GR_BK, GR_BM);
+            si_status s = x.e4m3 ? tc_make_map_e4m3(mp, x.J, x.ldk, x.mpad, GR_BM)
+                                 : tc_make_map_bf16(mp, x.J, x.ldk, x.mpad, GR_BK, GR_BM);
             if (s != SI_OK) return s;
             s = tc_make_map_bf16(mp + 1, x.qop, x.ldk, 2 * x.rpad_max, GR_BK, d.bn);
             if (s != SI_OK) return s;
@@ -651,7 +725,8 @@ static si_status group_launch_step(Group *g, int t, int steps) {
     a.single = g->policy == kPolicyWhole ? 1 : 0;
     a.stages = g->pol_stages[g->policy];
     a.stage_bytes = g->pol_stage_bytes[g->policy];
-    k_group_step<<<g->grid, GR_THREADS, GR_SMEM, g->stream>>>(a);
+    if (g->epi == 8) k_group_step<8><<<g->grid, gr_threads<8>(), GR_SMEM, g->stream>>>(a);
+    else k_group_step<12><<<g->grid, gr_threads<12>(), GR_SMEM, g->stream>>>(a);
     SI_CUDA_TRY(cudaGetLastError());
     return SI_OK;
 }
@@ -762,12 +837,12 @@ static si_status group_autotune(Group *g) {
 static void free_group(Group *g) {
     if (!g) return;
     for (auto &x : g->m) {
-        void *ptrs[] = {x.J, x.h, x.q, x.p, x.qop, x.spins, x.energy.dJ8, x.energy.dh8, x.energy.dspins_in,
-                        x.energy.e_sig, x.energy.e_sum};
+        void *ptrs[] = {x.J, x.h, x.q, x.p, x.qop, x.own_spins ? x.spins : nullptr, x.energy.dJ8, x.energy.dh8,
+                        x.energy.dspins_in, x.energy.e_sig, x.energy.e_sum};
         for (void *p : ptrs)
             if (p) cudaFree(p);
     }
-    void *ptrs[] = {g->d_inst, g->d_tiles, g->d_maps, g->d_kbl, g->d_zeta, g->d_dt, g->d_err};
+    void *ptrs[] = {g->d_inst, g->d_tiles, g->d_maps, g->d_kbl, g->d_zeta, g->d_dt, g->host ? nullptr : g->d_err};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (g->h_err) cudaFreeHost(g->h_err);
@@ -829,15 +904,24 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
             set_error("group member " + std::to_string(i) + ": SI_PREC_J_FP8_Q_BF16 needs J exact in e4m3");
             return SI_ERR_INVALID_ARG;
         }
-        SI_CUDA_TRY(si_dev_malloc(&x.J, (size_t)x.mpad * x.ldk * 2));
-        s = tc_convert_j(Jp, n, x.J, x.ldk, x.mpad, g->sms, g->stream);
+        x.e4m3 = prm[i].prec == SI_PREC_J_FP8_Q_BF16;
+        SI_CUDA_TRY(si_dev_malloc(&x.J, (size_t)x.mpad * x.ldk * (x.e4m3 ? 1 : 2)));
+        s = x.e4m3 ? tc_convert_j_e4m3(Jp, n, x.J, x.ldk, x.mpad, g->sms, g->stream)
+                   : tc_convert_j(Jp, n, x.J, x.ldk, x.mpad, g->sms, g->stream);
         if (s != SI_OK) return s;
         // block sparsity: all-zero 128 x 64 blocks of J are never loaded
         s = member_block_lists(g, x);
         if (s != SI_OK) return s;
         SI_CUDA_TRY(si_dev_malloc((void **)&x.q, sizeof(float) * (size_t)x.R * n));
         SI_CUDA_TRY(si_dev_malloc((void **)&x.p, sizeof(float) * (size_t)x.R * n));
-        SI_CUDA_TRY(si_dev_malloc((void **)&x.spins, (size_t)x.R * n));
+        if (g->host) {
+            x.spins = g->host->dspins;
+            x.lds = g->host->ld8;
+            x.own_spins = false;
+        } else {
+            SI_CUDA_TRY(si_dev_malloc((void **)&x.spins, (size_t)x.R * n));
+            x.lds = n;
+        }
         const size_t qb = 2ull * x.rpad_max * x.ldk * 2;
         SI_CUDA_TRY(si_dev_malloc((void **)&x.qop, qb));
         SI_CUDA_TRY(cudaMemsetAsync(x.qop, 0, qb, g->stream));
@@ -856,18 +940,19 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
         c.s_upper = c.integer_j ? s_upper : 0;
         c.ld8 = round_up(n, 16);
         c.dJ = x.J;
+        c.j_e4m3 = x.e4m3;
         c.ldk = x.ldk;
         c.mpad = x.mpad;
         SI_CUDA_TRY(si_dev_malloc((void **)&x.h, sizeof(float) * n));
         if (hp) SI_CUDA_TRY(cudaMemcpyAsync(x.h, hp, sizeof(float) * n, cudaMemcpyDeviceToDevice, g->stream));
         else SI_CUDA_TRY(cudaMemsetAsync(x.h, 0, sizeof(float) * n, g->stream));
         c.dhf = x.h;
-        if (c.integer_j) {
+        if (c.integer_j && !g->host) {
             SI_CUDA_TRY(si_dev_malloc((void **)&c.dJ8, (size_t)n * c.ld8));
             s = convert_j8(&c, Jp);
             if (s != SI_OK) return s;
         }
-        if (c.has_h && c.integer_h) {
+        if (c.has_h && c.integer_h && !g->host) {
             SI_CUDA_TRY(si_dev_malloc((void **)&c.dh8, n));
             s = h_to_int8(hp, n, c.dh8, g->stream);
             if (s != SI_OK) return s;
@@ -883,8 +968,12 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
     if (sb != SI_OK) return sb;
     SI_CUDA_TRY(si_dev_malloc((void **)&g->d_zeta, sizeof(float) * std::max(1, g->steps)));
     SI_CUDA_TRY(si_dev_malloc((void **)&g->d_dt, sizeof(float) * std::max(1, g->steps)));
-    SI_CUDA_TRY(si_dev_malloc((void **)&g->d_err, sizeof(int)));
-    SI_CUDA_TRY(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream));
+    if (g->host) {
+        g->d_err = g->host->derr;
+    } else {
+        SI_CUDA_TRY(si_dev_malloc((void **)&g->d_err, sizeof(int)));
+        SI_CUDA_TRY(cudaMemsetAsync(g->d_err, 0, sizeof(int), g->stream));
+    }
     if (cudaHostAlloc((void **)&g->h_err, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();   // optional: the read then goes through pageable memory
         g->h_err = nullptr;
@@ -893,15 +982,126 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
         x.energy.derr = g->d_err;
         x.energy.spin_limit_ns = g->limit_ns;
     }
-    SI_CUDA_TRY(cudaFuncSetAttribute(k_group_step, cudaFuncAttributeMaxDynamicSharedMemorySize, GR_SMEM));
+    g->epi = GR_EPI_DEFAULT;
+    if (const char *e = std::getenv("SI_GROUP_EPI")) g->epi = std::atoi(e) == 8 ? 8 : 12;
+    SI_CUDA_TRY(cudaFuncSetAttribute(k_group_step<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, GR_SMEM));
+    SI_CUDA_TRY(cudaFuncSetAttribute(k_group_step<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, GR_SMEM));
     int per_sm = 0;
-    SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_step, GR_THREADS, GR_SMEM));
+    if (g->epi == 8)
+        SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_step<8>, gr_threads<8>(), GR_SMEM));
+    else
+        SI_CUDA_TRY(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_step<12>, gr_threads<12>(), GR_SMEM));
     if (per_sm < 1) {
         set_error("grouped step kernel does not fit on an SM");
         return SI_ERR_UNSUPPORTED;
     }
     g->grid = per_sm * g->sms;
     return group_apply_policy(g, 0);
+}
+
+// ------------------------------------------------ serving one si_create context
+// A tensor-precision context whose persistent grid would not be co-resident
+// (many M tiles x replica blocks, e.g. n = 32768) runs on this grouped step
+// kernel as a one-member group: one launch per time step from a CUDA graph.
+// The member's J copy and FP32 state are the context's (c->dJ, c->dq, c->dp
+// point at them), its last step writes the context's padded spin buffer, and
+// its waits raise the context's error word, so every other call of the
+// context (readouts, state copies, continuation) works unchanged.
+si_status group_ctx_create(Ctx *c, const float *J_dev, const float *h_dev) {
+    Group *g = new (std::nothrow) Group();
+    if (!g) return SI_ERR_OOM;
+    c->grp = g;   // released by group_ctx_free, also after a failure below
+    g->count = 1;
+    g->steps = c->prm.steps;
+    g->common = c->prm;
+    g->stream = c->stream;
+    g->host = c;
+    const float *Js[1] = {J_dev};
+    const float *hs[1] = {h_dev};
+    si_status s = group_create_impl(g, &c->prm, Js, h_dev ? hs : nullptr);
+    if (s != SI_OK) return s;
+    GroupMember &x = g->m[0];
+    c->dJ = x.J;
+    c->j_e4m3 = x.e4m3;
+    c->ldk = x.ldk;
+    c->mpad = x.mpad;
+    c->dq = x.q;
+    c->dp = x.p;
+    c->rpad = x.rpad_max;
+    // Choose the tile policy now, on zeroed scratch state (timing does not
+    // depend on the values; the first si_run loads its own state).
+    const size_t bytes = sizeof(float) * (size_t)x.R * x.n;
+    SI_CUDA_TRY(cudaMemsetAsync(x.q, 0, bytes, g->stream));
+    SI_CUDA_TRY(cudaMemsetAsync(x.p, 0, bytes, g->stream));
+    SI_CUDA_TRY(cudaMemsetAsync(g->d_zeta, 0, sizeof(float) * std::max(1, g->steps), g->stream));
+    SI_CUDA_TRY(cudaMemsetAsync(g->d_dt, 0, sizeof(float) * std::max(1, g->steps), g->stream));
+    int cached = forced_policy();
+    if (cached < 0) tune_cache_find(group_key(g), &cached);
+    if (cached >= 0) return group_apply_policy(g, cached);
+    if (g->steps == 0) return group_apply_policy(g, 0);
+    return group_autotune(g);
+}
+
+// Start a run: the FP32 state is already in c->dq / c->dp (loaded by the
+// caller, or left by the last run); copy the schedule and build the bf16
+// operand plane of step 0 from the positions.
+si_status group_ctx_prepare(Ctx *c, int steps) {
+    Group *g = c->grp;
+    if (steps > 0) {
+        SI_CUDA_TRY(cudaMemcpyAsync(g->d_zeta, c->dzeta, sizeof(float) * steps, cudaMemcpyDeviceToDevice, g->stream));
+        SI_CUDA_TRY(cudaMemcpyAsync(g->d_dt, c->ddt, sizeof(float) * steps, cudaMemcpyDeviceToDevice, g->stream));
+    }
+    const GroupMember &x = g->m[0];
+    dim3 grid(std::min(8 * g->sms, std::max(1, cdiv((long long)x.R * x.n, 256))), 1);
+    k_group_init<<<grid, 256, 0, g->stream>>>(g->d_inst + (size_t)g->policy * g->count);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    return SI_OK;
+}
+
+// The `steps` time steps (one graph launch; asynchronous).
+si_status group_ctx_run(Ctx *c, int steps) {
+    Group *g = c->grp;
+    if (steps == 0) return SI_OK;
+    si_status s = group_graph(g, steps);
+    if (s != SI_OK) return s;
+    SI_CUDA_TRY(cudaGraphLaunch(g->graph, g->stream));
+    c->launches += steps;
+    return SI_OK;
+}
+
+// After si_set_params: the captured steps hold the old integrator values.
+void group_ctx_params(Ctx *c) {
+    Group *g = c->grp;
+    g->common = c->prm;
+    if (g->graph) {
+        cudaStreamSynchronize(g->stream);
+        cudaGraphExecDestroy(g->graph);
+        g->graph = nullptr;
+        g->graph_steps = -1;
+    }
+}
+
+void group_ctx_describe(const Ctx *c, char *buf, int len) {
+    const Group *g = c->grp;
+    const GroupMember &x = g->m[0];
+    std::snprintf(buf, len,
+                  "tcgen05 grouped-step prec=%s J=%s n=%d R=%d tiles=%d grid=%d policy=%s (one launch per step, "
+                  "CUDA graph)",
+                  c->prm.prec == SI_PREC_J_FP8_Q_BF16 ? "j_fp8_q_bf16" : "j_bf16_q_bf16",
+                  x.e4m3 ? "e4m3(1B)" : "bf16(2B)", c->n, c->R, g->ntiles, g->grid,
+                  g->policy >= 0 ? kPolicyName[g->policy] : "none");
+}
+
+void group_ctx_free(Ctx *c) {
+    if (!c->grp) return;
+    // the member owns J and the state that the context's pointers alias
+    c->dJ = nullptr;
+    c->dq = nullptr;
+    c->dp = nullptr;
+    free_group(c->grp);
+    c->grp = nullptr;
 }
 
 }  // namespace si
@@ -1079,7 +1279,7 @@ si_status si_group_describe(const si_group *grp, char *buf, int32_t len) {
         macs += (long long)x.n * x.n * x.R;
         long long nb = 0;
         for (int v : x.kb_cnt) nb += v;
-        jbytes += nb * GR_BM * GR_BK * 2 * cdiv(x.R, bn);
+        jbytes += nb * GR_BM * GR_BK * (x.e4m3 ? 1 : 2) * cdiv(x.R, bn);
     }
     std::snprintf(buf, len, "grouped tcgen05 count=%d tiles=%d grid=%d policy=%s graph-steps=%d macs/step=%lld jbytes/step=%lld",
                   g->count, g->ntiles, g->grid, g->policy >= 0 ? kPolicyName[g->policy] : "none", g->graph_steps,

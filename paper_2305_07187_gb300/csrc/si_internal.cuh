@@ -56,6 +56,7 @@ struct StepParams {
 
 enum class Path { PLAIN_PERSISTENT, SIMT_TILED, TENSOR };
 struct AdjTc;
+struct Group;
 
 struct Ctx {
     si_params prm;
@@ -76,7 +77,7 @@ struct Ctx {
     int stall_step = -1;
 
     // Storage of J.  FP32/FP64 paths: [n][ldj] in the state precision.
-    // Tensor path: bf16 [mpad][ldk], zero padded.
+    // Tensor path: [mpad][ldk], zero padded, bf16 or (j_e4m3) e4m3 bytes.
     int ldj = 0;                 // row stride (elements) of the SIMT J copy
     int ldk = 0, mpad = 0;       // tensor path padding
     void *dJ = nullptr;          // J in working precision
@@ -119,10 +120,15 @@ struct Ctx {
 
     // Tensor path configuration.
     int tile_n = 0;                      // replicas per CTA
+    bool j_e4m3 = false;                 // dJ holds e4m3 bytes [mpad][ldk] (else bf16)
     int tc_per_sm = 0;                   // co-resident CTAs per SM of the step kernel (0: not yet queried)
     int stages = 0;
     int rpad = 0;                        // R rounded up to tile_n
     CUtensorMap mapA, mapB;              // J tiles, q operand tiles
+    // Tensor contexts whose persistent grid would not be co-resident run on
+    // the grouped per-step kernel as a one-member group that owns J and the
+    // state (dJ, dq, dp alias its buffers).
+    Group *grp = nullptr;
 
     // Tensor-core energy readout workspace (allocated lazily).
     void *e_sig = nullptr;               // bf16 spin operand
@@ -183,6 +189,9 @@ si_status simt_copy_state(Ctx *c, float *q_out, float *p_out);
 si_status simt_copy_state_f64(Ctx *c, double *q_out, double *p_out);
 
 // Tensor-core path, si_tc.cu.
+// True when the persistent all-steps kernel can serve the context (its grid
+// of M tiles x replica blocks is co-resident and within the step flags).
+bool tc_persistent_fits(Ctx *c);
 si_status tc_prepare(Ctx *c, const float *J_dev);
 si_status tc_run(Ctx *c, int steps, int8_t *spins_dev);
 si_status tc_copy_state(Ctx *c, float *q_out, float *p_out);
@@ -200,12 +209,24 @@ __global__ void k_energy_finish(const unsigned long long *sum, const int8_t *h8,
                                 int R, long long s_upper, int32_t *E, int32_t *C);
 si_status tc_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E, int32_t *C);
 const char *tc_describe(const Ctx *c, char *buf, int len);
+// 2D tensor map of e4m3 (1-byte) tiles of 64 x box_outer with the 64-byte swizzle.
+si_status tc_make_map_e4m3(CUtensorMap *m, void *base, int inner, int outer, int box_outer);
+// J (fp32 n x n, e4m3-exact) -> e4m3 [mpad][ldk], zero padded.
+si_status tc_convert_j_e4m3(const float *J_dev, int n, void *out, int ldk, int mpad, int sms, cudaStream_t st);
 // 2D bf16 tensor map with the 128-byte swizzle (inner dimension contiguous).
 si_status tc_make_map_bf16(CUtensorMap *m, void *base, int inner, int outer, int box_inner,
                            int box_outer);
 // J (fp32 n x n) -> bf16 [mpad][ldk], zero padded.
 si_status tc_convert_j(const float *J_dev, int n, void *out, int ldk, int mpad, int sms,
                        cudaStream_t st);
+
+// One-member grouped service of a tensor context, si_group.cu.
+si_status group_ctx_create(Ctx *c, const float *J_dev, const float *h_dev);
+si_status group_ctx_prepare(Ctx *c, int steps);
+si_status group_ctx_run(Ctx *c, int steps);
+void group_ctx_params(Ctx *c);
+void group_ctx_describe(const Ctx *c, char *buf, int len);
+void group_ctx_free(Ctx *c);
 
 // Adjoint, si_adjoint.cu.
 // Tensor-core products of the adjoint sweep, si_adjoint_tc.cu.

@@ -8,7 +8,7 @@
 // monitor reports how far it moves over a stretch of constant zeta.
 //
 // One CTA per HM_R replicas; warps over rows of J, lanes over columns.  J is
-// the context's working copy (FP32, FP64 or bf16), so H is the energy of the
+// the context's working copy (FP32, FP64, bf16 or e4m3), so H is the energy of the
 // system the kernels actually integrate.  All sums are FP64 and reduced in a
 // fixed order, so the result is deterministic.
 #include <cuda_bf16.h>
@@ -24,6 +24,8 @@ template <typename TJ>
 __device__ __forceinline__ double to_f64(TJ x) { return (double)x; }
 template <>
 __device__ __forceinline__ double to_f64<__nv_bfloat16>(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
+template <>
+__device__ __forceinline__ double to_f64<__nv_fp8_e4m3>(__nv_fp8_e4m3 x) { return (double)(float)x; }
 
 template <typename TJ>
 __global__ void __launch_bounds__(HM_THREADS) k_hamiltonian(const TJ *J, int ldj, const float *h, int n, int R,
@@ -101,7 +103,10 @@ si_status monitor_hamiltonian(Ctx *c, const float *q, const float *p, int R, dou
     const int grid = cdiv(R, HM_R);
     const float *h = c->has_h ? c->dhf : nullptr;
     const double k = c->prm.k, m = c->prm.m, q0 = c->prm.q0;
-    if (c->path == Path::TENSOR) {
+    if (c->path == Path::TENSOR && c->j_e4m3) {
+        k_hamiltonian<__nv_fp8_e4m3><<<grid, HM_THREADS, 0, c->stream>>>(
+            (const __nv_fp8_e4m3 *)c->dJ, c->ldk, h, c->n, R, q, p, zeta, k, m, q0, H);
+    } else if (c->path == Path::TENSOR) {
         k_hamiltonian<__nv_bfloat16><<<grid, HM_THREADS, 0, c->stream>>>(
             (const __nv_bfloat16 *)c->dJ, c->ldk, h, c->n, R, q, p, zeta, k, m, q0, H);
     } else if (c->prm.prec == SI_PREC_FP64) {

@@ -729,6 +729,18 @@ si_status convert_j8(Ctx *c, const float *J_dev) {
     return SI_OK;
 }
 
+// int8 copy of an integer J from a tensor context's working copy (e4m3 or
+// bf16 [.][ldk]; integer values |J| <= 127 are exact in both).
+template <typename TJ>
+__global__ void k_convert_j8_from_tc(const TJ *J, int ldk, int n, int8_t *out, int ld8) {
+    const long long total = (long long)n * ld8;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ld8), j = (int)(e % ld8);
+        out[e] = j < n ? (int8_t)(int)(float)J[(size_t)i * ldk + j] : (int8_t)0;
+    }
+}
+
 __global__ void k_h_to_int8(const float *h, int n, int8_t *out) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = (int8_t)h[i];
 }
@@ -949,6 +961,19 @@ si_status simt_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E
             set_error("exact energy: n too large for the shared-memory spin tile");
             return SI_ERR_UNSUPPORTED;
         }
+        if (!c->dJ8 && c->path == Path::TENSOR) {
+            // tensor contexts read out on the tensor cores; their int8 copy of
+            // J for dp4a is built on first use, from the working copy
+            SI_CUDA_TRY(si_dev_malloc((void **)&c->dJ8, (size_t)c->n * c->ld8));
+            const int g = grid_for((long long)c->n * c->ld8, 256, c->num_sms);
+            if (c->j_e4m3)
+                k_convert_j8_from_tc<__nv_fp8_e4m3><<<g, 256, 0, c->stream>>>((const __nv_fp8_e4m3 *)c->dJ, c->ldk,
+                                                                              c->n, c->dJ8, c->ld8);
+            else
+                k_convert_j8_from_tc<__nv_bfloat16><<<g, 256, 0, c->stream>>>((const __nv_bfloat16 *)c->dJ, c->ldk,
+                                                                              c->n, c->dJ8, c->ld8);
+            SI_CUDA_TRY(cudaGetLastError());
+        }
         SI_CUDA_TRY(cudaFuncSetAttribute(k_energy_i8, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         // Few replica blocks (small R) leave most SMs idle while one CTA
         // streams all of J: split the rows too, at least 32 per CTA.
@@ -984,7 +1009,10 @@ si_status simt_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E
         c->launches += 1;
     } else if (Ef) {
         const float *hf = c->dhf;
-        if (c->path == Path::TENSOR) {
+        if (c->path == Path::TENSOR && c->j_e4m3) {
+            k_energy_f<__nv_fp8_e4m3><<<R, EN_THREADS, 0, c->stream>>>(
+                (const __nv_fp8_e4m3 *)c->dJ, c->ldk, hf, c->n, R, spins_dev, ld, Ef);
+        } else if (c->path == Path::TENSOR) {
             k_energy_f<__nv_bfloat16><<<R, EN_THREADS, 0, c->stream>>>(
                 (const __nv_bfloat16 *)c->dJ, c->ldk, hf, c->n, R, spins_dev, ld, Ef);
         } else if (c->prm.prec == SI_PREC_FP64) {

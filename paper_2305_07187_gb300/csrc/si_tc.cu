@@ -30,9 +30,10 @@ namespace si {
 
 constexpr int TC_BM = 128;       // spins per CTA (MMA M)
 constexpr int TC_BK = 64;        // K elements per stage (128 bytes of bf16)
-// Threads: producer warp, 2 MMA-issuing warps, EPI epilogue warps (4 or 8).
-template <int EPI>
-constexpr int tc_threads() { return 32 * (3 + EPI); }
+// Threads: producer warp, 2 MMA-issuing warps, EPI epilogue warps (4 or 8),
+// and with e4m3 J storage four converter warps.
+template <int EPI, bool E4>
+constexpr int tc_threads() { return 32 * (3 + EPI + (E4 ? 4 : 0)); }
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;
 
 struct TcArgs {
@@ -55,17 +56,21 @@ struct TcArgs {
 // ------------------------------------------------------------------ kernel
 // Shared memory: S ring stages (J tile + q tile), the staging tile of the
 // next q (bf16, two 64-spin halves in the 128-byte swizzled layout that the
-// TMA store and the MMA both read), then the mbarriers.
-template <int BN, int S>
+// TMA store and the MMA both read), then the mbarriers.  With e4m3 J storage
+// the J tile arrives as 8 KB of e4m3 in the upper half of the stage's 16 KB
+// A region and is widened there to bf16 before the MMAs read it.
+template <int BN, int S, bool E4>
 struct TcSmem {
     static constexpr int B_BYTES = BN * TC_BK * 2;
     static constexpr int STAGE_BYTES = TC_A_BYTES + B_BYTES;
+    // bytes TMA delivers per stage (the J tile in its storage type + q tile)
+    static constexpr int TX_BYTES = (E4 ? TC_BM * TC_BK : TC_A_BYTES) + B_BYTES;
     static constexpr int TILES = S * STAGE_BYTES;
     static constexpr int HALF_BYTES = BN * 128;           // BN replicas x 64 spins bf16
     static constexpr int STAGING = TILES;                 // 1024-aligned
     static constexpr int BARS = STAGING + 2 * HALF_BYTES;
-    // full[S], empty[S], accf, tmem_empty, epi_done, drain
-    static constexpr int NBARS = 2 * S + 4;
+    // full[S], empty[S], accf, tmem_empty, epi_done, drain, conv[S]
+    static constexpr int NBARS = 3 * S + 4;
     static constexpr int TOTAL = BARS + NBARS * 8 + 16;   // + tmem slot, abort flag
     static constexpr int TMEM_COLS = (4 * BN <= 256) ? 256 : 512;
 };
@@ -75,11 +80,11 @@ constexpr int TC_EPI_WARP0 = 1 + TC_MMA_WARPS;             // first epilogue war
 
 // EPI: epilogue warps (8 in both tile instantiations; a CTA that allocates
 // tensor memory occupies its SM alone, so a lighter CTA buys no second CTA).
-template <int BN, int S, int EPI>
-__global__ void __launch_bounds__(tc_threads<EPI>(), EPI == 4 ? 2 : 1)
+template <int BN, int S, int EPI, bool E4>
+__global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
     k_tc_run(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
              TcArgs a) {
-    using L = TcSmem<BN, S>;
+    using L = TcSmem<BN, S, E4>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -99,6 +104,7 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), EPI == 4 ? 2 : 1)
     const uint32_t tmem_empty_bar = bar0 + 8u * (2 * S + 1);
     const uint32_t epi_done_bar = bar0 + 8u * (2 * S + 2);
     const uint32_t drain_bar = bar0 + 8u * (2 * S + 3);
+    auto conv_bar = [&](int s) { return bar0 + 8u * (2 * S + 4 + s); };
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::BARS + L::NBARS * 8);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::BARS + L::NBARS * 8 + 4);
 
@@ -112,6 +118,7 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), EPI == 4 ? 2 : 1)
         for (int s = 0; s < S; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
+            mbar_init(conv_bar(s), 4);
         }
         mbar_init(accf_bar, TC_MMA_WARPS);
         mbar_init(tmem_empty_bar, EPI);
@@ -171,8 +178,8 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), EPI == 4 ? 2 : 1)
                 if (lane == 0) {
                     okw = mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns) ? 1 : 0;
                     if (okw) {
-                        mbar_arrive_expect_tx(full_bar(s), (uint32_t)L::STAGE_BYTES);
-                        tma_load_2d(dA, &mapA, full_bar(s), kb * TC_BK, m0);
+                        mbar_arrive_expect_tx(full_bar(s), (uint32_t)L::TX_BYTES);
+                        tma_load_2d(E4 ? dA + (uint32_t)E4M3_TILE_OFFSET : dA, &mapA, full_bar(s), kb * TC_BK, m0);
                     }
                 }
                 okw = __shfl_sync(0xffffffffu, okw, 0);
@@ -251,6 +258,7 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), EPI == 4 ? 2 : 1)
                     const int s = 2 * (int)(c % HS) + w;
                     const uint32_t ph = (c / HS) & 1u;
                     if (!mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                    if (E4 && !mbar_wait(conv_bar(s), ph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
                     tc_fence_after();
                     const uint64_t ad = sdesc_sw128(sbase + s * L::STAGE_BYTES);
                     const uint64_t bd = ad + (uint64_t)(TC_A_BYTES >> 4);
@@ -271,7 +279,7 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), EPI == 4 ? 2 : 1)
                 }
             }
         }
-    } else {
+    } else if (warp < TC_EPI_WARP0 + EPI) {
         // ------------------------------------------------ epilogue (8 warps)
         // Warp w reads TMEM lanes 32*(w%4) .. +31 (one spin per thread) and
         // half (w-3)/4 of the replica columns.
@@ -392,6 +400,31 @@ __global__ void __launch_bounds__(tc_threads<EPI>(), EPI == 4 ? 2 : 1)
                 }
             }
         }
+    } else if (E4) {
+        // ------------------------------------------------ e4m3 converters (4 warps)
+        // Widen every J tile in place, stage by stage in the order the
+        // producer fills them (the same two rings), then release the stage to
+        // its MMA warp.  Every converter thread waits for the stage itself;
+        // the four warps agree on success through one reducing barrier so
+        // that none of them can be left alone at the widening barrier.
+        const int row = (warp - (TC_EPI_WARP0 + EPI)) * 32 + lane;
+        constexpr int HS = S / 2;
+        uint32_t cnt0 = 0u, cnt1 = 0u;
+        bool ok = true;
+        for (int t = 0; t < a.steps && ok; ++t) {
+            for (int j = 0; j < a.kblocks; ++j) {
+                const int ring = j & 1;
+                const uint32_t c = ring ? cnt1 : cnt0;
+                const int s = 2 * (int)(c % HS) + ring;
+                const uint32_t ph = (c / HS) & 1u;
+                const int okw = mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns) ? 1 : 0;
+                if (!named_barrier_and(2, 128, okw)) { ok = false; break; }
+                if (ring) ++cnt1; else ++cnt0;
+                widen_e4m3_tile(sbase + s * L::STAGE_BYTES, row, 2);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(conv_bar(s));
+            }
+        }
     }
 
     tc_fence_before();
@@ -443,6 +476,50 @@ si_status tc_make_map_bf16(CUtensorMap *m, void *base, int inner, int outer, int
         set_error(msg);
         return SI_ERR_CUDA;
     }
+    return SI_OK;
+}
+
+// 2D tensor map of the e4m3 J copy (1-byte elements, [outer][inner]) with
+// the 64-byte swizzle: boxes of 64 K elements (64 bytes) x box_outer rows.
+si_status tc_make_map_e4m3(CUtensorMap *m, void *base, int inner, int outer, int box_outer) {
+    PFN_encodeTiled enc = get_encode();
+    if (!enc) {
+        set_error("cuTensorMapEncodeTiled unavailable");
+        return SI_ERR_CUDA;
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)inner};
+    cuuint32_t box[2] = {64u, (cuuint32_t)box_outer};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        char msg[96];
+        std::snprintf(msg, sizeof msg, "cuTensorMapEncodeTiled (e4m3) failed (%d)", (int)r);
+        set_error(msg);
+        return SI_ERR_CUDA;
+    }
+    return SI_OK;
+}
+
+// J (fp32 n x n, every entry exact in e4m3) -> e4m3 [mpad][ldk], zero padded.
+// Saturating round-to-nearest conversion; the values were validated exact, so
+// nothing rounds.
+__global__ void k_convert_j_e4m3(const float *J, int n, __nv_fp8_storage_t *out, int ldk, int mpad) {
+    const long long total = (long long)mpad * ldk;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ldk), j = (int)(e % ldk);
+        const float v = (i < n && j < n) ? J[(size_t)i * n + j] : 0.f;
+        out[e] = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+si_status tc_convert_j_e4m3(const float *J_dev, int n, void *out, int ldk, int mpad, int sms, cudaStream_t st) {
+    k_convert_j_e4m3<<<std::min(8 * sms, cdiv((long long)mpad * ldk, 256)), 256, 0, st>>>(
+        J_dev, n, (__nv_fp8_storage_t *)out, ldk, mpad);
+    SI_CUDA_TRY(cudaGetLastError());
     return SI_OK;
 }
 
@@ -504,9 +581,9 @@ __global__ void k_tc_spins(const float *q_state, int n, int R, int8_t *spins, in
     }
 }
 
-template <int BN, int S, int EPI>
+template <int BN, int S, int EPI, bool E4>
 static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
-    using L = TcSmem<BN, S>;
+    using L = TcSmem<BN, S, E4>;
     TcArgs a;
     a.n = c->n;
     a.R = c->R;
@@ -540,12 +617,12 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
     // launch attributes and the co-residency check once per context (its
     // device and tile are fixed)
     if (c->tc_per_sm <= 0) {
-        SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S, EPI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S, EPI, E4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S, EPI, E4>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          (int)cudaSharedmemCarveoutMaxShared));
         int per_sm = 0;
-        SI_CUDA_TRY(
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_run<BN, S, EPI>, tc_threads<EPI>(), smem));
+        SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_run<BN, S, EPI, E4>,
+                                                                  tc_threads<EPI, E4>(), smem));
         c->tc_per_sm = per_sm;
     }
     const int per_sm = c->tc_per_sm;
@@ -555,33 +632,44 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
     }
     SI_CUDA_TRY(cudaMemsetAsync(c->dbar, 0, sizeof(unsigned) * grid, c->stream));
     void *args[] = {(void *)&c->mapA, (void *)&c->mapB, (void *)&a};
-    SI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_tc_run<BN, S, EPI>, dim3(grid), dim3(tc_threads<EPI>()),
-                                            args, smem, c->stream));
+    SI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_tc_run<BN, S, EPI, E4>, dim3(grid),
+                                            dim3(tc_threads<EPI, E4>()), args, smem, c->stream));
     c->launches += 1;
     return SI_OK;
 }
 
 si_status tc_run(Ctx *c, int steps, int8_t *spins_dev) {
     if (steps == 0) return SI_OK;
-    switch (c->tile_n) {
-        case 64: return tc_launch_t<64, 8, 8>(c, steps, spins_dev);
-        case 128: return tc_launch_t<128, 6, 8>(c, steps, spins_dev);
-        default: set_error("tensor path: unsupported tile"); return SI_ERR_UNSUPPORTED;
+    if (c->j_e4m3) {
+        switch (c->tile_n) {
+            case 64: return tc_launch_t<64, 8, 8, true>(c, steps, spins_dev);
+            case 128: return tc_launch_t<128, 6, 8, true>(c, steps, spins_dev);
+            default: break;
+        }
+    } else {
+        switch (c->tile_n) {
+            case 64: return tc_launch_t<64, 8, 8, false>(c, steps, spins_dev);
+            case 128: return tc_launch_t<128, 6, 8, false>(c, steps, spins_dev);
+            default: break;
+        }
     }
+    set_error("tensor path: unsupported tile");
+    return SI_ERR_UNSUPPORTED;
 }
 
-template <int BN, int S, int EPI>
+template <int BN, int S, int EPI, bool E4>
 static int tc_occupancy() {
-    using L = TcSmem<BN, S>;
+    using L = TcSmem<BN, S, E4>;
     const int smem = L::TOTAL + (EPI == 4 ? 256 : 1024);
-    if (cudaFuncSetAttribute(k_tc_run<BN, S, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_tc_run<BN, S, EPI, E4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+        cudaSuccess)
         return 0;
-    if (cudaFuncSetAttribute(k_tc_run<BN, S, EPI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+    if (cudaFuncSetAttribute(k_tc_run<BN, S, EPI, E4>, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
         return 0;
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_run<BN, S, EPI>, tc_threads<EPI>(), smem) !=
-        cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_run<BN, S, EPI, E4>, tc_threads<EPI, E4>(),
+                                                      smem) != cudaSuccess)
         return 0;
     return per_sm;
 }
@@ -590,7 +678,8 @@ static int tc_occupancy() {
 // unless the caller fixed tile_n.  Returns the CTAs per SM of the choice.
 static int choose_tile(const Ctx *c, int *per_sm) {
     const int mtiles = c->mpad / TC_BM;
-    const int occ128 = tc_occupancy<128, 6, 8>(), occ64 = tc_occupancy<64, 8, 8>();
+    const int occ128 = c->j_e4m3 ? tc_occupancy<128, 6, 8, true>() : tc_occupancy<128, 6, 8, false>();
+    const int occ64 = c->j_e4m3 ? tc_occupancy<64, 8, 8, true>() : tc_occupancy<64, 8, 8, false>();
     int bn;
     if (c->prm.tile_n == 64 || c->prm.tile_n == 128) {
         bn = c->prm.tile_n;
@@ -603,23 +692,38 @@ static int choose_tile(const Ctx *c, int *per_sm) {
     return bn;
 }
 
+bool tc_persistent_fits(Ctx *c) {
+    c->ldk = round_up(c->n, TC_BK);
+    c->mpad = round_up(c->n, TC_BM);
+    c->j_e4m3 = c->prm.prec == SI_PREC_J_FP8_Q_BF16;
+    const int mtiles = c->mpad / TC_BM;
+    int per_sm = 0;
+    const int bn = choose_tile(c, &per_sm);
+    const long long grid = (long long)mtiles * cdiv(c->R, bn);
+    return mtiles <= 64 && grid <= 4096 && per_sm > 0 && grid <= (long long)per_sm * c->num_sms;
+}
+
 si_status tc_prepare(Ctx *c, const float *J_dev) {
     const int n = c->n;
     c->ldk = round_up(n, TC_BK);
     c->mpad = round_up(n, TC_BM);
+    // SI_PREC_J_FP8_Q_BF16 keeps J in HBM as 1-byte e4m3 (validated exact);
+    // the kernels widen each tile to bf16 in shared memory.
+    c->j_e4m3 = c->prm.prec == SI_PREC_J_FP8_Q_BF16;
     int per_sm = 0;
     c->tile_n = choose_tile(c, &per_sm);
     c->rpad = round_up(c->R, c->tile_n);
-    SI_CUDA_TRY(si_dev_malloc(&c->dJ, (size_t)c->mpad * c->ldk * 2));
-    k_convert_j_bf16<<<std::min(8 * c->num_sms, cdiv((long long)c->mpad * c->ldk, 256)), 256, 0, c->stream>>>(
-        J_dev, n, (__nv_bfloat16 *)c->dJ, c->ldk, c->mpad);
-    SI_CUDA_TRY(cudaGetLastError());
+    SI_CUDA_TRY(si_dev_malloc(&c->dJ, (size_t)c->mpad * c->ldk * (c->j_e4m3 ? 1 : 2)));
+    si_status sc = c->j_e4m3 ? tc_convert_j_e4m3(J_dev, n, c->dJ, c->ldk, c->mpad, c->num_sms, c->stream)
+                             : tc_convert_j(J_dev, n, c->dJ, c->ldk, c->mpad, c->num_sms, c->stream);
+    if (sc != SI_OK) return sc;
     c->qbuf_bytes = 2ull * c->rpad * c->ldk * 2;
     SI_CUDA_TRY(si_dev_malloc(&c->dqbuf, c->qbuf_bytes));
     SI_CUDA_TRY(cudaMemsetAsync(c->dqbuf, 0, c->qbuf_bytes, c->stream));
     SI_CUDA_TRY(si_dev_malloc(&c->dq, sizeof(float) * (size_t)c->R * n));
     SI_CUDA_TRY(si_dev_malloc(&c->dp, sizeof(float) * (size_t)c->R * n));
-    si_status s = tc_make_map_bf16(&c->mapA, c->dJ, c->ldk, c->mpad, TC_BK, TC_BM);
+    si_status s = c->j_e4m3 ? tc_make_map_e4m3(&c->mapA, c->dJ, c->ldk, c->mpad, TC_BM)
+                            : tc_make_map_bf16(&c->mapA, c->dJ, c->ldk, c->mpad, TC_BK, TC_BM);
     if (s != SI_OK) return s;
     s = tc_make_map_bf16(&c->mapB, c->dqbuf, c->ldk, 2 * c->rpad, TC_BK, c->tile_n);
     if (s != SI_OK) return s;
@@ -679,8 +783,9 @@ si_status tc_spins(Ctx *c, int8_t *spins, int ld) {
 
 const char *tc_describe(const Ctx *c, char *buf, int len) {
     std::snprintf(buf, len,
-                  "tcgen05 prec=%s n=%d R=%d tile=128x%d stages=%d grid=%d (mtiles=%d rblocks=%d) kblocks=%d",
-                  c->prm.prec == SI_PREC_J_FP8_Q_BF16 ? "j_fp8_q_bf16" : "j_bf16_q_bf16", c->n, c->R,
+                  "tcgen05 prec=%s J=%s n=%d R=%d tile=128x%d stages=%d grid=%d (mtiles=%d rblocks=%d) kblocks=%d",
+                  c->prm.prec == SI_PREC_J_FP8_Q_BF16 ? "j_fp8_q_bf16" : "j_bf16_q_bf16",
+                  c->j_e4m3 ? "e4m3(1B)" : "bf16(2B)", c->n, c->R,
                   c->tile_n, c->tile_n == 128 ? 6 : 8, (c->mpad / TC_BM) * (c->rpad / c->tile_n),
                   c->mpad / TC_BM, c->rpad / c->tile_n, c->ldk / TC_BK);
     return buf;

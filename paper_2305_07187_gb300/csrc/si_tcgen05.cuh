@@ -165,6 +165,98 @@ __device__ __forceinline__ void tmem_wait_st() {
 }
 
 
+// ------------------------------------------------------------ e4m3 J tiles
+// A J tile of 128 rows x 64 K elements stored as e4m3 (1 byte each) is loaded
+// by TMA with the 64-byte swizzle into the upper half of the 16 KB bf16 A
+// region of a ring stage: row r at byte 8192 + 64 r, its 16-byte chunk c (K
+// elements 16c .. 16c+15) at chunk position c ^ ((r >> 1) & 3).  Four
+// converter warps (128 threads, thread = row) widen it in place to the bf16
+// tile that the MMA descriptors read, in the 128-byte swizzled layout TMA
+// gives a bf16 tile: row r at byte 128 r, chunk c (K elements 8c .. 8c+7) at
+// chunk position c ^ (r & 7).  Every thread first reads its whole e4m3 row
+// into registers; only after a barrier of the four warps does any of them
+// write, because bf16 rows 64..127 overwrite the e4m3 rows.  Every e4m3 value
+// (3 mantissa bits, magnitudes 2^-9 .. 448) is exact in bf16, so the widening
+// is exact.
+constexpr int E4M3_TILE_OFFSET = 8192;   // e4m3 tile inside the 16 KB A region
+
+// Four e4m3 values (bytes of w, lowest first) -> two bf16x2 words, on the
+// integer and FMA pipes (no conversion-unit instructions).  For a byte
+// s eeee mmm, PRMT builds the 16-bit word ssssssss s eeee mmm (the high
+// byte replicates the sign); shifted left by 4 and masked with 0x87F0 it is
+// s 0000 eeee mmm 0000: as bf16 that is the sign with exponent field eeee
+// and mantissa mmm, i.e. the e4m3 magnitude times 2^(7 - 127) (for eeee = 0
+// the bf16 subnormal m 2^-3 2^-126 is the e4m3 subnormal m 2^-9 times
+// 2^-120 as well).  One exact bf16 multiply by 2^120 restores the value;
+// zeros keep their sign.
+__device__ __forceinline__ void e4m3x4_to_bf16x4(uint32_t w, uint32_t &lo, uint32_t &hi) {
+    uint32_t z0, z1;
+    asm("prmt.b32 %0, %1, 0, 0x9180;" : "=r"(z0) : "r"(w));   // bytes a0, sign(a0), a1, sign(a1)
+    asm("prmt.b32 %0, %1, 0, 0xB3A2;" : "=r"(z1) : "r"(w));   // bytes a2, sign(a2), a3, sign(a3)
+    z0 = (z0 << 4) & 0x87F087F0u;
+    z1 = (z1 << 4) & 0x87F087F0u;
+    const uint32_t two120 = 0x7B807B80u;                       // bf16 2^120 in both halves
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(lo) : "r"(z0), "r"(two120));
+    asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(hi) : "r"(z1), "r"(two120));
+}
+
+// Row r of the e4m3 tile at a_region + E4M3_TILE_OFFSET into 16 registers.
+__device__ __forceinline__ void e4m3_row_load(uint32_t a_region, int r, uint32_t (&w)[16]) {
+    const uint32_t row = a_region + (uint32_t)E4M3_TILE_OFFSET + (uint32_t)r * 64u;
+    const uint32_t sw = (uint32_t)((r >> 1) & 3);
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
+                     : "=r"(w[4 * c]), "=r"(w[4 * c + 1]), "=r"(w[4 * c + 2]), "=r"(w[4 * c + 3])
+                     : "r"(row + ((((uint32_t)c) ^ sw) << 4))
+                     : "memory");
+}
+
+// Row r of the bf16 tile at a_region from the 16 e4m3 words of e4m3_row_load.
+__device__ __forceinline__ void bf16_row_store(uint32_t a_region, int r, const uint32_t (&w)[16]) {
+    const uint32_t row = a_region + (uint32_t)r * 128u;
+    const uint32_t sw = (uint32_t)(r & 7);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        // bf16 chunk c holds K elements 8c .. 8c+7 = e4m3 words 2c, 2c+1
+        uint32_t o0, o1, o2, o3;
+        e4m3x4_to_bf16x4(w[2 * c], o0, o1);
+        e4m3x4_to_bf16x4(w[2 * c + 1], o2, o3);
+        asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(row + ((((uint32_t)c) ^ sw) << 4)), "r"(o0),
+                     "r"(o1), "r"(o2), "r"(o3)
+                     : "memory");
+    }
+}
+
+__device__ __forceinline__ void named_barrier_sync(int id, int threads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Named barrier over `threads` threads that also ANDs a predicate: every
+// participant gets true iff every participant passed a non-zero value.
+__device__ __forceinline__ bool named_barrier_and(int id, int threads, int pred) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, %2, %3, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(pred), "r"(id), "r"(threads)
+        : "memory");
+    return r != 0;
+}
+
+// Widen one e4m3 J tile in place (all 128 threads of the four converter
+// warps call this, thread t converting row t; barrier id `bar_id` is private
+// to them).  The generic-proxy stores are then made visible to the tensor
+// cores (async proxy) before the caller signals the MMA issuer.
+__device__ __forceinline__ void widen_e4m3_tile(uint32_t a_region, int row, int bar_id) {
+    uint32_t w[16];
+    e4m3_row_load(a_region, row, w);
+    named_barrier_sync(bar_id, 128);
+    bf16_row_store(a_region, row, w);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
                      reinterpret_cast<uint64_t>(map)),

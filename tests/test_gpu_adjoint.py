@@ -129,6 +129,81 @@ def test_fp32_adjoint_close_to_oracle(kind, n, R, monkeypatch):
     o_obj, o_gz, o_gd, o_gk = oracle.grad(J, None, zeta, dt, q0, **kw)
     assert abs(obj - o_obj) <= 1e-4 * abs(o_obj)
     assert _rel(gz, o_gz) <= 1e-3 and _rel(gd, o_gd) <= 1e-3
+    assert abs(gk - o_gk) <= 1e-3 * max(abs(o_gk), np.abs(o_gd).max())
+
+
+def test_fp32_tensor_adjoint_at_the_timed_shape():
+    """The shape the gradient workload times: N=2000 +-1 couplings, so the
+    products run on the tensor cores with K split over the same thread-block
+    cluster size as the R=64 workload (asserted through si_describe), here
+    with R=4 replicas and T=20 steps so that the oracle's FP64 reverse mode
+    finishes in seconds.  Every output is compared, g_k included, at the
+    FP32 bar of 1e-3 relative."""
+    n, R, T = 2000, 4, 20
+    J, q0, zeta, dt = _case(n, R, T, seed=1)
+    with b.Context(J, replicas=64, steps=T, prec="fp32", ckpt_every=10) as cw:
+        cw.grad(zeta, dt, inputs.positions(n, 64, seed0=10))
+        split_workload = cw.describe().split("ksplit=")[1].split()[0]
+    with b.Context(J, replicas=R, steps=T, prec="fp32", ckpt_every=10) as ctx:
+        obj, gz, gd, gk = ctx.grad(zeta, dt, q0)
+        desc = ctx.describe()
+        kw = params_f64(ctx)
+    assert "grad=tcgen05-bf16x3" in desc
+    assert desc.split("ksplit=")[1].split()[0] == split_workload and int(split_workload) > 1
+    kw.pop("wall_zero_p")
+    o_obj, o_gz, o_gd, o_gk = oracle.grad(J, None, zeta, dt, q0, **kw)
+    assert abs(obj - o_obj) <= 1e-4 * abs(o_obj)
+    assert _rel(gz, o_gz) <= 1e-3 and _rel(gd, o_gd) <= 1e-3
+    assert abs(gk - o_gk) <= 1e-3 * max(abs(o_gk), np.abs(o_gd).max())
+
+
+def test_set_params_changes_k_without_a_new_context():
+    """si_set_params on a live context: the gradient under the new spring
+    constant equals that of a context created with it, bit for bit."""
+    n, R, T = 96, 8, 30
+    J, q0, zeta, dt = _case(n, R, T, seed=12)
+    with b.Context(J, replicas=R, steps=T, prec="fp32", ckpt_every=10) as ctx:
+        ctx.grad(zeta, dt, q0)
+        ctx.set_params(k=0.7, ckpt_every=7)
+        r1 = ctx.grad(zeta, dt, q0)
+        q1, p1, _ = ctx.run(zeta, dt, q0)
+        with pytest.raises(b.SpringIsingError):
+            ctx.set_params(replicas=R + 1)
+    with b.Context(J, replicas=R, steps=T, prec="fp32", ckpt_every=7, k=0.7) as cx:
+        r2 = cx.grad(zeta, dt, q0)
+        q2, p2, _ = cx.run(zeta, dt, q0)
+    assert r1[0] == r2[0] and np.array_equal(r1[1], r2[1]) and np.array_equal(r1[2], r2[2]) and r1[3] == r2[3]
+    assert np.array_equal(q1, q2) and np.array_equal(p1, p2)
+
+
+def test_autograd_device_binding_reuses_one_context():
+    """relaxed_energy with CUDA tensors: J is copied into a library context
+    once; later forward/backward passes (with a new k each time, set through
+    si_set_params) reuse it, keep every tensor on the device, and equal
+    si_grad bit for bit."""
+    import torch
+    from paper_2305_07187_gb300 import autograd as ag
+    ag.clear_cache()
+    dev = torch.device("cuda")
+    n, R, T = 96, 8, 30
+    J, q0, zeta, dt = _case(n, R, T, seed=13)
+    Jd, qd = torch.from_numpy(J).to(dev), torch.from_numpy(q0).to(dev)
+    created0, reused0 = ag.stats["created"], ag.stats["reused"]
+    for it in range(3):
+        kval = float(np.float32(0.5 + 0.01 * it))
+        z = torch.tensor(zeta, device=dev, requires_grad=True)
+        d = torch.tensor(dt, device=dev, requires_grad=True)
+        k = torch.tensor(kval, device=dev, requires_grad=True)
+        E = ag.relaxed_energy(Jd, z, d, k, qd)
+        E.backward()
+        assert E.is_cuda and z.grad.is_cuda and d.grad.is_cuda and k.grad.is_cuda
+        with b.Context(J, replicas=R, steps=T, k=kval) as ctx:
+            obj, gz, gd, gk = ctx.grad(zeta, dt, q0)
+        assert E.item() == obj
+        assert np.array_equal(z.grad.cpu().numpy(), gz) and np.array_equal(d.grad.cpu().numpy(), gd)
+        assert k.grad.item() == np.float32(gk)
+    assert ag.stats["created"] - created0 == 1 and ag.stats["reused"] - reused0 == 2
+    ag.clear_cache()
 
 
 def test_checkpoint_interval_does_not_change_the_gradient():

@@ -125,3 +125,33 @@ def test_early_returning_calls_give_the_synchronous_results(prec, n, R):
     np.testing.assert_array_equal(so.cpu().numpy(), s_h)
     np.testing.assert_array_equal(eo.cpu().numpy(), e_h)
     np.testing.assert_array_equal(co.cpu().numpy(), c_h)
+
+
+@pytest.mark.parametrize("prec,R", [("fp32", 1), ("j_fp8_q_bf16", 256)])
+def test_pinned_host_schedule_may_be_reused_once_the_call_returns(prec, R):
+    """si_run with a host input returns only after its work has finished, so
+    a pinned schedule may be overwritten as soon as the call returns: queue a
+    long run first (device arguments only, returns early), then a run whose
+    zeta and dt are pinned host memory and whose outputs are device memory,
+    overwrite zeta and dt at once, and compare with a synchronous run."""
+    import torch
+    dev = torch.device("cuda")
+    n, T = 2000, 2000
+    J = inputs.pm1_coupling(n, seed=36)
+    zeta, dt = inputs.zeta_ramp(T), inputs.dt_const(T)
+    q0 = inputs.positions(n, R, seed0=3600)
+    with b.Context(J, replicas=R, steps=T, prec=prec) as c:
+        q_ref, p_ref, s_ref = c.run(zeta, dt, q0)
+        z_d, d_d, q_d = (torch.from_numpy(x).to(dev) for x in (zeta, dt, q0))
+        z_h, d_h = torch.from_numpy(zeta.copy()).pin_memory(), torch.from_numpy(dt.copy()).pin_memory()
+        qo = torch.empty((R, n), dtype=torch.float32, device=dev)
+        po, so = torch.empty_like(qo), torch.empty((R, n), dtype=torch.int8, device=dev)
+        c.run_into(z_d, d_d, q_d)                       # long, returns once enqueued
+        c.run_into(z_h, d_h, q_d, None, qo, po, so)     # host inputs: returns when done
+        z_h.fill_(123.0)
+        d_h.fill_(-7.0)
+        c.synchronize()
+        torch.cuda.synchronize()
+    np.testing.assert_array_equal(qo.cpu().numpy(), q_ref)
+    np.testing.assert_array_equal(po.cpu().numpy(), p_ref)
+    np.testing.assert_array_equal(so.cpu().numpy(), s_ref)

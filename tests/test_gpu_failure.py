@@ -60,3 +60,24 @@ def test_error_of_an_early_returning_run_surfaces_at_the_next_synchronising_call
             ctx.energy(None)
         assert ei.value.status == b.SI_ERR_INVALID_ARG
         ctx.synchronize()   # nothing pending any more
+
+
+@pytest.mark.parametrize("prec,R", [("fp32", 1), ("j_fp8_q_bf16", 256)])
+def test_kernel_time_of_a_timed_out_run_reports_the_error(prec, R, monkeypatch):
+    """si_last_kernel_time after an early-returning run whose wait ran out
+    returns SI_ERR_TIMEOUT instead of the duration of the aborted kernel."""
+    import torch
+    n, T = 300, 12
+    J = inputs.pm1_coupling(n, seed=6)
+    z = torch.from_numpy(inputs.zeta_ramp(T)).cuda()
+    d = torch.from_numpy(inputs.dt_const(T)).cuda()
+    q = torch.from_numpy(inputs.positions(n, R, seed0=60)).cuda()
+    monkeypatch.setenv("SI_DEBUG_STALL_STEP", "3")
+    monkeypatch.setenv("SI_SPIN_LIMIT_NS", "200000000")
+    with b.Context(J, replicas=R, steps=T, prec=prec) as ctx:
+        ctx.enable_timing(True)
+        ctx.run_into(z, d, q)
+        with pytest.raises(b.SpringIsingError) as ei:
+            ctx.last_kernel_ms()
+        assert ei.value.status == b.SI_ERR_TIMEOUT
+        ctx.synchronize()   # the error was reported once
