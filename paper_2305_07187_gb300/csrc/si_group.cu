@@ -18,9 +18,11 @@
 // group and caches the winner by group shape.
 //
 // Members of precision SI_PREC_J_FP8_Q_BF16 keep J in HBM as 1-byte e4m3
-// (validated exact); four converter warps widen each of their J tiles to bf16
-// in shared memory before the MMAs read it, so the step streams half the J
-// bytes of a bf16 member.
+// (validated exact), so the step streams half the J bytes of a bf16 member.
+// Four converter warps widen each e4m3 J tile to bf16: under the policy
+// "whole-instance-tmem-a" into tensor memory, where the MMA reads its A
+// operand (one accumulator slot of up to 256 columns, the other 256 columns
+// hold eight A slots), under every other policy in place in shared memory.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -43,7 +45,12 @@ constexpr int GR_EPI_DEFAULT = 12;
 constexpr int GR_A_BYTES = GR_BM * GR_BK * 2;
 constexpr int GR_SMAX = 8;                       // most ring stages of any policy
 constexpr int GR_TILES = 196608;                 // shared memory for the ring
-constexpr int GR_NBARS = 3 * GR_SMAX + 2 + 2 + 1;  // full, empty, accf[2], tmem_empty[2], drain, conv
+constexpr int GR_NA = 8;                          // tensor-memory A slots (single-accumulator policy)
+constexpr int GR_NBARS = 3 * GR_SMAX + 2 + 2 + 1 + GR_NA;  // full, empty, accf[2], tmem_empty[2], drain, conv, aempty
+
+// TMEM column of A slot k (tensor-memory A policy: one accumulator slot in
+// columns 0 .. 255, the A slots after it).
+__device__ __forceinline__ uint32_t gr_acol(int k) { return 256u + 32u * k; }
 constexpr int GR_SMEM = GR_TILES + GR_NBARS * 8 + 16 + 1024;
 
 struct GroupInst {
@@ -74,6 +81,8 @@ struct GroupArgs {
     int *err;
     long long limit_ns;
     int single;                // 1: one accumulator per tile (N = bn <= 256), one MMA warp
+    int tmem_a;                // 1 (single mode, one slot): e4m3 J tiles widened into TMEM A slots
+    int nslots;                // accumulator slots in TMEM (2: the epilogue of tile u overlaps tile u+1)
     int stages;                // ring stages (even, <= GR_SMAX)
     int stage_bytes;           // A tile + largest B tile of the policy (multiple of 1024)
 };
@@ -92,6 +101,7 @@ __global__ void __launch_bounds__(gr_threads<GR_EPI>(), 1) k_group_step(const __
     auto tmem_empty_bar = [&](int k) { return bar0 + 8u * (2 * GR_SMAX + 2 + k); };
     const uint32_t drain_bar = bar0 + 8u * (2 * GR_SMAX + 4);
     auto conv_bar = [&](int s) { return bar0 + 8u * (2 * GR_SMAX + 5 + s); };
+    auto aempty_bar = [&](int k) { return bar0 + 8u * (3 * GR_SMAX + 5 + k); };
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + GR_TILES + GR_NBARS * 8);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + GR_TILES + GR_NBARS * 8 + 4);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -108,6 +118,7 @@ __global__ void __launch_bounds__(gr_threads<GR_EPI>(), 1) k_group_step(const __
             mbar_init(tmem_empty_bar(k), GR_EPI);
         }
         mbar_init(drain_bar, 2);
+        for (int k = 0; k < GR_NA; ++k) mbar_init(aempty_bar(k), 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -196,13 +207,15 @@ __global__ void __launch_bounds__(gr_threads<GR_EPI>(), 1) k_group_step(const __
             const int w = warp - 1;
             int rk = 0;          // index within this warp's ring of stages
             uint32_t rph = 0u;   // and its phase parity
+            uint32_t ce = 0u;    // e4m3 K blocks taken from TMEM A slots so far
             bool ok = true;
             int u = 0;
             for (int k = blockIdx.x; k < a.ntiles && ok; k += gridDim.x, ++u) {
                 const GroupTile tl = a.tiles[k];
-                const int slot = u & 1;
-                if (u >= 2) {
-                    if (!mbar_wait(tmem_empty_bar(slot), (uint32_t)(((u >> 1) - 1) & 1), a.err, abort_flag,
+                const int slot = a.nslots == 2 ? (u & 1) : 0;
+                const int use = a.nslots == 2 ? (u >> 1) : u;   // earlier tiles in this slot
+                if (use >= 1) {
+                    if (!mbar_wait(tmem_empty_bar(slot), (uint32_t)((use - 1) & 1), a.err, abort_flag,
                                    a.limit_ns)) {
                         ok = false;
                         break;
@@ -213,6 +226,7 @@ __global__ void __launch_bounds__(gr_threads<GR_EPI>(), 1) k_group_step(const __
                 if (a.single) {
                     if (w == 0) {
                         const uint32_t d_tmem = tmem + (uint32_t)slot * 256u;
+                        const bool ta = a.tmem_a && a.inst[tl.inst].e4m3;
                         for (int kb = 0; kb < tl.kb_cnt; ++kb) {
                             const int s = ring_stage(rk, 0);
                             if (!mbar_wait(full_bar(s), rph, a.err, abort_flag, a.limit_ns) ||
@@ -227,10 +241,25 @@ __global__ void __launch_bounds__(gr_threads<GR_EPI>(), 1) k_group_step(const __
                             tc_fence_after();
                             const uint64_t ad = sdesc_sw128(sbase + s * a.stage_bytes);
                             const uint64_t bd = ad + (uint64_t)(GR_A_BYTES >> 4);
+                            if (ta) {
+                                // A from the tensor-memory slot the converters filled
+                                // (conv_bar of this stage came after their store)
+                                const int as = (int)(ce % GR_NA);
+                                ++ce;
+                                const uint32_t at = tmem + gr_acol(as);
 #pragma unroll
-                            for (int kk = 0; kk < GR_BK / 16; ++kk)
-                                mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (kb != 0 || kk != 0) ? 1u : 0u);
-                            mma_commit(empty_bar(s));
+                                for (int kk = 0; kk < GR_BK / 16; ++kk)
+                                    mma_bf16_tmem_a(d_tmem, at + 8u * kk, bd + 2u * kk, idesc,
+                                                    (kb != 0 || kk != 0) ? 1u : 0u);
+                                mma_commit(empty_bar(s));
+                                mma_commit(aempty_bar(as));
+                            } else {
+#pragma unroll
+                                for (int kk = 0; kk < GR_BK / 16; ++kk)
+                                    mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc,
+                                             (kb != 0 || kk != 0) ? 1u : 0u);
+                                mma_commit(empty_bar(s));
+                            }
                         }
                     }
                 } else {
@@ -280,9 +309,10 @@ __global__ void __launch_bounds__(gr_threads<GR_EPI>(), 1) k_group_step(const __
         for (int k = blockIdx.x; k < a.ntiles; k += gridDim.x, ++u) {
             const GroupTile tl = a.tiles[k];
             const GroupInst &in = a.inst[tl.inst];
-            const int slot = u & 1;
+            const int slot = a.nslots == 2 ? (u & 1) : 0;
+            const int use = a.nslots == 2 ? (u >> 1) : u;
             bool ok = true;
-            if (lane == 0) ok = mbar_wait(accf_bar(slot), (uint32_t)((u >> 1) & 1), a.err, abort_flag, a.limit_ns);
+            if (lane == 0) ok = mbar_wait(accf_bar(slot), (uint32_t)(use & 1), a.err, abort_flag, a.limit_ns);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             tc_fence_after();
@@ -341,26 +371,44 @@ __global__ void __launch_bounds__(gr_threads<GR_EPI>(), 1) k_group_step(const __
         // keeps conv_bar one phase behind full_bar, so no waiter can see a
         // phase two ahead.  Every thread waits itself; the four warps agree
         // on success through one reducing barrier.
-        const int row = (warp - GR_CONV_WARP0) * 32 + lane;
+        // Warp w writes TMEM lanes 32*(w%4) .. +31: thread = row (w%4)*32 + lane.
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16);
         int rk0 = 0, rk1 = 0;
         uint32_t rph0 = 0u, rph1 = 0u;
+        uint32_t ce = 0u;   // e4m3 K blocks widened into TMEM A slots so far
         bool ok = true;
         for (int k = blockIdx.x; k < a.ntiles && ok; k += gridDim.x) {
             const GroupTile tl = a.tiles[k];
             const int e4 = a.inst[tl.inst].e4m3;
+            const bool ta = a.tmem_a && e4;
             for (int j = 0; j < tl.kb_cnt; ++j) {
                 const int ring = a.single ? 0 : (j & 1);
                 int &rk = ring ? rk1 : rk0;
                 uint32_t &rph = ring ? rph1 : rph0;
                 const int s = ring_stage(rk, ring);
                 const uint32_t ph = rph;
-                const int okw = mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns) ? 1 : 0;
-                if (!named_barrier_and(2, 128, okw)) { ok = false; break; }
+                const int as = (int)(ce % GR_NA);
+                bool okl = mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns);
+                if (ta) okl = okl && mbar_wait(aempty_bar(as), ((ce / GR_NA) & 1u) ^ 1u, a.err, abort_flag, a.limit_ns);
+                if (!named_barrier_and(2, 128, okl ? 1 : 0)) { ok = false; break; }
                 if (++rk == ring_len) {
                     rk = 0;
                     rph ^= 1u;
                 }
-                if (e4) widen_e4m3_tile(sbase + s * a.stage_bytes, row, 2);
+                if (ta) {
+                    tc_fence_after();
+                    uint32_t wv[16], o[32];
+                    e4m3_row_load(sbase + s * a.stage_bytes + (uint32_t)E4M3_TILE_OFFSET, row, wv);
+                    e4m3_row_to_bf16x2(wv, o);
+                    tmem_st32(tq + gr_acol(as), o);
+                    tmem_wait_st();
+                    tc_fence_before();
+                    ++ce;
+                } else if (e4) {
+                    widen_e4m3_tile(sbase + s * a.stage_bytes, row, 2);
+                }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(conv_bar(s));
             }
@@ -403,6 +451,8 @@ struct GroupMember {
     std::vector<int> kb_off, kb_cnt;   // per M tile: its non-zero K blocks in Group::kbl
 };
 
+constexpr int kMaxPolicies = 8;   // room in the per-policy tables (kPolicies are used)
+
 struct Group {
     int count = 0, steps = 0;
     // Set when the group serves one si_create context whose persistent grid
@@ -417,8 +467,9 @@ struct Group {
     GroupInst *d_inst = nullptr;
     GroupTile *d_tiles = nullptr;
     int ntiles = 0;
-    int pol_tiles_off[4] = {0, 0, 0, 0}, pol_ntiles[4] = {0, 0, 0, 0};
-    int pol_stages[4] = {0, 0, 0, 0}, pol_stage_bytes[4] = {0, 0, 0, 0};
+    // per tile policy (kPolicies of them)
+    int pol_tiles_off[kMaxPolicies] = {}, pol_ntiles[kMaxPolicies] = {};
+    int pol_stages[kMaxPolicies] = {}, pol_stage_bytes[kMaxPolicies] = {};
     CUtensorMap *d_maps = nullptr;
     std::vector<int> kbl;       // K-block lists of every (member, M tile), host copy
     int *d_kbl = nullptr;
@@ -426,6 +477,7 @@ struct Group {
     int *d_err = nullptr;
     int *h_err = nullptr;   // pinned host copy of the error word
     int policy = -1;            // chosen tile policy
+    bool any_e4m3 = false;      // some member stores J as e4m3
     int epi = 12;               // epilogue warps of the step kernel (8 or 12)
     int grid = 0;
     cudaGraphExec_t graph = nullptr;
@@ -436,18 +488,22 @@ struct Group {
     int launches = 0;
 };
 
-static const char *kPolicyName[] = {"bn64-if-R<=64-else-128", "all-64", "all-128", "whole-instance"};
-constexpr int kPolicies = 4;
+static const char *kPolicyName[] = {"bn64-if-R<=64-else-128", "all-64", "all-128", "whole-instance",
+                                    "whole-instance-tmem-a"};
+constexpr int kPolicies = 5;
+static_assert(kPolicies <= kMaxPolicies, "per-policy tables too small");
 constexpr int kPolicyWhole = 3;
+constexpr int kPolicyWholeTmemA = 4;   // whole-instance tiles, e4m3 J widened into TMEM, one accumulator slot
 
 // Replicas per tile of a member under a policy.  "whole-instance" covers all
 // R replicas of the member in one tile (R <= 256, a multiple of 16), so each
 // J slab is read once per step, and larger R in tiles of 256; it runs the
 // single-accumulator mode (one MMA of N up to 256 per K step).
-static int policy_bn(int policy, int R) {
+static int policy_bn(int policy, int R, bool any_e4m3) {
     if (policy == 1) return 64;
     if (policy == 2) return 128;
-    if (policy == kPolicyWhole) return round_up(R, 16) <= 256 ? round_up(R, 16) : 256;
+    (void)any_e4m3;
+    if (policy == kPolicyWhole || policy == kPolicyWholeTmemA) return round_up(R, 16) <= 256 ? round_up(R, 16) : 256;
     return R <= 64 ? 64 : 128;
 }
 
@@ -459,7 +515,7 @@ static void policy_ring(int policy, const std::vector<int> &bns, int *stages, in
     int sb = GR_BM * GR_BK * 2 + round_up(bmax * GR_BK * 2, 1024);
     int st = std::min(GR_SMAX, GR_TILES / sb);
     st &= ~1;
-    if (policy == kPolicyWhole) st = std::max(st, 2);
+    if (policy == kPolicyWhole || policy == kPolicyWholeTmemA) st = std::max(st, 2);
     *stages = st;
     *stage_bytes = sb;
 }
@@ -515,7 +571,7 @@ static std::string group_key(const Group *g) {
     for (const auto &x : g->m) {
         long long nb = 0;
         for (int v : x.kb_cnt) nb += v;
-        k += std::to_string(x.n) + "x" + std::to_string(x.R) + "b" + std::to_string(nb) + ",";
+        k += std::to_string(x.n) + "x" + std::to_string(x.R) + "b" + std::to_string(nb) + (x.e4m3 ? "e" : "") + ",";
     }
     return k;
 }
@@ -637,7 +693,7 @@ static si_status group_build_policies(Group *g) {
     std::vector<std::vector<GroupTile>> tiles(kPolicies);
     for (int pol = 0; pol < kPolicies; ++pol) {
         std::vector<int> bns;
-        for (int i = 0; i < c; ++i) bns.push_back(policy_bn(pol, g->m[i].R));
+        for (int i = 0; i < c; ++i) bns.push_back(policy_bn(pol, g->m[i].R, g->any_e4m3));
         policy_ring(pol, bns, &g->pol_stages[pol], &g->pol_stage_bytes[pol]);
         for (int i = 0; i < c; ++i) {
             GroupMember &x = g->m[i];
@@ -645,7 +701,7 @@ static si_status group_build_policies(Group *g) {
             d.n = x.n;
             d.R = x.R;
             d.ldk = x.ldk;
-            d.bn = policy_bn(pol, x.R);
+            d.bn = policy_bn(pol, x.R, g->any_e4m3);
             d.rpad = x.rpad_max;
             d.mtiles = x.mpad / GR_BM;
             d.rblocks = cdiv(x.R, d.bn);
@@ -722,7 +778,9 @@ static si_status group_launch_step(Group *g, int t, int steps) {
                       g->common.update_order, g->common.wall_zero_p};
     a.err = g->d_err;
     a.limit_ns = g->limit_ns;
-    a.single = g->policy == kPolicyWhole ? 1 : 0;
+    a.single = (g->policy == kPolicyWhole || g->policy == kPolicyWholeTmemA) ? 1 : 0;
+    a.tmem_a = g->policy == kPolicyWholeTmemA ? 1 : 0;
+    a.nslots = g->policy == kPolicyWholeTmemA ? 1 : 2;
     a.stages = g->pol_stages[g->policy];
     a.stage_bytes = g->pol_stage_bytes[g->policy];
     if (g->epi == 8) k_group_step<8><<<g->grid, gr_threads<8>(), GR_SMEM, g->stream>>>(a);
@@ -817,6 +875,7 @@ static si_status group_autotune(Group *g) {
     } else if (!(env && std::atoi(env) < 0)) {
         float best_ms = 1e30f;
         for (int pol = 0; pol < kPolicies; ++pol) {
+            if (pol == kPolicyWholeTmemA && !g->any_e4m3) continue;   // only differs for e4m3 members
             float ms = 0.f;
             si_status s = group_time_policy(g, pol, 3, &ms);
             if (s != SI_OK) return s;
@@ -964,6 +1023,7 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
             c.dhf = nullptr;
         }
     }
+    for (const auto &x : g->m) g->any_e4m3 = g->any_e4m3 || x.e4m3;
     si_status sb = group_build_policies(g);
     if (sb != SI_OK) return sb;
     SI_CUDA_TRY(si_dev_malloc((void **)&g->d_zeta, sizeof(float) * std::max(1, g->steps)));
@@ -1275,7 +1335,7 @@ si_status si_group_describe(const si_group *grp, char *buf, int32_t len) {
     if (!g || !buf || len <= 0) return SI_ERR_INVALID_ARG;
     long long macs = 0, jbytes = 0;
     for (const auto &x : g->m) {
-        const int bn = policy_bn(g->policy, x.R);
+        const int bn = policy_bn(g->policy, x.R, g->any_e4m3);
         macs += (long long)x.n * x.n * x.R;
         long long nb = 0;
         for (int v : x.kb_cnt) nb += v;

@@ -23,6 +23,7 @@
 // and returns.
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 
 #include "si_tcgen05.cuh"
 
@@ -56,23 +57,30 @@ struct TcArgs {
 // ------------------------------------------------------------------ kernel
 // Shared memory: S ring stages (J tile + q tile), the staging tile of the
 // next q (bf16, two 64-spin halves in the 128-byte swizzled layout that the
-// TMA store and the MMA both read), then the mbarriers.  With e4m3 J storage
-// the J tile arrives as 8 KB of e4m3 in the upper half of the stage's 16 KB
-// A region and is widened there to bf16 before the MMAs read it.
+// TMA store and the MMA both read), then the mbarriers.
+//
+// With e4m3 J storage (E4) a stage holds the J tile as 8 KB of e4m3 (64-byte
+// swizzle) and four converter warps widen it into tensor memory, where the
+// MMAs read their A operand: the J tile then costs 8 KB of TMA traffic and
+// 8 KB of shared-memory reads instead of 16 + 16 KB.  Tensor memory holds
+// the two accumulators, q and NA A slots, so the momenta p move to shared
+// memory ([replica][spin] within the tile).
 template <int BN, int S, bool E4>
 struct TcSmem {
     static constexpr int B_BYTES = BN * TC_BK * 2;
-    static constexpr int STAGE_BYTES = TC_A_BYTES + B_BYTES;
-    // bytes TMA delivers per stage (the J tile in its storage type + q tile)
-    static constexpr int TX_BYTES = (E4 ? TC_BM * TC_BK : TC_A_BYTES) + B_BYTES;
+    static constexpr int A_STAGE = E4 ? TC_BM * TC_BK : TC_A_BYTES;   // J tile in its storage type
+    static constexpr int STAGE_BYTES = A_STAGE + B_BYTES;
+    static constexpr int TX_BYTES = STAGE_BYTES;          // bytes TMA delivers per stage
     static constexpr int TILES = S * STAGE_BYTES;
     static constexpr int HALF_BYTES = BN * 128;           // BN replicas x 64 spins bf16
     static constexpr int STAGING = TILES;                 // 1024-aligned
-    static constexpr int BARS = STAGING + 2 * HALF_BYTES;
-    // full[S], empty[S], accf, tmem_empty, epi_done, drain, conv[S]
-    static constexpr int NBARS = 3 * S + 4;
+    static constexpr int PTILE = STAGING + 2 * HALF_BYTES;    // p of the tile (E4), [BN][128] floats
+    static constexpr int BARS = PTILE + (E4 ? BN * TC_BM * 4 : 0);
+    static constexpr int NA = E4 ? 4 : 0;                 // A slots in tensor memory (two per MMA warp)
+    // full[S], empty[S], accf, tmem_empty, epi_done, drain, afull[NA], aempty[NA]
+    static constexpr int NBARS = 2 * S + 4 + 2 * NA;
     static constexpr int TOTAL = BARS + NBARS * 8 + 16;   // + tmem slot, abort flag
-    static constexpr int TMEM_COLS = (4 * BN <= 256) ? 256 : 512;
+    static constexpr int TMEM_COLS = (E4 || 4 * BN > 256) ? 512 : 256;
 };
 
 constexpr int TC_MMA_WARPS = 2;
@@ -104,21 +112,27 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
     const uint32_t tmem_empty_bar = bar0 + 8u * (2 * S + 1);
     const uint32_t epi_done_bar = bar0 + 8u * (2 * S + 2);
     const uint32_t drain_bar = bar0 + 8u * (2 * S + 3);
-    auto conv_bar = [&](int s) { return bar0 + 8u * (2 * S + 4 + s); };
+    auto afull_bar = [&](int k) { return bar0 + 8u * (2 * S + 4 + k); };
+    auto aempty_bar = [&](int k) { return bar0 + 8u * (2 * S + 4 + L::NA + k); };
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::BARS + L::NBARS * 8);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::BARS + L::NBARS * 8 + 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt = blockIdx.x % a.mtiles, rb = blockIdx.x / a.mtiles;
     const int m0 = mt * TC_BM, r0 = rb * BN;
-    // TMEM columns: two partial accumulators, then the q and p state.
-    constexpr uint32_t COL_ACC0 = 0, COL_ACC1 = BN, COL_Q = 2 * BN, COL_P = 3 * BN;
+    // TMEM columns: two partial accumulators, then the q and p state (E4:
+    // q, then the A slots of 32 columns; p lives in shared memory).
+    constexpr uint32_t COL_ACC0 = 0, COL_ACC1 = BN, COL_Q = 2 * BN, COL_P = 3 * BN, COL_A = 3 * BN;
+    constexpr int NAR = L::NA / 2;   // A slots per MMA warp
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
-            mbar_init(conv_bar(s), 4);
+        }
+        for (int k = 0; k < L::NA; ++k) {
+            mbar_init(afull_bar(k), 4);
+            mbar_init(aempty_bar(k), 1);
         }
         mbar_init(accf_bar, TC_MMA_WARPS);
         mbar_init(tmem_empty_bar, EPI);
@@ -173,13 +187,13 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
                 const int s = 2 * (int)(c % HS) + ring;
                 const uint32_t ph = (c / HS) & 1u;
                 const uint32_t dA = sbase + s * L::STAGE_BYTES;
-                const uint32_t dB = dA + TC_A_BYTES;
+                const uint32_t dB = dA + L::A_STAGE;
                 int okw = 1;
                 if (lane == 0) {
                     okw = mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns) ? 1 : 0;
                     if (okw) {
                         mbar_arrive_expect_tx(full_bar(s), (uint32_t)L::TX_BYTES);
-                        tma_load_2d(E4 ? dA + (uint32_t)E4M3_TILE_OFFSET : dA, &mapA, full_bar(s), kb * TC_BK, m0);
+                        tma_load_2d(dA, &mapA, full_bar(s), kb * TC_BK, m0);
                     }
                 }
                 okw = __shfl_sync(0xffffffffu, okw, 0);
@@ -258,14 +272,31 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
                     const int s = 2 * (int)(c % HS) + w;
                     const uint32_t ph = (c / HS) & 1u;
                     if (!mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
-                    if (E4 && !mbar_wait(conv_bar(s), ph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint64_t ad = sdesc_sw128(sbase + s * L::STAGE_BYTES);
-                    const uint64_t bd = ad + (uint64_t)(TC_A_BYTES >> 4);
+                    if constexpr (E4) {
+                        // A from the tensor-memory slot the converters filled
+                        const int as = 2 * (int)(c % NAR) + w;
+                        if (!mbar_wait(afull_bar(as), (c / NAR) & 1u, a.err, abort_flag, a.limit_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t bd = sdesc_sw128(sbase + s * L::STAGE_BYTES + L::A_STAGE);
+                        const uint32_t at = tmem + COL_A + 32u * (uint32_t)as;
 #pragma unroll
-                    for (int kk = 0; kk < TC_BK / 16; ++kk)
-                        mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (j != w || kk != 0) ? 1u : 0u);
-                    mma_commit(empty_bar(s));
+                        for (int kk = 0; kk < TC_BK / 16; ++kk)
+                            mma_bf16_tmem_a(d_tmem, at + 8u * kk, bd + 2u * kk, idesc,
+                                            (j != w || kk != 0) ? 1u : 0u);
+                        mma_commit(empty_bar(s));
+                        mma_commit(aempty_bar(as));
+                    } else {
+                        tc_fence_after();
+                        const uint64_t ad = sdesc_sw128(sbase + s * L::STAGE_BYTES);
+                        const uint64_t bd = ad + (uint64_t)(TC_A_BYTES >> 4);
+#pragma unroll
+                        for (int kk = 0; kk < TC_BK / 16; ++kk)
+                            mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (j != w || kk != 0) ? 1u : 0u);
+                        mma_commit(empty_bar(s));
+                    }
                 }
                 if (ok) mma_commit(accf_bar);
             }
@@ -299,7 +330,10 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
         const int kq = row & 63;
         const uint32_t st_base = stage_q + (uint32_t)(row >> 6) * L::HALF_BYTES + (uint32_t)(kq & 7) * 2u;
         const bool publisher = (warp == TC_EPI_WARP0 && lane == 0);
-        // Load the initial state into TMEM.
+        // E4: p of this thread's spin at p_tile[col * 128 + row] (a warp's
+        // 32 consecutive rows are consecutive words: no bank conflicts)
+        float *p_tile = reinterpret_cast<float *>(smem + L::PTILE);
+        // Load the initial state into TMEM (E4: p into shared memory).
 #pragma unroll 1
         for (int c = c_begin; c < c_begin + CPH; ++c) {
             uint32_t vq[32], vp[32];
@@ -311,7 +345,12 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
                 vp[j] = __float_as_uint(ok ? a.p_state[(size_t)r * a.n + i] : 0.f);
             }
             tmem_st32(tl + COL_Q + c * 32, vq);
-            tmem_st32(tl + COL_P + c * 32, vp);
+            if constexpr (E4) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) p_tile[(c * 32 + j) * TC_BM + row] = __uint_as_float(vp[j]);
+            } else {
+                tmem_st32(tl + COL_P + c * 32, vp);
+            }
         }
         tmem_wait_st();
 #pragma unroll 1
@@ -336,7 +375,12 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
                         vf[j] = __float_as_uint(__uint_as_float(vf[j]) + __uint_as_float(vp[j]));
                 }
                 tmem_ld32(tl + COL_Q + c * 32, vq);
-                tmem_ld32(tl + COL_P + c * 32, vp);
+                if constexpr (E4) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) vp[j] = __float_as_uint(p_tile[(c * 32 + j) * TC_BM + row]);
+                } else {
+                    tmem_ld32(tl + COL_P + c * 32, vp);
+                }
                 tmem_wait_ld();
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
@@ -348,7 +392,12 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
                     vp[j] = __float_as_uint(po);
                 }
                 tmem_st32(tl + COL_Q + c * 32, vq);
-                tmem_st32(tl + COL_P + c * 32, vp);
+                if constexpr (E4) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) p_tile[(c * 32 + j) * TC_BM + row] = __uint_as_float(vp[j]);
+                } else {
+                    tmem_st32(tl + COL_P + c * 32, vp);
+                }
                 if (!last) {
                     // bf16 copy into the staging tile (zeros outside n x R).
 #pragma unroll
@@ -400,14 +449,18 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
                 }
             }
         }
-    } else if (E4) {
+    } else if constexpr (E4) {
         // ------------------------------------------------ e4m3 converters (4 warps)
-        // Widen every J tile in place, stage by stage in the order the
-        // producer fills them (the same two rings), then release the stage to
-        // its MMA warp.  Every converter thread waits for the stage itself;
-        // the four warps agree on success through one reducing barrier so
-        // that none of them can be left alone at the widening barrier.
-        const int row = (warp - (TC_EPI_WARP0 + EPI)) * 32 + lane;
+        // Widen every J tile into a tensor-memory A slot, stage by stage in
+        // the order the producer fills them (the same two rings; slot ring w
+        // feeds MMA warp w).  Warp w writes TMEM lanes 32*(w%4) .. +31, so
+        // thread = row of the tile; the four warps work independently and
+        // the MMA warp waits for all four (afull counts 4 arrivals).  Every
+        // lane waits itself and the warp goes on only if all lanes saw the
+        // stage, so the .sync.aligned tensor-memory store stays convergent.
+        const int quad = warp & 3;
+        const int row = quad * 32 + lane;
+        const uint32_t tq = tmem + ((uint32_t)(quad * 32) << 16);
         constexpr int HS = S / 2;
         uint32_t cnt0 = 0u, cnt1 = 0u;
         bool ok = true;
@@ -416,13 +469,20 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
                 const int ring = j & 1;
                 const uint32_t c = ring ? cnt1 : cnt0;
                 const int s = 2 * (int)(c % HS) + ring;
-                const uint32_t ph = (c / HS) & 1u;
-                const int okw = mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns) ? 1 : 0;
-                if (!named_barrier_and(2, 128, okw)) { ok = false; break; }
+                const int as = 2 * (int)(c % NAR) + ring;
+                bool okl = mbar_wait(full_bar(s), (c / HS) & 1u, a.err, abort_flag, a.limit_ns);
+                okl = okl && mbar_wait(aempty_bar(as), ((c / NAR) & 1u) ^ 1u, a.err, abort_flag, a.limit_ns);
+                if (!__all_sync(0xffffffffu, okl)) { ok = false; break; }
                 if (ring) ++cnt1; else ++cnt0;
-                widen_e4m3_tile(sbase + s * L::STAGE_BYTES, row, 2);
+                tc_fence_after();
+                uint32_t w[16], o[32];
+                e4m3_row_load(sbase + s * L::STAGE_BYTES, row, w);
+                e4m3_row_to_bf16x2(w, o);
+                tmem_st32(tq + COL_A + 32u * (uint32_t)as, o);
+                tmem_wait_st();
+                tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(conv_bar(s));
+                if (lane == 0) mbar_arrive(afull_bar(as));
             }
         }
     }
@@ -643,7 +703,7 @@ si_status tc_run(Ctx *c, int steps, int8_t *spins_dev) {
     if (c->j_e4m3) {
         switch (c->tile_n) {
             case 64: return tc_launch_t<64, 8, 8, true>(c, steps, spins_dev);
-            case 128: return tc_launch_t<128, 6, 8, true>(c, steps, spins_dev);
+            case 128: return tc_launch_t<128, 4, 8, true>(c, steps, spins_dev);
             default: break;
         }
     } else {
@@ -678,7 +738,7 @@ static int tc_occupancy() {
 // unless the caller fixed tile_n.  Returns the CTAs per SM of the choice.
 static int choose_tile(const Ctx *c, int *per_sm) {
     const int mtiles = c->mpad / TC_BM;
-    const int occ128 = c->j_e4m3 ? tc_occupancy<128, 6, 8, true>() : tc_occupancy<128, 6, 8, false>();
+    const int occ128 = c->j_e4m3 ? tc_occupancy<128, 4, 8, true>() : tc_occupancy<128, 6, 8, false>();
     const int occ64 = c->j_e4m3 ? tc_occupancy<64, 8, 8, true>() : tc_occupancy<64, 8, 8, false>();
     int bn;
     if (c->prm.tile_n == 64 || c->prm.tile_n == 128) {
@@ -692,10 +752,22 @@ static int choose_tile(const Ctx *c, int *per_sm) {
     return bn;
 }
 
+// Operand of J for the persistent kernel.  Its J tiles are re-read from L2
+// at every step, so it keeps J as bf16: widening each e4m3 tile at every step
+// (into tensor memory, the fastest of the forms measured) costs more time
+// than the 8 KB of L2 traffic it saves per 128 x 64 tile.  SI_TC_J_E4M3=1
+// selects the e4m3 operand with per-tile widening (same results, bit for
+// bit).  The grouped per-step kernel, which streams J from HBM, reads e4m3.
+static bool tc_e4m3_operand(const Ctx *c) {
+    if (c->prm.prec != SI_PREC_J_FP8_Q_BF16) return false;
+    const char *e = std::getenv("SI_TC_J_E4M3");
+    return e && std::atoi(e) == 1;
+}
+
 bool tc_persistent_fits(Ctx *c) {
     c->ldk = round_up(c->n, TC_BK);
     c->mpad = round_up(c->n, TC_BM);
-    c->j_e4m3 = c->prm.prec == SI_PREC_J_FP8_Q_BF16;
+    c->j_e4m3 = tc_e4m3_operand(c);
     const int mtiles = c->mpad / TC_BM;
     int per_sm = 0;
     const int bn = choose_tile(c, &per_sm);
@@ -707,9 +779,7 @@ si_status tc_prepare(Ctx *c, const float *J_dev) {
     const int n = c->n;
     c->ldk = round_up(n, TC_BK);
     c->mpad = round_up(n, TC_BM);
-    // SI_PREC_J_FP8_Q_BF16 keeps J in HBM as 1-byte e4m3 (validated exact);
-    // the kernels widen each tile to bf16 in shared memory.
-    c->j_e4m3 = c->prm.prec == SI_PREC_J_FP8_Q_BF16;
+    c->j_e4m3 = tc_e4m3_operand(c);
     int per_sm = 0;
     c->tile_n = choose_tile(c, &per_sm);
     c->rpad = round_up(c->R, c->tile_n);
@@ -786,7 +856,7 @@ const char *tc_describe(const Ctx *c, char *buf, int len) {
                   "tcgen05 prec=%s J=%s n=%d R=%d tile=128x%d stages=%d grid=%d (mtiles=%d rblocks=%d) kblocks=%d",
                   c->prm.prec == SI_PREC_J_FP8_Q_BF16 ? "j_fp8_q_bf16" : "j_bf16_q_bf16",
                   c->j_e4m3 ? "e4m3(1B)" : "bf16(2B)", c->n, c->R,
-                  c->tile_n, c->tile_n == 128 ? 6 : 8, (c->mpad / TC_BM) * (c->rpad / c->tile_n),
+                  c->tile_n, c->tile_n == 128 ? (c->j_e4m3 ? 4 : 6) : 8, (c->mpad / TC_BM) * (c->rpad / c->tile_n),
                   c->mpad / TC_BM, c->rpad / c->tile_n, c->ldk / TC_BK);
     return buf;
 }

@@ -200,9 +200,10 @@ __device__ __forceinline__ void e4m3x4_to_bf16x4(uint32_t w, uint32_t &lo, uint3
     asm("mul.rn.bf16x2 %0, %1, %2;" : "=r"(hi) : "r"(z1), "r"(two120));
 }
 
-// Row r of the e4m3 tile at a_region + E4M3_TILE_OFFSET into 16 registers.
-__device__ __forceinline__ void e4m3_row_load(uint32_t a_region, int r, uint32_t (&w)[16]) {
-    const uint32_t row = a_region + (uint32_t)E4M3_TILE_OFFSET + (uint32_t)r * 64u;
+// Row r (64 e4m3 bytes, 64-byte swizzle) of the e4m3 tile at `tile` into 16
+// registers: word m holds K elements 4m .. 4m+3, lowest first.
+__device__ __forceinline__ void e4m3_row_load(uint32_t tile, int r, uint32_t (&w)[16]) {
+    const uint32_t row = tile + (uint32_t)r * 64u;
     const uint32_t sw = (uint32_t)((r >> 1) & 3);
 #pragma unroll
     for (int c = 0; c < 4; ++c)
@@ -228,6 +229,26 @@ __device__ __forceinline__ void bf16_row_store(uint32_t a_region, int r, const u
     }
 }
 
+// One row of 64 e4m3 values (16 words of e4m3_row_load) as 32 bf16x2 words,
+// word m holding K elements 2m, 2m+1: the layout of one lane of a 128 x 64
+// bf16 A operand in tensor memory (row = lane, two K elements per column).
+__device__ __forceinline__ void e4m3_row_to_bf16x2(const uint32_t (&w)[16], uint32_t (&o)[32]) {
+#pragma unroll
+    for (int m = 0; m < 16; ++m) e4m3x4_to_bf16x4(w[m], o[2 * m], o[2 * m + 1]);
+}
+
+// MMA with the A operand (M = 128 rows x K = 16 bf16) read from tensor memory
+// at column a_tmem (lane = row, 8 columns of two K elements each) and B from
+// shared memory.
+__device__ __forceinline__ void mma_bf16_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                                uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 __device__ __forceinline__ void named_barrier_sync(int id, int threads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
@@ -251,7 +272,7 @@ __device__ __forceinline__ bool named_barrier_and(int id, int threads, int pred)
 // cores (async proxy) before the caller signals the MMA issuer.
 __device__ __forceinline__ void widen_e4m3_tile(uint32_t a_region, int row, int bar_id) {
     uint32_t w[16];
-    e4m3_row_load(a_region, row, w);
+    e4m3_row_load(a_region + (uint32_t)E4M3_TILE_OFFSET, row, w);
     named_barrier_sync(bar_id, 128);
     bf16_row_store(a_region, row, w);
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");

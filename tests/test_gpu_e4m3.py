@@ -1,10 +1,13 @@
 """FP8 e4m3 storage of J (SI_PREC_J_FP8_Q_BF16).
 
-J is kept in HBM as 1-byte e4m3 and each 128 x 64 tile is widened to bf16 in
-shared memory before the tensor cores read it.  Every finite e4m3 value is
-exact in bf16, so a context that stores J as e4m3 must compute exactly what
-a context storing the same J as bf16 computes: bit-identical states, spins
-and energies.  J here takes every finite e4m3 value (both signs, subnormals
+The grouped per-step kernel (and every context it serves) keeps J in HBM as
+1-byte e4m3 and widens each 128 x 64 tile to bf16 before the tensor cores
+read it (in shared memory, or in tensor memory as the MMA's A operand); the
+persistent kernel does the same into tensor memory when SI_TC_J_E4M3=1 (by
+default it keeps a bf16 copy, its J tiles being L2-resident).  Every finite
+e4m3 value is exact in bf16, so a context that stores J as e4m3 must compute
+exactly what a context storing the same J as bf16 computes: bit-identical
+states, spins and energies.  J here takes every finite e4m3 value (both signs, subnormals
 included), so a wrong swizzle position, byte order or exponent mapping of
 the widening shows up as a difference.  The per-step parity of both against
 the oracle is in test_gpu_tc / test_gpu_group.
@@ -54,8 +57,14 @@ def test_e4m3_values_are_the_format():
 ZETA_SMALL = 2.0 ** -8   # keeps zeta * dt * |J| < p_max for |J| <= 448: no momentum saturates
 
 
+@pytest.fixture
+def e4m3_operand(monkeypatch):
+    """The persistent kernel with the e4m3 operand widened per tile."""
+    monkeypatch.setenv("SI_TC_J_E4M3", "1")
+
+
 @pytest.mark.parametrize("tile_n", [64, 128])
-def test_widened_coupling_read_back_through_one_step(tile_n):
+def test_widened_coupling_read_back_through_one_step(tile_n, e4m3_operand):
     """One step from q_r = e_r / 2 (replica r displaced at spin r only, exact
     in bf16): F_ir = J_ir / 2 exactly, so the new momenta read J back column
     by column.  FP8 storage must give the bf16-storage result bit for bit,
@@ -79,7 +88,7 @@ def test_widened_coupling_read_back_through_one_step(tile_n):
 
 
 @pytest.mark.parametrize("n,R,tile_n", [(300, 40, 64), (300, 40, 128), (129, 17, 0)])
-def test_fp8_storage_equals_bf16_storage_every_code(n, R, tile_n):
+def test_fp8_storage_equals_bf16_storage_every_code(n, R, tile_n, e4m3_operand):
     J = _all_codes_coupling(n, seed=n)
     T = 15
     zeta, dt = np.full(T, ZETA_SMALL, np.float32), inputs.dt_const(T)
@@ -97,7 +106,7 @@ def test_fp8_storage_equals_bf16_storage_every_code(n, R, tile_n):
         np.testing.assert_array_equal(a_, b_)
 
 
-def test_fp8_storage_equals_bf16_storage_full_workload_shape():
+def test_fp8_storage_equals_bf16_storage_full_workload_shape(e4m3_operand):
     """N=2000, R=1024 (the batched workload's shape and tile), 50 steps."""
     n, R, T = 2000, 1024, 50
     J = inputs.pm1_coupling(n, seed=1)
@@ -115,7 +124,7 @@ def test_fp8_storage_equals_bf16_storage_full_workload_shape():
 
 
 @pytest.mark.parametrize("n,R", [(17, 1), (300, 100), (2001, 130)])
-def test_exact_readout_from_e4m3_storage(n, R):
+def test_exact_readout_from_e4m3_storage(n, R, e4m3_operand):
     """The tensor-core exact readout widens the e4m3 tiles too: integer J
     (values +-3, e4m3-exact) with an integer field, against the oracle."""
     J = inputs.pm1_coupling(n, seed=n) * 3
@@ -128,7 +137,7 @@ def test_exact_readout_from_e4m3_storage(n, R):
     np.testing.assert_array_equal(c, oracle.cut(J, s).astype(np.int64))
 
 
-@pytest.mark.parametrize("policy", [0, 1, 2, 3])
+@pytest.mark.parametrize("policy", [0, 1, 2, 3, 4])
 def test_group_fp8_members_equal_bf16_members(policy, monkeypatch):
     """Grouped kernel: the same members stored as e4m3 and as bf16 give
     bit-identical runs under every tile policy (mixed with a Gaussian bf16
@@ -149,3 +158,11 @@ def test_group_fp8_members_equal_bf16_members(policy, monkeypatch):
     for arrs_a, arrs_b in zip(res["j_fp8_q_bf16"], res["j_bf16_q_bf16"]):
         for x, y in zip(arrs_a, arrs_b):
             np.testing.assert_array_equal(x, y)
+
+
+def test_persistent_kernel_keeps_a_bf16_operand_by_default():
+    J = inputs.pm1_coupling(300, seed=4)
+    with b.Context(J, replicas=64, steps=1, prec="j_fp8_q_bf16") as c:
+        assert "J=bf16(2B)" in c.describe()
+    with b.Group([J], None, replicas=[64], steps=1, precs=["j_fp8_q_bf16"]) as g:
+        assert "jbytes/step" in g.describe()

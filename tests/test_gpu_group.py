@@ -24,7 +24,7 @@ def _build(members, seed=0):
     return Js, hs, qs
 
 
-@pytest.mark.parametrize("policy", [0, 1, 2, 3])
+@pytest.mark.parametrize("policy", [0, 1, 2, 3, 4])
 def test_group_per_step_within_bf16_bound(policy, monkeypatch):
     """Every tile policy (replica blocks of 64 / 128, whole-instance tiles in
     one accumulator) takes the same step within the bf16 bound."""
@@ -37,7 +37,7 @@ def test_group_per_step_within_bf16_bound(policy, monkeypatch):
     precs = ["j_fp8_q_bf16" if kind == "pm1" else "j_bf16_q_bf16" for (_, _, kind) in members]
     with b.Group(Js, hs, replicas=[R for (_, R, _) in members], steps=1, precs=precs) as g:
         assert "grouped" in g.describe()
-        names = ["bn64-if-R<=64-else-128", "all-64", "all-128", "whole-instance"]
+        names = ["bn64-if-R<=64-else-128", "all-64", "all-128", "whole-instance", "whole-instance-tmem-a"]
         p0 = b.default_params()
         kw = dict(k=float(p0.k), m=float(p0.m), q0=float(p0.q0), q_max=float(np.float32(p0.q_max)),
                   p_max=float(p0.p_max))
@@ -171,7 +171,7 @@ def test_autotune_cache_persists_across_processes(tmp_path):
     assert len(lines) == 1
     key, pol = lines[0].rsplit(" ", 1)
     assert "96x48" in key and "160x80" in key
-    names = ["bn64-if-R<=64-else-128", "all-64", "all-128", "whole-instance"]
+    names = ["bn64-if-R<=64-else-128", "all-64", "all-128", "whole-instance", "whole-instance-tmem-a"]
     assert "policy=" + names[int(pol)] in out1.stdout
     other = (int(pol) + 1) % 4
     cache.write_text("%s %d\n" % (key, other))

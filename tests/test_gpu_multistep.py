@@ -41,11 +41,13 @@ def _assert_same(a, b_, what):
     np.testing.assert_array_equal(sa, sb, err_msg=what + ": spins")
 
 
-@pytest.mark.parametrize("n,R,T,tile_n", [(2000, 1024, 64, 0), (2001, 130, 33, 64), (2001, 130, 33, 128),
-                                          (300, 17, 21, 64)])
-def test_tc_run_equals_chained_single_steps(n, R, T, tile_n):
+@pytest.mark.parametrize("n,R,T,tile_n,e4", [(2000, 1024, 64, 0, 0), (2001, 130, 33, 64, 0), (2001, 130, 33, 128, 0),
+                                             (300, 17, 21, 64, 0), (2001, 130, 33, 64, 1), (2001, 130, 33, 128, 1)])
+def test_tc_run_equals_chained_single_steps(n, R, T, tile_n, e4, monkeypatch):
     """k_tc_run over T steps in one launch == T launches of one step each,
-    restarted from the host outputs (both replica tiles, ragged n and R)."""
+    restarted from the host outputs (both replica tiles, ragged n and R; also
+    with the e4m3 J operand widened into tensor memory, e4=1)."""
+    monkeypatch.setenv("SI_TC_J_E4M3", str(e4))
     J = inputs.pm1_coupling(n, seed=1)
     zeta = inputs.zeta_ramp(2000)[1000:1000 + T]   # the middle of the workload's ramp
     dt = inputs.dt_const(T)
@@ -157,7 +159,7 @@ def test_fp64_equals_chained_single_steps(n, R):
     _assert_same((q_full, p_full, s_full), (q_ch, p_ch, s), "fp64 n=%d R=%d" % (n, R))
 
 
-@pytest.mark.parametrize("policy", [0, 1, 2, 3])
+@pytest.mark.parametrize("policy", [0, 1, 2, 3, 4])
 def test_grouped_graph_equals_chained_single_steps(policy, monkeypatch):
     """The captured graph of T grouped steps == T one-step group runs restarted
     from the outputs, over a mixed member list (+-1 and Gaussian, ragged n and
