@@ -692,7 +692,8 @@ def ncu_case_grouped(args):
     specs = inputs.uneven_instances(256)[:args.group_count]
     Js = [inputs.instance_coupling_torch(sp, dev) for sp in specs]
     qs = [inputs.positions_torch(sp.n, sp.replicas, seed=9000 + sp.index, device=dev) for sp in specs]
-    precs = ["j_fp8_q_bf16" if sp.kind == "pm1" else "j_bf16_q_bf16" for sp in specs]
+    pm1 = "j_fp8_q_bf16" if args.pm1_storage == "e4m3" else "j_bf16_q_bf16"
+    precs = [pm1 if sp.kind == "pm1" else "j_bf16_q_bf16" for sp in specs]
     T = args.time_steps
     zeta = torch.from_numpy(inputs.zeta_ramp(T)).to(dev)
     dt = torch.from_numpy(inputs.dt_const(T)).to(dev)
@@ -805,9 +806,11 @@ SPARSE_L, SPARSE_R, SPARSE_T = 128, 512, 1000
 def run_sparse(args):
     """Sparse topology: a king graph on a 128 x 128 grid (N = 16384, open
     boundaries, +-1 couplings, banded J), R=512, T=1000, as a one-member
-    group whose all-zero 128 x 64 blocks of J are never loaded.  HBM roofline
-    on the algorithmic bytes: the non-zero blocks once (e4m3-exact, 1 B) plus
-    the state."""
+    group whose all-zero 128 x 64 blocks of J are never loaded.  J is stored
+    as bf16 (exact for +-1): with so few J blocks the step is bound by the
+    state traffic, and e4m3 storage would only add the widening work.  HBM
+    roofline on the algorithmic bytes: the non-zero blocks once (2 B per
+    element) plus the state."""
     import torch
 
     from paper_2305_07187_gb300 import _binding as b
@@ -824,7 +827,7 @@ def run_sparse(args):
     zeta = torch.from_numpy(inputs.zeta_ramp(T)).to(dev)
     dt = torch.from_numpy(inputs.dt_const(T)).to(dev)
     stream = torch.cuda.current_stream(dev)
-    g = b.Group([J], None, replicas=[R], steps=T, precs=["j_fp8_q_bf16"], stream=stream.cuda_stream)
+    g = b.Group([J], None, replicas=[R], steps=T, precs=["j_bf16_q_bf16"], stream=stream.cuda_stream)
     del J
     torch.cuda.empty_cache()
     spins = [torch.empty((R, n), dtype=torch.int8, device=dev)]
@@ -855,7 +858,7 @@ def run_sparse(args):
     g.close()
     ms = sum(step_ms) / len(step_ms)
     k_ms = sum(kern_ms) / len(kern_ms)
-    bytes_step = nz_blocks * 128 * 64 * 1 + R * n * (16 + 4)
+    bytes_step = nz_blocks * 128 * 64 * 2 + R * n * (16 + 4)
     peaks, src = load_peaks()
     achieved = bytes_step * T / (k_ms * 1e-3) / 1e9
     peak = float(peaks.get("hbm_gbs", 6800.0))
@@ -1042,6 +1045,8 @@ def main():
                     help="profiling case: one warm-up and one si_run of the batched "
                          "workload with --time-steps steps, no timing output")
     ap.add_argument("--time-steps", type=int, default=T_STEPS)
+    ap.add_argument("--pm1-storage", default="bf16", choices=["bf16", "e4m3"],
+                    help="grouped profiling case: storage of the +-1 members' J")
     ap.add_argument("--group-count", type=int, default=256,
                     help="grouped workload: number of instances (profiling uses a prefix)")
     ap.add_argument("--workload", default="batched", choices=["batched", "plain", "grouped", "scale", "grad", "study", "sparse"],

@@ -37,11 +37,11 @@
 namespace si {
 
 constexpr int GR_BM = 128, GR_BK = 64;
-// Warps: producer, 2 MMA issuers, EPI epilogue warps (EPI / 4 per TMEM lane
-// quadrant), then 4 converter warps (e4m3 J tiles).
-template <int EPI>
-constexpr int gr_threads() { return 32 * (3 + EPI + 4); }
-constexpr int GR_EPI_DEFAULT = 12;
+// Warps: producer, 2 MMA issuers, GR_EPI epilogue warps (three per TMEM lane
+// quadrant), then, in groups with e4m3 members (CONV), 4 converter warps.
+constexpr int GR_EPI = 12;
+template <bool CONV>
+constexpr int gr_threads() { return 32 * (3 + GR_EPI + (CONV ? 4 : 0)); }
 constexpr int GR_A_BYTES = GR_BM * GR_BK * 2;
 constexpr int GR_SMAX = 8;                       // most ring stages of any policy
 constexpr int GR_TILES = 196608;                 // shared memory for the ring
@@ -87,8 +87,8 @@ struct GroupArgs {
     int stage_bytes;           // A tile + largest B tile of the policy (multiple of 1024)
 };
 
-template <int GR_EPI>
-__global__ void __launch_bounds__(gr_threads<GR_EPI>(), 1) k_group_step(const __grid_constant__ GroupArgs a) {
+template <bool CONV>
+__global__ void __launch_bounds__(gr_threads<CONV>(), 1) k_group_step(const __grid_constant__ GroupArgs a) {
     constexpr int GR_CONV_WARP0 = 3 + GR_EPI;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(gr_threads<GR_EPI>(), 1) k_group_step(const __
                         for (int kb = 0; kb < tl.kb_cnt; ++kb) {
                             const int s = ring_stage(rk, 0);
                             if (!mbar_wait(full_bar(s), rph, a.err, abort_flag, a.limit_ns) ||
-                                !mbar_wait(conv_bar(s), rph, a.err, abort_flag, a.limit_ns)) {
+                                (CONV && !mbar_wait(conv_bar(s), rph, a.err, abort_flag, a.limit_ns))) {
                                 ok = false;
                                 break;
                             }
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(gr_threads<GR_EPI>(), 1) k_group_step(const __
                     for (int kb = w; kb < tl.kb_cnt; kb += 2) {
                         const int s = ring_stage(rk, w);
                         if (!mbar_wait(full_bar(s), rph, a.err, abort_flag, a.limit_ns) ||
-                            !mbar_wait(conv_bar(s), rph, a.err, abort_flag, a.limit_ns)) {
+                            (CONV && !mbar_wait(conv_bar(s), rph, a.err, abort_flag, a.limit_ns))) {
                             ok = false;
                             break;
                         }
@@ -362,7 +362,7 @@ __global__ void __launch_bounds__(gr_threads<GR_EPI>(), 1) k_group_step(const __
             __syncwarp();
             if (lane == 0) mbar_arrive(tmem_empty_bar(slot));
         }
-    } else {
+    } else if constexpr (CONV) {
         // ---------------------------------------------- converters (4 warps)
         // Walk the stages in the producer's order.  Every use of a stage is
         // released to the MMA warp through conv_bar, after its e4m3 J tile
@@ -478,7 +478,6 @@ struct Group {
     int *h_err = nullptr;   // pinned host copy of the error word
     int policy = -1;            // chosen tile policy
     bool any_e4m3 = false;      // some member stores J as e4m3
-    int epi = 12;               // epilogue warps of the step kernel (8 or 12)
     int grid = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_steps = -1;
@@ -783,8 +782,8 @@ static si_status group_launch_step(Group *g, int t, int steps) {
     a.nslots = g->policy == kPolicyWholeTmemA ? 1 : 2;
     a.stages = g->pol_stages[g->policy];
     a.stage_bytes = g->pol_stage_bytes[g->policy];
-    if (g->epi == 8) k_group_step<8><<<g->grid, gr_threads<8>(), GR_SMEM, g->stream>>>(a);
-    else k_group_step<12><<<g->grid, gr_threads<12>(), GR_SMEM, g->stream>>>(a);
+    if (g->any_e4m3) k_group_step<true><<<g->grid, gr_threads<true>(), GR_SMEM, g->stream>>>(a);
+    else k_group_step<false><<<g->grid, gr_threads<false>(), GR_SMEM, g->stream>>>(a);
     SI_CUDA_TRY(cudaGetLastError());
     return SI_OK;
 }
@@ -1042,16 +1041,17 @@ static si_status group_create_impl(Group *g, const si_params *prm, const float *
         x.energy.derr = g->d_err;
         x.energy.spin_limit_ns = g->limit_ns;
     }
-    g->epi = GR_EPI_DEFAULT;
-    if (const char *e = std::getenv("SI_GROUP_EPI")) g->epi = std::atoi(e) == 8 ? 8 : 12;
-    SI_CUDA_TRY(cudaFuncSetAttribute(k_group_step<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, GR_SMEM));
-    SI_CUDA_TRY(cudaFuncSetAttribute(k_group_step<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, GR_SMEM));
+    // the converter warps exist only in groups with e4m3 members
     int per_sm = 0;
-    if (g->epi == 8)
-        SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_step<8>, gr_threads<8>(), GR_SMEM));
-    else
+    if (g->any_e4m3) {
+        SI_CUDA_TRY(cudaFuncSetAttribute(k_group_step<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, GR_SMEM));
         SI_CUDA_TRY(
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_step<12>, gr_threads<12>(), GR_SMEM));
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_step<true>, gr_threads<true>(), GR_SMEM));
+    } else {
+        SI_CUDA_TRY(cudaFuncSetAttribute(k_group_step<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, GR_SMEM));
+        SI_CUDA_TRY(
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_group_step<false>, gr_threads<false>(), GR_SMEM));
+    }
     if (per_sm < 1) {
         set_error("grouped step kernel does not fit on an SM");
         return SI_ERR_UNSUPPORTED;
