@@ -3,8 +3,10 @@
 // One persistent launch runs all T steps.  CTA (mt, rb) owns the output tile
 // F[mt*128 .. +128][rb*BN .. +BN] of F = J Q^T (rows = spins, columns =
 // replicas) for the whole run:
-//   warp 0      TMA producer: J tile (128 x 64 bf16) and q tile (BN x 64 bf16)
-//               per K block into an S-stage shared-memory ring (128B swizzle)
+//   warp 0      TMA producers in lanes 0 and 1: J tile (128 x 64 bf16) and q
+//               tile (BN x 64 bf16) per K block into the two halves of an
+//               S-stage shared-memory ring (128B swizzle), lane 0 the even
+//               and lane 1 the odd positions of the K loop
 //   warps 1, 2  issue tcgen05.mma (M=128, N=BN, K=16) for alternating K
 //               blocks into two FP32 accumulators in TMEM (warp 1 also
 //               allocates TMEM)
@@ -32,9 +34,12 @@ namespace si {
 constexpr int TC_BM = 128;       // spins per CTA (MMA M)
 constexpr int TC_BK = 64;        // K elements per stage (128 bytes of bf16)
 // Threads: producer warp, 2 MMA-issuing warps, EPI epilogue warps (4 or 8),
-// and with e4m3 J storage four converter warps.
+// with e4m3 J storage four converter warps, and the warp that mirrors the
+// owners' step flags into shared memory.
 template <int EPI, bool E4>
-constexpr int tc_threads() { return 32 * (3 + EPI + (E4 ? 4 : 0)); }
+constexpr int tc_threads() { return 32 * (4 + EPI + (E4 ? 4 : 0)); }
+template <int EPI, bool E4>
+constexpr int tc_poll_warp() { return 3 + EPI + (E4 ? 4 : 0); }
 constexpr int TC_A_BYTES = TC_BM * TC_BK * 2;
 
 struct TcArgs {
@@ -79,7 +84,8 @@ struct TcSmem {
     static constexpr int NA = E4 ? 4 : 0;                 // A slots in tensor memory (two per MMA warp)
     // full[S], empty[S], accf, tmem_empty, epi_done, drain, afull[NA], aempty[NA]
     static constexpr int NBARS = 2 * S + 4 + 2 * NA;
-    static constexpr int TOTAL = BARS + NBARS * 8 + 16;   // + tmem slot, abort flag
+    static constexpr int SEEN = BARS + NBARS * 8 + 16;     // after the tmem slot and abort flag
+    static constexpr int TOTAL = SEEN + 64 * 4;            // mirrored step flags of up to 64 owners
     static constexpr int TMEM_COLS = (E4 || 4 * BN > 256) ? 512 : 256;
 };
 
@@ -89,7 +95,7 @@ constexpr int TC_EPI_WARP0 = 1 + TC_MMA_WARPS;             // first epilogue war
 // EPI: epilogue warps (8 in both tile instantiations; a CTA that allocates
 // tensor memory occupies its SM alone, so a lighter CTA buys no second CTA).
 template <int BN, int S, int EPI, bool E4>
-__global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
+__global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
     k_tc_run(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
              TcArgs a) {
     using L = TcSmem<BN, S, E4>;
@@ -116,6 +122,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
     auto aempty_bar = [&](int k) { return bar0 + 8u * (2 * S + 4 + L::NA + k); };
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::BARS + L::NBARS * 8);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::BARS + L::NBARS * 8 + 4);
+    const uint32_t seen = sbase + L::SEEN;   // mirrored step flags of the owners
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt = blockIdx.x % a.mtiles, rb = blockIdx.x / a.mtiles;
@@ -139,6 +146,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
         mbar_init(epi_done_bar, EPI);
         mbar_init(drain_bar, TC_MMA_WARPS);
         *abort_flag = 0;
+        for (int o = 0; o < 64; ++o) reinterpret_cast<unsigned *>(smem + L::SEEN)[o] = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
@@ -157,99 +165,74 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), EPI == 4 ? 2 : 1)
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
-        // ------------------------------------------------ TMA producer (whole warp)
+        // ------------------------------------------------ TMA producers (lanes 0 and 1)
         // Step t needs the positions q(t) of its replica block.  The K block kb
         // (spins 64kb .. 64kb+63) of q(t) is written by the CTA owning M tile
         // kb/2 at the end of its step t-1 and announced through that CTA's flag
-        // (number of steps published).  The K loop starts at this CTA's own
-        // rows and the warp polls all owners' flags in parallel only when the
-        // next block's owner is not yet known to be ready.  J tiles do not
-        // depend on the step and are issued before the wait.
-        // Stages are split into two rings, the even stages consumed only by
-        // MMA warp 1 (even positions of the K loop) and the odd stages only by
-        // warp 2, so that every stage has one in-order consumer and no waiter
-        // can run two phases ahead of a stage's barrier.
+        // (number of steps published), which the poller warp mirrors into
+        // shared memory.  The K loop starts at this CTA's own rows; the copy
+        // is read only when the next block's owner is not yet known to be
+        // ready.  J tiles do not depend on the step and are issued before the
+        // wait.
+        // Stages are split into two rings, the even stages filled by lane 0
+        // for the even positions of the K loop and consumed only by MMA warp
+        // 1, the odd stages filled by lane 1 and consumed only by MMA warp 2,
+        // so that every stage has one in-order producer and consumer and no
+        // waiter can run two phases ahead of a stage's barrier.  One thread's
+        // chain of barrier wait, arming and two TMA instructions per K block
+        // takes about as long as the K block's MMAs; the two lanes run that
+        // chain side by side (positions 2i and 2i+1, whose q blocks have the
+        // same owner), so a K block costs half of it.
         constexpr int HS = S / 2;
         static_assert(S % 2 == 0, "stage count must be even");
-        uint32_t cnt0 = 0u, cnt1 = 0u;   // stages armed in ring 0 / ring 1
-        bool ok = true;
-        const int kb0 = mt * (TC_BM / TC_BK);
-        const unsigned *flags = a.bar + (size_t)rb * a.mtiles;
-        for (int t = 0; t < a.steps && ok; ++t) {
-            uint32_t ready0 = 0u, ready1 = 0u;
-            if (t == 0) ready0 = ready1 = 0xffffffffu;
-            const int yb = (t & 1) * a.rpad + r0;
-            for (int j = 0; j < a.kblocks; ++j) {
-                int kb = kb0 + j;
-                if (kb >= a.kblocks) kb -= a.kblocks;
-                const int ring = j & 1;
-                const uint32_t c = ring ? cnt1 : cnt0;
-                const int s = 2 * (int)(c % HS) + ring;
-                const uint32_t ph = (c / HS) & 1u;
-                const uint32_t dA = sbase + s * L::STAGE_BYTES;
-                const uint32_t dB = dA + L::A_STAGE;
-                int okw = 1;
-                if (lane == 0) {
-                    okw = mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns) ? 1 : 0;
-                    if (okw) {
-                        mbar_arrive_expect_tx(full_bar(s), (uint32_t)L::TX_BYTES);
-                        tma_load_2d(dA, &mapA, full_bar(s), kb * TC_BK, m0);
+        if (lane < 2) {
+            const int ring = lane;
+            uint32_t cnt = 0u;   // stages armed in this ring
+            bool ok = true;
+            const int kb0 = mt * (TC_BM / TC_BK);
+            for (int t = 0; t < a.steps && ok; ++t) {
+                unsigned long long ready = t == 0 ? ~0ull : 0ull;   // owners known to have published step t
+                const unsigned need = (unsigned)t + (t == a.stall_step ? 1000000u : 0u);
+                const int yb = (t & 1) * a.rpad + r0;
+                for (int j = ring; j < a.kblocks; j += 2) {
+                    int kb = kb0 + j;
+                    if (kb >= a.kblocks) kb -= a.kblocks;
+                    const int s = 2 * (int)(cnt % HS) + ring;
+                    const uint32_t ph = (cnt / HS) & 1u;
+                    const uint32_t dA = sbase + s * L::STAGE_BYTES;
+                    if (!mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                    mbar_arrive_expect_tx(full_bar(s), (uint32_t)L::TX_BYTES);
+                    tma_load_2d(dA, &mapA, full_bar(s), kb * TC_BK, m0);
+                    ++cnt;
+                    const int mo = kb >> 1;
+                    bool have = ((ready >> mo) & 1ull) != 0ull;
+                    if (!have) {
+                        have = wait_owner(seen, mo, need, a.err, abort_flag, a.limit_ns);
+                        if (have) ready |= 1ull << mo;
                     }
+                    // The q tile is issued even on abort so that the stage's
+                    // transaction count completes and the drain below ends.
+                    tma_load_2d(dA + L::A_STAGE, &mapB, full_bar(s), kb * TC_BK, yb);
+                    if (!have) { ok = false; break; }
                 }
-                okw = __shfl_sync(0xffffffffu, okw, 0);
-                if (!okw) { ok = false; break; }
-                if (ring) ++cnt1; else ++cnt0;
-                const int mo = kb >> 1;
-                bool have = mo < 32 ? ((ready0 >> mo) & 1u) != 0u : ((ready1 >> (mo - 32)) & 1u) != 0u;
-                if (!have) {
-                    const unsigned long long t0 = globaltimer_ns();
-                    for (unsigned pit = 1;; ++pit) {
-                        bool r_lo = false, r_hi = false;
-                        const unsigned need = (unsigned)t + (t == a.stall_step ? 1000000u : 0u);
-                        if (lane < a.mtiles) r_lo = (int)(ld_acquire_gpu(flags + lane) - need) >= 0;
-                        if (lane + 32 < a.mtiles) r_hi = (int)(ld_acquire_gpu(flags + lane + 32) - need) >= 0;
-                        ready0 |= __ballot_sync(0xffffffffu, r_lo);
-                        ready1 |= __ballot_sync(0xffffffffu, r_hi);
-                        have = mo < 32 ? ((ready0 >> mo) & 1u) != 0u : ((ready1 >> (mo - 32)) & 1u) != 0u;
-                        if (have) break;
-                        int stop = 0;
-                        if (lane == 0 && (pit & 7u) == 0u) {
-                            if (*abort_flag || ld_volatile_int(a.err) != 0) {
-                                stop = 1;
-                            } else if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
-                                atomicCAS(a.err, 0, DEV_TIMEOUT_BARRIER);
-                                stop = 1;
-                            }
-                            if (stop) *abort_flag = 1;
-                        }
-                        if (__shfl_sync(0xffffffffu, stop, 0)) break;
-                    }
-                    // Order this lane's TMA after the other lanes' acquire loads.
-                    __syncwarp();
-                    if (lane == 0) fence_proxy_async_global();
-                }
-                // The q tile is issued even on abort so that the stage's
-                // transaction count completes and the drain below ends.
-                if (lane == 0) tma_load_2d(dB, &mapB, full_bar(s), kb * TC_BK, yb);
-                if (!have) { ok = false; break; }
             }
-        }
-        // Let every copy this warp issued land before the CTA exits.
-        if (lane == 0) {
-            for (int ring = 0; ring < 2; ++ring) {
-                const uint32_t cr = ring ? cnt1 : cnt0;
-                const uint32_t first = cr > (uint32_t)HS ? cr - HS : 0u;
-                for (uint32_t k = first; k < cr; ++k) {
-                    const unsigned long long t0 = globaltimer_ns();
-                    while (!mbar_try_wait(full_bar(2 * (int)(k % HS) + ring), (k / HS) & 1u)) {
-                        if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
-                            atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
-                            break;
-                        }
+            // Let every copy this thread issued land before the CTA exits.
+            const uint32_t first = cnt > (uint32_t)HS ? cnt - HS : 0u;
+            for (uint32_t k = first; k < cnt; ++k) {
+                const unsigned long long t0 = globaltimer_ns();
+                while (!mbar_try_wait(full_bar(2 * (int)(k % HS) + ring), (k / HS) & 1u)) {
+                    if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                        atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
+                        break;
                     }
                 }
             }
         }
+    } else if (warp == tc_poll_warp<EPI, E4>()) {
+        // ------------------------------------------------ step-flag mirror
+        if (a.steps > 1)
+            mirror_flags(a.bar + (size_t)rb * a.mtiles, a.mtiles, (unsigned)(a.steps - 1), seen, lane, a.err,
+                         abort_flag, a.limit_ns);
     } else if (warp <= TC_MMA_WARPS) {
         // ------------------------------------------------ MMA issuers
         // Warp 1 takes the even positions of the K loop into accumulator 0,

@@ -71,6 +71,90 @@ __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
+__device__ __forceinline__ unsigned ld_acquire_cta_shared(uint32_t addr) {
+    unsigned v;
+    asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_cta_shared(uint32_t addr, unsigned v) {
+    asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// Step flags of the CTAs that own the q blocks of a replica block, mirrored
+// into shared memory by one warp of the consuming CTA (mirror_flags), so that
+// the TMA producers test a shared-memory word instead of polling global
+// memory on their critical path.  Lane o (and o + 32) reads owner o's flag
+// with an acquire load, all lanes at once (one memory round trip per sweep),
+// and stores every new value with a release store; a producer that reads the
+// copy with an acquire load is then ordered after the owner's published q
+// block (the two synchronisations compose).  The warp stops once every owner
+// has published `last` steps, when the run is being aborted, or when no flag
+// has moved for limit_ns (the waiting producer raises the error then).
+__device__ __forceinline__ void mirror_flags(const unsigned *flags, int nown, unsigned last, uint32_t seen,
+                                             int lane, int *err, volatile int *abort_flag, long long limit_ns) {
+    unsigned m0 = 0u, m1 = 0u;   // last values mirrored by this lane
+    unsigned long long t_last = globaltimer_ns();
+    for (unsigned it = 1;; ++it) {
+        bool moved = false, done = true;
+        if (lane < nown) {
+            const unsigned v = ld_acquire_gpu(flags + lane);
+            if (v != m0) {
+                st_release_cta_shared(seen + 4u * lane, v);
+                m0 = v;
+                moved = true;
+            }
+            done = (int)(v - last) >= 0;
+        }
+        if (lane + 32 < nown) {
+            const unsigned v = ld_acquire_gpu(flags + lane + 32);
+            if (v != m1) {
+                st_release_cta_shared(seen + 4u * (lane + 32), v);
+                m1 = v;
+                moved = true;
+            }
+            done = done && (int)(v - last) >= 0;
+        }
+        if (__all_sync(0xffffffffu, done)) return;
+        const unsigned long long now = globaltimer_ns();
+        if (__any_sync(0xffffffffu, moved)) t_last = now;
+        if ((it & 7u) == 0u) {
+            int stop = 0;
+            if (lane == 0) stop = (*abort_flag || ld_volatile_int(err) != 0) ? 1 : 0;
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            if (stop || (long long)(now - t_last) > limit_ns) return;
+        }
+    }
+}
+
+// A producer's bounded wait until the mirrored flag of owner mo shows step
+// `need` (acquire load of the shared copy), followed by the proxy fence that
+// orders its next TMA loads after the published data.  Returns false on
+// abort or timeout (raising DEV_TIMEOUT_BARRIER).
+__device__ __forceinline__ bool wait_owner(uint32_t seen, int mo, unsigned need, int *err,
+                                           volatile int *abort_flag, long long limit_ns) {
+    const uint32_t addr = seen + 4u * (uint32_t)mo;
+    if ((int)(ld_acquire_cta_shared(addr) - need) < 0) {
+        const unsigned long long t0 = globaltimer_ns();
+        for (unsigned it = 1;; ++it) {
+            if ((int)(ld_acquire_cta_shared(addr) - need) >= 0) break;
+            if ((it & 15u) == 0u) {
+                if (*abort_flag || ld_volatile_int(err) != 0) {
+                    *abort_flag = 1;
+                    return false;
+                }
+                if ((long long)(globaltimer_ns() - t0) > limit_ns) {
+                    atomicCAS(err, 0, DEV_TIMEOUT_BARRIER);
+                    *abort_flag = 1;
+                    return false;
+                }
+            }
+        }
+    }
+    fence_proxy_async_global();
+    return true;
+}
+
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
