@@ -66,15 +66,19 @@ __device__ __forceinline__ bool grid_barrier(unsigned *ctr, unsigned target, int
 // order 1 (Eq. 5): both from the old state.
 // Walls (Eq. 6): clamp q to [-q_max, q_max], p to [-p_max, p_max]; with
 // wall_zero_p the momentum of a clipped spin is set to zero.
-template <typename T>
+// MODE 1 is the same arithmetic with order 0 and wall_zero_p off fixed at
+// compile time (for loops that test those parameters once, outside).
+template <typename T, int MODE = 0>
 __device__ __forceinline__ void integrate(T q, T p, T F, T zeta, T dt, T dtm,
                                           const StepParams &sp, T &q_out, T &p_out) {
     const T k = (T)sp.k, q0 = (T)sp.q0, qmax = (T)sp.q_max, pmax = (T)sp.p_max;
+    const int order = MODE == 1 ? 0 : sp.order;
+    const bool wall_zero_p = MODE == 1 ? false : sp.wall_zero_p != 0;
     T a = p + dt * (-k * (q - q0) + zeta * F);
-    T b = q + dtm * (sp.order == 0 ? fmin(fmax(a, -pmax), pmax) : p);
+    T b = q + dtm * (order == 0 ? fmin(fmax(a, -pmax), pmax) : p);
     T pn = fmin(fmax(a, -pmax), pmax);
     T qn = fmin(fmax(b, -qmax), qmax);
-    if (sp.wall_zero_p && qn != b) pn = (T)0;
+    if (wall_zero_p && qn != b) pn = (T)0;
     q_out = qn;
     p_out = pn;
 }

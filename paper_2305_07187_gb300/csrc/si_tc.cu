@@ -24,6 +24,7 @@
 // raises the device error word, drains its own copies and MMAs, frees TMEM
 // and returns.
 #include <algorithm>
+#include <type_traits>
 #include <cstdio>
 #include <cstdlib>
 
@@ -85,7 +86,7 @@ struct TcSmem {
     // full[S], empty[S], accf, tmem_empty, epi_done, drain, afull[NA], aempty[NA]
     static constexpr int NBARS = 2 * S + 4 + 2 * NA;
     static constexpr int SEEN = BARS + NBARS * 8 + 16;     // after the tmem slot and abort flag
-    static constexpr int TOTAL = SEEN + 64 * 4;            // mirrored step flags of up to 64 owners
+    static constexpr int TOTAL = SEEN + 68 * 4;            // mirrored step flags of up to 64 owners, their minimum
     static constexpr int TMEM_COLS = (E4 || 4 * BN > 256) ? 512 : 256;
 };
 
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
         mbar_init(epi_done_bar, EPI);
         mbar_init(drain_bar, TC_MMA_WARPS);
         *abort_flag = 0;
-        for (int o = 0; o < 64; ++o) reinterpret_cast<unsigned *>(smem + L::SEEN)[o] = 0u;
+        for (int o = 0; o <= MIRROR_MIN; ++o) reinterpret_cast<unsigned *>(smem + L::SEEN)[o] = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
@@ -206,10 +207,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                     ++cnt;
                     const int mo = kb >> 1;
                     bool have = ((ready >> mo) & 1ull) != 0ull;
-                    if (!have) {
-                        have = wait_owner(seen, mo, need, a.err, abort_flag, a.limit_ns);
-                        if (have) ready |= 1ull << mo;
-                    }
+                    if (!have) have = wait_owner(seen, mo, need, ready, a.err, abort_flag, a.limit_ns);
                     // The q tile is issued even on abort so that the stage's
                     // transaction count completes and the drain below ends.
                     tma_load_2d(dA + L::A_STAGE, &mapB, full_bar(s), kb * TC_BK, yb);
@@ -346,6 +344,12 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
             const float zt = a.zeta[t], dtt = a.dt[t];
             const float dtm = dtt / a.sp.m;
             const bool last = (t == a.steps - 1);
+            // The chunk loop, instantiated once with the update order and the
+            // wall variant as run-time parameters and once for the default
+            // (kick-drift, no momentum zeroing) so that the integrator does
+            // not test them per element.
+            auto chunks = [&](auto mode_tag) {
+            constexpr int MODE = decltype(mode_tag)::value;
 #pragma unroll 1
             for (int c = c_begin; c < c_begin + CPH; ++c) {
                 uint32_t vf[32], vp[32], vq[32];
@@ -369,8 +373,8 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                 for (int j = 0; j < 32; ++j) {
                     const float F = __uint_as_float(vf[j]);
                     float qo, po;
-                    integrate<float>(__uint_as_float(vq[j]), __uint_as_float(vp[j]), F + hi, zt, dtt,
-                                     dtm, a.sp, qo, po);
+                    integrate<float, MODE>(__uint_as_float(vq[j]), __uint_as_float(vp[j]), F + hi, zt, dtt,
+                                           dtm, a.sp, qo, po);
                     vq[j] = __float_as_uint(qo);
                     vp[j] = __float_as_uint(po);
                 }
@@ -383,16 +387,29 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                 }
                 if (!last) {
                     // bf16 copy into the staging tile (zeros outside n x R).
+                    if (row_ok && r0 + c * 32 + 32 <= a.R) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int rl = c * 32 + j;
-                        const bool ok2 = row_ok && (r0 + rl) < a.R;
-                        const __nv_bfloat16 v = __float2bfloat16_rn(ok2 ? __uint_as_float(vq[j]) : 0.f);
-                        const uint32_t addr = st_base + (uint32_t)rl * 128u +
-                                              ((uint32_t)(((kq >> 3) ^ (rl & 7)) << 4));
-                        asm volatile("st.shared.b16 [%0], %1;" ::"r"(addr),
-                                     "h"(*reinterpret_cast<const unsigned short *>(&v))
-                                     : "memory");
+                        for (int j = 0; j < 32; ++j) {
+                            const int rl = c * 32 + j;
+                            const __nv_bfloat16 v = __float2bfloat16_rn(__uint_as_float(vq[j]));
+                            const uint32_t addr = st_base + (uint32_t)rl * 128u +
+                                                  ((uint32_t)(((kq >> 3) ^ (rl & 7)) << 4));
+                            asm volatile("st.shared.b16 [%0], %1;" ::"r"(addr),
+                                         "h"(*reinterpret_cast<const unsigned short *>(&v))
+                                         : "memory");
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int rl = c * 32 + j;
+                            const bool ok2 = row_ok && (r0 + rl) < a.R;
+                            const __nv_bfloat16 v = __float2bfloat16_rn(ok2 ? __uint_as_float(vq[j]) : 0.f);
+                            const uint32_t addr = st_base + (uint32_t)rl * 128u +
+                                                  ((uint32_t)(((kq >> 3) ^ (rl & 7)) << 4));
+                            asm volatile("st.shared.b16 [%0], %1;" ::"r"(addr),
+                                         "h"(*reinterpret_cast<const unsigned short *>(&v))
+                                         : "memory");
+                        }
                     }
                 } else if (row_ok) {
 #pragma unroll
@@ -407,6 +424,11 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                     }
                 }
             }
+            };
+            if (a.sp.order == 0 && !a.sp.wall_zero_p)
+                chunks(std::integral_constant<int, 1>{});
+            else
+                chunks(std::integral_constant<int, 0>{});
             tmem_wait_st();
             tc_fence_before();
             // Generic-proxy writes of the staging tile become visible to the
@@ -426,8 +448,9 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                     if (m0 + 64 < a.ldk) tma_store_2d(&mapB, stage_q + L::HALF_BYTES, m0 + 64, y);
                     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+                    // The completed store is ordered before the release
+                    // increment that publishes it.
                     fence_proxy_async_global();
-                    __threadfence();
                     red_release_gpu_add(a.bar + (size_t)rb * a.mtiles + mt, 1u);
                 }
             }

@@ -88,15 +88,21 @@ __device__ __forceinline__ void st_release_cta_shared(uint32_t addr, unsigned v)
 // with an acquire load, all lanes at once (one memory round trip per sweep),
 // and stores every new value with a release store; a producer that reads the
 // copy with an acquire load is then ordered after the owner's published q
-// block (the two synchronisations compose).  The warp stops once every owner
-// has published `last` steps, when the run is being aborted, or when no flag
-// has moved for limit_ns (the waiting producer raises the error then).
+// block (the two synchronisations compose).  Word MIRROR_MIN holds the
+// smallest flag of all owners, stored by lane 0 after a warp barrier that
+// orders every lane's acquire loads before it, so that one test of it shows
+// a producer every owner ready.  The warp stops once every owner has
+// published `last` steps, when the run is being aborted, or when no flag has
+// moved for limit_ns (the waiting producer raises the error then).
+constexpr int MIRROR_MIN = 64;   // word index of the minimum (words 0..63: owners)
+
 __device__ __forceinline__ void mirror_flags(const unsigned *flags, int nown, unsigned last, uint32_t seen,
                                              int lane, int *err, volatile int *abort_flag, long long limit_ns) {
-    unsigned m0 = 0u, m1 = 0u;   // last values mirrored by this lane
+    unsigned m0 = 0u, m1 = 0u, mmin = 0u;   // last values mirrored by this lane
     unsigned long long t_last = globaltimer_ns();
     for (unsigned it = 1;; ++it) {
         bool moved = false, done = true;
+        unsigned vmin = 0xffffffffu;
         if (lane < nown) {
             const unsigned v = ld_acquire_gpu(flags + lane);
             if (v != m0) {
@@ -105,6 +111,7 @@ __device__ __forceinline__ void mirror_flags(const unsigned *flags, int nown, un
                 moved = true;
             }
             done = (int)(v - last) >= 0;
+            vmin = v;
         }
         if (lane + 32 < nown) {
             const unsigned v = ld_acquire_gpu(flags + lane + 32);
@@ -114,6 +121,13 @@ __device__ __forceinline__ void mirror_flags(const unsigned *flags, int nown, un
                 moved = true;
             }
             done = done && (int)(v - last) >= 0;
+            vmin = min(vmin, v);
+        }
+        vmin = __reduce_min_sync(0xffffffffu, vmin);
+        __syncwarp();
+        if (lane == 0 && vmin != mmin) {
+            st_release_cta_shared(seen + 4u * MIRROR_MIN, vmin);
+            mmin = vmin;
         }
         if (__all_sync(0xffffffffu, done)) return;
         const unsigned long long now = globaltimer_ns();
@@ -127,17 +141,30 @@ __device__ __forceinline__ void mirror_flags(const unsigned *flags, int nown, un
     }
 }
 
-// A producer's bounded wait until the mirrored flag of owner mo shows step
-// `need` (acquire load of the shared copy), followed by the proxy fence that
-// orders its next TMA loads after the published data.  Returns false on
-// abort or timeout (raising DEV_TIMEOUT_BARRIER).
-__device__ __forceinline__ bool wait_owner(uint32_t seen, int mo, unsigned need, int *err,
-                                           volatile int *abort_flag, long long limit_ns) {
+// A producer's bounded wait until the mirrored flags show that owner mo has
+// published step `need` (acquire loads of the shared copies), followed by
+// the proxy fence that orders its next TMA loads after the published data.
+// When the mirrored minimum shows the step, every owner is marked ready.
+// Returns false on abort or timeout (raising DEV_TIMEOUT_BARRIER).
+__device__ __forceinline__ bool wait_owner(uint32_t seen, int mo, unsigned need, unsigned long long &ready,
+                                           int *err, volatile int *abort_flag, long long limit_ns) {
     const uint32_t addr = seen + 4u * (uint32_t)mo;
-    if ((int)(ld_acquire_cta_shared(addr) - need) < 0) {
+    const uint32_t amin = seen + 4u * MIRROR_MIN;
+    auto test = [&]() -> bool {
+        if ((int)(ld_acquire_cta_shared(amin) - need) >= 0) {
+            ready = ~0ull;
+            return true;
+        }
+        if ((int)(ld_acquire_cta_shared(addr) - need) >= 0) {
+            ready |= 1ull << mo;
+            return true;
+        }
+        return false;
+    };
+    if (!test()) {
         const unsigned long long t0 = globaltimer_ns();
         for (unsigned it = 1;; ++it) {
-            if ((int)(ld_acquire_cta_shared(addr) - need) >= 0) break;
+            if (test()) break;
             if ((it & 15u) == 0u) {
                 if (*abort_flag || ld_volatile_int(err) != 0) {
                     *abort_flag = 1;
