@@ -13,8 +13,8 @@
 //   warps 3..10 epilogue: tcgen05.ld of the accumulators, the spring
 //               integrator of Eq. 8 with the walls of Eq. 6 on the q, p state
 //               that lives in TMEM next to the accumulators, and the bf16
-//               copy of the new q (the next step's MMA operand), staged in
-//               shared memory and written back with one TMA store
+//               copy of the new q (the next step's MMA operand), stored by
+//               the epilogue threads straight into the operand plane
 // CTAs of one replica block exchange q through the double-buffered operand
 // array in L2.  There is no step barrier: each CTA publishes a per-CTA step
 // counter after writing its rows of q, and a consumer waits only for the
@@ -61,9 +61,8 @@ struct TcArgs {
 };
 
 // ------------------------------------------------------------------ kernel
-// Shared memory: S ring stages (J tile + q tile), the staging tile of the
-// next q (bf16, two 64-spin halves in the 128-byte swizzled layout that the
-// TMA store and the MMA both read), then the mbarriers.
+// Shared memory: S ring stages (J tile + q tile), then the mbarriers and the
+// mirrored step flags.
 //
 // With e4m3 J storage (E4) a stage holds the J tile as 8 KB of e4m3 (64-byte
 // swizzle) and four converter warps widen it into tensor memory, where the
@@ -78,9 +77,7 @@ struct TcSmem {
     static constexpr int STAGE_BYTES = A_STAGE + B_BYTES;
     static constexpr int TX_BYTES = STAGE_BYTES;          // bytes TMA delivers per stage
     static constexpr int TILES = S * STAGE_BYTES;
-    static constexpr int HALF_BYTES = BN * 128;           // BN replicas x 64 spins bf16
-    static constexpr int STAGING = TILES;                 // 1024-aligned
-    static constexpr int PTILE = STAGING + 2 * HALF_BYTES;    // p of the tile (E4), [BN][128] floats
+    static constexpr int PTILE = TILES;                   // p of the tile (E4), [BN][128] floats
     static constexpr int BARS = PTILE + (E4 ? BN * TC_BM * 4 : 0);
     static constexpr int NA = E4 ? 4 : 0;                 // A slots in tensor memory (two per MMA warp)
     // full[S], empty[S], accf, tmem_empty, epi_done, drain, afull[NA], aempty[NA]
@@ -111,7 +108,6 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
         return;
     }
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t stage_q = sbase + L::STAGING;
     const uint32_t bar0 = sbase + L::BARS;
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (S + s); };
@@ -305,11 +301,6 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
         const bool row_ok = i < a.n;
         const bool two_acc = a.kblocks > 1;
         const float hi = (a.h && row_ok) ? a.h[i] : 0.f;
-        // This thread's byte offset inside the staging tile of the next q:
-        // half hq = row/64 holds spins 64hq..64hq+63 as BN rows of 128 bytes,
-        // 16-byte chunks swizzled by (replica row % 8).
-        const int kq = row & 63;
-        const uint32_t st_base = stage_q + (uint32_t)(row >> 6) * L::HALF_BYTES + (uint32_t)(kq & 7) * 2u;
         const bool publisher = (warp == TC_EPI_WARP0 && lane == 0);
         // E4: p of this thread's spin at p_tile[col * 128 + row] (a warp's
         // 32 consecutive rows are consecutive words: no bank conflicts)
@@ -386,30 +377,20 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                     tmem_st32(tl + COL_P + c * 32, vp);
                 }
                 if (!last) {
-                    // bf16 copy into the staging tile (zeros outside n x R).
+                    // bf16 copy into the operand plane of step t+1, written
+                    // directly: a warp's 32 consecutive spins of one replica
+                    // are 64 contiguous bytes.  Entries outside n x R are
+                    // never written and keep the zeros of the initial fill.
+                    __nv_bfloat16 *dst =
+                        a.qop + ((size_t)((t + 1) & 1) * a.rpad + (size_t)(r0 + c * 32)) * a.ldk + i;
                     if (row_ok && r0 + c * 32 + 32 <= a.R) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int rl = c * 32 + j;
-                            const __nv_bfloat16 v = __float2bfloat16_rn(__uint_as_float(vq[j]));
-                            const uint32_t addr = st_base + (uint32_t)rl * 128u +
-                                                  ((uint32_t)(((kq >> 3) ^ (rl & 7)) << 4));
-                            asm volatile("st.shared.b16 [%0], %1;" ::"r"(addr),
-                                         "h"(*reinterpret_cast<const unsigned short *>(&v))
-                                         : "memory");
-                        }
-                    } else {
+                        for (int j = 0; j < 32; ++j) dst[(size_t)j * a.ldk] = __float2bfloat16_rn(__uint_as_float(vq[j]));
+                    } else if (row_ok) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const int rl = c * 32 + j;
-                            const bool ok2 = row_ok && (r0 + rl) < a.R;
-                            const __nv_bfloat16 v = __float2bfloat16_rn(ok2 ? __uint_as_float(vq[j]) : 0.f);
-                            const uint32_t addr = st_base + (uint32_t)rl * 128u +
-                                                  ((uint32_t)(((kq >> 3) ^ (rl & 7)) << 4));
-                            asm volatile("st.shared.b16 [%0], %1;" ::"r"(addr),
-                                         "h"(*reinterpret_cast<const unsigned short *>(&v))
-                                         : "memory");
-                        }
+                        for (int j = 0; j < 32; ++j)
+                            if (r0 + c * 32 + j < a.R)
+                                dst[(size_t)j * a.ldk] = __float2bfloat16_rn(__uint_as_float(vq[j]));
                     }
                 } else if (row_ok) {
 #pragma unroll
@@ -431,28 +412,19 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                 chunks(std::integral_constant<int, 0>{});
             tmem_wait_st();
             tc_fence_before();
-            // Generic-proxy writes of the staging tile become visible to the
-            // TMA store (async proxy) issued below.
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            // The warp's stores of q are ordered before lane 0's arrivals
+            // (warp barrier), the arrivals (release, CTA scope) before the
+            // publisher's wait (acquire), and that before its release
+            // increment at GPU scope, which the consumers' acquire loads read.
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(tmem_empty_bar);
                 mbar_arrive(epi_done_bar);
             }
             if (publisher && !last) {
-                // All 8 warps have written their part: store the tile to the
-                // operand plane of step t+1, wait for the writes, publish.
-                if (mbar_wait(epi_done_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns)) {
-                    const int y = ((t + 1) & 1) * a.rpad + r0;
-                    tma_store_2d(&mapB, stage_q, m0, y);
-                    if (m0 + 64 < a.ldk) tma_store_2d(&mapB, stage_q + L::HALF_BYTES, m0 + 64, y);
-                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-                    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-                    // The completed store is ordered before the release
-                    // increment that publishes it.
-                    fence_proxy_async_global();
+                // All 8 warps have written their part of q(t+1): publish.
+                if (mbar_wait(epi_done_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns))
                     red_release_gpu_add(a.bar + (size_t)rb * a.mtiles + mt, 1u);
-                }
             }
         }
     } else if constexpr (E4) {
