@@ -121,6 +121,7 @@ struct Ctx {
     // Tensor path configuration.
     int tile_n = 0;                      // replicas per CTA
     bool j_e4m3 = false;                 // dJ holds e4m3 bytes [mpad][ldk] (else bf16)
+    bool tc_pair = false;                // k_tc_run on CTA pairs (cta_group::2, M = 256)
     int tc_per_sm = 0;                   // co-resident CTAs per SM of the step kernel (0: not yet queried)
     int stages = 0;
     int rpad = 0;                        // R rounded up to tile_n

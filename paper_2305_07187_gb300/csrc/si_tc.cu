@@ -70,9 +70,9 @@ struct TcArgs {
 // 8 KB of shared-memory reads instead of 16 + 16 KB.  Tensor memory holds
 // the two accumulators, q and NA A slots, so the momenta p move to shared
 // memory ([replica][spin] within the tile).
-template <int BN, int S, bool E4>
+template <int BN, int S, bool E4, bool CG2 = false>
 struct TcSmem {
-    static constexpr int B_BYTES = BN * TC_BK * 2;
+    static constexpr int B_BYTES = (CG2 ? BN / 2 : BN) * TC_BK * 2;   // a CTA pair holds half of q each
     static constexpr int A_STAGE = E4 ? TC_BM * TC_BK : TC_A_BYTES;   // J tile in its storage type
     static constexpr int STAGE_BYTES = A_STAGE + B_BYTES;
     static constexpr int TX_BYTES = STAGE_BYTES;          // bytes TMA delivers per stage
@@ -92,11 +92,25 @@ constexpr int TC_EPI_WARP0 = 1 + TC_MMA_WARPS;             // first epilogue war
 
 // EPI: epilogue warps (8 in both tile instantiations; a CTA that allocates
 // tensor memory occupies its SM alone, so a lighter CTA buys no second CTA).
-template <int BN, int S, int EPI, bool E4>
+//
+// CG2: CTA pairs.  The two CTAs of a cluster (consecutive M tiles of one
+// replica block) share each MMA of M = 256 (tcgen05 cta_group::2): each loads
+// its own 128 rows of J and half of the q tile (BN/2 replicas), so a K block
+// costs a CTA 24 KB of TMA traffic instead of 32 KB.  The even CTA issues the
+// MMAs.  Each CTA's copies complete on its own full barrier; in the odd CTA
+// the two idle MMA warps forward every completed stage to the even CTA's
+// full barrier (which counts its own producer and that forward), so that no
+// copy ever signals the other CTA's memory.  The MMA completions are
+// multicast to the empty and accumulator barriers of both CTAs; the odd CTA's
+// epilogue frees the accumulators on the even CTA's barrier.  Both CTAs stay
+// until a cluster barrier before TMEM is freed, so neither leaves while the
+// other may still read its shared memory or signal its barriers.
+template <int BN, int S, int EPI, bool E4, bool CG2 = false>
 __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
     k_tc_run(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
              TcArgs a) {
-    using L = TcSmem<BN, S, E4>;
+    static_assert(!(E4 && CG2), "CTA pairs take the bf16 J operand");
+    using L = TcSmem<BN, S, E4, CG2>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -124,6 +138,8 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt = blockIdx.x % a.mtiles, rb = blockIdx.x / a.mtiles;
     const int m0 = mt * TC_BM, r0 = rb * BN;
+    const uint32_t crank = CG2 ? cluster_ctarank() : 0u;   // rank in the CTA pair (mt & 1)
+    const bool leader = crank == 0u;
     // TMEM columns: two partial accumulators, then the q and p state (E4:
     // q, then the A slots of 32 columns; p lives in shared memory).
     constexpr uint32_t COL_ACC0 = 0, COL_ACC1 = BN, COL_Q = 2 * BN, COL_P = 3 * BN, COL_A = 3 * BN;
@@ -131,7 +147,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(full_bar(s), 1);
+            mbar_init(full_bar(s), CG2 && leader ? 2 : 1);   // pair: own copies + the odd CTA's forward
             mbar_init(empty_bar(s), 1);
         }
         for (int k = 0; k < L::NA; ++k) {
@@ -139,7 +155,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
             mbar_init(aempty_bar(k), 1);
         }
         mbar_init(accf_bar, TC_MMA_WARPS);
-        mbar_init(tmem_empty_bar, EPI);
+        mbar_init(tmem_empty_bar, CG2 ? 2 * EPI : EPI);   // pair: both CTAs' epilogues
         mbar_init(epi_done_bar, EPI);
         mbar_init(drain_bar, TC_MMA_WARPS);
         *abort_flag = 0;
@@ -150,14 +166,25 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(tmem_slot)),
-                     "n"(L::TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if constexpr (CG2) {
+            // one warp of each CTA of the pair allocates, collectively
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "n"(L::TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(tmem_slot)),
+                         "n"(L::TMEM_COLS)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
     __syncthreads();
+    // pair: both CTAs' barriers are initialised before either signals the other
+    if constexpr (CG2) cluster_sync_all();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -186,11 +213,12 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
             const int ring = lane;
             uint32_t cnt = 0u;   // stages armed in this ring
             bool ok = true;
-            const int kb0 = mt * (TC_BM / TC_BK);
+            // pair: both CTAs walk the K blocks in the same order (the pair's rows first)
+            const int kb0 = (CG2 ? (mt & ~1) : mt) * (TC_BM / TC_BK);
             for (int t = 0; t < a.steps && ok; ++t) {
                 unsigned long long ready = t == 0 ? ~0ull : 0ull;   // owners known to have published step t
                 const unsigned need = (unsigned)t + (t == a.stall_step ? 1000000u : 0u);
-                const int yb = (t & 1) * a.rpad + r0;
+                const int yb = (t & 1) * a.rpad + r0 + (int)crank * (BN / 2);
                 for (int j = ring; j < a.kblocks; j += 2) {
                     int kb = kb0 + j;
                     if (kb >= a.kblocks) kb -= a.kblocks;
@@ -233,22 +261,41 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
         // warp 2 the odd ones into accumulator 1; the epilogue adds the two.
         // Two issuing threads keep the tensor pipe fed: one thread alone
         // issues a 128x128x16 MMA no faster than the pipe executes it.
-        if (lane == 0) {
+        // In the odd CTA of a pair the two warps forward its completed
+        // stages to the even CTA instead (ring w each).
+        if (lane == 0 && CG2 && !leader) {
             const int w = warp - 1;
-            constexpr uint32_t idesc = idesc_bf16(TC_BM, BN);
+            constexpr int HS = S / 2;
+            uint32_t c = 0;
+            bool ok = true;
+            for (int t = 0; t < a.steps && ok; ++t) {
+                for (int j = w; j < a.kblocks; j += TC_MMA_WARPS, ++c) {
+                    const int s = 2 * (int)(c % HS) + w;
+                    if (!mbar_wait(full_bar(s), (c / HS) & 1u, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                    mbar_arrive_remote(mapa_shared(full_bar(s), 0u));
+                }
+            }
+        } else if (lane == 0) {
+            const int w = warp - 1;
+            constexpr uint32_t idesc = idesc_bf16(CG2 ? 2 * TC_BM : TC_BM, BN);
             const uint32_t d_tmem = tmem + (w == 0 ? COL_ACC0 : COL_ACC1);
             constexpr int HS = S / 2;
             uint32_t c = 0;  // this warp's position in its ring of stages
             bool ok = true;
+            // pair barriers receive arrivals from the other CTA: acquire at cluster scope
+            auto wait_bar = [&](uint32_t bar, uint32_t parity) {
+                return CG2 ? mbar_wait_cluster(bar, parity, a.err, abort_flag, a.limit_ns)
+                           : mbar_wait(bar, parity, a.err, abort_flag, a.limit_ns);
+            };
             for (int t = 0; t < a.steps && ok; ++t) {
                 if (t > 0) {
-                    if (!mbar_wait(tmem_empty_bar, (uint32_t)((t - 1) & 1), a.err, abort_flag, a.limit_ns)) break;
+                    if (!wait_bar(tmem_empty_bar, (uint32_t)((t - 1) & 1))) break;
                 }
                 tc_fence_after();
                 for (int j = w; j < a.kblocks; j += TC_MMA_WARPS, ++c) {
                     const int s = 2 * (int)(c % HS) + w;
                     const uint32_t ph = (c / HS) & 1u;
-                    if (!mbar_wait(full_bar(s), ph, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                    if (!wait_bar(full_bar(s), ph)) { ok = false; break; }
                     if constexpr (E4) {
                         // A from the tensor-memory slot the converters filled
                         const int as = 2 * (int)(c % NAR) + w;
@@ -269,16 +316,28 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                         tc_fence_after();
                         const uint64_t ad = sdesc_sw128(sbase + s * L::STAGE_BYTES);
                         const uint64_t bd = ad + (uint64_t)(TC_A_BYTES >> 4);
+                        if constexpr (CG2) {
 #pragma unroll
-                        for (int kk = 0; kk < TC_BK / 16; ++kk)
-                            mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (j != w || kk != 0) ? 1u : 0u);
-                        mma_commit(empty_bar(s));
+                            for (int kk = 0; kk < TC_BK / 16; ++kk)
+                                mma_bf16_pair(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc,
+                                              (j != w || kk != 0) ? 1u : 0u);
+                            mma_commit_pair(empty_bar(s));
+                        } else {
+#pragma unroll
+                            for (int kk = 0; kk < TC_BK / 16; ++kk)
+                                mma_bf16(d_tmem, ad + 2u * kk, bd + 2u * kk, idesc, (j != w || kk != 0) ? 1u : 0u);
+                            mma_commit(empty_bar(s));
+                        }
                     }
                 }
-                if (ok) mma_commit(accf_bar);
+                if (ok) {
+                    if constexpr (CG2) mma_commit_pair(accf_bar);
+                    else mma_commit(accf_bar);
+                }
             }
             // Drain: wait until every MMA this thread issued has completed.
-            mma_commit(drain_bar);
+            if constexpr (CG2) mma_commit_pair_local(drain_bar);
+            else mma_commit(drain_bar);
             const unsigned long long t0 = globaltimer_ns();
             while (!mbar_try_wait(drain_bar, 0u)) {
                 if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
@@ -328,7 +387,9 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
 #pragma unroll 1
         for (int t = 0; t < a.steps; ++t) {
             bool ok = true;
-            if (lane == 0) ok = mbar_wait(accf_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns);
+            if (lane == 0)
+                ok = CG2 ? mbar_wait_cluster(accf_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns)
+                         : mbar_wait(accf_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns);
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             tc_fence_after();
@@ -418,7 +479,8 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
             // increment at GPU scope, which the consumers' acquire loads read.
             __syncwarp();
             if (lane == 0) {
-                mbar_arrive(tmem_empty_bar);
+                if (CG2 && !leader) mbar_arrive_remote(mapa_shared(tmem_empty_bar, 0u));
+                else mbar_arrive(tmem_empty_bar);
                 mbar_arrive(epi_done_bar);
             }
             if (publisher && !last) {
@@ -467,11 +529,18 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
 
     tc_fence_before();
     __syncthreads();
+    // pair: neither CTA frees TMEM or leaves while the other may still read
+    // its shared memory or arrive on its barriers
+    if constexpr (CG2) cluster_sync_all();
     tc_fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "n"(L::TMEM_COLS)
-                     : "memory");
+        if constexpr (CG2) {
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(L::TMEM_COLS)
+                         : "memory");
+        } else {
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(L::TMEM_COLS)
+                         : "memory");
+        }
     }
 }
 
@@ -619,9 +688,9 @@ __global__ void k_tc_spins(const float *q_state, int n, int R, int8_t *spins, in
     }
 }
 
-template <int BN, int S, int EPI, bool E4>
+template <int BN, int S, int EPI, bool E4, bool CG2 = false>
 static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
-    using L = TcSmem<BN, S, E4>;
+    using L = TcSmem<BN, S, E4, CG2>;
     TcArgs a;
     a.n = c->n;
     a.R = c->R;
@@ -650,17 +719,34 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
         set_error("tensor path: too many tiles for the step flags (n <= 8192 per context)");
         return SI_ERR_UNSUPPORTED;
     }
-    const int smem = L::TOTAL + (EPI == 4 ? 256 : 1024);
+    const int smem = L::TOTAL + 1024;
     a.smem_bytes = smem;
+    auto kern = k_tc_run<BN, S, EPI, E4, CG2>;
     // launch attributes and the co-residency check once per context (its
     // device and tile are fixed)
     if (c->tc_per_sm <= 0) {
-        SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S, EPI, E4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        SI_CUDA_TRY(cudaFuncSetAttribute(k_tc_run<BN, S, EPI, E4>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        SI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        SI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          (int)cudaSharedmemCarveoutMaxShared));
         int per_sm = 0;
-        SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tc_run<BN, S, EPI, E4>,
-                                                                  tc_threads<EPI, E4>(), smem));
+        SI_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tc_threads<EPI, E4>(), smem));
+        if (CG2 && per_sm > 0) {
+            // every pair of the grid must be resident at once (the CTAs wait on each other)
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(grid);
+            cfg.blockDim = dim3(tc_threads<EPI, E4>());
+            cfg.dynamicSmemBytes = smem;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = 2;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int clusters = 0;
+            SI_CUDA_TRY(cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg));
+            if (2 * clusters < grid) per_sm = 0;
+        }
         c->tc_per_sm = per_sm;
     }
     const int per_sm = c->tc_per_sm;
@@ -669,9 +755,25 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
         return SI_ERR_UNSUPPORTED;
     }
     SI_CUDA_TRY(cudaMemsetAsync(c->dbar, 0, sizeof(unsigned) * grid, c->stream));
-    void *args[] = {(void *)&c->mapA, (void *)&c->mapB, (void *)&a};
-    SI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)k_tc_run<BN, S, EPI, E4>, dim3(grid),
-                                            dim3(tc_threads<EPI, E4>()), args, smem, c->stream));
+    if constexpr (CG2) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(tc_threads<EPI, E4>());
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = c->stream;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        SI_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, c->mapA, c->mapB, a));
+    } else {
+        void *args[] = {(void *)&c->mapA, (void *)&c->mapB, (void *)&a};
+        SI_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(tc_threads<EPI, E4>()), args,
+                                                smem, c->stream));
+    }
     c->launches += 1;
     return SI_OK;
 }
@@ -684,6 +786,8 @@ si_status tc_run(Ctx *c, int steps, int8_t *spins_dev) {
             case 128: return tc_launch_t<128, 4, 8, true>(c, steps, spins_dev);
             default: break;
         }
+    } else if (c->tc_pair) {
+        return tc_launch_t<128, 6, 8, false, true>(c, steps, spins_dev);
     } else {
         switch (c->tile_n) {
             case 64: return tc_launch_t<64, 8, 8, false>(c, steps, spins_dev);
@@ -742,6 +846,42 @@ static bool tc_e4m3_operand(const Ctx *c) {
     return e && std::atoi(e) == 1;
 }
 
+// Pairs of consecutive 128-row tiles sharing each MMA (k_tc_run with CG2)
+// for the 128-replica tile that the library chose itself on a bf16 J
+// operand, when every pair of the grid (J rows padded to 256) can be
+// resident at once.  SI_TC_PAIR=1 turns them on.
+static bool tc_pair_choice(const Ctx *c) {
+    const char *e = std::getenv("SI_TC_PAIR");
+    if (!(e && std::atoi(e) == 1)) return false;
+    if (c->j_e4m3 || c->prm.tile_n != 0 || c->tile_n != 128) return false;
+    using L = TcSmem<128, 6, false, true>;
+    auto kern = k_tc_run<128, 6, 8, false, true>;
+    const int smem = L::TOTAL + 1024;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return false;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        return false;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(tc_threads<8, false>());
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int mtiles = round_up(c->n, 2 * TC_BM) / TC_BM;
+    const long long grid = (long long)mtiles * cdiv(c->R, 128);
+    return mtiles <= 64 && grid <= 2LL * clusters;
+}
+
 bool tc_persistent_fits(Ctx *c) {
     c->ldk = round_up(c->n, TC_BK);
     c->mpad = round_up(c->n, TC_BM);
@@ -761,6 +901,11 @@ si_status tc_prepare(Ctx *c, const float *J_dev) {
     int per_sm = 0;
     c->tile_n = choose_tile(c, &per_sm);
     c->rpad = round_up(c->R, c->tile_n);
+    c->tc_pair = tc_pair_choice(c);
+    if (c->tc_pair) {
+        c->mpad = round_up(n, 2 * TC_BM);   // whole pairs of 128-row tiles
+        per_sm = 1;
+    }
     SI_CUDA_TRY(si_dev_malloc(&c->dJ, (size_t)c->mpad * c->ldk * (c->j_e4m3 ? 1 : 2)));
     si_status sc = c->j_e4m3 ? tc_convert_j_e4m3(J_dev, n, c->dJ, c->ldk, c->mpad, c->num_sms, c->stream)
                              : tc_convert_j(J_dev, n, c->dJ, c->ldk, c->mpad, c->num_sms, c->stream);
@@ -773,7 +918,8 @@ si_status tc_prepare(Ctx *c, const float *J_dev) {
     si_status s = c->j_e4m3 ? tc_make_map_e4m3(&c->mapA, c->dJ, c->ldk, c->mpad, TC_BM)
                             : tc_make_map_bf16(&c->mapA, c->dJ, c->ldk, c->mpad, TC_BK, TC_BM);
     if (s != SI_OK) return s;
-    s = tc_make_map_bf16(&c->mapB, c->dqbuf, c->ldk, 2 * c->rpad, TC_BK, c->tile_n);
+    // pairs load half of the q tile per CTA
+    s = tc_make_map_bf16(&c->mapB, c->dqbuf, c->ldk, 2 * c->rpad, TC_BK, c->tc_pair ? c->tile_n / 2 : c->tile_n);
     if (s != SI_OK) return s;
     const int mtiles = c->mpad / TC_BM;
     const int grid = mtiles * (c->rpad / c->tile_n);
@@ -831,11 +977,11 @@ si_status tc_spins(Ctx *c, int8_t *spins, int ld) {
 
 const char *tc_describe(const Ctx *c, char *buf, int len) {
     std::snprintf(buf, len,
-                  "tcgen05 prec=%s J=%s n=%d R=%d tile=128x%d stages=%d grid=%d (mtiles=%d rblocks=%d) kblocks=%d",
+                  "tcgen05 prec=%s J=%s n=%d R=%d tile=128x%d%s stages=%d grid=%d (mtiles=%d rblocks=%d) kblocks=%d",
                   c->prm.prec == SI_PREC_J_FP8_Q_BF16 ? "j_fp8_q_bf16" : "j_bf16_q_bf16",
-                  c->j_e4m3 ? "e4m3(1B)" : "bf16(2B)", c->n, c->R,
-                  c->tile_n, c->tile_n == 128 ? (c->j_e4m3 ? 4 : 6) : 8, (c->mpad / TC_BM) * (c->rpad / c->tile_n),
-                  c->mpad / TC_BM, c->rpad / c->tile_n, c->ldk / TC_BK);
+                  c->j_e4m3 ? "e4m3(1B)" : "bf16(2B)", c->n, c->R, c->tile_n,
+                  c->tc_pair ? " cta_pairs(M=256)" : "", c->tile_n == 128 ? (c->j_e4m3 ? 4 : 6) : 8,
+                  (c->mpad / TC_BM) * (c->rpad / c->tile_n), c->mpad / TC_BM, c->rpad / c->tile_n, c->ldk / TC_BK);
     return buf;
 }
 
