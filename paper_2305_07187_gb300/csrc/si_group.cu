@@ -37,11 +37,14 @@
 namespace si {
 
 constexpr int GR_BM = 128, GR_BK = 64;
-// Warps: producer, 2 MMA issuers, GR_EPI epilogue warps (three per TMEM lane
-// quadrant), then, in groups with e4m3 members (CONV), 4 converter warps.
+// Warps: producer of the even stages, 2 MMA issuers, GR_EPI epilogue warps
+// (three per TMEM lane quadrant), in groups with e4m3 members (CONV) 4
+// converter warps, then the producer of the odd stages.
 constexpr int GR_EPI = 12;
 template <bool CONV>
-constexpr int gr_threads() { return 32 * (3 + GR_EPI + (CONV ? 4 : 0)); }
+constexpr int gr_threads() { return 32 * (4 + GR_EPI + (CONV ? 4 : 0)); }
+template <bool CONV>
+constexpr int gr_prod1_warp() { return 3 + GR_EPI + (CONV ? 4 : 0); }
 constexpr int GR_A_BYTES = GR_BM * GR_BK * 2;
 constexpr int GR_SMAX = 8;                       // most ring stages of any policy
 constexpr int GR_TILES = 196608;                 // shared memory for the ring
@@ -135,25 +138,29 @@ __global__ void __launch_bounds__(gr_threads<CONV>(), 1) k_group_step(const __gr
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     const int plane_in = a.t & 1;
-    // Stage of the c-th use of ring `ring`: split mode has two rings (even /
-    // odd stages, one per MMA warp), single mode one ring of all stages.
-    auto stage_of = [&](uint32_t c, int ring) -> int {
-        return a.single ? (int)(c % (uint32_t)S) : 2 * (int)(c % (uint32_t)HS) + ring;
-    };
-    auto phase_of = [&](uint32_t c) -> uint32_t {
-        return a.single ? (c / (uint32_t)S) & 1u : (c / (uint32_t)HS) & 1u;
-    };
-    // The hot loops track (index within the ring, phase) incrementally; the
-    // divisions above are only for the drain at the end.
+    // The hot loops track (index within the ring, phase) incrementally: split
+    // mode has two rings (even / odd stages, one per MMA warp), single mode
+    // one ring of all stages.
     const int ring_len = a.single ? S : HS;
     auto ring_stage = [&](int k, int ring) -> int { return a.single ? k : 2 * k + ring; };
 
-    if (warp == 0) {
-        // ---------------------------------------------- TMA producer
+    if (warp == 0 || warp == gr_prod1_warp<CONV>()) {
+        // ---------------------------------------------- TMA producers (warp 0, last warp)
+        // One thread's chain of barrier wait, arming and two TMA issues per K
+        // block takes about as long as the K block's MMAs, so two producers
+        // fill the ring, producer l the stages 2i + l.  In split mode that is
+        // ring l (the K blocks of parity l within a tile, for MMA warp l + 1);
+        // in single mode the one consumer takes the stages in order, the g-th
+        // K block of this CTA in stage g mod S (S even), so producer l takes
+        // the K blocks g of parity l.  The two are in separate warps, so that
+        // neither waits for the other's stage (in single mode those come one
+        // MMA apart).
         if (lane == 0) {
-            uint32_t cnt0 = 0u, cnt1 = 0u;   // stages armed in ring 0 / ring 1
-            int rk0 = 0, rk1 = 0;            // next index within ring 0 / 1
-            uint32_t rph0 = 0u, rph1 = 0u;   // and its phase parity
+            const int ring = warp == 0 ? 0 : 1;
+            uint32_t cnt = 0u;   // stages armed by this producer
+            int rk = 0;          // next index within this producer's stages
+            uint32_t rph = 0u;   // and its phase parity
+            int gpar = 0;        // single mode: parity of this CTA's K blocks before the tile
             bool ok = true;
             for (int k = blockIdx.x; k < a.ntiles && ok; k += gridDim.x) {
                 const GroupTile tl = a.tiles[k];
@@ -163,16 +170,13 @@ __global__ void __launch_bounds__(gr_threads<CONV>(), 1) k_group_step(const __gr
                 const uint32_t bytes = (uint32_t)((in.e4m3 ? GR_BM * GR_BK : GR_A_BYTES) + tl.bn * GR_BK * 2);
                 const uint32_t a_off = in.e4m3 ? (uint32_t)E4M3_TILE_OFFSET : 0u;
                 const int yq = plane_in * in.rpad + tl.r0;
-                for (int j = 0; j < tl.kb_cnt; ++j) {
+                const int j0 = a.single ? (ring ^ gpar) : ring;
+                for (int j = j0; j < tl.kb_cnt; j += 2) {
                     const int kb = a.kbl[tl.kb_off + j];
-                    const int ring = a.single ? 0 : (j & 1);
-                    int &rk = ring ? rk1 : rk0;
-                    uint32_t &rph = ring ? rph1 : rph0;
-                    const int s = ring_stage(rk, ring);
-                    const uint32_t ph = rph;
-                    if (!mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
-                    if (ring) ++cnt1; else ++cnt0;
-                    if (++rk == ring_len) {
+                    const int s = 2 * rk + ring;
+                    if (!mbar_wait(empty_bar(s), rph ^ 1u, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                    ++cnt;
+                    if (++rk == HS) {
                         rk = 0;
                         rph ^= 1u;
                     }
@@ -181,18 +185,16 @@ __global__ void __launch_bounds__(gr_threads<CONV>(), 1) k_group_step(const __gr
                     tma_load_2d(dA + a_off, mJ, full_bar(s), kb * GR_BK, tl.mt * GR_BM);
                     tma_load_2d(dA + GR_A_BYTES, mQ, full_bar(s), kb * GR_BK, yq);
                 }
+                gpar = (gpar + tl.kb_cnt) & 1;
             }
-            for (int ring = 0; ring < 2; ++ring) {
-                const uint32_t cr = ring ? cnt1 : cnt0;
-                const uint32_t depth = a.single ? (uint32_t)S : (uint32_t)HS;
-                const uint32_t first = cr > depth ? cr - depth : 0u;
-                for (uint32_t k = first; k < cr; ++k) {
-                    const unsigned long long t0 = globaltimer_ns();
-                    while (!mbar_try_wait(full_bar(stage_of(k, ring)), phase_of(k))) {
-                        if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
-                            atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
-                            break;
-                        }
+            // Let every copy this producer issued land before the CTA exits.
+            const uint32_t first = cnt > (uint32_t)HS ? cnt - HS : 0u;
+            for (uint32_t k = first; k < cnt; ++k) {
+                const unsigned long long t0 = globaltimer_ns();
+                while (!mbar_try_wait(full_bar(2 * (int)(k % (uint32_t)HS) + ring), (k / (uint32_t)HS) & 1u)) {
+                    if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                        atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
+                        break;
                     }
                 }
             }
