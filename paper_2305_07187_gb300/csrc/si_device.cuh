@@ -68,19 +68,83 @@ __device__ __forceinline__ bool grid_barrier(unsigned *ctr, unsigned target, int
 // wall_zero_p the momentum of a clipped spin is set to zero.
 // MODE 1 is the same arithmetic with order 0 and wall_zero_p off fixed at
 // compile time (for loops that test those parameters once, outside).
+// The roundings are pinned (no contraction left to the compiler), in this
+// order: d = q - q0, u = (-k) d, w = zeta F + u (fused), a = dt w + p
+// (fused), b = dtm x + q (fused), so that the two-wide form below and every
+// kernel compute the same values.
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
 template <typename T, int MODE = 0>
 __device__ __forceinline__ void integrate(T q, T p, T F, T zeta, T dt, T dtm,
                                           const StepParams &sp, T &q_out, T &p_out) {
     const T k = (T)sp.k, q0 = (T)sp.q0, qmax = (T)sp.q_max, pmax = (T)sp.p_max;
     const int order = MODE == 1 ? 0 : sp.order;
     const bool wall_zero_p = MODE == 1 ? false : sp.wall_zero_p != 0;
-    T a = p + dt * (-k * (q - q0) + zeta * F);
-    T b = q + dtm * (order == 0 ? fmin(fmax(a, -pmax), pmax) : p);
-    T pn = fmin(fmax(a, -pmax), pmax);
-    T qn = fmin(fmax(b, -qmax), qmax);
+    const T d = rn_add(q, -q0);
+    const T u = rn_mul(-k, d);
+    const T w = rn_fma(zeta, F, u);
+    const T a = rn_fma(dt, w, p);
+    const T pn0 = fmin(fmax(a, -pmax), pmax);
+    const T b = rn_fma(dtm, order == 0 ? pn0 : p, q);
+    T pn = pn0;
+    const T qn = fmin(fmax(b, -qmax), qmax);
     if (wall_zero_p && qn != b) pn = (T)0;
     q_out = qn;
     p_out = pn;
+}
+
+// Two (spin, replica) pairs of the default update (kick-drift, walls without
+// momentum zeroing) with Blackwell's two-wide FP32 instructions: the same
+// roundings as integrate<float, 1> element by element.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+__device__ __forceinline__ void integrate2_kd(float q_lo, float q_hi, float p_lo, float p_hi, float F_lo, float F_hi,
+                                              float zeta, float dt, float dtm, const StepParams &sp,
+                                              float &qo_lo, float &qo_hi, float &po_lo, float &po_hi) {
+    const float qmax = sp.q_max, pmax = sp.p_max;
+    const unsigned long long Q = f2_pack(q_lo, q_hi);
+    const unsigned long long d = f2_add(Q, f2_pack(-sp.q0, -sp.q0));
+    const unsigned long long u = f2_mul(f2_pack(-sp.k, -sp.k), d);
+    const unsigned long long w = f2_fma(f2_pack(zeta, zeta), f2_pack(F_lo, F_hi), u);
+    const unsigned long long av = f2_fma(f2_pack(dt, dt), w, f2_pack(p_lo, p_hi));
+    float a0, a1;
+    f2_unpack(av, a0, a1);
+    const float pn0 = fminf(fmaxf(a0, -pmax), pmax), pn1 = fminf(fmaxf(a1, -pmax), pmax);
+    const unsigned long long bv = f2_fma(f2_pack(dtm, dtm), f2_pack(pn0, pn1), Q);
+    float b0, b1;
+    f2_unpack(bv, b0, b1);
+    qo_lo = fminf(fmaxf(b0, -qmax), qmax);
+    qo_hi = fminf(fmaxf(b1, -qmax), qmax);
+    po_lo = pn0;
+    po_hi = pn1;
 }
 
 // Error-free sum (Knuth's TwoSum): s + e == a + b exactly.

@@ -421,14 +421,30 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                     tmem_ld32(tl + COL_P + c * 32, vp);
                 }
                 tmem_wait_ld();
+                if constexpr (MODE == 1) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float F = __uint_as_float(vf[j]);
-                    float qo, po;
-                    integrate<float, MODE>(__uint_as_float(vq[j]), __uint_as_float(vp[j]), F + hi, zt, dtt,
-                                           dtm, a.sp, qo, po);
-                    vq[j] = __float_as_uint(qo);
-                    vp[j] = __float_as_uint(po);
+                    for (int j = 0; j < 32; j += 2) {
+                        float F0 = __uint_as_float(vf[j]), F1 = __uint_as_float(vf[j + 1]);
+                        F0 = __fadd_rn(F0, hi);
+                        F1 = __fadd_rn(F1, hi);
+                        float q0o, q1o, p0o, p1o;
+                        integrate2_kd(__uint_as_float(vq[j]), __uint_as_float(vq[j + 1]), __uint_as_float(vp[j]),
+                                      __uint_as_float(vp[j + 1]), F0, F1, zt, dtt, dtm, a.sp, q0o, q1o, p0o, p1o);
+                        vq[j] = __float_as_uint(q0o);
+                        vq[j + 1] = __float_as_uint(q1o);
+                        vp[j] = __float_as_uint(p0o);
+                        vp[j + 1] = __float_as_uint(p1o);
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float F = __uint_as_float(vf[j]);
+                        float qo, po;
+                        integrate<float, MODE>(__uint_as_float(vq[j]), __uint_as_float(vp[j]), __fadd_rn(F, hi), zt,
+                                               dtt, dtm, a.sp, qo, po);
+                        vq[j] = __float_as_uint(qo);
+                        vp[j] = __float_as_uint(po);
+                    }
                 }
                 tmem_st32(tl + COL_Q + c * 32, vq);
                 if constexpr (E4) {
