@@ -276,7 +276,10 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
     db = torch.from_numpy(inputs.dt_const(T_STEPS)).to(dev)
     ttts, hit_steps = [], []
     nseg = T_STEPS // every
-    with b.Context(J, replicas=R, steps=every, prec="j_fp8_q_bf16", stream=stream.cuda_stream) as cb:
+    # the exact cuts of each segment are summed inside the step kernel (one
+    # more pass over J after the segment's last step, si_params.fused_readout)
+    with b.Context(J, replicas=R, steps=every, prec="j_fp8_q_bf16", stream=stream.cuda_stream,
+                   fused_readout=1) as cb:
         cut_d = torch.empty((nseg, R), dtype=torch.int32, device=dev)
         cut_p = torch.empty((nseg, R), dtype=torch.int32).pin_memory()
         ready = [torch.cuda.Event() for _ in range(nseg)]
@@ -333,6 +336,7 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
             "speedup_vs_fp32_plain": (tts99 / ttt) if ttt > 0 else None,
             "batched_full_run_s": t_b, "batched_p_success_final": p_b,
             "batched_tts99_per_replica_s": tts99_rep,
+            "readout": "fused into the step kernel: one more pass over J with the segment's final spins",
             "note": "batched_ttt_s: any of R=1024 replicas reaches C* (readout every 10 steps); "
                     "batched_tts99_per_replica_s: TTS99 of one replica of the batched path, each replica "
                     "charged 1/R of a full T=2000 batched run, p from the run's final cuts"}

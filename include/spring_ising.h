@@ -90,7 +90,14 @@ typedef struct {
     int32_t wall_zero_p;    /* 1: zero p of a spin whose q was clipped        */
     int32_t ckpt_every;     /* si_grad checkpoint interval (0: 50)            */
     int32_t tile_n;         /* tensor-core replica tile (0: autotuned)        */
-    int32_t reserved[4];    /* must be zero                                   */
+    int32_t fused_readout;  /* 1: a tensor-path si_run also sums sigma^T J
+                               sigma of its final spins inside the step
+                               kernel (one more pass over J), so that the
+                               next si_energy with spins NULL only finishes
+                               E and the cut (Eq. 1, 2); 0: off.  Contexts
+                               served by the grouped kernel, with the e4m3
+                               operand or on CTA pairs ignore it.            */
+    int32_t reserved[3];    /* must be zero                                   */
 } si_params;
 
 /* Fill *p with the paper's parameters (k=0.5, m=1, q0=0, q_max=sqrt 2,
@@ -137,8 +144,8 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt,
 
 /*
  * Change the integrator parameters of an existing context without copying J
- * again: k, m, q0, q_max, p_max, update_order, wall_zero_p and ckpt_every
- * take the values in *prm for every later call (e.g. the spring constant
+ * again: k, m, q0, q_max, p_max, update_order, wall_zero_p, ckpt_every and
+ * fused_readout take the values in *prm for every later call (e.g. the spring constant
  * being tuned by gradient descent).  n, replicas, steps, prec and tile_n
  * must equal the context's (else SI_ERR_INVALID_ARG); the other fields are
  * checked as in si_create.  The context's state, J and h are kept, so a
@@ -168,7 +175,10 @@ si_status si_get_state(si_ctx *ctx, double *q_out, double *p_out);
  *   energy_f   [R] energy as double for any J; exact (the integer energy)
  *              when J and h are integer-valued, else computed in FP32;
  *              or NULL
- * R may differ from the context's replica count.
+ * R may differ from the context's replica count.  With spins NULL after a
+ * run whose step kernel summed sigma^T J sigma itself (si_params
+ * fused_readout), only E and the cut are finished here (one small kernel);
+ * the results are the same, bit for bit.
  */
 si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R,
                     int32_t *energy_out, int32_t *cut_out, double *energy_f);

@@ -46,7 +46,7 @@ class SiParams(ctypes.Structure):
                 ("q_max", ctypes.c_float), ("p_max", ctypes.c_float),
                 ("prec", ctypes.c_int32), ("update_order", ctypes.c_int32),
                 ("wall_zero_p", ctypes.c_int32), ("ckpt_every", ctypes.c_int32),
-                ("tile_n", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("tile_n", ctypes.c_int32), ("fused_readout", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class SpringIsingError(RuntimeError):

@@ -193,7 +193,11 @@ static si_status check_params(const si_params *p) {
         set_error("ckpt_every and tile_n must be >= 0");
         return SI_ERR_INVALID_ARG;
     }
-    for (int i = 0; i < 4; ++i)
+    if (p->fused_readout != 0 && p->fused_readout != 1) {
+        set_error("fused_readout must be 0 or 1");
+        return SI_ERR_INVALID_ARG;
+    }
+    for (int i = 0; i < 3; ++i)
         if (p->reserved[i] != 0) {
             set_error("reserved fields must be zero");
             return SI_ERR_INVALID_ARG;
@@ -431,6 +435,7 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
     // the state is rewritten from here on: only a successful run leaves one
     // to continue from or to read back
     c->have_run = false;
+    c->fused_valid = false;
     if (c->path == Path::TENSOR && c->grp) {
         if (!cont) {
             const size_t bytes = sizeof(float) * (size_t)R * n;
@@ -442,10 +447,24 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
         if (c->timing) SI_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
         if ((s = group_ctx_run(c, steps)) != SI_OK) return s;
     } else if (c->path == Path::TENSOR) {
-        s = cont ? tc_continue_state(c) : tc_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr);
+        // A continuing run starts from the bf16 plane the last run left
+        // (rebuilt from the FP32 state only when that plane is not current).
+        if (!cont) {
+            s = tc_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr);
+            c->tc_p0 = 0;
+        } else if (c->tc_plane >= 0) {
+            c->tc_p0 = c->tc_plane;
+        } else {
+            s = tc_continue_state(c);
+            c->tc_p0 = 0;
+        }
         if (s != SI_OK) return s;
+        c->tc_plane = -1;
+        c->tc_readout = c->prm.fused_readout == 1 && steps > 0 && tc_readout_supported(c);
+        if (c->tc_readout && (s = tc_readout_buffer(c)) != SI_OK) return s;
         if (c->timing) SI_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
         if ((s = tc_run(c, steps, c->dspins)) != SI_OK) return s;
+        c->tc_plane = (steps + c->tc_p0) & 1;
     } else {
         s = cont ? simt_continue_state(c) : simt_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr);
         if (s != SI_OK) return s;
@@ -480,6 +499,7 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
     if ((s = finish_call(c, {&qo, &po, &so}, true, host_in)) != SI_OK) return s;
     c->have_run = true;
     c->run_spins_valid = true;
+    c->fused_valid = c->path == Path::TENSOR && !c->grp && c->tc_readout;
     return SI_OK;
 }
 
@@ -539,6 +559,12 @@ si_status si_energy(si_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energy
     if ((s = stage_out(eo, energy_out, sizeof(int32_t) * R)) != SI_OK) return s;
     if ((s = stage_out(co, cut_out, sizeof(int32_t) * R)) != SI_OK) return s;
     if ((s = stage_out(fo, energy_f, sizeof(double) * R)) != SI_OK) return s;
+    if (!spins && c->fused_valid && !energy_f) {
+        // the step kernel already summed sigma^T J sigma of these spins
+        s = tc_energy_finish(c, R, (int32_t *)eo.ptr, (int32_t *)co.ptr);
+        if (s != SI_OK) return s;
+        return finish_call(c, {&eo, &co, &fo}, true);
+    }
     if (!spins) {
         // the last run's spins, already in the padded layout
         s = simt_energy(c, c->dspins, R, c->ld8, (int32_t *)eo.ptr, (int32_t *)co.ptr, (double *)fo.ptr);
@@ -621,6 +647,7 @@ si_status si_grad(si_ctx *ctx, const float *zeta, const float *dt, const float *
     if ((s = stage_out(gk, g_k, sizeof(float))) != SI_OK) return s;
     if ((s = stage_out(ob, objective, sizeof(float))) != SI_OK) return s;
     c->run_spins_valid = false;   // the sweep replaces the context's state
+    c->fused_valid = false;
     s = adjoint_grad(c, steps, (float *)gz.ptr, (float *)gd.ptr, (float *)gk.ptr, (float *)ob.ptr,
                      (const float *)qi.ptr, (const float *)pi.ptr);
     if (s != SI_OK) return s;

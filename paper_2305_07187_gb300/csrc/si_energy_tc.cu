@@ -211,6 +211,25 @@ __global__ void k_energy_finish(const unsigned long long *sum, const int8_t *h8,
     }
 }
 
+si_status tc_readout_buffer(Ctx *c) {
+    if (c->R > c->e_sum_cap) {
+        if (c->e_sum) cudaFree(c->e_sum);
+        c->e_sum = nullptr;
+        c->e_sum_cap = 0;
+        SI_CUDA_TRY(si_dev_malloc((void **)&c->e_sum, sizeof(unsigned long long) * c->R));
+        c->e_sum_cap = c->R;
+    }
+    return SI_OK;
+}
+
+si_status tc_energy_finish(Ctx *c, int R, int32_t *E, int32_t *C) {
+    k_energy_finish<<<R, 128, 0, c->stream>>>(c->e_sum, c->has_h ? c->dh8 : nullptr, c->dspins, c->ld8, c->n, R,
+                                              c->s_upper, E, C);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    return SI_OK;
+}
+
 // Exact energy/cut of R spin vectors (staged in spins_dev [R][ld], ld == c->ld8)
 // for a tensor-path context with integer J.  Returns SI_ERR_UNSUPPORTED when
 // the tensor readout does not apply (the caller falls back to dp4a).

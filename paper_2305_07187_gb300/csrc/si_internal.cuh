@@ -122,6 +122,10 @@ struct Ctx {
     int tile_n = 0;                      // replicas per CTA
     bool j_e4m3 = false;                 // dJ holds e4m3 bytes [mpad][ldk] (else bf16)
     bool tc_pair = false;                // k_tc_run on CTA pairs (cta_group::2, M = 256)
+    int tc_plane = -1;                   // operand plane holding bf16 q of the state (-1: not current)
+    int tc_p0 = 0;                       // operand plane the next k_tc_run starts from
+    bool tc_readout = false;             // the launch also sums sigma^T J sigma of its final spins
+    bool fused_valid = false;            // e_sum holds those sums for the last run's spins
     int tc_per_sm = 0;                   // co-resident CTAs per SM of the step kernel (0: not yet queried)
     int stages = 0;
     int rpad = 0;                        // R rounded up to tile_n
@@ -209,6 +213,13 @@ si_status tc_spins(Ctx *c, int8_t *spins, int ld);
 __global__ void k_energy_finish(const unsigned long long *sum, const int8_t *h8, const int8_t *s, int lds, int n,
                                 int R, long long s_upper, int32_t *E, int32_t *C);
 si_status tc_energy(Ctx *c, const int8_t *spins_dev, int R, int ld, int32_t *E, int32_t *C);
+// The per-replica sums the step kernel's readout pass left in c->e_sum: E and
+// the cut of the last run's spins (c->dspins).
+si_status tc_energy_finish(Ctx *c, int R, int32_t *E, int32_t *C);
+// c->e_sum with room for the context's replicas.
+si_status tc_readout_buffer(Ctx *c);
+// Whether a run of this context can sum its final energies in the step kernel.
+bool tc_readout_supported(const Ctx *c);
 const char *tc_describe(const Ctx *c, char *buf, int len);
 // 2D tensor map of e4m3 (1-byte) tiles of 64 x box_outer with the 64-byte swizzle.
 si_status tc_make_map_e4m3(CUtensorMap *m, void *base, int inner, int outer, int box_outer);

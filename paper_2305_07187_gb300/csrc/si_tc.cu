@@ -49,7 +49,7 @@ struct TcArgs {
     int ldk, rpad;
     const float *zeta, *dt, *h;
     float *q_state, *p_state;    // [R][n], initial in / final out
-    __nv_bfloat16 *qop;          // [2][rpad][ldk] bf16 operand of step t in plane t&1
+    __nv_bfloat16 *qop;          // [3][rpad][ldk]: bf16 q of step t in plane (t + p0) & 1, sign(q(T)) in plane 2
     int8_t *spins;               // [R][lds] or null
     int lds;
     unsigned *bar;               // [rblocks * mtiles] published-step flags
@@ -58,6 +58,9 @@ struct TcArgs {
     StepParams sp;
     int stall_step;              // failure-detection test hook (-1: off)
     int smem_bytes;              // dynamic shared memory the launch provides
+    int p0;                      // operand plane holding q(0)
+    int readout;                 // 1: one more pass with sign(q(T)) as the operand (exact energy)
+    unsigned long long *e_sum;   // [R] sigma^T J sigma of the final spins (readout), zeroed by the caller
 };
 
 // ------------------------------------------------------------------ kernel
@@ -215,10 +218,12 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
             bool ok = true;
             // pair: both CTAs walk the K blocks in the same order (the pair's rows first)
             const int kb0 = (CG2 ? (mt & ~1) : mt) * (TC_BM / TC_BK);
-            for (int t = 0; t < a.steps && ok; ++t) {
+            const int nsteps = a.steps + a.readout;
+            for (int t = 0; t < nsteps && ok; ++t) {
                 unsigned long long ready = t == 0 ? ~0ull : 0ull;   // owners known to have published step t
                 const unsigned need = (unsigned)t + (t == a.stall_step ? 1000000u : 0u);
-                const int yb = (t & 1) * a.rpad + r0 + (int)crank * (BN / 2);
+                // q(t) in plane (t + p0) & 1; the readout pass reads sign(q(T)) in plane 2
+                const int yb = (t == a.steps ? 2 : ((t + a.p0) & 1)) * a.rpad + r0 + (int)crank * (BN / 2);
                 for (int j = ring; j < a.kblocks; j += 2) {
                     int kb = kb0 + j;
                     if (kb >= a.kblocks) kb -= a.kblocks;
@@ -252,9 +257,9 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
         }
     } else if (warp == tc_poll_warp<EPI, E4>()) {
         // ------------------------------------------------ step-flag mirror
-        if (a.steps > 1)
-            mirror_flags(a.bar + (size_t)rb * a.mtiles, a.mtiles, (unsigned)(a.steps - 1), seen, lane, a.err,
-                         abort_flag, a.limit_ns);
+        if (a.steps + a.readout > 1)
+            mirror_flags(a.bar + (size_t)rb * a.mtiles, a.mtiles, (unsigned)(a.steps + a.readout - 1), seen, lane,
+                         a.err, abort_flag, a.limit_ns);
     } else if (warp <= TC_MMA_WARPS) {
         // ------------------------------------------------ MMA issuers
         // Warp 1 takes the even positions of the K loop into accumulator 0,
@@ -268,7 +273,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
             constexpr int HS = S / 2;
             uint32_t c = 0;
             bool ok = true;
-            for (int t = 0; t < a.steps && ok; ++t) {
+            for (int t = 0; t < a.steps + a.readout && ok; ++t) {
                 for (int j = w; j < a.kblocks; j += TC_MMA_WARPS, ++c) {
                     const int s = 2 * (int)(c % HS) + w;
                     if (!mbar_wait(full_bar(s), (c / HS) & 1u, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                 return CG2 ? mbar_wait_cluster(bar, parity, a.err, abort_flag, a.limit_ns)
                            : mbar_wait(bar, parity, a.err, abort_flag, a.limit_ns);
             };
-            for (int t = 0; t < a.steps && ok; ++t) {
+            for (int t = 0; t < a.steps + a.readout && ok; ++t) {
                 if (t > 0) {
                     if (!wait_bar(tmem_empty_bar, (uint32_t)((t - 1) & 1))) break;
                 }
@@ -385,7 +390,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
         }
         tmem_wait_st();
 #pragma unroll 1
-        for (int t = 0; t < a.steps; ++t) {
+        for (int t = 0; t < a.steps + a.readout; ++t) {
             bool ok = true;
             if (lane == 0)
                 ok = CG2 ? mbar_wait_cluster(accf_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns)
@@ -393,6 +398,47 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             tc_fence_after();
+            if (t == a.steps) {
+                // Readout pass: the accumulators hold G = J sigma of the final
+                // spins (integers below 2^24, exact in FP32); sigma_i G_ir goes
+                // to shared memory as [replica][row] (the ring is idle: every
+                // MMA has completed), then thread e adds replica column e over
+                // the tile's rows in 64-bit integers.
+                int *prod = reinterpret_cast<int *>(smem);
+#pragma unroll 1
+                for (int c = c_begin; c < c_begin + CPH; ++c) {
+                    uint32_t vf[32], vg[32], vq[32];
+                    tmem_ld32(tl + COL_ACC0 + c * 32, vf);
+                    if (two_acc) tmem_ld32(tl + COL_ACC1 + c * 32, vg);
+                    tmem_ld32(tl + COL_Q + c * 32, vq);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float G = two_acc ? __uint_as_float(vf[j]) + __uint_as_float(vg[j]) : __uint_as_float(vf[j]);
+                        const int sg = spin_of(__uint_as_float(vq[j]));
+                        prod[(c * 32 + j) * (TC_BM + 1) + row] = row_ok ? (int)G * sg : 0;
+                    }
+                }
+                // All epilogue warps have written their products (the
+                // epilogue barrier's phase of this pass: every warp arrives
+                // once per pass, and none can arrive for a later one).  The
+                // wait is bounded, so a warp that left on an abort cannot
+                // hold the others.
+                __syncwarp();
+                if (lane == 0) mbar_arrive(epi_done_bar);
+                bool okr = true;
+                if (lane == 0) okr = mbar_wait(epi_done_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns);
+                okr = __shfl_sync(0xffffffffu, okr ? 1 : 0, 0) != 0;
+                const int e = (int)threadIdx.x - 32 * TC_EPI_WARP0;
+                if (okr && e < BN && r0 + e < a.R) {
+                    long long x = 0;
+                    const int *col = prod + e * (TC_BM + 1);
+#pragma unroll 8
+                    for (int w2 = 0; w2 < TC_BM; ++w2) x += col[w2];
+                    if (x != 0) atomicAdd(a.e_sum + r0 + e, (unsigned long long)x);
+                }
+                break;
+            }
             const float zt = a.zeta[t], dtt = a.dt[t];
             const float dtm = dtt / a.sp.m;
             const bool last = (t == a.steps - 1);
@@ -453,13 +499,14 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                 } else {
                     tmem_st32(tl + COL_P + c * 32, vp);
                 }
-                if (!last) {
-                    // bf16 copy into the operand plane of step t+1, written
-                    // directly: a warp's 32 consecutive spins of one replica
-                    // are 64 contiguous bytes.  Entries outside n x R are
-                    // never written and keep the zeros of the initial fill.
+                {
+                    // bf16 copy into the operand plane of step t+1 (after the
+                    // last step: the plane a continuing run starts from),
+                    // written directly: a warp's 32 consecutive spins of one
+                    // replica are 64 contiguous bytes.  Entries outside n x R
+                    // are never written and keep the zeros of the initial fill.
                     __nv_bfloat16 *dst =
-                        a.qop + ((size_t)((t + 1) & 1) * a.rpad + (size_t)(r0 + c * 32)) * a.ldk + i;
+                        a.qop + ((size_t)((t + 1 + a.p0) & 1) * a.rpad + (size_t)(r0 + c * 32)) * a.ldk + i;
                     if (row_ok && r0 + c * 32 + 32 <= a.R) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) dst[(size_t)j * a.ldk] = __float2bfloat16_rn(__uint_as_float(vq[j]));
@@ -469,7 +516,16 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                             if (r0 + c * 32 + j < a.R)
                                 dst[(size_t)j * a.ldk] = __float2bfloat16_rn(__uint_as_float(vq[j]));
                     }
-                } else if (row_ok) {
+                }
+                if (last && a.readout && row_ok) {
+                    // sign(q(T)) as the operand of the readout pass (plane 2)
+                    __nv_bfloat16 *dst = a.qop + ((size_t)2 * a.rpad + (size_t)(r0 + c * 32)) * a.ldk + i;
+#pragma unroll
+                    for (int j = 0; j < 32; ++j)
+                        if (r0 + c * 32 + j < a.R)
+                            dst[(size_t)j * a.ldk] = __float2bfloat16_rn((float)spin_of(__uint_as_float(vq[j])));
+                }
+                if (last && row_ok) {
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int r = r0 + c * 32 + j;
@@ -499,8 +555,8 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                 else mbar_arrive(tmem_empty_bar);
                 mbar_arrive(epi_done_bar);
             }
-            if (publisher && !last) {
-                // All 8 warps have written their part of q(t+1): publish.
+            if (publisher && (!last || a.readout)) {
+                // All 8 warps have written their part of q(t+1) (or sign(q(T))): publish.
                 if (mbar_wait(epi_done_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns))
                     red_release_gpu_add(a.bar + (size_t)rb * a.mtiles + mt, 1u);
             }
@@ -520,7 +576,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
         constexpr int HS = S / 2;
         uint32_t cnt0 = 0u, cnt1 = 0u;
         bool ok = true;
-        for (int t = 0; t < a.steps && ok; ++t) {
+        for (int t = 0; t < a.steps + a.readout && ok; ++t) {
             for (int j = 0; j < a.kblocks; ++j) {
                 const int ring = j & 1;
                 const uint32_t c = ring ? cnt1 : cnt0;
@@ -730,6 +786,9 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
     a.stall_step = c->stall_step;
     a.sp = StepParams{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max,
                       c->prm.update_order, c->prm.wall_zero_p};
+    a.p0 = c->tc_p0;
+    a.readout = c->tc_readout ? 1 : 0;
+    a.e_sum = c->e_sum;
     const int grid = a.mtiles * a.rblocks;
     if (a.rblocks * a.mtiles > c->nbar || a.mtiles > 64) {
         set_error("tensor path: too many tiles for the step flags (n <= 8192 per context)");
@@ -771,6 +830,7 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
         return SI_ERR_UNSUPPORTED;
     }
     SI_CUDA_TRY(cudaMemsetAsync(c->dbar, 0, sizeof(unsigned) * grid, c->stream));
+    if (a.readout) SI_CUDA_TRY(cudaMemsetAsync(c->e_sum, 0, sizeof(unsigned long long) * c->R, c->stream));
     if constexpr (CG2) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
@@ -792,6 +852,10 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
     }
     c->launches += 1;
     return SI_OK;
+}
+
+bool tc_readout_supported(const Ctx *c) {
+    return !c->grp && !c->j_e4m3 && !c->tc_pair && c->integer_j && (!c->has_h || c->integer_h);
 }
 
 si_status tc_run(Ctx *c, int steps, int8_t *spins_dev) {
@@ -926,7 +990,7 @@ si_status tc_prepare(Ctx *c, const float *J_dev) {
     si_status sc = c->j_e4m3 ? tc_convert_j_e4m3(J_dev, n, c->dJ, c->ldk, c->mpad, c->num_sms, c->stream)
                              : tc_convert_j(J_dev, n, c->dJ, c->ldk, c->mpad, c->num_sms, c->stream);
     if (sc != SI_OK) return sc;
-    c->qbuf_bytes = 2ull * c->rpad * c->ldk * 2;
+    c->qbuf_bytes = 3ull * c->rpad * c->ldk * 2;   // planes 0, 1: q; plane 2: sign(q(T)) for the readout pass
     SI_CUDA_TRY(si_dev_malloc(&c->dqbuf, c->qbuf_bytes));
     SI_CUDA_TRY(cudaMemsetAsync(c->dqbuf, 0, c->qbuf_bytes, c->stream));
     SI_CUDA_TRY(si_dev_malloc(&c->dq, sizeof(float) * (size_t)c->R * n));
@@ -935,7 +999,7 @@ si_status tc_prepare(Ctx *c, const float *J_dev) {
                             : tc_make_map_bf16(&c->mapA, c->dJ, c->ldk, c->mpad, TC_BK, TC_BM);
     if (s != SI_OK) return s;
     // pairs load half of the q tile per CTA
-    s = tc_make_map_bf16(&c->mapB, c->dqbuf, c->ldk, 2 * c->rpad, TC_BK, c->tc_pair ? c->tile_n / 2 : c->tile_n);
+    s = tc_make_map_bf16(&c->mapB, c->dqbuf, c->ldk, 3 * c->rpad, TC_BK, c->tc_pair ? c->tile_n / 2 : c->tile_n);
     if (s != SI_OK) return s;
     const int mtiles = c->mpad / TC_BM;
     const int grid = mtiles * (c->rpad / c->tile_n);
