@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstdio>
+#include <type_traits>
 
 #include "si_device.cuh"
 
@@ -135,7 +136,7 @@ __global__ void __launch_bounds__(AG_THREADS) k_adj_gemm(AdjGemmArgs<T> a) {
                 objp += (T)-0.5 * x * G - hi * x;
             } else {
                 const T la = a.X[e];
-                a.LQ[e] = a.LB[e] + dtt * (-k * la + zt * G);
+                a.LQ[e] = adj_lq(a.LB[e], la, G, dtt, zt, k);
                 a.LP[e] = la;
             }
         }
@@ -176,10 +177,8 @@ __global__ void __launch_bounds__(AE_THREADS) k_adj_elem(
          e += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(e / n), i = (int)(e % n);
         const size_t x = (size_t)r * ld + i;
-        const T Dq = (fabs(qn[x]) < qmax) ? (T)1 : (T)0;
-        const T Dp = (fabs(pn[x]) < pmax) ? (T)1 : (T)0;
-        const T lb = Dq * lq[x];
-        const T la = Dp * (lp[x] + dtm * lb);
+        T la, lb;
+        adj_clamps(lq[x], lp[x], qn[x], pn[x], qmax, pmax, dtm, la, lb);
         la_out[x] = la;
         lb_out[x] = lb;
         if (xs_la) {
@@ -190,11 +189,11 @@ __global__ void __launch_bounds__(AE_THREADS) k_adj_elem(
             xb[(size_t)ADJ_TC_RB * ldk] = p1;
             xb[(size_t)2 * ADJ_TC_RB * ldk] = p2;
         }
-        const T dq = q[x] - q0;
-        const T force = -k * dq + zt * F[x];
-        s0.add(lb * pn[x] / m + la * force);
-        s1.add(dtt * la * F[x]);
-        s2.add(-dtt * la * dq);
+        T g0, g1, g2;
+        adj_terms(la, lb, q[x], F[x], pn[x], q0, k, m, zt, dtt, g0, g1, g2);
+        s0.add(g0);
+        s1.add(g1);
+        s2.add(g2);
     }
     (void)p;
     // fixed-shape reduction: warp shuffle trees of the compensated sums,
@@ -236,18 +235,18 @@ __global__ void __launch_bounds__(AE_THREADS) k_adj_elem(
 // sums steps u, u+128, ... and thread 0 adds the 128 results in order) and
 // the objective.  Launched with 128 threads per block.
 template <typename T>
-__global__ void k_adj_finish(int T_steps, const T *part, int nobj, const T *obj_part, float *g_zeta,
+__global__ void k_adj_finish(int T_steps, const T *part, int nb, int nobj, const T *obj_part, float *g_zeta,
                              float *g_dt, float *g_k, float *objective) {
     __shared__ T gks[128];
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < T_steps) {
-        const T *pp = part + (size_t)t * 3 * AE_BLOCKS;
+        const T *pp = part + (size_t)t * 3 * nb;
         CompSum<T> a0, a1;
         a0.init();
         a1.init();
-        for (int b = 0; b < AE_BLOCKS; ++b) {
+        for (int b = 0; b < nb; ++b) {
             a0.add(pp[b]);
-            a1.add(pp[AE_BLOCKS + b]);
+            a1.add(pp[nb + b]);
         }
         if (g_dt) g_dt[t] = (float)a0.value();
         if (g_zeta) g_zeta[t] = (float)a1.value();
@@ -256,8 +255,8 @@ __global__ void k_adj_finish(int T_steps, const T *part, int nobj, const T *obj_
         CompSum<T> gk;
         gk.init();
         for (int s = threadIdx.x; s < T_steps; s += blockDim.x) {
-            const T *pp = part + (size_t)s * 3 * AE_BLOCKS + 2 * AE_BLOCKS;
-            for (int b = 0; b < AE_BLOCKS; ++b) gk.add(pp[b]);
+            const T *pp = part + (size_t)s * 3 * nb + 2 * nb;
+            for (int b = 0; b < nb; ++b) gk.add(pp[b]);
         }
         gks[threadIdx.x] = gk.value();
         __syncthreads();
@@ -294,12 +293,19 @@ static si_status adjoint_impl(Ctx *c, int steps, float *g_zeta, float *g_dt, flo
     const size_t plane = (size_t)R * ld;
     const dim3 ggrid(cdiv(n, AG_M), cdiv(R, AG_R));
     const int nobj = tc ? adj_tc_nobj(tc) : (int)(ggrid.x * ggrid.y);
-    // workspace: ckpt (nseg+1) x {q,p}; slots (K+1) x {q,p}; F K; lq, lp, la, lb;
-    // partials 3 * AE_BLOCKS * steps; objective partials.
-    const size_t n_planes = 2 * (size_t)(nseg + 1) + 2 * (size_t)(K + 1) + (size_t)K + 4;
+    // The persistent sweep (tensor cores) keeps two sets of slots, so that a
+    // segment can be recomputed while the next one is swept back, and writes
+    // one gradient partial per CTA and step.
+    const bool persistent = tc && adj_tc_run_splits(tc) > 0;
+    const int nb = persistent ? adj_tc_run_nparts(tc) : AE_BLOCKS;
+    const int nsets = persistent ? 2 : 1;
+    // workspace: ckpt (nseg+1) x {q,p}; nsets x slots (K+1) x {q,p}, F K;
+    // lq, lp, la, lb; partials 3 * nb * steps; objective partials.
+    const size_t n_planes =
+        2 * (size_t)(nseg + 1) + (size_t)nsets * (2 * (size_t)(K + 1) + (size_t)K) + 4;
     // + the outputs g_zeta[T], g_dt[T], g_k, objective (float) at the end
     const size_t out_floats = 2 * (size_t)std::max(steps, 1) + 2;
-    const size_t bytes = sizeof(T) * (n_planes * plane + 3 * (size_t)AE_BLOCKS * std::max(steps, 1) +
+    const size_t bytes = sizeof(T) * (n_planes * plane + 3 * (size_t)nb * std::max(steps, 1) +
                                       (size_t)nobj) + sizeof(float) * out_floats;
     if (c->g_ws_bytes < bytes) {
         if (c->g_ws) cudaFree(c->g_ws);
@@ -317,11 +323,17 @@ static si_status adjoint_impl(Ctx *c, int steps, float *g_zeta, float *g_dt, flo
     T *sq = w;                             w += (size_t)(K + 1) * plane;
     T *sp = w;                             w += (size_t)(K + 1) * plane;
     T *sF = w;                             w += (size_t)K * plane;
+    T *sq1 = sq, *sp1 = sp, *sF1 = sF;     // second slot set (persistent sweep)
+    if (persistent) {
+        sq1 = w;                           w += (size_t)(K + 1) * plane;
+        sp1 = w;                           w += (size_t)(K + 1) * plane;
+        sF1 = w;                           w += (size_t)K * plane;
+    }
     T *lq = w;                             w += plane;
     T *lp = w;                             w += plane;
     T *la = w;                             w += plane;
     T *lb = w;                             w += plane;
-    T *part = w;                           w += 3 * (size_t)AE_BLOCKS * std::max(steps, 1);
+    T *part = w;                           w += 3 * (size_t)nb * std::max(steps, 1);
     T *objp = w;                           w += nobj;
     float *gout = reinterpret_cast<float *>(w);   // g_zeta[T], g_dt[T], g_k, objective
     const StepParams spar{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max, 0, 0};
@@ -412,6 +424,68 @@ static si_status adjoint_impl(Ctx *c, int steps, float *g_zeta, float *g_dt, flo
             return SI_OK;
         };
 
+        if (persistent) {
+            // Persistent sweep: the forward pass is one launch (checkpoints at
+            // segment ends, segment s's slots in set s & 1); each later
+            // launch sweeps segment s back while segment s - 1 is recomputed
+            // into the other set (side by side when both chains fit, else
+            // one after the other).
+            if constexpr (std::is_same<T, float>::value) {
+                AdjChain f{};
+                f.reverse = 0;
+                f.buf0 = 0;
+                f.flags = adj_tc_run_flags(tc, 0);
+                f.sq[0] = sq; f.sp[0] = sp; f.sF[0] = sF;
+                f.sq[1] = sq1; f.sp[1] = sp1; f.sF[1] = sF1;
+                AdjChain r = f;
+                r.reverse = 1;
+                r.buf0 = 2;
+                r.flags = adj_tc_run_flags(tc, 1);
+                r.lq = lq;
+                r.lp = lp;
+                r.part = part;
+                f.t_start = 0;
+                f.len = steps;
+                f.q_in = ckq;
+                f.p_in = ckp;
+                f.ckq = ckq;
+                f.ckp = ckp;
+                if (steps > 0 && (st = adj_tc_run(c, tc, &f, 1, K)) != SI_OK) return st;
+                SI_CUDA_TRY(cudaMemcpyAsync(c->dqbuf, ckq + (size_t)nseg * plane, sizeof(T) * plane,
+                                            cudaMemcpyDeviceToDevice, c->stream));
+                SI_CUDA_TRY(cudaMemcpy2DAsync(c->dp, sizeof(T) * n, ckp + (size_t)nseg * plane, sizeof(T) * ld,
+                                              sizeof(T) * n, R, cudaMemcpyDeviceToDevice, c->stream));
+                if ((st = gemm_terminal(ckq + (size_t)nseg * plane)) != SI_OK) return st;
+                const bool pair = adj_tc_run_pair(tc);
+                for (int s = nseg - 1; s >= 0; --s) {
+                    r.t_start = s * K;
+                    r.len = std::min(K, steps - s * K);
+                    AdjChain ch2[2] = {r, f};
+                    int nch = 1;
+                    if (s > 0) {
+                        ch2[1].t_start = (s - 1) * K;
+                        ch2[1].len = K;
+                        ch2[1].q_in = ckq + (size_t)(s - 1) * plane;
+                        ch2[1].p_in = ckp + (size_t)(s - 1) * plane;
+                        ch2[1].ckq = nullptr;
+                        ch2[1].ckp = nullptr;
+                        nch = 2;
+                    }
+                    if (nch == 2 && !pair) {
+                        if ((st = adj_tc_run(c, tc, &ch2[0], 1, K)) != SI_OK) return st;
+                        if ((st = adj_tc_run(c, tc, &ch2[1], 1, K)) != SI_OK) return st;
+                    } else if ((st = adj_tc_run(c, tc, ch2, nch, K)) != SI_OK) {
+                        return st;
+                    }
+                }
+                const int T1 = std::max(steps, 1);
+                k_adj_finish<T><<<cdiv(T1, 128), 128, 0, c->stream>>>(steps, part, nb, nobj, objp, gout, gout + T1,
+                                                                      gout + 2 * T1, gout + 2 * T1 + 1);
+                SI_CUDA_TRY(cudaGetLastError());
+                c->launches += 1;
+                return SI_OK;
+            }
+        }
         // Forward pass: checkpoints at the start of every segment and at T.
         for (int s = 0; s < nseg; ++s) {
             if ((st = recompute(s)) != SI_OK) return st;
@@ -461,8 +535,8 @@ static si_status adjoint_impl(Ctx *c, int steps, float *g_zeta, float *g_dt, flo
             }
         }
         const int T1 = std::max(steps, 1);
-        k_adj_finish<T><<<cdiv(T1, 128), 128, 0, c->stream>>>(steps, part, nobj, objp, gout, gout + T1, gout + 2 * T1,
-                                                              gout + 2 * T1 + 1);
+        k_adj_finish<T><<<cdiv(T1, 128), 128, 0, c->stream>>>(steps, part, nb, nobj, objp, gout, gout + T1,
+                                                              gout + 2 * T1, gout + 2 * T1 + 1);
         SI_CUDA_TRY(cudaGetLastError());
         c->launches += 1;
         return SI_OK;

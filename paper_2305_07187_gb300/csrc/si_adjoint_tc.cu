@@ -49,8 +49,15 @@ enum { AT_FORWARD = 0, AT_TERMINAL = 1, AT_ADJOINT = 2 };
 
 struct AdjTc {
     int n, R, ld, ldk, mpad, mtiles, nrb, kblocks, kb_per, splits;
+    // persistent sweep (k_adj_run): cluster size, K blocks per split, and
+    // whether a recompute chain and a reverse chain fit side by side
+    int run_splits = 0, run_kb_per = 0;
+    bool run_pair = false;
+    unsigned *run_flags = nullptr;  // [2][mtiles * nrb] slices published, per chain
     __nv_bfloat16 *jb = nullptr;    // [mpad][ldk]
-    __nv_bfloat16 *xs = nullptr;    // [3][nrb * 192][ldk]: forward chain (two buffers), lambda_a
+    // [4][nrb * 192][ldk]: per-step sweep: forward chain (buffers 0, 1),
+    // lambda_a (2); persistent sweep: forward chain (0, 1), reverse chain (2, 3)
+    __nv_bfloat16 *xs = nullptr;
     CUtensorMap mapA, mapB;
 };
 
@@ -140,7 +147,7 @@ __device__ __forceinline__ void at_apply16(const AdjTcArgs &a, int i, int r0, co
             objp += -0.5f * x * G[u] - hi * x;
         } else {
             const float la = u0[u];
-            a.LQ[e] = u1[u] + dtt * (-a.sp.k * la + zt * G[u]);
+            a.LQ[e] = adj_lq(u1[u], la, G[u], dtt, zt, a.sp.k);
             a.LP[e] = la;
         }
     }
@@ -397,6 +404,483 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
     }
 }
 
+// ------------------------------------------------------------------ persistent sweep
+// k_adj_run runs a stretch of the sweep in one launch: the forward products
+// of consecutive steps (the first forward pass, which also writes the
+// checkpoints, or the recomputation of one segment), the reverse steps of
+// one segment, or a recomputation and a reverse sweep side by side (segment
+// s-1 is recomputed into the other set of slots while segment s is swept
+// back).  A chain's CTAs are the (M tile, replica block, K split) CTAs of
+// k_adj_tc with the same products and the same split-K reduction through
+// distributed shared memory, so every value equals the per-step kernels'.
+// The state of a CTA's slice (128 spins x 64/S replicas) stays in registers
+// for the whole launch: q, p on a forward chain; lambda_a, lambda_b on a
+// reverse chain, where the elementwise part of the next reverse step is
+// fused into the epilogue of each adjoint product.
+//
+// Consecutive products exchange their operand pieces through two buffers
+// per chain in L2: product u reads buffer u & 1 and its epilogue writes the
+// pieces of the next operand into the other one.  Each CTA publishes its
+// slice with a release increment of its tile's counter; a producer waits
+// until the counters of the M tiles its K range covers show all S slices of
+// the step (dataflow, no grid barrier).  The cluster barrier of every step
+// makes the double buffer safe: a cluster's epilogue of product u comes
+// after the MMAs of product u in all its CTAs, whose K ranges cover every
+// M tile, so every tile has published the operand of product u and thus
+// finished reading buffer (u - 1) & 1 before it is overwritten.
+//
+// Every thread of a CTA takes part in one cluster barrier per product (and
+// one at the start), whatever happens, so the barriers cannot hang; every
+// other wait has a time limit, after which the kernel raises the device
+// error word and skips the remaining work.
+constexpr int AR_RECV = AT_RB * AT_BM * 4;               // 32 KB: one buffer of pushed partials
+constexpr int AR_NBARS = 2 * AT_S + 3;                   // full, empty, accf, drain, pub
+constexpr int AR_EPI = 16;                               // epilogue warps
+constexpr int AR_THREADS = 32 * (2 + AR_EPI);            // producer, MMA issuer, epilogue
+constexpr int AR_SMEM = AT_TILES + AT_MISC + 2 * AR_RECV + 1024;
+static_assert(AR_NBARS * 8 + 16 + AR_EPI * 6 * 4 <= AT_MISC, "misc area too small");
+static_assert(AR_SMEM <= 232448, "persistent sweep exceeds the shared memory of a CTA");
+
+struct AdjRunArgs {
+    int n, R, ld, ldk, nrb, mtiles, kblocks, kb_per, splits, K, nparts;
+    size_t plane;                // R * ld
+    const float *h;
+    StepParams sp;
+    const float *zeta, *dt;
+    __nv_bfloat16 *xs;           // operand buffers [4][nrb * 192][ldk]
+    AdjChain ch[2];
+    int *err;
+    long long limit_ns;
+};
+
+template <int SR>
+__global__ void __launch_bounds__(AR_THREADS, 1)
+    k_adj_run(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+              const __grid_constant__ AdjRunArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bar0 = sbase + AT_TILES;
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (AT_S + s); };
+    const uint32_t accf_bar = bar0 + 8u * (2 * AT_S);
+    const uint32_t drain_bar = bar0 + 8u * (2 * AT_S + 1);
+    const uint32_t pub_bar = bar0 + 8u * (2 * AT_S + 2);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + AT_TILES + AR_NBARS * 8);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + AT_TILES + AR_NBARS * 8 + 4);
+    float *red = reinterpret_cast<float *>(smem + AT_TILES + AR_NBARS * 8 + 16);   // [16 warps][3 sums][hi, lo]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    const int per_chain = a.mtiles * a.nrb * a.splits;
+    const AdjChain &ch = a.ch[blockIdx.x / per_chain];
+    const int local = blockIdx.x % per_chain;            // index of the CTA's gradient partials
+    const int mn = local / a.splits, ks = local % a.splits;
+    const int mt = mn / a.nrb, rb = mn % a.nrb;
+    const int S = a.splits;                               // == AT_RB / SR
+    const int kb0 = ks * a.kb_per;
+    const int nk = min(a.kblocks, kb0 + a.kb_per) - kb0;   // >= 1 by construction
+    const int len = ch.len;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < AT_S; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        mbar_init(accf_bar, 1);
+        mbar_init(drain_bar, 1);
+        mbar_init(pub_bar, AR_EPI);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_slot)),
+                     "n"(256)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // every CTA of the cluster is running before any pushes partials to it
+    cluster_arrive_relaxed();
+    cluster_wait_acquire();
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer
+        // Lanes 0 .. nown-1 wait for the counters of the M tiles that the
+        // CTA's K range covers (K block kb holds spins of M tile kb / 2);
+        // lane 0 then issues the J tile and the operand tile of every K block.
+        const int o0 = kb0 >> 1, nown = ((kb0 + nk - 1) >> 1) - o0 + 1;
+        uint32_t cnt = 0;
+        bool ok = true;
+        for (int u = 0; u < len; ++u) {
+            if (ok) {
+                bool mine = true;
+                if (lane < nown)
+                    mine = wait_counter_geq(ch.flags + (size_t)(o0 + lane) * a.nrb + rb, (unsigned)(S * (u + 1)),
+                                            a.err, a.limit_ns);
+                ok = __all_sync(0xffffffffu, mine);
+                // orders every lane's acquire before lane 0's copies
+                __syncwarp();
+                if (ok && lane == 0) {
+                    fence_proxy_async_global();
+                    const int yb = ((ch.buf0 + (u & 1)) * a.nrb + rb) * AT_BN;
+                    for (int c = 0; c < nk; ++c, ++cnt) {
+                        const int s = (int)(cnt % AT_S);
+                        const uint32_t ph = (cnt / AT_S) & 1u;
+                        if (!mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t dA = sbase + s * AT_STAGE;
+                        mbar_arrive_expect_tx(full_bar(s), (uint32_t)AT_STAGE);
+                        tma_load_2d(dA, &mapA, full_bar(s), (kb0 + c) * AT_BK, mt * AT_BM);
+                        tma_load_2d(dA + AT_A_BYTES, &mapB, full_bar(s), (kb0 + c) * AT_BK, yb);
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            }
+            cluster_arrive_relaxed();
+            cluster_wait_acquire();
+        }
+        // Let every copy land before the CTA exits.
+        if (lane == 0) {
+            const uint32_t first = cnt > (uint32_t)AT_S ? cnt - AT_S : 0u;
+            for (uint32_t c = first; c < cnt; ++c) {
+                const unsigned long long t0 = globaltimer_ns();
+                while (!mbar_try_wait(full_bar((int)(c % AT_S)), (c / AT_S) & 1u)) {
+                    if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                        atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
+                        break;
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        uint32_t c = 0;
+        bool ok = true;
+        constexpr uint32_t idesc = idesc_bf16(AT_BM, AT_BN);
+        for (int u = 0; u < len; ++u) {
+            if (ok) {
+                if (lane == 0) {
+                    // after the previous step's cluster barrier: the epilogue has read the accumulator
+                    tc_fence_after();
+                    for (int cc = 0; cc < nk; ++cc, ++c) {
+                        const int s = (int)(c % AT_S);
+                        if (!mbar_wait(full_bar(s), (c / AT_S) & 1u, a.err, abort_flag, a.limit_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t ad = sdesc_sw128(sbase + s * AT_STAGE);
+                        const uint64_t bd = sdesc_sw128(sbase + s * AT_STAGE + AT_A_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < AT_BK / 16; ++kk)
+                            mma_bf16(tmem, ad + 2u * kk, bd + 2u * kk, idesc, (cc != 0 || kk != 0) ? 1u : 0u);
+                        mma_commit(empty_bar(s));
+                    }
+                    if (ok) mma_commit(accf_bar);
+                }
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            }
+            cluster_arrive_relaxed();
+            cluster_wait_acquire();
+        }
+        // Drain: every MMA this thread issued has completed.
+        if (lane == 0) {
+            mma_commit(drain_bar);
+            const unsigned long long t0 = globaltimer_ns();
+            while (!mbar_try_wait(drain_bar, 0u)) {
+                if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                    atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
+                    break;
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue (16 warps)
+        // Warp w reads TMEM lanes 32 (w % 4) .. +31 (thread = spin i); the four
+        // warps of a lane quadrant (sub = 0..3) take a quarter of the columns
+        // when pushing partials and W = SR/4 replicas of the CTA's slice
+        // afterwards, so that four warps per SM sub-partition hide each
+        // other's latencies.
+        constexpr int W = SR / 4;
+        const int e = warp - 2;
+        const int quad = warp & 3, sub = e >> 2;
+        const int row = quad * 32 + lane;
+        const int i = mt * AT_BM + row;
+        const bool row_ok = i < a.n;
+        const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+        const int rl0 = ks * SR + sub * W;                    // first replica of the thread, within the tile
+        const int rs0 = rb * AT_RB + rl0;
+        const int nv = row_ok ? max(0, min(W, a.R - rs0)) : 0;
+        const float hi = (!ch.reverse && a.h && row_ok) ? a.h[i] : 0.f;
+        const size_t pl = a.plane;
+        const float kq = a.sp.k, mq = a.sp.m, q0 = a.sp.q0, qmax = a.sp.q_max, pmax = a.sp.p_max;
+        const int zrev = (ch.t_start / a.K) & 1;             // slot set of a reverse chain's segment
+        float x0[W], x1[W];      // forward: q, p; reverse: lambda_a, lambda_b
+#pragma unroll
+        for (int u = 0; u < W; ++u) x0[u] = x1[u] = 0.f;
+        uint32_t pubs = 0;
+        bool ok = true;
+        auto eidx = [&](int u) { return (size_t)(rs0 + u) * a.ld + i; };
+        // bf16 pieces of x0 as rows of the B operand in buffer `buf`
+        auto pieces = [&](int buf) {
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                if (u < nv) {
+                    __nv_bfloat16 p0, p1, p2;
+                    bf16_split3(x0[u], p0, p1, p2);
+                    __nv_bfloat16 *xb =
+                        a.xs + ((size_t)(buf * a.nrb + rb) * AT_BN + (size_t)(rl0 + u)) * a.ldk + i;
+                    xb[0] = p0;
+                    xb[(size_t)AT_RB * a.ldk] = p1;
+                    xb[(size_t)2 * AT_RB * a.ldk] = p2;
+                }
+            }
+        };
+        // The warps' stores are ordered before lane 0's arrivals (warp
+        // barrier), the arrivals before thread 0's wait, and that before its
+        // release increment of the tile's counter.  On a reverse chain the
+        // CTA's gradient partials of step tau are written too (warp shuffle
+        // trees of the compensated sums, then the 16 warps in order).
+        auto publish = [&](CompSum<float> *g, int tau) {
+            if (g) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+#pragma unroll
+                    for (int off = 16; off > 0; off >>= 1) {
+                        const float oh = __shfl_down_sync(0xffffffffu, g[j].hi, off);
+                        const float ol = __shfl_down_sync(0xffffffffu, g[j].lo, off);
+                        g[j].merge(oh, ol);
+                    }
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        red[(e * 3 + j) * 2] = g[j].hi;
+                        red[(e * 3 + j) * 2 + 1] = g[j].lo;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(pub_bar);
+            if (e == 0 && lane == 0) {
+                if (mbar_wait(pub_bar, pubs & 1u, a.err, abort_flag, a.limit_ns)) {
+                    if (g) {
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            CompSum<float> s;
+                            s.init();
+                            for (int w = 0; w < AR_EPI; ++w) s.merge(red[(w * 3 + j) * 2], red[(w * 3 + j) * 2 + 1]);
+                            ch.part[(size_t)tau * 3 * a.nparts + (size_t)j * a.nparts + local] = s.value();
+                        }
+                    }
+                    red_release_gpu_add(ch.flags + (size_t)mt * a.nrb + rb, 1u);
+                }
+            }
+            ++pubs;
+        };
+        // Slot values of reverse step tau (slot jj of the segment): q_{tau+1},
+        // p_{tau+1} (the clamp indicators, lb p'/m), q_tau and F_tau.
+        float pre[4][W];
+        auto fetch = [&](int jj) {
+            const float *sqz = ch.sq[zrev], *spz = ch.sp[zrev], *sFz = ch.sF[zrev];
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                if (u < nv) {
+                    const size_t x = eidx(u);
+                    pre[0][u] = sqz[(size_t)(jj + 1) * pl + x];
+                    pre[1][u] = spz[(size_t)(jj + 1) * pl + x];
+                    pre[2][u] = sqz[(size_t)jj * pl + x];
+                    pre[3][u] = sFz[(size_t)jj * pl + x];
+                }
+            }
+        };
+        // Elementwise part of reverse step tau from the adjoint state (lq, lp)
+        // of step tau + 1 and the fetched slot values: lambda_a and lambda_b
+        // into x0, x1 and the gradient terms into g.
+        auto elem = [&](int tau, const float *lqv, const float *lpv, CompSum<float> *g) {
+            const float zt = a.zeta[tau], dtt = a.dt[tau];
+            const float dtm = dtt / mq;
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                if (u < nv) {
+                    adj_clamps(lqv[u], lpv[u], pre[0][u], pre[1][u], qmax, pmax, dtm, x0[u], x1[u]);
+                    float g0, g1, g2;
+                    adj_terms(x0[u], x1[u], pre[2][u], pre[3][u], pre[1][u], q0, kq, mq, zt, dtt, g0, g1, g2);
+                    g[0].add(g0);
+                    g[1].add(g1);
+                    g[2].add(g2);
+                }
+            }
+        };
+
+        // ---------------- prologue: the operand of product 0
+        if (!ch.reverse) {
+#pragma unroll
+            for (int u = 0; u < W; ++u)
+                if (u < nv) {
+                    x0[u] = ch.q_in[eidx(u)];
+                    x1[u] = ch.p_in[eidx(u)];
+                }
+            pieces(ch.buf0);
+            publish(nullptr, 0);
+        } else {
+            float lqv[W], lpv[W];
+#pragma unroll
+            for (int u = 0; u < W; ++u) {
+                lqv[u] = u < nv ? ch.lq[eidx(u)] : 0.f;
+                lpv[u] = u < nv ? ch.lp[eidx(u)] : 0.f;
+            }
+            fetch(len - 1);
+            CompSum<float> g[3];
+            g[0].init();
+            g[1].init();
+            g[2].init();
+            const int tau = ch.t_start + len - 1;
+            elem(tau, lqv, lpv, g);
+            pieces(ch.buf0);
+            publish(g, tau);
+        }
+
+        // ---------------- products
+#pragma unroll 1
+        for (int u = 0; u < len; ++u) {
+            // a reverse chain's slot values for the next elementwise step load
+            // while the product runs
+            if (ch.reverse && u + 1 < len) fetch(len - 2 - u);
+            bool okw = true;
+            if (ok && lane == 0) okw = mbar_wait(accf_bar, (uint32_t)(u & 1), a.err, abort_flag, a.limit_ns);
+            ok = ok && __shfl_sync(0xffffffffu, okw ? 1 : 0, 0) != 0;
+            tc_fence_after();
+            const uint32_t recv = sbase + AT_TILES + AT_MISC + (uint32_t)(u & 1) * AR_RECV;
+            if (ok) {
+                // this warp's 16 replicas of the tile, pieces added (hi + mid) + lo;
+                // replicas [j SR, j SR + SR) go to cluster rank j as [source][SR / 4][row] float4
+                uint32_t v0[16], v1[16], v2[16];
+                tmem_ld16(tmem + lane_off + sub * 16, v0);
+                tmem_ld16(tmem + lane_off + AT_RB + sub * 16, v1);
+                tmem_ld16(tmem + lane_off + 2 * AT_RB + sub * 16, v2);
+                tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    float G4[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        G4[j] = (__uint_as_float(v0[4 * q + j]) + __uint_as_float(v1[4 * q + j])) +
+                                __uint_as_float(v2[4 * q + j]);
+                    const int rl = sub * 16 + 4 * q;
+                    const int owner = rl / SR, c4 = (rl % SR) / 4;
+                    const uint32_t off = (uint32_t)(((ks * (SR / 4) + c4) * AT_BM + row) * 16);
+                    st_dsmem_v4(recv + off, (uint32_t)owner, make_float4(G4[0], G4[1], G4[2], G4[3]));
+                }
+            }
+            tc_fence_before();
+            cluster_arrive_release();
+            cluster_wait_acquire();
+            if (!ok || *abort_flag) {
+                ok = false;
+                continue;
+            }
+            // the partials of this thread's replicas, added in source-rank order
+            float G[W];
+#pragma unroll
+            for (int u2 = 0; u2 < W; ++u2) G[u2] = 0.f;
+            const float4 *rv = reinterpret_cast<const float4 *>(smem + AT_TILES + AT_MISC + (u & 1) * AR_RECV);
+            for (int p = 0; p < S; ++p) {
+                if constexpr (W >= 4) {
+#pragma unroll
+                    for (int cc = 0; cc < W / 4; ++cc) {
+                        const float4 v = rv[(p * (SR / 4) + sub * (W / 4) + cc) * AT_BM + row];
+                        G[4 * cc] += v.x;
+                        G[4 * cc + 1] += v.y;
+                        G[4 * cc + 2] += v.z;
+                        G[4 * cc + 3] += v.w;
+                    }
+                } else {
+                    // W == 2: half of the chunk (sub / 2)
+                    const float4 v = rv[(p * (SR / 4) + (sub >> 1)) * AT_BM + row];
+                    G[0] += (sub & 1) ? v.z : v.x;
+                    G[1] += (sub & 1) ? v.w : v.y;
+                }
+            }
+            if (!ch.reverse) {
+                // forward step t: Eq. 8 with the walls of Eq. 6
+                const int t = ch.t_start + u, sg = t / a.K, j = t - sg * a.K, z = sg & 1;
+                const float zt = a.zeta[t], dtt = a.dt[t];
+                const float dtm = dtt / a.sp.m;
+                float *sqz = ch.sq[z], *spz = ch.sp[z], *sFz = ch.sF[z];
+                const bool ck_end = ch.ckq != nullptr && (t + 1 == ch.t_start + len || j + 1 == a.K);
+#pragma unroll
+                for (int u2 = 0; u2 < W; ++u2) {
+                    if (u2 < nv) {
+                        const size_t x = eidx(u2);
+                        const float F = G[u2] + hi;
+                        float qo, po;
+                        integrate<float>(x0[u2], x1[u2], F, zt, dtt, dtm, a.sp, qo, po);
+                        if (j == 0) {
+                            sqz[x] = x0[u2];
+                            spz[x] = x1[u2];
+                        }
+                        sFz[(size_t)j * pl + x] = F;
+                        sqz[(size_t)(j + 1) * pl + x] = qo;
+                        spz[(size_t)(j + 1) * pl + x] = po;
+                        if (ck_end) {
+                            ch.ckq[(size_t)(sg + 1) * pl + x] = qo;
+                            ch.ckp[(size_t)(sg + 1) * pl + x] = po;
+                        }
+                        x0[u2] = qo;
+                        x1[u2] = po;
+                    }
+                }
+                if (u + 1 < len) {
+                    pieces(ch.buf0 + ((u + 1) & 1));
+                    publish(nullptr, 0);
+                }
+            } else {
+                // adjoint product of step t, then the elementwise part of step t - 1
+                const int t = ch.t_start + len - 1 - u;
+                const float zt = a.zeta[t], dtt = a.dt[t];
+                float lqv[W], lpv[W];
+#pragma unroll
+                for (int u2 = 0; u2 < W; ++u2) {
+                    lqv[u2] = adj_lq(x1[u2], x0[u2], G[u2], dtt, zt, kq);
+                    lpv[u2] = x0[u2];
+                }
+                if (u + 1 < len) {
+                    CompSum<float> g[3];
+                    g[0].init();
+                    g[1].init();
+                    g[2].init();
+                    elem(t - 1, lqv, lpv, g);
+                    pieces(ch.buf0 + ((u + 1) & 1));
+                    publish(g, t - 1);
+                } else {
+#pragma unroll
+                    for (int u2 = 0; u2 < W; ++u2)
+                        if (u2 < nv) {
+                            ch.lq[eidx(u2)] = lqv[u2];
+                            ch.lp[eidx(u2)] = lpv[u2];
+                        }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(256) : "memory");
+    }
+}
+
 // Split of the FP32 operand X [R][ld] into bf16 pieces, laid out as the B
 // operand rows [rb][piece][64][ldk] (zero for padded replicas and spins).
 __global__ void k_adj_split(const float *X, int n, int R, int ld, int nrb, int ldk, __nv_bfloat16 *xs) {
@@ -431,6 +915,7 @@ void adj_tc_free(AdjTc *t) {
     if (!t) return;
     if (t->jb) cudaFree(t->jb);
     if (t->xs) cudaFree(t->xs);
+    if (t->run_flags) cudaFree(t->run_flags);
     delete t;
 }
 
@@ -514,13 +999,58 @@ si_status adj_tc_prepare(Ctx *c, AdjTc **out) {
     }
     t->splits = splits;
     t->kb_per = cdiv(t->kblocks, splits);
+    // Persistent sweep: cluster size S in {8, 4, 2} (64/S replicas per CTA
+    // in registers), every split non-empty, and all clusters of one chain
+    // (and, for side-by-side chains, of two) resident at once, since the
+    // chains' CTAs wait on each other's step counters.
+    {
+        const char *pe = std::getenv("SI_ADJOINT_PERSISTENT");
+        const char *pp = std::getenv("SI_ADJOINT_PAIR");
+        const bool allow = !(pe && std::atoi(pe) == 0);
+        auto fits = [&](int S, int nch) -> bool {
+            if (nch * tiles * S > c->num_sms || (S - 1) * cdiv(t->kblocks, S) >= t->kblocks) return false;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)(nch * tiles * S));
+            cfg.blockDim = dim3(AR_THREADS);
+            cfg.dynamicSmemBytes = AR_SMEM;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = (unsigned)S;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            cudaError_t e = S == 8   ? cudaOccupancyMaxActiveClusters(&nclusters, k_adj_run<8>, &cfg)
+                            : S == 4 ? cudaOccupancyMaxActiveClusters(&nclusters, k_adj_run<16>, &cfg)
+                                     : cudaOccupancyMaxActiveClusters(&nclusters, k_adj_run<32>, &cfg);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+            return nclusters >= nch * tiles;
+        };
+        int rs = 0;
+        if (allow &&
+            cudaFuncSetAttribute(k_adj_run<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, AR_SMEM) == cudaSuccess &&
+            cudaFuncSetAttribute(k_adj_run<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, AR_SMEM) == cudaSuccess &&
+            cudaFuncSetAttribute(k_adj_run<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, AR_SMEM) == cudaSuccess) {
+            for (int S = 8; S >= 2 && rs == 0; S >>= 1)
+                if (fits(S, 1)) rs = S;
+        }
+        cudaGetLastError();
+        t->run_splits = rs;
+        t->run_kb_per = rs ? cdiv(t->kblocks, rs) : 0;
+        t->run_pair = rs && !(pp && std::atoi(pp) == 0) && fits(rs, 2);
+    }
     if (si_dev_malloc((void **)&t->jb, sizeof(__nv_bfloat16) * (size_t)t->mpad * t->ldk) != cudaSuccess ||
-        si_dev_malloc((void **)&t->xs, sizeof(__nv_bfloat16) * 3 * (size_t)t->nrb * AT_BN * t->ldk) != cudaSuccess) {
+        si_dev_malloc((void **)&t->xs, sizeof(__nv_bfloat16) * 4 * (size_t)t->nrb * AT_BN * t->ldk) != cudaSuccess ||
+        si_dev_malloc((void **)&t->run_flags, sizeof(unsigned) * 2 * (size_t)tiles) != cudaSuccess) {
         cudaGetLastError();
         set_error("si_grad: out of device memory for the tensor-core workspace");
         return fail(SI_ERR_OOM);
     }
-    if (cudaMemsetAsync(t->xs, 0, sizeof(__nv_bfloat16) * 3 * (size_t)t->nrb * AT_BN * t->ldk, c->stream) !=
+    if (cudaMemsetAsync(t->xs, 0, sizeof(__nv_bfloat16) * 4 * (size_t)t->nrb * AT_BN * t->ldk, c->stream) !=
         cudaSuccess) {
         set_error("si_grad: cudaMemsetAsync failed");
         return fail(SI_ERR_CUDA);
@@ -533,10 +1063,73 @@ si_status adj_tc_prepare(Ctx *c, AdjTc **out) {
     }
     si_status s;
     if ((s = tc_make_map_bf16(&t->mapA, t->jb, t->ldk, t->mpad, AT_BK, AT_BM)) != SI_OK) return fail(s);
-    if ((s = tc_make_map_bf16(&t->mapB, t->xs, t->ldk, 3 * t->nrb * AT_BN, AT_BK, AT_BN)) != SI_OK) return fail(s);
+    if ((s = tc_make_map_bf16(&t->mapB, t->xs, t->ldk, 4 * t->nrb * AT_BN, AT_BK, AT_BN)) != SI_OK) return fail(s);
     c->launches += 1;
     c->g_tc = t;
     *out = t;
+    return SI_OK;
+}
+
+int adj_tc_run_splits(const AdjTc *t) { return t ? t->run_splits : 0; }
+bool adj_tc_run_pair(const AdjTc *t) { return t && t->run_pair; }
+int adj_tc_run_nparts(const AdjTc *t) { return t->mtiles * t->nrb * t->run_splits; }
+unsigned *adj_tc_run_flags(const AdjTc *t, int chain) { return t->run_flags + (size_t)chain * t->mtiles * t->nrb; }
+
+template <int SR>
+static cudaError_t launch_run(const AdjTc *t, const AdjRunArgs &a, int nch, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(nch * t->mtiles * t->nrb * t->run_splits));
+    cfg.blockDim = dim3(AR_THREADS);
+    cfg.dynamicSmemBytes = AR_SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)t->run_splits;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_adj_run<SR>, t->mapA, t->mapB, a);
+}
+
+si_status adj_tc_run(Ctx *c, AdjTc *t, const AdjChain *chains, int nch, int K) {
+    if (!t->run_splits || nch < 1 || nch > 2 || (nch == 2 && !t->run_pair)) {
+        set_error("si_grad: persistent sweep not available for this context");
+        return SI_ERR_UNSUPPORTED;
+    }
+    AdjRunArgs a{};
+    a.n = t->n;
+    a.R = t->R;
+    a.ld = t->ld;
+    a.ldk = t->ldk;
+    a.nrb = t->nrb;
+    a.mtiles = t->mtiles;
+    a.kblocks = t->kblocks;
+    a.kb_per = t->run_kb_per;
+    a.splits = t->run_splits;
+    a.K = K;
+    a.nparts = adj_tc_run_nparts(t);
+    a.plane = (size_t)t->R * t->ld;
+    a.h = c->has_h ? c->dhf : nullptr;
+    a.sp = StepParams{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max, 0, 0};
+    a.zeta = c->dzeta;
+    a.dt = c->ddt;
+    a.xs = t->xs;
+    a.err = c->derr;
+    a.limit_ns = c->spin_limit_ns;
+    for (int k = 0; k < nch; ++k) {
+        a.ch[k] = chains[k];
+        if (chains[k].len < 1) {
+            set_error("si_grad: empty chain in the persistent sweep");
+            return SI_ERR_INVALID_ARG;
+        }
+        SI_CUDA_TRY(cudaMemsetAsync(chains[k].flags, 0, sizeof(unsigned) * (size_t)t->mtiles * t->nrb, c->stream));
+    }
+    cudaError_t e = t->run_splits == 8   ? launch_run<8>(t, a, nch, c->stream)
+                    : t->run_splits == 4 ? launch_run<16>(t, a, nch, c->stream)
+                                         : launch_run<32>(t, a, nch, c->stream);
+    SI_CUDA_TRY(e);
+    c->launches += 1;
     return SI_OK;
 }
 

@@ -699,8 +699,12 @@ si_status si_describe(const si_ctx *ctx, char *buf, int32_t len) {
     if (c->g_path) {
         const size_t l = std::strlen(buf);
         if ((int)l + 1 < len) {
-            if (c->g_path == 2)
-                std::snprintf(buf + l, len - l, " grad=tcgen05-bf16x3 ksplit=%d", adj_tc_splits(c->g_tc));
+            if (c->g_path == 2 && adj_tc_run_splits(c->g_tc) > 0)
+                std::snprintf(buf + l, len - l, " grad=tcgen05-bf16x3 ksplit=%d sweep=persistent%s",
+                              adj_tc_run_splits(c->g_tc), adj_tc_run_pair(c->g_tc) ? "-side-by-side" : "");
+            else if (c->g_path == 2)
+                std::snprintf(buf + l, len - l, " grad=tcgen05-bf16x3 ksplit=%d sweep=per-step",
+                              adj_tc_splits(c->g_tc));
             else
                 std::snprintf(buf + l, len - l, " grad=cuda-core");
         }

@@ -147,6 +147,35 @@ __device__ __forceinline__ void integrate2_kd(float q_lo, float q_hi, float p_lo
     po_hi = pn1;
 }
 
+// One reverse step of the kick-drift iteration (the adjoint of Eq. 8 with
+// the walls of Eq. 6), with pinned roundings so that every adjoint kernel
+// computes the same values.  Through the clamps, with the interior
+// indicators of the stored next state (|q'| < q_max, |p'| < p_max):
+//   lb = D_q lq',  la = D_p (lp' + (dt/m) lb).
+template <typename T>
+__device__ __forceinline__ void adj_clamps(T lq, T lp, T qn, T pn, T qmax, T pmax, T dtm, T &la, T &lb) {
+    lb = (fabs(qn) < qmax) ? lq : (T)0;
+    la = (fabs(pn) < pmax) ? rn_fma(dtm, lb, lp) : (T)0;
+}
+// lq = lb + dt (-k la + zeta G) with G = J la (and lp = la).
+template <typename T>
+__device__ __forceinline__ T adj_lq(T lb, T la, T G, T dtt, T zt, T k) {
+    return rn_fma(dtt, rn_fma(-k, la, rn_mul(zt, G)), lb);
+}
+// One element's terms of g_dt, g_zeta and g_k at step t (q, F of step t,
+// p' of step t+1):
+//   lb p'/m + la (-k (q - q0) + zeta F),   dt la F,   -dt la (q - q0).
+template <typename T>
+__device__ __forceinline__ void adj_terms(T la, T lb, T q, T F, T pn, T q0, T k, T m, T zt, T dtt, T &g_dt,
+                                          T &g_zeta, T &g_k) {
+    const T dq = rn_add(q, -q0);
+    const T force = rn_fma(-k, dq, rn_mul(zt, F));
+    g_dt = rn_fma(la, force, rn_mul(lb, pn) / m);
+    const T dla = rn_mul(dtt, la);
+    g_zeta = rn_mul(dla, F);
+    g_k = -rn_mul(dla, dq);
+}
+
 // Error-free sum (Knuth's TwoSum): s + e == a + b exactly.
 template <typename T>
 __device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {

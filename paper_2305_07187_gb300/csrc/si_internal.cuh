@@ -258,6 +258,28 @@ int adj_tc_nobj(const AdjTc *a);
 int adj_tc_splits(const AdjTc *a);
 void adj_tc_free(AdjTc *a);
 
+// Persistent sweep (k_adj_run): one launch runs one or two chains of
+// products, each over every (M tile, replica block, K split) CTA.
+struct AdjChain {
+    int reverse;                 // 0: forward products, 1: reverse steps of one segment
+    int t_start, len;            // forward: steps t_start .. t_start+len-1; reverse: t_start+len-1 down to t_start
+    int buf0;                    // first of the chain's two operand buffers
+    unsigned *flags;             // [mtiles * nrb] slices published (zeroed by adj_tc_run)
+    const float *q_in, *p_in;    // forward: state at t_start, [R][ld]
+    float *sq[2], *sp[2], *sF[2];   // slot sets (segment parity): q, p [K+1] planes, F [K] planes
+    float *ckq, *ckp;            // forward: checkpoint planes written at segment ends, or null
+    float *lq, *lp;              // reverse: adjoint state at t_start+len on entry, at t_start on exit
+    float *part;                 // reverse: gradient partials [T][3][nparts]
+};
+// Cluster size of the persistent sweep (0: not available for this context,
+// the per-step kernels run instead), whether two chains run side by side,
+// the number of gradient partials per step, and a chain's step counters.
+int adj_tc_run_splits(const AdjTc *a);
+bool adj_tc_run_pair(const AdjTc *a);
+int adj_tc_run_nparts(const AdjTc *a);
+unsigned *adj_tc_run_flags(const AdjTc *a, int chain);
+si_status adj_tc_run(Ctx *c, AdjTc *a, const AdjChain *chains, int nch, int K);
+
 si_status adjoint_grad(Ctx *c, int steps, float *g_zeta, float *g_dt,
                        float *g_k, float *objective, const float *q_init,
                        const float *p_init);
