@@ -434,7 +434,7 @@ __global__ void __launch_bounds__(AT_THREADS, 1)
 // other wait has a time limit, after which the kernel raises the device
 // error word and skips the remaining work.
 constexpr int AR_RECV = AT_RB * AT_BM * 4;               // 32 KB: one buffer of pushed partials
-constexpr int AR_NBARS = 2 * AT_S + 3;                   // full, empty, accf, drain, pub
+constexpr int AR_NBARS = 2 * AT_S + 4;                   // full, empty, accf, drain, pub, red
 constexpr int AR_EPI = 16;                               // epilogue warps
 constexpr int AR_THREADS = 32 * (2 + AR_EPI);            // producer, MMA issuer, epilogue
 constexpr int AR_SMEM = AT_TILES + AT_MISC + 2 * AR_RECV + 1024;
@@ -467,6 +467,7 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
     const uint32_t accf_bar = bar0 + 8u * (2 * AT_S);
     const uint32_t drain_bar = bar0 + 8u * (2 * AT_S + 1);
     const uint32_t pub_bar = bar0 + 8u * (2 * AT_S + 2);
+    const uint32_t red_bar = bar0 + 8u * (2 * AT_S + 3);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + AT_TILES + AR_NBARS * 8);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + AT_TILES + AR_NBARS * 8 + 4);
     float *red = reinterpret_cast<float *>(smem + AT_TILES + AR_NBARS * 8 + 16);   // [16 warps][3 sums][hi, lo]
@@ -490,6 +491,7 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
         mbar_init(accf_bar, 1);
         mbar_init(drain_bar, 1);
         mbar_init(pub_bar, AR_EPI);
+        mbar_init(red_bar, AR_EPI);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -514,33 +516,58 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
         // Lanes 0 .. nown-1 wait for the counters of the M tiles that the
         // CTA's K range covers (K block kb holds spins of M tile kb / 2);
         // lane 0 then issues the J tile and the operand tile of every K block.
+        // The J tiles do not depend on the step: the first min(nk, S)
+        // stages are armed and their J tiles issued before the wait (every
+        // stage is free by then: the previous product has completed), and
+        // only the operand tiles follow it.
         const int o0 = kb0 >> 1, nown = ((kb0 + nk - 1) >> 1) - o0 + 1;
+        const int npre = min(nk, AT_S);
         uint32_t cnt = 0;
         bool ok = true;
         for (int u = 0; u < len; ++u) {
             if (ok) {
-                bool mine = true;
-                if (lane < nown)
-                    mine = wait_counter_geq(ch.flags + (size_t)(o0 + lane) * a.nrb + rb, (unsigned)(S * (u + 1)),
-                                            a.err, a.limit_ns);
-                ok = __all_sync(0xffffffffu, mine);
-                // orders every lane's acquire before lane 0's copies
-                __syncwarp();
-                if (ok && lane == 0) {
-                    fence_proxy_async_global();
-                    const int yb = ((ch.buf0 + (u & 1)) * a.nrb + rb) * AT_BN;
-                    for (int c = 0; c < nk; ++c, ++cnt) {
-                        const int s = (int)(cnt % AT_S);
-                        const uint32_t ph = (cnt / AT_S) & 1u;
-                        if (!mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns)) {
+                int armed = 0;
+                if (lane == 0) {
+                    for (; armed < npre; ++armed) {
+                        const uint32_t k = cnt + (uint32_t)armed;
+                        const int s = (int)(k % AT_S);
+                        if (!mbar_wait(empty_bar(s), ((k / AT_S) & 1u) ^ 1u, a.err, abort_flag, a.limit_ns)) {
                             ok = false;
                             break;
                         }
-                        const uint32_t dA = sbase + s * AT_STAGE;
                         mbar_arrive_expect_tx(full_bar(s), (uint32_t)AT_STAGE);
-                        tma_load_2d(dA, &mapA, full_bar(s), (kb0 + c) * AT_BK, mt * AT_BM);
+                        tma_load_2d(sbase + s * AT_STAGE, &mapA, full_bar(s), (kb0 + armed) * AT_BK, mt * AT_BM);
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                bool mine = true;
+                if (ok && lane < nown)
+                    mine = wait_counter_geq(ch.flags + (size_t)(o0 + lane) * a.nrb + rb, (unsigned)(S * (u + 1)),
+                                            a.err, a.limit_ns);
+                const bool ready = ok && __all_sync(0xffffffffu, mine);
+                // orders every lane's acquire before lane 0's copies
+                __syncwarp();
+                if (lane == 0) {
+                    // The operand tiles of the armed stages are issued even
+                    // after a failed wait, so that their transaction counts
+                    // complete and the drain below ends.
+                    if (ready) fence_proxy_async_global();
+                    const int yb = ((ch.buf0 + (u & 1)) * a.nrb + rb) * AT_BN;
+                    for (int c = 0; c < nk; ++c, ++cnt) {
+                        const int s = (int)(cnt % AT_S);
+                        const uint32_t dA = sbase + s * AT_STAGE;
+                        if (c >= armed) {
+                            if (!ready) break;
+                            if (!mbar_wait(empty_bar(s), ((cnt / AT_S) & 1u) ^ 1u, a.err, abort_flag, a.limit_ns)) {
+                                ok = false;
+                                break;
+                            }
+                            mbar_arrive_expect_tx(full_bar(s), (uint32_t)AT_STAGE);
+                            tma_load_2d(dA, &mapA, full_bar(s), (kb0 + c) * AT_BK, mt * AT_BM);
+                        }
                         tma_load_2d(dA + AT_A_BYTES, &mapB, full_bar(s), (kb0 + c) * AT_BK, yb);
                     }
+                    ok = ok && ready;
                 }
                 ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             }
@@ -644,47 +671,52 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
                 }
             }
         };
-        // The warps' stores are ordered before lane 0's arrivals (warp
-        // barrier), the arrivals before thread 0's wait, and that before its
-        // release increment of the tile's counter.  On a reverse chain the
-        // CTA's gradient partials of step tau are written too (warp shuffle
-        // trees of the compensated sums, then the 16 warps in order).
-        auto publish = [&](CompSum<float> *g, int tau) {
-            if (g) {
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-#pragma unroll
-                    for (int off = 16; off > 0; off >>= 1) {
-                        const float oh = __shfl_down_sync(0xffffffffu, g[j].hi, off);
-                        const float ol = __shfl_down_sync(0xffffffffu, g[j].lo, off);
-                        g[j].merge(oh, ol);
-                    }
-                }
-                if (lane == 0) {
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        red[(e * 3 + j) * 2] = g[j].hi;
-                        red[(e * 3 + j) * 2 + 1] = g[j].lo;
-                    }
-                }
-            }
+        // The warps' stores of the next operand are ordered before lane 0's
+        // arrivals (warp barrier), the arrivals before thread 0's wait, and
+        // that before its release increment of the tile's counter.
+        uint32_t reds = 0;
+        auto publish = [&]() {
             __syncwarp();
             if (lane == 0) mbar_arrive(pub_bar);
             if (e == 0 && lane == 0) {
-                if (mbar_wait(pub_bar, pubs & 1u, a.err, abort_flag, a.limit_ns)) {
-                    if (g) {
-#pragma unroll
-                        for (int j = 0; j < 3; ++j) {
-                            CompSum<float> s;
-                            s.init();
-                            for (int w = 0; w < AR_EPI; ++w) s.merge(red[(w * 3 + j) * 2], red[(w * 3 + j) * 2 + 1]);
-                            ch.part[(size_t)tau * 3 * a.nparts + (size_t)j * a.nparts + local] = s.value();
-                        }
-                    }
+                if (mbar_wait(pub_bar, pubs & 1u, a.err, abort_flag, a.limit_ns))
                     red_release_gpu_add(ch.flags + (size_t)mt * a.nrb + rb, 1u);
-                }
             }
             ++pubs;
+        };
+        // The CTA's gradient partials of step tau: warp shuffle trees of the
+        // compensated sums, then the 16 warps in order (off the critical path:
+        // after the publication).
+        auto partials = [&](CompSum<float> *g, int tau) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const float oh = __shfl_down_sync(0xffffffffu, g[j].hi, off);
+                    const float ol = __shfl_down_sync(0xffffffffu, g[j].lo, off);
+                    g[j].merge(oh, ol);
+                }
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    red[(e * 3 + j) * 2] = g[j].hi;
+                    red[(e * 3 + j) * 2 + 1] = g[j].lo;
+                }
+                mbar_arrive(red_bar);
+            }
+            if (e == 0 && lane == 0) {
+                if (mbar_wait(red_bar, reds & 1u, a.err, abort_flag, a.limit_ns)) {
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        CompSum<float> sm;
+                        sm.init();
+                        for (int w = 0; w < AR_EPI; ++w) sm.merge(red[(w * 3 + j) * 2], red[(w * 3 + j) * 2 + 1]);
+                        ch.part[(size_t)tau * 3 * a.nparts + (size_t)j * a.nparts + local] = sm.value();
+                    }
+                }
+            }
+            ++reds;
         };
         // Slot values of reverse step tau (slot jj of the segment): q_{tau+1},
         // p_{tau+1} (the clamp indicators, lb p'/m), q_tau and F_tau.
@@ -730,7 +762,7 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
                     x1[u] = ch.p_in[eidx(u)];
                 }
             pieces(ch.buf0);
-            publish(nullptr, 0);
+            publish();
         } else {
             float lqv[W], lpv[W];
 #pragma unroll
@@ -746,7 +778,8 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
             const int tau = ch.t_start + len - 1;
             elem(tau, lqv, lpv, g);
             pieces(ch.buf0);
-            publish(g, tau);
+            publish();
+            partials(g, tau);
         }
 
         // ---------------- products
@@ -817,31 +850,35 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
                 const float dtm = dtt / a.sp.m;
                 float *sqz = ch.sq[z], *spz = ch.sp[z], *sFz = ch.sF[z];
                 const bool ck_end = ch.ckq != nullptr && (t + 1 == ch.t_start + len || j + 1 == a.K);
+                float Fv[W], qv[W], pv[W];   // F_t and the state before the step
+#pragma unroll
+                for (int u2 = 0; u2 < W; ++u2) {
+                    Fv[u2] = G[u2] + hi;
+                    qv[u2] = x0[u2];
+                    pv[u2] = x1[u2];
+                    integrate<float>(qv[u2], pv[u2], Fv[u2], zt, dtt, dtm, a.sp, x0[u2], x1[u2]);
+                }
+                // the next operand first, then the slots of the sweep
+                if (u + 1 < len) {
+                    pieces(ch.buf0 + ((u + 1) & 1));
+                    publish();
+                }
 #pragma unroll
                 for (int u2 = 0; u2 < W; ++u2) {
                     if (u2 < nv) {
                         const size_t x = eidx(u2);
-                        const float F = G[u2] + hi;
-                        float qo, po;
-                        integrate<float>(x0[u2], x1[u2], F, zt, dtt, dtm, a.sp, qo, po);
                         if (j == 0) {
-                            sqz[x] = x0[u2];
-                            spz[x] = x1[u2];
+                            sqz[x] = qv[u2];
+                            spz[x] = pv[u2];
                         }
-                        sFz[(size_t)j * pl + x] = F;
-                        sqz[(size_t)(j + 1) * pl + x] = qo;
-                        spz[(size_t)(j + 1) * pl + x] = po;
+                        sFz[(size_t)j * pl + x] = Fv[u2];
+                        sqz[(size_t)(j + 1) * pl + x] = x0[u2];
+                        spz[(size_t)(j + 1) * pl + x] = x1[u2];
                         if (ck_end) {
-                            ch.ckq[(size_t)(sg + 1) * pl + x] = qo;
-                            ch.ckp[(size_t)(sg + 1) * pl + x] = po;
+                            ch.ckq[(size_t)(sg + 1) * pl + x] = x0[u2];
+                            ch.ckp[(size_t)(sg + 1) * pl + x] = x1[u2];
                         }
-                        x0[u2] = qo;
-                        x1[u2] = po;
                     }
-                }
-                if (u + 1 < len) {
-                    pieces(ch.buf0 + ((u + 1) & 1));
-                    publish(nullptr, 0);
                 }
             } else {
                 // adjoint product of step t, then the elementwise part of step t - 1
@@ -860,7 +897,8 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
                     g[2].init();
                     elem(t - 1, lqv, lpv, g);
                     pieces(ch.buf0 + ((u + 1) & 1));
-                    publish(g, t - 1);
+                    publish();
+                    partials(g, t - 1);
                 } else {
 #pragma unroll
                     for (int u2 = 0; u2 < W; ++u2)
