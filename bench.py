@@ -241,16 +241,15 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
 
     Target C*: median final cut of the plain FP32 path over 1000 replicas
     (T=1000, linear zeta ramp, seeds 100..1099).  Batched path (tensor cores,
-    R=1024, the T=2000 schedule): wall time from the first launch to the host
-    seeing the first readout (every `every` steps; exact int32 cuts of all
-    replicas, readout included) at which any replica reaches C*; the run is
-    advanced segment by segment from its own FP32 state.  The loop is
-    pipelined: segment s (run, readout into device memory, cuts copied to
-    pinned host memory) is queued before the cuts of segment s-1 are checked,
-    so the GPU never waits for the host; at most one segment runs past the
-    hit, after the clock has stopped.  Median over `seeds` initial-position
-    seeds.  FP32 plain (R=1): TTS99 = t_run ln(0.01)/ln(1 - p_s), p_s the
-    fraction of the 1000 FP32 replicas that reach C*."""
+    R=1024, the T=2000 schedule): wall time of one si_run_watch call, from
+    the host's call to its return with the stop known, the state at the stop
+    and every replica's exact energy (Eq. 1) of the stopping readout in host
+    memory.  The readout (every `every` steps) and the decision to stop at
+    the first readout at which any replica's cut reaches C* (energy
+    -2 C* - sum_{i<j} J_ij) run inside the persistent step kernel.  Median
+    over `seeds` initial-position seeds.  FP32 plain (R=1): TTS99 = t_run
+    ln(0.01)/ln(1 - p_s), p_s the fraction of the 1000 FP32 replicas that
+    reach C*."""
     n = N_SPINS
     J = inputs.pm1_coupling(n, seed=1)
     T1 = 1000
@@ -274,38 +273,19 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
     R = REPLICAS
     zb = torch.from_numpy(inputs.zeta_ramp(T_STEPS)).to(dev)
     db = torch.from_numpy(inputs.dt_const(T_STEPS)).to(dev)
+    s_upper = int(np.triu(J.astype(np.int64), 1).sum())
+    e_target = int(-2 * int(c_star) - s_upper)        # cut >= C*  <=>  energy <= e_target
     ttts, hit_steps = [], []
-    nseg = T_STEPS // every
-    # the exact cuts of each segment are summed inside the step kernel (one
-    # more pass over J after the segment's last step, si_params.fused_readout)
-    with b.Context(J, replicas=R, steps=every, prec="j_fp8_q_bf16", stream=stream.cuda_stream,
-                   fused_readout=1) as cb:
-        cut_d = torch.empty((nseg, R), dtype=torch.int32, device=dev)
-        cut_p = torch.empty((nseg, R), dtype=torch.int32).pin_memory()
-        ready = [torch.cuda.Event() for _ in range(nseg)]
+    with b.Context(J, replicas=R, steps=T_STEPS, prec="j_fp8_q_bf16", stream=stream.cuda_stream) as cb:
+        e_host = torch.empty(R, dtype=torch.int32).pin_memory()
         for seed in range(seeds + 1):
             q_init = torch.from_numpy(inputs.positions(n, R, seed0=200000 + 4096 * seed)).to(dev)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            hit = None
-            for seg in range(nseg + 1):
-                if seg < nseg:
-                    sl = slice(seg * every, (seg + 1) * every)
-                    # the first segment starts from q_init (zero momenta), the
-                    # others continue from the context's FP32 state; both
-                    # calls return once queued (device data only)
-                    cb.run_into(zb[sl], db[sl], q_init if seg == 0 else None, None, None, None, None)
-                    cb.energy_into(None, R, None, cut_d[seg], None)
-                    cut_p[seg].copy_(cut_d[seg], non_blocking=True)
-                    ready[seg].record(stream)
-                if seg >= 1:
-                    # the previous segment's cuts, while this one runs
-                    ready[seg - 1].synchronize()
-                    if int(cut_p[seg - 1].numpy().max()) >= c_star:
-                        hit = seg * every
-                        break
+            done = cb.run_watch_into(zb, db, q_init, every, e_target, energy_out=e_host)
             el = time.perf_counter() - t0
-            cb.synchronize()   # the segment queued past the hit, and any pending device error
+            best_cut = -(int(e_host.numpy().min()) + s_upper) / 2.0
+            hit = done if best_cut >= c_star else None
             if seed == 0:
                 continue          # warm-up
             ttts.append(el if hit is not None else float("inf"))
@@ -336,7 +316,8 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
             "speedup_vs_fp32_plain": (tts99 / ttt) if ttt > 0 else None,
             "batched_full_run_s": t_b, "batched_p_success_final": p_b,
             "batched_tts99_per_replica_s": tts99_rep,
-            "readout": "fused into the step kernel: one more pass over J with the segment's final spins",
+            "readout": "inside the persistent step kernel (si_run_watch): a pass over J with sign(q) every "
+                       "10 steps, evaluated and the stop decided on the GPU; one launch per run",
             "note": "batched_ttt_s: any of R=1024 replicas reaches C* (readout every 10 steps); "
                     "batched_tts99_per_replica_s: TTS99 of one replica of the batched path, each replica "
                     "charged 1/R of a full T=2000 batched run, p from the run's final cuts"}

@@ -143,6 +143,38 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt,
                  float *p_out, int8_t *spins_out);
 
 /*
+ * si_run with a watch on the energy (the time-to-target use of the method):
+ * after every `every` steps, and after the last one, the exact Ising energy
+ * of Eq. 1 of every replica's spins sign(q) is summed inside the step kernel
+ * (one more pass over J with the spins as the operand), and the run stops at
+ * the first such readout at which some replica's energy is at most
+ * target_energy.  A target cut C of the MAX-CUT instance with w_ij = -J_ij
+ * (and h = 0) is the energy -2 C - sum_{i<j} J_ij.  Every CTA takes the same
+ * decision at the same readout, so all replicas stop at the same step.
+ *   zeta, dt, q_init, p_init   as for si_run (prm.steps entries; the run
+ *                    reads only those of the steps it makes)
+ *   every           readout interval in steps, >= 1
+ *   q_out, p_out, spins_out    the state at the stop (or after prm.steps
+ *                    steps), as for si_run; a continuing call (q_init NULL)
+ *                    of si_run or si_run_watch starts from it
+ *   steps_done      [1] steps made: min(prm.steps, (k + 1) every) for the
+ *                    stopping readout k; host memory; or NULL
+ *   energy_out      [R] int32 energies of the last readout, host or device,
+ *                    or NULL
+ * The call returns after the run has completed (it needs the decision).
+ * Requires a context whose steps all run in one tensor-core kernel (the
+ * bf16 operand of SI_PREC_J_FP8_Q_BF16 or SI_PREC_J_BF16_Q_BF16 on single
+ * CTAs) with J and h integer-valued, |J_ij|, |h_i| <= 127; else
+ * SI_ERR_UNSUPPORTED.  Deterministic: the same inputs give the same stop and
+ * bit-identical outputs, equal to those of si_run over the steps made.
+ */
+si_status si_run_watch(si_ctx *ctx, const float *zeta, const float *dt,
+                       const float *q_init, const float *p_init, int32_t every,
+                       int64_t target_energy, float *q_out, float *p_out,
+                       int8_t *spins_out, int32_t *steps_done,
+                       int32_t *energy_out);
+
+/*
  * Change the integrator parameters of an existing context without copying J
  * again: k, m, q0, q_max, p_max, update_order, wall_zero_p, ckpt_every and
  * fused_readout take the values in *prm for every later call (e.g. the spring constant

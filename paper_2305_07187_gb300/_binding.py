@@ -76,6 +76,8 @@ def load():
     lib.si_set_params.argtypes = [P, ctypes.POINTER(SiParams)]
     lib.si_set_params.restype = ctypes.c_int
     lib.si_run.argtypes = [P, P, P, P, P, P, P, P]
+    lib.si_run_watch.argtypes = [P, P, P, P, P, I32, ctypes.c_int64, P, P, P, P, P]
+    lib.si_run_watch.restype = ctypes.c_int
     lib.si_run.restype = ctypes.c_int
     lib.si_get_state.argtypes = [P, P, P]
     lib.si_get_state.restype = ctypes.c_int
@@ -267,6 +269,35 @@ class Context:
         po = _Arg(p_out, np.float32, nR, writable=True)
         so = _Arg(spins_out, np.int8, nR, writable=True)
         _check(load().si_run(self.ctx, z.ptr, d.ptr, qi.ptr, pi.ptr, qo.ptr, po.ptr, so.ptr))
+
+    def run_watch_into(self, zeta, dt, q_init, every, target_energy, p_init=None, q_out=None, p_out=None,
+                       spins_out=None, energy_out=None):
+        """si_run_watch: run until the first readout (every `every` steps)
+        at which some replica's energy is <= target_energy; returns the
+        number of steps made."""
+        nR = self.n * self.replicas
+        z = _Arg(zeta, np.float32, self.steps)
+        d = _Arg(dt, np.float32, self.steps)
+        qi = _Arg(q_init, np.float32, nR)
+        pi = _Arg(p_init, np.float32, nR)
+        qo = _Arg(q_out, np.float32, nR, writable=True)
+        po = _Arg(p_out, np.float32, nR, writable=True)
+        so = _Arg(spins_out, np.int8, nR, writable=True)
+        eo = _Arg(energy_out, np.int32, self.replicas, writable=True)
+        done = ctypes.c_int32(0)
+        _check(load().si_run_watch(self.ctx, z.ptr, d.ptr, qi.ptr, pi.ptr, int(every), int(target_energy),
+                                   qo.ptr, po.ptr, so.ptr, ctypes.c_void_p(ctypes.addressof(done)), eo.ptr))
+        return int(done.value)
+
+    def run_watch(self, zeta, dt, q_init, every, target_energy, p_init=None):
+        """Host convenience: returns (steps_done, q, p, spins, energies)."""
+        R, n = self.replicas, self.n
+        q = np.empty((R, n), np.float32)
+        p = np.empty((R, n), np.float32)
+        s = np.empty((R, n), np.int8)
+        e = np.empty(R, np.int32)
+        done = self.run_watch_into(zeta, dt, q_init, every, target_energy, p_init, q, p, s, e)
+        return done, q, p, s, e
 
     def run(self, zeta, dt, q_init, p_init=None):
         """Host convenience: returns (q, p, spins) as NumPy arrays."""

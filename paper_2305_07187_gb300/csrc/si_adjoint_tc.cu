@@ -817,10 +817,9 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
             tc_fence_before();
             cluster_arrive_release();
             cluster_wait_acquire();
-            if (!ok || *abort_flag) {
-                ok = false;
-                continue;
-            }
+            // one decision per warp (the abort word may change between its lanes' reads)
+            ok = ok && !__any_sync(0xffffffffu, *abort_flag != 0);
+            if (!ok) continue;
             // the partials of this thread's replicas, added in source-rank order
             float G[W];
 #pragma unroll

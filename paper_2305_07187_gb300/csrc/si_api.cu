@@ -158,7 +158,8 @@ static void free_ctx(Ctx *c) {
     }
     void *ptrs[] = {c->dJ, c->dJ8, c->dh, c->dhf, c->dh8, c->dq, c->dp, c->dqbuf,
                     c->dzeta, c->ddt, c->dbar, c->derr, c->dspins, c->dspins_in,
-                    c->dE, c->dC, c->dEf, c->dstage, c->g_ws, c->e_sig, c->e_sum, c->dxch, c->dqT};
+                    c->dE, c->dC, c->dEf, c->dstage, c->g_ws, c->e_sig, c->e_sum, c->dxch, c->dqT,
+                    c->w_sum, c->w_ctl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->herr) cudaFreeHost(c->herr);
@@ -500,6 +501,105 @@ si_status si_run(si_ctx *ctx, const float *zeta, const float *dt, const float *q
     c->have_run = true;
     c->run_spins_valid = true;
     c->fused_valid = c->path == Path::TENSOR && !c->grp && c->tc_readout;
+    return SI_OK;
+}
+
+si_status si_run_watch(si_ctx *ctx, const float *zeta, const float *dt, const float *q_init,
+                       const float *p_init, int32_t every, int64_t target_energy, float *q_out, float *p_out,
+                       int8_t *spins_out, int32_t *steps_done, int32_t *energy_out) {
+    NvtxRange nvtx_range("si_run_watch");
+    set_error("");
+    Ctx *c = reinterpret_cast<Ctx *>(ctx);
+    if (!c || (c->prm.steps > 0 && (!zeta || !dt)) || every < 1) {
+        set_error("si_run_watch: ctx, zeta and dt are required, every >= 1");
+        return SI_ERR_INVALID_ARG;
+    }
+    if (c->path != Path::TENSOR || !tc_readout_supported(c)) {
+        set_error("si_run_watch: needs a tensor-path context (one kernel for all steps) with integer J and h");
+        return SI_ERR_UNSUPPORTED;
+    }
+    const bool cont = (q_init == nullptr);
+    if (cont && (p_init || !c->have_run)) {
+        set_error("si_run_watch: q_init NULL continues from the context's state: needs a completed run, "
+                  "and p_init NULL");
+        return SI_ERR_INVALID_ARG;
+    }
+    c->launches = 0;
+    const int steps = c->prm.steps, n = c->n, R = c->R;
+    if (steps > 0) {
+        SI_CUDA_TRY(cudaMemcpyAsync(c->dzeta, zeta, sizeof(float) * steps, cudaMemcpyDefault, c->stream));
+        SI_CUDA_TRY(cudaMemcpyAsync(c->ddt, dt, sizeof(float) * steps, cudaMemcpyDefault, c->stream));
+    }
+    DevIn qi, pi;
+    si_status s = stage_in(qi, q_init, sizeof(float) * (size_t)R * n, c->stream);
+    if (s != SI_OK) return s;
+    s = stage_in(pi, p_init, sizeof(float) * (size_t)R * n, c->stream);
+    if (s != SI_OK) return s;
+    DevOut qo, po, so, eo;
+    if ((s = stage_out(qo, q_out, sizeof(float) * (size_t)R * n)) != SI_OK) return s;
+    if ((s = stage_out(po, p_out, sizeof(float) * (size_t)R * n)) != SI_OK) return s;
+    if ((s = stage_out(so, spins_out, (size_t)R * n)) != SI_OK) return s;
+    if ((s = stage_out(eo, energy_out, sizeof(int32_t) * (size_t)R)) != SI_OK) return s;
+    c->ev_valid = false;
+    c->have_run = false;
+    c->fused_valid = false;
+    if (!cont) {
+        s = tc_init_state(c, (const float *)qi.ptr, (const float *)pi.ptr);
+        c->tc_p0 = 0;
+    } else if (c->tc_plane >= 0) {
+        c->tc_p0 = c->tc_plane;
+    } else {
+        s = tc_continue_state(c);
+        c->tc_p0 = 0;
+    }
+    if (s != SI_OK) return s;
+    c->tc_plane = -1;
+    int done = steps, kstop = -1;
+    if (steps > 0) {
+        if ((s = tc_watch_buffers(c, steps, every)) != SI_OK) return s;
+        c->tc_readout = false;
+        c->tc_watch_every = every;
+        c->tc_watch_target = target_energy;
+        if (c->timing) SI_CUDA_TRY(cudaEventRecord(c->ev0, c->stream));
+        s = tc_run(c, steps, c->dspins);
+        c->tc_watch_every = 0;
+        if (s != SI_OK) return s;
+        if (c->timing) {
+            SI_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
+            c->ev_valid = true;
+        }
+        // the first readout that reached the target decides how far the run went
+        if (c->derr && (s = check_device_error(c)) != SI_OK) return s;
+        int hit = 0;
+        SI_CUDA_TRY(cudaMemcpyAsync(&hit, c->w_ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        const int nread = cdiv(steps, every);
+        kstop = (hit >= 0 && hit < nread) ? hit : nread - 1;
+        done = std::min(steps, (kstop + 1) * every);
+    } else if ((s = tc_spins(c, c->dspins, c->ld8)) != SI_OK) {
+        return s;
+    }
+    c->tc_plane = (done + c->tc_p0) & 1;
+    if (q_out || p_out) {
+        if ((s = tc_copy_state(c, (float *)qo.ptr, (float *)po.ptr)) != SI_OK) return s;
+    }
+    if (spins_out) {
+        k_unpad_spins<<<std::min(4096, cdiv((long long)R * n, 256)), 256, 0, c->stream>>>(c->dspins, c->ld8, n, R,
+                                                                                        (int8_t *)so.ptr);
+        SI_CUDA_TRY(cudaGetLastError());
+        c->launches += 1;
+    }
+    if (energy_out) {
+        if (kstop < 0) {
+            set_error("si_run_watch: no readout without steps");
+            return SI_ERR_INVALID_ARG;
+        }
+        if ((s = tc_watch_energy(c, kstop, (int32_t *)eo.ptr)) != SI_OK) return s;
+    }
+    if ((s = finish_call(c, {&qo, &po, &so, &eo}, false, true)) != SI_OK) return s;
+    if (steps_done) *steps_done = done;
+    c->have_run = true;
+    c->run_spins_valid = true;
     return SI_OK;
 }
 

@@ -126,7 +126,11 @@ struct Ctx {
     int tc_p0 = 0;                       // operand plane the next k_tc_run starts from
     bool tc_readout = false;             // the launch also sums sigma^T J sigma of its final spins
     bool fused_valid = false;            // e_sum holds those sums for the last run's spins
-    int tc_per_sm = 0;                   // co-resident CTAs per SM of the step kernel (0: not yet queried)
+    // watched run (si_run_watch): readout interval (0: none) and target energy
+    int tc_watch_every = 0;
+    long long tc_watch_target = 0;
+    int tc_per_sm[2] = {0, 0};           // co-resident CTAs per SM of the step kernel without / with
+                                         // readout passes (0: not yet queried)
     int stages = 0;
     int rpad = 0;                        // R rounded up to tile_n
     CUtensorMap mapA, mapB;              // J tiles, q operand tiles
@@ -140,6 +144,13 @@ struct Ctx {
     size_t e_sig_bytes = 0;
     unsigned long long *e_sum = nullptr; // per-replica sigma^T J sigma
     int e_sum_cap = 0;
+    // watched run: per-readout sums [nread][R], evaluation counters
+    // [nread][rblocks], then the finished evaluations and the first readout
+    // that reached the target
+    unsigned long long *w_sum = nullptr;
+    size_t w_sum_cap = 0;
+    unsigned *w_ctl = nullptr;
+    size_t w_ctl_cap = 0;
 
     // Gradient workspace (allocated lazily by si_grad).
     void *g_ws = nullptr;
@@ -220,6 +231,10 @@ si_status tc_energy_finish(Ctx *c, int R, int32_t *E, int32_t *C);
 si_status tc_readout_buffer(Ctx *c);
 // Whether a run of this context can sum its final energies in the step kernel.
 bool tc_readout_supported(const Ctx *c);
+// Buffers of a watched run of `steps` steps with a readout every `every`.
+si_status tc_watch_buffers(Ctx *c, int steps, int every);
+// Energies (Eq. 1) of readout k of the last watched run into E [R] (device).
+si_status tc_watch_energy(Ctx *c, int k, int32_t *E);
 const char *tc_describe(const Ctx *c, char *buf, int len);
 // 2D tensor map of e4m3 (1-byte) tiles of 64 x box_outer with the 64-byte swizzle.
 si_status tc_make_map_e4m3(CUtensorMap *m, void *base, int inner, int outer, int box_outer);

@@ -59,8 +59,38 @@ struct TcArgs {
     int stall_step;              // failure-detection test hook (-1: off)
     int smem_bytes;              // dynamic shared memory the launch provides
     int p0;                      // operand plane holding q(0)
-    int readout;                 // 1: one more pass with sign(q(T)) as the operand (exact energy)
-    unsigned long long *e_sum;   // [R] sigma^T J sigma of the final spins (readout), zeroed by the caller
+    // Readout passes: after every `every` steps and after the last one, one
+    // more pass over J with sign(q) as the operand sums sigma^T J sigma per
+    // replica (0: no readout; `steps`: only the final one).
+    int every;
+    unsigned long long *e_sum;   // [number of readouts][R], zeroed by the caller
+    // Watch: readout k of replica block rb is evaluated by the last of its
+    // M-tile CTAs to add its part (w_cnt); the run stops after the first
+    // readout at which some replica's energy is at most `target` (w_hit:
+    // first such readout, atomic minimum; w_done: evaluations finished, all
+    // replica blocks of readout k once it reaches rblocks (k + 1)).  The
+    // readout then adds 2 h_i sigma_i per spin (integer h8), so that the
+    // energy of Eq. 1 is minus half the sum.
+    int watch;
+    long long target;
+    unsigned *w_cnt;             // [number of readouts][rblocks]
+    unsigned *w_done;
+    int *w_hit;
+    const int8_t *h8;            // integer h, or null
+};
+
+// Pass schedule of one launch: step t of the iteration, or a readout pass
+// (after every `every` steps and after the last).  Passes are what the
+// step flags count.
+struct TcPasses {
+    int E, nread, npass;
+    __device__ __forceinline__ TcPasses(int steps, int every)
+        : E(every), nread(every > 0 ? (steps + every - 1) / every : 0), npass(steps + nread) {}
+    __device__ __forceinline__ bool readout(int p) const {
+        return E > 0 && ((p + 1) % (E + 1) == 0 || p == npass - 1);
+    }
+    __device__ __forceinline__ int step(int p) const { return E > 0 ? p - p / (E + 1) : p; }
+    __device__ __forceinline__ int index(int p) const { return p / (E + 1); }   // readout number of pass p
 };
 
 // ------------------------------------------------------------------ kernel
@@ -108,7 +138,126 @@ constexpr int TC_EPI_WARP0 = 1 + TC_MMA_WARPS;             // first epilogue war
 // epilogue frees the accumulators on the even CTA's barrier.  Both CTAs stay
 // until a cluster barrier before TMEM is freed, so neither leaves while the
 // other may still read its shared memory or signal its barriers.
-template <int BN, int S, int EPI, bool E4, bool CG2 = false>
+// Epilogue of a readout pass (one warp): the accumulators hold G = J sigma
+// (integers below 2^24, exact in FP32).  sigma_i (G_ir + h2) per element,
+// h2 = 2 h_i on a watched run (else 0), is added over the warp's 32 rows by
+// a transposing shuffle reduction (lane j ends with column j), and each warp
+// adds its column sums to the readout's per-replica totals `es` in 64-bit
+// integers.  Unless this is the final pass, the pass is published, and on a
+// watched run the last M-tile CTA of the replica block to add its part
+// evaluates the readout (any replica at or below the target: atomic minimum
+// of the readout index into w_hit, then one release increment of w_done);
+// every warp then waits for the grid's decision.  Returns 0 to go on with
+// the next pass, 1 to stop after this readout, 2 to end (final pass or a
+// failed wait).
+template <int BN, int CPH, bool CG2>
+__device__ __forceinline__ int tc_readout_epi(uint32_t tl, int c_begin, bool two_acc, bool row_ok, int h2,
+                                           unsigned long long *es, int r0, int R, int lane, bool pub_warp,
+                                           bool final_pass, uint32_t tmem_empty_bar, uint32_t epi_done_bar,
+                                           bool remote_tmem_empty, int t, unsigned *flag, int watch, unsigned *w_cnt,
+                                           unsigned last_cta, long long target, unsigned *w_done, int *w_hit,
+                                           int k, uint32_t seen, int *err, volatile int *abort_flag,
+                                           long long limit_ns) {
+    constexpr uint32_t COL_ACC0 = 0, COL_ACC1 = BN, COL_Q = 2 * BN;
+#pragma unroll 1
+    for (int c = c_begin; c < c_begin + CPH; ++c) {
+        uint32_t vf[32], vg[32], vq[32];
+        tmem_ld32(tl + COL_ACC0 + c * 32, vf);
+        if (two_acc) tmem_ld32(tl + COL_ACC1 + c * 32, vg);
+        tmem_ld32(tl + COL_Q + c * 32, vq);
+        tmem_wait_ld();
+        int v[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const float G = two_acc ? __uint_as_float(vf[j]) + __uint_as_float(vg[j]) : __uint_as_float(vf[j]);
+            v[j] = row_ok ? ((int)G + h2) * (int)spin_of(__uint_as_float(vq[j])) : 0;
+        }
+        column_sums32(v, lane);
+        const int r = r0 + c * 32 + lane;
+        if (r < R && v[0] != 0) atomicAdd(es + r, (unsigned long long)(long long)v[0]);
+    }
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) {
+        if (!final_pass) {
+            if (remote_tmem_empty) mbar_arrive_remote(mapa_shared(tmem_empty_bar, 0u));
+            else mbar_arrive(tmem_empty_bar);
+        }
+        mbar_arrive(epi_done_bar);
+    }
+    if (final_pass) return 2;
+    if (pub_warp) {
+        bool lastc = false;
+        if (lane == 0) {
+            if (mbar_wait(epi_done_bar, (uint32_t)(t & 1), err, abort_flag, limit_ns)) {
+                red_release_gpu_add(flag, 1u);
+                if (watch) lastc = atom_add_acq_rel_gpu(w_cnt, 1u) == last_cta;
+            }
+        }
+        lastc = __shfl_sync(0xffffffffu, lastc ? 1 : 0, 0) != 0;
+        if (lastc) {
+            // every CTA's additions are ordered before this acquire
+            (void)ld_acquire_gpu(w_cnt);
+            bool hit = false;
+#pragma unroll
+            for (int j = 0; j < BN / 32; ++j) {
+                const int r = r0 + j * 32 + lane;
+                if (r < R) {
+                    const long long sum = (long long)ld_relaxed_gpu_u64(es + r);
+                    hit = hit || (-(sum / 2) <= target);
+                }
+            }
+            hit = __any_sync(0xffffffffu, hit);
+            if (lane == 0) {
+                if (hit) atomicMin(w_hit, k);
+                red_release_gpu_add(w_done, 1u);
+            }
+        }
+    }
+    if (!watch) return 0;
+    // one decision for the whole grid: stop after this readout?
+    bool okd = true, stop = false;
+    if (lane == 0) okd = wait_decision(seen, k, stop, err, abort_flag, limit_ns);
+    okd = __shfl_sync(0xffffffffu, okd ? 1 : 0, 0) != 0;
+    stop = __shfl_sync(0xffffffffu, stop ? 1 : 0, 0) != 0;
+    if (!okd) return 2;
+    return stop ? 1 : 0;
+}
+
+// The state in tensor memory as the run's final state (a watched run that
+// stops after a readout: the state of the readout's step), one warp's rows
+// (E4: p from the shared-memory tile).  Every lane takes part in the
+// tensor-memory loads (.sync.aligned); only the stores depend on the row.
+template <int BN, bool E4>
+__device__ __forceinline__ void tc_write_state(uint32_t tl, int c_begin, int cph, bool row_ok, int r0, int R, int n,
+                                            int i, int row, float *q_state, float *p_state, int8_t *spins, int lds,
+                                            const float *p_tile) {
+    constexpr uint32_t COL_Q = 2 * BN, COL_P = 3 * BN;
+#pragma unroll 1
+    for (int c = c_begin; c < c_begin + cph; ++c) {
+        uint32_t vq[32], vp[32];
+        tmem_ld32(tl + COL_Q + c * 32, vq);
+        if constexpr (!E4) tmem_ld32(tl + COL_P + c * 32, vp);
+        tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int r = r0 + c * 32 + j;
+            if (row_ok && r < R) {
+                const float qv = __uint_as_float(vq[j]);
+                q_state[(size_t)r * n + i] = qv;
+                if constexpr (E4) p_state[(size_t)r * n + i] = p_tile[(c * 32 + j) * TC_BM + row];
+                else p_state[(size_t)r * n + i] = __uint_as_float(vp[j]);
+                if (spins) spins[(size_t)r * lds + i] = spin_of(qv);
+            }
+        }
+    }
+}
+
+// RO: the launch may have readout passes (a fused final readout or a
+// watched run).  The steps' loop of the instantiation without them carries
+// no readout code, which its register allocation and schedule would pay
+// for (about 5 % per step).
+template <int BN, int S, int EPI, bool E4, bool CG2 = false, bool RO = false>
 __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
     k_tc_run(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
              TcArgs a) {
@@ -137,6 +286,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L::BARS + L::NBARS * 8);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + L::BARS + L::NBARS * 8 + 4);
     const uint32_t seen = sbase + L::SEEN;   // mirrored step flags of the owners
+    const TcPasses P(a.steps, a.every);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int mt = blockIdx.x % a.mtiles, rb = blockIdx.x / a.mtiles;
@@ -162,7 +312,10 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
         mbar_init(epi_done_bar, EPI);
         mbar_init(drain_bar, TC_MMA_WARPS);
         *abort_flag = 0;
-        for (int o = 0; o <= MIRROR_MIN; ++o) reinterpret_cast<unsigned *>(smem + L::SEEN)[o] = 0u;
+        // mirrored owners' flags and minimum: 0; decisions final: 0; first
+        // readout at the target: none
+        for (int o = 0; o <= MIRROR_HIT; ++o)
+            reinterpret_cast<unsigned *>(smem + L::SEEN)[o] = o == MIRROR_HIT ? 0x7fffffffu : 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
@@ -218,12 +371,18 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
             bool ok = true;
             // pair: both CTAs walk the K blocks in the same order (the pair's rows first)
             const int kb0 = (CG2 ? (mt & ~1) : mt) * (TC_BM / TC_BK);
-            const int nsteps = a.steps + a.readout;
-            for (int t = 0; t < nsteps && ok; ++t) {
-                unsigned long long ready = t == 0 ? ~0ull : 0ull;   // owners known to have published step t
+            for (int t = 0; t < P.npass && ok; ++t) {
+                // watch: after a readout pass, every CTA goes on only if the
+                // run has not reached its target (one decision for the grid)
+                if (a.watch && t > 0 && P.readout(t - 1)) {
+                    bool stop = false;
+                    if (!wait_decision(seen, P.index(t - 1), stop, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                    if (stop) break;
+                }
+                unsigned long long ready = t == 0 ? ~0ull : 0ull;   // owners known to have published pass t
                 const unsigned need = (unsigned)t + (t == a.stall_step ? 1000000u : 0u);
-                // q(t) in plane (t + p0) & 1; the readout pass reads sign(q(T)) in plane 2
-                const int yb = (t == a.steps ? 2 : ((t + a.p0) & 1)) * a.rpad + r0 + (int)crank * (BN / 2);
+                // q of step s in plane (s + p0) & 1; a readout pass reads sign(q) in plane 2
+                const int yb = (P.readout(t) ? 2 : ((P.step(t) + a.p0) & 1)) * a.rpad + r0 + (int)crank * (BN / 2);
                 for (int j = ring; j < a.kblocks; j += 2) {
                     int kb = kb0 + j;
                     if (kb >= a.kblocks) kb -= a.kblocks;
@@ -257,9 +416,9 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
         }
     } else if (warp == tc_poll_warp<EPI, E4>()) {
         // ------------------------------------------------ step-flag mirror
-        if (a.steps + a.readout > 1)
-            mirror_flags(a.bar + (size_t)rb * a.mtiles, a.mtiles, (unsigned)(a.steps + a.readout - 1), seen, lane,
-                         a.err, abort_flag, a.limit_ns);
+        if (P.npass > 1)
+            mirror_flags(a.bar + (size_t)rb * a.mtiles, a.mtiles, (unsigned)(P.npass - 1), seen, lane, a.err,
+                         abort_flag, a.limit_ns, a.watch ? a.w_done : nullptr, a.w_hit, (unsigned)a.rblocks);
     } else if (warp <= TC_MMA_WARPS) {
         // ------------------------------------------------ MMA issuers
         // Warp 1 takes the even positions of the K loop into accumulator 0,
@@ -273,7 +432,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
             constexpr int HS = S / 2;
             uint32_t c = 0;
             bool ok = true;
-            for (int t = 0; t < a.steps + a.readout && ok; ++t) {
+            for (int t = 0; t < P.npass && ok; ++t) {
                 for (int j = w; j < a.kblocks; j += TC_MMA_WARPS, ++c) {
                     const int s = 2 * (int)(c % HS) + w;
                     if (!mbar_wait(full_bar(s), (c / HS) & 1u, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
@@ -292,7 +451,12 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                 return CG2 ? mbar_wait_cluster(bar, parity, a.err, abort_flag, a.limit_ns)
                            : mbar_wait(bar, parity, a.err, abort_flag, a.limit_ns);
             };
-            for (int t = 0; t < a.steps + a.readout && ok; ++t) {
+            for (int t = 0; t < P.npass && ok; ++t) {
+                if (a.watch && t > 0 && P.readout(t - 1)) {
+                    bool stop = false;
+                    if (!wait_decision(seen, P.index(t - 1), stop, a.err, abort_flag, a.limit_ns)) break;
+                    if (stop) break;
+                }
                 if (t > 0) {
                     if (!wait_bar(tmem_empty_bar, (uint32_t)((t - 1) & 1))) break;
                 }
@@ -390,7 +554,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
         }
         tmem_wait_st();
 #pragma unroll 1
-        for (int t = 0; t < a.steps + a.readout; ++t) {
+        for (int t = 0; t < P.npass; ++t) {
             bool ok = true;
             if (lane == 0)
                 ok = CG2 ? mbar_wait_cluster(accf_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns)
@@ -398,50 +562,26 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
             ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
             if (!ok) break;
             tc_fence_after();
-            if (t == a.steps) {
-                // Readout pass: the accumulators hold G = J sigma of the final
-                // spins (integers below 2^24, exact in FP32); sigma_i G_ir goes
-                // to shared memory as [replica][row] (the ring is idle: every
-                // MMA has completed), then thread e adds replica column e over
-                // the tile's rows in 64-bit integers.
-                int *prod = reinterpret_cast<int *>(smem);
-#pragma unroll 1
-                for (int c = c_begin; c < c_begin + CPH; ++c) {
-                    uint32_t vf[32], vg[32], vq[32];
-                    tmem_ld32(tl + COL_ACC0 + c * 32, vf);
-                    if (two_acc) tmem_ld32(tl + COL_ACC1 + c * 32, vg);
-                    tmem_ld32(tl + COL_Q + c * 32, vq);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float G = two_acc ? __uint_as_float(vf[j]) + __uint_as_float(vg[j]) : __uint_as_float(vf[j]);
-                        const int sg = spin_of(__uint_as_float(vq[j]));
-                        prod[(c * 32 + j) * (TC_BM + 1) + row] = row_ok ? (int)G * sg : 0;
-                    }
-                }
-                // All epilogue warps have written their products (the
-                // epilogue barrier's phase of this pass: every warp arrives
-                // once per pass, and none can arrive for a later one).  The
-                // wait is bounded, so a warp that left on an abort cannot
-                // hold the others.
-                __syncwarp();
-                if (lane == 0) mbar_arrive(epi_done_bar);
-                bool okr = true;
-                if (lane == 0) okr = mbar_wait(epi_done_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns);
-                okr = __shfl_sync(0xffffffffu, okr ? 1 : 0, 0) != 0;
-                const int e = (int)threadIdx.x - 32 * TC_EPI_WARP0;
-                if (okr && e < BN && r0 + e < a.R) {
-                    long long x = 0;
-                    const int *col = prod + e * (TC_BM + 1);
-#pragma unroll 8
-                    for (int w2 = 0; w2 < TC_BM; ++w2) x += col[w2];
-                    if (x != 0) atomicAdd(a.e_sum + r0 + e, (unsigned long long)x);
-                }
-                break;
+            if (P.readout(t)) {
+                if constexpr (!RO) break;   // not launched with readout passes
+                const int k = P.index(t);
+                const int rc = tc_readout_epi<BN, CPH, CG2>(
+                    tl, c_begin, two_acc, row_ok, (a.watch && a.h8 && row_ok) ? 2 * (int)a.h8[i] : 0,
+                    a.e_sum + (size_t)k * a.R, r0, a.R, lane, warp == TC_EPI_WARP0, t == P.npass - 1,
+                    tmem_empty_bar, epi_done_bar, CG2 && !leader, t, a.bar + (size_t)rb * a.mtiles + mt, a.watch,
+                    a.w_cnt ? a.w_cnt + (size_t)k * a.rblocks + rb : nullptr, (unsigned)(a.mtiles - 1), a.target,
+                    a.w_done, a.w_hit, k, seen, a.err, abort_flag, a.limit_ns);
+                if (rc == 1)
+                    tc_write_state<BN, E4>(tl, c_begin, CPH, row_ok, r0, a.R, a.n, i, row, a.q_state, a.p_state,
+                                           a.spins, a.lds, p_tile);
+                if (rc != 0) break;
+                continue;
             }
-            const float zt = a.zeta[t], dtt = a.dt[t];
+            const int st = P.step(t);
+            const float zt = a.zeta[st], dtt = a.dt[st];
             const float dtm = dtt / a.sp.m;
-            const bool last = (t == a.steps - 1);
+            const bool last = (st == a.steps - 1);
+            const bool pre_ro = t + 1 < P.npass && P.readout(t + 1);   // the next pass reads sign(q) of this step
             // The chunk loop, instantiated once with the update order and the
             // wall variant as run-time parameters and once for the default
             // (kick-drift, no momentum zeroing) so that the integrator does
@@ -506,7 +646,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                     // replica are 64 contiguous bytes.  Entries outside n x R
                     // are never written and keep the zeros of the initial fill.
                     __nv_bfloat16 *dst =
-                        a.qop + ((size_t)((t + 1 + a.p0) & 1) * a.rpad + (size_t)(r0 + c * 32)) * a.ldk + i;
+                        a.qop + ((size_t)((st + 1 + a.p0) & 1) * a.rpad + (size_t)(r0 + c * 32)) * a.ldk + i;
                     if (row_ok && r0 + c * 32 + 32 <= a.R) {
 #pragma unroll
                         for (int j = 0; j < 32; ++j) dst[(size_t)j * a.ldk] = __float2bfloat16_rn(__uint_as_float(vq[j]));
@@ -517,8 +657,8 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                                 dst[(size_t)j * a.ldk] = __float2bfloat16_rn(__uint_as_float(vq[j]));
                     }
                 }
-                if (last && a.readout && row_ok) {
-                    // sign(q(T)) as the operand of the readout pass (plane 2)
+                if (pre_ro && row_ok) {
+                    // sign(q) as the operand of the readout pass (plane 2)
                     __nv_bfloat16 *dst = a.qop + ((size_t)2 * a.rpad + (size_t)(r0 + c * 32)) * a.ldk + i;
 #pragma unroll
                     for (int j = 0; j < 32; ++j)
@@ -555,7 +695,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                 else mbar_arrive(tmem_empty_bar);
                 mbar_arrive(epi_done_bar);
             }
-            if (publisher && (!last || a.readout)) {
+            if (publisher && t + 1 < P.npass) {
                 // All 8 warps have written their part of q(t+1) (or sign(q(T))): publish.
                 if (mbar_wait(epi_done_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns))
                     red_release_gpu_add(a.bar + (size_t)rb * a.mtiles + mt, 1u);
@@ -576,7 +716,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
         constexpr int HS = S / 2;
         uint32_t cnt0 = 0u, cnt1 = 0u;
         bool ok = true;
-        for (int t = 0; t < a.steps + a.readout && ok; ++t) {
+        for (int t = 0; t < P.npass && ok; ++t) {
             for (int j = 0; j < a.kblocks; ++j) {
                 const int ring = j & 1;
                 const uint32_t c = ring ? cnt1 : cnt0;
@@ -760,7 +900,7 @@ __global__ void k_tc_spins(const float *q_state, int n, int R, int8_t *spins, in
     }
 }
 
-template <int BN, int S, int EPI, bool E4, bool CG2 = false>
+template <int BN, int S, int EPI, bool E4, bool CG2 = false, bool RO = false>
 static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
     using L = TcSmem<BN, S, E4, CG2>;
     TcArgs a;
@@ -787,8 +927,20 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
     a.sp = StepParams{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max,
                       c->prm.update_order, c->prm.wall_zero_p};
     a.p0 = c->tc_p0;
-    a.readout = c->tc_readout ? 1 : 0;
-    a.e_sum = c->e_sum;
+    const bool watch = c->tc_watch_every > 0;
+    a.every = watch ? c->tc_watch_every : (c->tc_readout ? steps : 0);
+    a.watch = watch ? 1 : 0;
+    a.target = c->tc_watch_target;
+    const int nread = a.every > 0 ? cdiv(steps, a.every) : 0;
+    a.e_sum = watch ? c->w_sum : c->e_sum;
+    a.w_cnt = watch ? c->w_ctl + 2 : nullptr;
+    a.w_done = watch ? c->w_ctl : nullptr;
+    a.w_hit = watch ? reinterpret_cast<int *>(c->w_ctl + 1) : nullptr;
+    a.h8 = c->has_h ? c->dh8 : nullptr;
+    if ((watch || a.every > 0) && (CG2 || E4 || !RO)) {
+        set_error("tensor path: readout passes need the bf16 operand on single CTAs");
+        return SI_ERR_UNSUPPORTED;
+    }
     const int grid = a.mtiles * a.rblocks;
     if (a.rblocks * a.mtiles > c->nbar || a.mtiles > 64) {
         set_error("tensor path: too many tiles for the step flags (n <= 8192 per context)");
@@ -796,10 +948,10 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
     }
     const int smem = L::TOTAL + 1024;
     a.smem_bytes = smem;
-    auto kern = k_tc_run<BN, S, EPI, E4, CG2>;
+    auto kern = k_tc_run<BN, S, EPI, E4, CG2, RO>;
     // launch attributes and the co-residency check once per context (its
     // device and tile are fixed)
-    if (c->tc_per_sm <= 0) {
+    if (c->tc_per_sm[RO ? 1 : 0] <= 0) {
         SI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         SI_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                          (int)cudaSharedmemCarveoutMaxShared));
@@ -822,15 +974,21 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
             SI_CUDA_TRY(cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg));
             if (2 * clusters < grid) per_sm = 0;
         }
-        c->tc_per_sm = per_sm;
+        c->tc_per_sm[RO ? 1 : 0] = per_sm;
     }
-    const int per_sm = c->tc_per_sm;
+    const int per_sm = c->tc_per_sm[RO ? 1 : 0];
     if (per_sm * c->num_sms < grid) {
         set_error("tensor path: grid cannot be co-resident (reduce replicas per context)");
         return SI_ERR_UNSUPPORTED;
     }
     SI_CUDA_TRY(cudaMemsetAsync(c->dbar, 0, sizeof(unsigned) * grid, c->stream));
-    if (a.readout) SI_CUDA_TRY(cudaMemsetAsync(c->e_sum, 0, sizeof(unsigned long long) * c->R, c->stream));
+    if (nread > 0)
+        SI_CUDA_TRY(cudaMemsetAsync(a.e_sum, 0, sizeof(unsigned long long) * (size_t)nread * c->R, c->stream));
+    if (watch) {
+        // finished evaluations 0, first hit "none" (0x7f7f7f7f), counters 0
+        SI_CUDA_TRY(cudaMemsetAsync(c->w_ctl, 0, sizeof(unsigned) * (2 + (size_t)nread * a.rblocks), c->stream));
+        SI_CUDA_TRY(cudaMemsetAsync(c->w_ctl + 1, 0x7f, sizeof(unsigned), c->stream));
+    }
     if constexpr (CG2) {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
@@ -858,6 +1016,40 @@ bool tc_readout_supported(const Ctx *c) {
     return !c->grp && !c->j_e4m3 && !c->tc_pair && c->integer_j && (!c->has_h || c->integer_h);
 }
 
+si_status tc_watch_buffers(Ctx *c, int steps, int every) {
+    const size_t nread = (size_t)cdiv(steps, every);
+    // counters for the smallest replica tile (64): room for any tile choice
+    const size_t ns = nread * c->R, nc = 2 + nread * (size_t)(c->rpad / 64);
+    if (ns > c->w_sum_cap) {
+        if (c->w_sum) cudaFree(c->w_sum);
+        c->w_sum = nullptr;
+        c->w_sum_cap = 0;
+        SI_CUDA_TRY(si_dev_malloc((void **)&c->w_sum, sizeof(unsigned long long) * ns));
+        c->w_sum_cap = ns;
+    }
+    if (nc > c->w_ctl_cap) {
+        if (c->w_ctl) cudaFree(c->w_ctl);
+        c->w_ctl = nullptr;
+        c->w_ctl_cap = 0;
+        SI_CUDA_TRY(si_dev_malloc((void **)&c->w_ctl, sizeof(unsigned) * nc));
+        c->w_ctl_cap = nc;
+    }
+    return SI_OK;
+}
+
+// E = -(sigma^T J sigma + 2 h^T sigma) / 2, the readout's sum (exact: even).
+__global__ void k_watch_energy(const unsigned long long *sum, int R, int32_t *E) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < R) E[r] = (int32_t)(-((long long)sum[r] / 2));
+}
+
+si_status tc_watch_energy(Ctx *c, int k, int32_t *E) {
+    k_watch_energy<<<cdiv(c->R, 256), 256, 0, c->stream>>>(c->w_sum + (size_t)k * c->R, c->R, E);
+    SI_CUDA_TRY(cudaGetLastError());
+    c->launches += 1;
+    return SI_OK;
+}
+
 si_status tc_run(Ctx *c, int steps, int8_t *spins_dev) {
     if (steps == 0) return SI_OK;
     if (c->j_e4m3) {
@@ -868,6 +1060,12 @@ si_status tc_run(Ctx *c, int steps, int8_t *spins_dev) {
         }
     } else if (c->tc_pair) {
         return tc_launch_t<128, 6, 8, false, true>(c, steps, spins_dev);
+    } else if (c->tc_readout || c->tc_watch_every > 0) {
+        switch (c->tile_n) {
+            case 64: return tc_launch_t<64, 8, 8, false, false, true>(c, steps, spins_dev);
+            case 128: return tc_launch_t<128, 6, 8, false, false, true>(c, steps, spins_dev);
+            default: break;
+        }
     } else {
         switch (c->tile_n) {
             case 64: return tc_launch_t<64, 8, 8, false>(c, steps, spins_dev);

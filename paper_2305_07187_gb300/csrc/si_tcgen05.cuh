@@ -94,14 +94,38 @@ __device__ __forceinline__ void st_release_cta_shared(uint32_t addr, unsigned v)
 // a producer every owner ready.  The warp stops once every owner has
 // published `last` steps, when the run is being aborted, or when no flag has
 // moved for limit_ns (the waiting producer raises the error then).
-constexpr int MIRROR_MIN = 64;   // word index of the minimum (words 0..63: owners)
+//
+// A watched run (w_done non-null) also mirrors the grid's stop decision:
+// lane 0 reads the number of finished readout evaluations (acquire) and
+// then the first readout that reached the target, stores the latter in
+// word MIRROR_HIT and then (release) the number of readouts whose decision
+// is final, floor(w_done / rblocks), in word MIRROR_FINAL.  Once a final
+// readout has reached the target the run ends after it, and the warp stops.
+constexpr int MIRROR_MIN = 64;     // word index of the minimum (words 0..63: owners)
+constexpr int MIRROR_FINAL = 65;   // readouts whose stop decision is final
+constexpr int MIRROR_HIT = 66;     // first readout that reached the target (large: none yet)
 
 __device__ __forceinline__ void mirror_flags(const unsigned *flags, int nown, unsigned last, uint32_t seen,
-                                             int lane, int *err, volatile int *abort_flag, long long limit_ns) {
+                                             int lane, int *err, volatile int *abort_flag, long long limit_ns,
+                                             const unsigned *w_done = nullptr, const int *w_hit = nullptr,
+                                             unsigned rblocks = 1u) {
     unsigned m0 = 0u, m1 = 0u, mmin = 0u;   // last values mirrored by this lane
+    unsigned mfin = 0u;
     unsigned long long t_last = globaltimer_ns();
     for (unsigned it = 1;; ++it) {
-        bool moved = false, done = true;
+        bool moved = false, done = true, decided = false;
+        if (w_done && lane == 0) {
+            const unsigned fin = ld_acquire_gpu(w_done) / rblocks;
+            if (fin != mfin) {
+                const int h = ld_volatile_int(w_hit);
+                st_release_cta_shared(seen + 4u * MIRROR_HIT, (unsigned)h);
+                st_release_cta_shared(seen + 4u * MIRROR_FINAL, fin);
+                mfin = fin;
+                moved = true;
+                decided = h < (int)fin;
+            }
+        }
+        if (__any_sync(0xffffffffu, decided)) return;
         unsigned vmin = 0xffffffffu;
         if (lane < nown) {
             const unsigned v = ld_acquire_gpu(flags + lane);
@@ -180,6 +204,64 @@ __device__ __forceinline__ bool wait_owner(uint32_t seen, int mo, unsigned need,
     }
     fence_proxy_async_global();
     return true;
+}
+
+// Bounded wait until the mirrored decision of readout k is final; `stop` is
+// then whether the run reached its target at a readout <= k.  Returns false
+// on abort or timeout (raising DEV_TIMEOUT_BARRIER).
+__device__ __forceinline__ bool wait_decision(uint32_t seen, int k, bool &stop, int *err, volatile int *abort_flag,
+                                              long long limit_ns) {
+    const uint32_t afin = seen + 4u * MIRROR_FINAL;
+    const unsigned need = (unsigned)k + 1u;
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        if ((int)(ld_acquire_cta_shared(afin) - need) >= 0) {
+            stop = (int)ld_acquire_cta_shared(seen + 4u * MIRROR_HIT) <= k;
+            return true;
+        }
+        if (it == 0) t0 = globaltimer_ns();
+        if ((it & 15u) == 15u) {
+            if (*abort_flag || ld_volatile_int(err) != 0) {
+                *abort_flag = 1;
+                return false;
+            }
+            if ((long long)(globaltimer_ns() - t0) > limit_ns) {
+                atomicCAS(err, 0, DEV_TIMEOUT_BARRIER);
+                *abort_flag = 1;
+                return false;
+            }
+        }
+    }
+}
+
+// Atomic add with acquire-release semantics at GPU scope (returns the old value).
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Column sums of a warp's 32 x 32 block (lane = row, v[j] = column j): a
+// transposing butterfly of 31 shuffles, after which v[0] of lane j holds the
+// sum of column j.  At the round of width s a lane keeps the half of its
+// current columns selected by bit s of its index and adds its partner's
+// copy of that half.
+__device__ __forceinline__ void column_sums32(int (&v)[32], int lane) {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool upper = (lane & s) != 0;
+#pragma unroll
+        for (int j = 0; j < s; ++j) {
+            const int give = upper ? v[j] : v[j + s];
+            const int keep = upper ? v[j + s] : v[j];
+            v[j] = keep + __shfl_xor_sync(0xffffffffu, give, s);
+        }
+    }
 }
 
 __device__ __forceinline__ void tc_fence_before() {
