@@ -275,14 +275,20 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
     db = torch.from_numpy(inputs.dt_const(T_STEPS)).to(dev)
     s_upper = int(np.triu(J.astype(np.int64), 1).sum())
     e_target = int(-2 * int(c_star) - s_upper)        # cut >= C*  <=>  energy <= e_target
-    ttts, hit_steps = [], []
+    ttts, hit_steps, kern = [], [], []
     with b.Context(J, replicas=R, steps=T_STEPS, prec="j_fp8_q_bf16", stream=stream.cuda_stream) as cb:
+        cb.enable_timing(True)
+        e_dev = torch.empty(R, dtype=torch.int32, device=dev)
         e_host = torch.empty(R, dtype=torch.int32).pin_memory()
         for seed in range(seeds + 1):
             q_init = torch.from_numpy(inputs.positions(n, R, seed0=200000 + 4096 * seed)).to(dev)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            done = cb.run_watch_into(zb, db, q_init, every, e_target, energy_out=e_host)
+            # returns with the stop known; the energies of the stopping
+            # readout then come to pinned host memory
+            done = cb.run_watch_into(zb, db, q_init, every, e_target, energy_out=e_dev)
+            e_host.copy_(e_dev, non_blocking=True)
+            stream.synchronize()
             el = time.perf_counter() - t0
             best_cut = -(int(e_host.numpy().min()) + s_upper) / 2.0
             hit = done if best_cut >= c_star else None
@@ -290,6 +296,7 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
                 continue          # warm-up
             ttts.append(el if hit is not None else float("inf"))
             hit_steps.append(hit)
+            kern.append(cb.last_kernel_ms() * 1e-3)
     ttt = float(np.median(ttts))
     # Like-for-like with the plain path: the batched path's own per-replica
     # TTS99.  One full batched run (R replicas, T=2000) takes t_b; each of its
@@ -311,6 +318,7 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
     tts99_rep = (t_b / R) * math.log(0.01) / math.log(max(1e-12, 1.0 - p_b)) if p_b < 1 else t_b / R
     return {"target_cut": c_star, "target_from": "median final cut of the FP32 plain path, 1000 replicas, T=1000",
             "batched_ttt_s": ttt, "batched_hit_steps_median": float(np.median([h or T_STEPS for h in hit_steps])),
+            "batched_ttt_kernel_s": float(np.median(kern)) if kern else None,
             "batched_seeds": seeds, "readout_every_steps": every,
             "fp32_plain_tts99_s": tts99, "fp32_plain_run_s": t_run_fp32, "fp32_plain_p_success": p_s,
             "speedup_vs_fp32_plain": (tts99 / ttt) if ttt > 0 else None,
@@ -318,7 +326,8 @@ def time_to_target(b, torch, dev, stream, seeds=10, every=10):
             "batched_tts99_per_replica_s": tts99_rep,
             "readout": "inside the persistent step kernel (si_run_watch): a pass over J with sign(q) every "
                        "10 steps, evaluated and the stop decided on the GPU; one launch per run",
-            "note": "batched_ttt_s: any of R=1024 replicas reaches C* (readout every 10 steps); "
+            "note": "batched_ttt_s: any of R=1024 replicas reaches C* (readout every 10 steps), host wall time of "
+                    "the call; batched_ttt_kernel_s: the watched launch alone (CUDA events); "
                     "batched_tts99_per_replica_s: TTS99 of one replica of the batched path, each replica "
                     "charged 1/R of a full T=2000 batched run, p from the run's final cuts"}
 
@@ -570,11 +579,12 @@ def run_grad(args):
                    "kernel": desc, "l2": "256 MiB buffer written between timed steps"},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
-                     "kernel": "k_adj_tc (forward, recompute and adjoint products, K split over a cluster)",
+                     "kernel": "k_adj_run (persistent sweep: forward, recompute and adjoint products, K split "
+                               "over a cluster, the elementwise adjoint step fused)",
                      "peak_source": "%s bf16_tflops (burst)" % src, "algorithmic_flops": flops,
-                     "note": "whole si_grad time: per step 3 products (forward, recompute, adjoint) and 1 "
-                             "elementwise adjoint kernel, dependent launches replayed from a CUDA graph; "
-                             "latency-bound"},
+                     "note": "whole si_grad time: one launch for the forward pass, then one per segment "
+                             "sweeping it back beside the recomputation of the segment before; "
+                             "latency-bound (cross-CTA step exchange, split-K cluster reduction)"},
         "e2e": {"value": R * n * T / (statistics.median(e2e) * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 4 * (2 * T + R * n), "d2h_bytes_per_step": 4 * (2 * T + 2)},
         "gpu_launches": launches,
@@ -638,13 +648,13 @@ def run_study(args):
 
 def ncu_case_grad(args):
     """Profiling case of the differentiation workload: N=2000 +-1, R=64,
-    --time-steps steps (checkpoints every 10), one warm-up and one profiled
-    si_grad."""
+    --time-steps steps (checkpoints every 50, as the workload), one warm-up
+    and one profiled si_grad."""
     from paper_2305_07187_gb300 import _binding as b
     T = args.time_steps
     J = inputs.pm1_coupling(GRAD_N, seed=1)
     q0 = inputs.positions(GRAD_N, GRAD_R, seed0=100)
-    with b.Context(J, replicas=GRAD_R, steps=T, prec="fp32", ckpt_every=10) as ctx:
+    with b.Context(J, replicas=GRAD_R, steps=T, prec="fp32", ckpt_every=GRAD_K) as ctx:
         for _ in range(2):
             ctx.grad(inputs.zeta_ramp(T), inputs.dt_const(T), q0)
         print(ctx.describe())

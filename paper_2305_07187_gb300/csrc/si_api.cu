@@ -264,7 +264,8 @@ static si_status create_impl(Ctx *c, const float *J, const float *h) {
     // context writes both).
     SI_CUDA_TRY(si_dev_malloc((void **)&c->derr, sizeof(int)));
     SI_CUDA_TRY(cudaMemsetAsync(c->derr, 0, sizeof(int), c->stream));
-    if (cudaHostAlloc((void **)&c->herr, sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+    // word 0: the device error word's copy; word 1: a watched run's first hit
+    if (cudaHostAlloc((void **)&c->herr, 2 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();   // optional: the read then goes through pageable memory
         c->herr = nullptr;
     }
@@ -568,11 +569,17 @@ si_status si_run_watch(si_ctx *ctx, const float *zeta, const float *dt, const fl
             SI_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
             c->ev_valid = true;
         }
-        // the first readout that reached the target decides how far the run went
-        if (c->derr && (s = check_device_error(c)) != SI_OK) return s;
-        int hit = 0;
-        SI_CUDA_TRY(cudaMemcpyAsync(&hit, c->w_ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        // The first readout that reached the target decides how far the run
+        // went: its copy and the error word's share one synchronisation.
+        int local = 0;
+        int *hh = c->herr ? c->herr + 1 : &local;
+        SI_CUDA_TRY(cudaMemcpyAsync(hh, c->w_ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        if (c->derr) {
+            if ((s = check_device_error(c)) != SI_OK) return s;
+        } else {
+            SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        }
+        const int hit = *hh;
         const int nread = cdiv(steps, every);
         kstop = (hit >= 0 && hit < nread) ? hit : nread - 1;
         done = std::min(steps, (kstop + 1) * every);
