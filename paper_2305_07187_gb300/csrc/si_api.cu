@@ -555,7 +555,9 @@ si_status si_run_watch(si_ctx *ctx, const float *zeta, const float *dt, const fl
     }
     if (s != SI_OK) return s;
     c->tc_plane = -1;
-    int done = steps, kstop = -1;
+    const int nread = steps > 0 ? cdiv(steps, every) : 0;
+    int local = 0x7fffffff;
+    int *hh = c->herr ? c->herr + 1 : &local;
     if (steps > 0) {
         if ((s = tc_watch_buffers(c, steps, every)) != SI_OK) return s;
         c->tc_readout = false;
@@ -569,24 +571,12 @@ si_status si_run_watch(si_ctx *ctx, const float *zeta, const float *dt, const fl
             SI_CUDA_TRY(cudaEventRecord(c->ev1, c->stream));
             c->ev_valid = true;
         }
-        // The first readout that reached the target decides how far the run
-        // went: its copy and the error word's share one synchronisation.
-        int local = 0;
-        int *hh = c->herr ? c->herr + 1 : &local;
+        // the first readout that reached the target (read after the one
+        // synchronisation at the end of the call)
         SI_CUDA_TRY(cudaMemcpyAsync(hh, c->w_ctl + 1, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-        if (c->derr) {
-            if ((s = check_device_error(c)) != SI_OK) return s;
-        } else {
-            SI_CUDA_TRY(cudaStreamSynchronize(c->stream));
-        }
-        const int hit = *hh;
-        const int nread = cdiv(steps, every);
-        kstop = (hit >= 0 && hit < nread) ? hit : nread - 1;
-        done = std::min(steps, (kstop + 1) * every);
     } else if ((s = tc_spins(c, c->dspins, c->ld8)) != SI_OK) {
         return s;
     }
-    c->tc_plane = (done + c->tc_p0) & 1;
     if (q_out || p_out) {
         if ((s = tc_copy_state(c, (float *)qo.ptr, (float *)po.ptr)) != SI_OK) return s;
     }
@@ -597,13 +587,20 @@ si_status si_run_watch(si_ctx *ctx, const float *zeta, const float *dt, const fl
         c->launches += 1;
     }
     if (energy_out) {
-        if (kstop < 0) {
+        if (nread == 0) {
             set_error("si_run_watch: no readout without steps");
             return SI_ERR_INVALID_ARG;
         }
-        if ((s = tc_watch_energy(c, kstop, (int32_t *)eo.ptr)) != SI_OK) return s;
+        if ((s = tc_watch_energy(c, nread, (int32_t *)eo.ptr)) != SI_OK) return s;
     }
     if ((s = finish_call(c, {&qo, &po, &so, &eo}, false, true)) != SI_OK) return s;
+    int done = steps;
+    if (nread > 0) {
+        const int hit = *hh;
+        const int kstop = (hit >= 0 && hit < nread) ? hit : nread - 1;
+        done = std::min(steps, (kstop + 1) * every);
+    }
+    c->tc_plane = (done + c->tc_p0) & 1;
     if (steps_done) *steps_done = done;
     c->have_run = true;
     c->run_spins_valid = true;

@@ -233,8 +233,9 @@ si_status tc_readout_buffer(Ctx *c);
 bool tc_readout_supported(const Ctx *c);
 // Buffers of a watched run of `steps` steps with a readout every `every`.
 si_status tc_watch_buffers(Ctx *c, int steps, int every);
-// Energies (Eq. 1) of readout k of the last watched run into E [R] (device).
-si_status tc_watch_energy(Ctx *c, int k, int32_t *E);
+// Energies (Eq. 1) of the stopping readout of the last watched run (of
+// nread) into E [R] (device); the kernel reads the stop itself.
+si_status tc_watch_energy(Ctx *c, int nread, int32_t *E);
 const char *tc_describe(const Ctx *c, char *buf, int len);
 // 2D tensor map of e4m3 (1-byte) tiles of 64 x box_outer with the 64-byte swizzle.
 si_status tc_make_map_e4m3(CUtensorMap *m, void *base, int inner, int outer, int box_outer);

@@ -91,6 +91,12 @@ struct TcPasses {
     }
     __device__ __forceinline__ int step(int p) const { return E > 0 ? p - p / (E + 1) : p; }
     __device__ __forceinline__ int index(int p) const { return p / (E + 1); }   // readout number of pass p
+    // the first readout pass at or after pass p (npass if there is none)
+    __device__ __forceinline__ int next_readout(int p) const {
+        if (E <= 0) return npass;
+        const int r = p + (E - p % (E + 1));
+        return r < npass - 1 ? r : npass - 1;
+    }
 };
 
 // ------------------------------------------------------------------ kernel
@@ -146,32 +152,34 @@ constexpr int TC_EPI_WARP0 = 1 + TC_MMA_WARPS;             // first epilogue war
 // integers.  Unless this is the final pass, the pass is published, and on a
 // watched run the last M-tile CTA of the replica block to add its part
 // evaluates the readout (any replica at or below the target: atomic minimum
-// of the readout index into w_hit, then one release increment of w_done);
-// every warp then waits for the grid's decision.  Returns 0 to go on with
-// the next pass, 1 to stop after this readout, 2 to end (final pass or a
-// failed wait).
+// of the readout index into w_hit, then one release increment of w_done).
+// The grid's decision is waited for later, before the next step's update.
+// Returns 0 to go on with the next pass, 2 after the final pass.
 template <int BN, int CPH, bool CG2>
 __device__ __forceinline__ int tc_readout_epi(uint32_t tl, int c_begin, bool two_acc, bool row_ok, int h2,
                                            unsigned long long *es, int r0, int R, int lane, bool pub_warp,
                                            bool final_pass, uint32_t tmem_empty_bar, uint32_t epi_done_bar,
                                            bool remote_tmem_empty, int t, unsigned *flag, int watch, unsigned *w_cnt,
                                            unsigned last_cta, long long target, unsigned *w_done, int *w_hit,
-                                           int k, uint32_t seen, int *err, volatile int *abort_flag,
-                                           long long limit_ns) {
+                                           int k, int *err, volatile int *abort_flag, long long limit_ns) {
     constexpr uint32_t COL_ACC0 = 0, COL_ACC1 = BN, COL_Q = 2 * BN;
 #pragma unroll 1
     for (int c = c_begin; c < c_begin + CPH; ++c) {
-        uint32_t vf[32], vg[32], vq[32];
+        // two 32-register arrays at a time (G in place, then q into the other)
+        uint32_t vf[32], vg[32];
         tmem_ld32(tl + COL_ACC0 + c * 32, vf);
-        if (two_acc) tmem_ld32(tl + COL_ACC1 + c * 32, vg);
-        tmem_ld32(tl + COL_Q + c * 32, vq);
+        if (two_acc) {
+            tmem_ld32(tl + COL_ACC1 + c * 32, vg);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 32; ++j) vf[j] = __float_as_uint(__uint_as_float(vf[j]) + __uint_as_float(vg[j]));
+        }
+        tmem_ld32(tl + COL_Q + c * 32, vg);
         tmem_wait_ld();
         int v[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const float G = two_acc ? __uint_as_float(vf[j]) + __uint_as_float(vg[j]) : __uint_as_float(vf[j]);
-            v[j] = row_ok ? ((int)G + h2) * (int)spin_of(__uint_as_float(vq[j])) : 0;
-        }
+        for (int j = 0; j < 32; ++j)
+            v[j] = row_ok ? ((int)__uint_as_float(vf[j]) + h2) * (int)spin_of(__uint_as_float(vg[j])) : 0;
         column_sums32(v, lane);
         const int r = r0 + c * 32 + lane;
         if (r < R && v[0] != 0) atomicAdd(es + r, (unsigned long long)(long long)v[0]);
@@ -214,14 +222,7 @@ __device__ __forceinline__ int tc_readout_epi(uint32_t tl, int c_begin, bool two
             }
         }
     }
-    if (!watch) return 0;
-    // one decision for the whole grid: stop after this readout?
-    bool okd = true, stop = false;
-    if (lane == 0) okd = wait_decision(seen, k, stop, err, abort_flag, limit_ns);
-    okd = __shfl_sync(0xffffffffu, okd ? 1 : 0, 0) != 0;
-    stop = __shfl_sync(0xffffffffu, stop ? 1 : 0, 0) != 0;
-    if (!okd) return 2;
-    return stop ? 1 : 0;
+    return 0;
 }
 
 // The state in tensor memory as the run's final state (a watched run that
@@ -372,11 +373,14 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
             // pair: both CTAs walk the K blocks in the same order (the pair's rows first)
             const int kb0 = (CG2 ? (mt & ~1) : mt) * (TC_BM / TC_BK);
             for (int t = 0; t < P.npass && ok; ++t) {
-                // watch: after a readout pass, every CTA goes on only if the
-                // run has not reached its target (one decision for the grid)
-                if (a.watch && t > 0 && P.readout(t - 1)) {
+                // Watch: the grid's decision after readout pass t - 2 (one for
+                // the grid).  The pass right after a readout is loaded and
+                // multiplied before the decision is known, so that waiting for
+                // it overlaps that pass; its update is applied only if the run
+                // goes on (the epilogue waits for the decision before it).
+                if (a.watch && t > 1 && P.readout(t - 2)) {
                     bool stop = false;
-                    if (!wait_decision(seen, P.index(t - 1), stop, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                    if (!wait_decision(seen, P.index(t - 2), stop, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
                     if (stop) break;
                 }
                 unsigned long long ready = t == 0 ? ~0ull : 0ull;   // owners known to have published pass t
@@ -452,9 +456,9 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                            : mbar_wait(bar, parity, a.err, abort_flag, a.limit_ns);
             };
             for (int t = 0; t < P.npass && ok; ++t) {
-                if (a.watch && t > 0 && P.readout(t - 1)) {
+                if (a.watch && t > 1 && P.readout(t - 2)) {
                     bool stop = false;
-                    if (!wait_decision(seen, P.index(t - 1), stop, a.err, abort_flag, a.limit_ns)) break;
+                    if (!wait_decision(seen, P.index(t - 2), stop, a.err, abort_flag, a.limit_ns)) break;
                     if (stop) break;
                 }
                 if (t > 0) {
@@ -553,152 +557,200 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
             }
         }
         tmem_wait_st();
+        // Normal passes run in an inner loop up to the next readout pass, so
+        // that its body carries no readout code: the register allocation and
+        // schedule of the steps' loop would pay for it at every step.
+        int t = 0;
+        bool run = true;
 #pragma unroll 1
-        for (int t = 0; t < P.npass; ++t) {
-            bool ok = true;
-            if (lane == 0)
-                ok = CG2 ? mbar_wait_cluster(accf_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns)
-                         : mbar_wait(accf_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns);
-            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-            if (!ok) break;
-            tc_fence_after();
-            if (P.readout(t)) {
-                if constexpr (!RO) break;   // not launched with readout passes
-                const int k = P.index(t);
-                const int rc = tc_readout_epi<BN, CPH, CG2>(
-                    tl, c_begin, two_acc, row_ok, (a.watch && a.h8 && row_ok) ? 2 * (int)a.h8[i] : 0,
-                    a.e_sum + (size_t)k * a.R, r0, a.R, lane, warp == TC_EPI_WARP0, t == P.npass - 1,
-                    tmem_empty_bar, epi_done_bar, CG2 && !leader, t, a.bar + (size_t)rb * a.mtiles + mt, a.watch,
-                    a.w_cnt ? a.w_cnt + (size_t)k * a.rblocks + rb : nullptr, (unsigned)(a.mtiles - 1), a.target,
-                    a.w_done, a.w_hit, k, seen, a.err, abort_flag, a.limit_ns);
-                if (rc == 1)
-                    tc_write_state<BN, E4>(tl, c_begin, CPH, row_ok, r0, a.R, a.n, i, row, a.q_state, a.p_state,
-                                           a.spins, a.lds, p_tile);
-                if (rc != 0) break;
-                continue;
-            }
-            const int st = P.step(t);
-            const float zt = a.zeta[st], dtt = a.dt[st];
-            const float dtm = dtt / a.sp.m;
-            const bool last = (st == a.steps - 1);
-            const bool pre_ro = t + 1 < P.npass && P.readout(t + 1);   // the next pass reads sign(q) of this step
-            // The chunk loop, instantiated once with the update order and the
-            // wall variant as run-time parameters and once for the default
-            // (kick-drift, no momentum zeroing) so that the integrator does
-            // not test them per element.
-            auto chunks = [&](auto mode_tag) {
-            constexpr int MODE = decltype(mode_tag)::value;
+        while (run && t < P.npass) {
+            const int t_end = RO ? P.next_readout(t) : P.npass;
 #pragma unroll 1
-            for (int c = c_begin; c < c_begin + CPH; ++c) {
-                uint32_t vf[32], vp[32], vq[32];
-                tmem_ld32(tl + COL_ACC0 + c * 32, vf);
-                if (two_acc) {
-                    tmem_ld32(tl + COL_ACC1 + c * 32, vp);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        vf[j] = __float_as_uint(__uint_as_float(vf[j]) + __uint_as_float(vp[j]));
+            for (; t < t_end; ++t) {
+                bool ok = true;
+                if (lane == 0)
+                    ok = CG2 ? mbar_wait_cluster(accf_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns)
+                             : mbar_wait(accf_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                if (!ok) {
+                    run = false;
+                    break;
                 }
-                tmem_ld32(tl + COL_Q + c * 32, vq);
-                if constexpr (E4) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) vp[j] = __float_as_uint(p_tile[(c * 32 + j) * TC_BM + row]);
-                } else {
-                    tmem_ld32(tl + COL_P + c * 32, vp);
-                }
-                tmem_wait_ld();
-                if constexpr (MODE == 1) {
-#pragma unroll
-                    for (int j = 0; j < 32; j += 2) {
-                        float F0 = __uint_as_float(vf[j]), F1 = __uint_as_float(vf[j + 1]);
-                        F0 = __fadd_rn(F0, hi);
-                        F1 = __fadd_rn(F1, hi);
-                        float q0o, q1o, p0o, p1o;
-                        integrate2_kd(__uint_as_float(vq[j]), __uint_as_float(vq[j + 1]), __uint_as_float(vp[j]),
-                                      __uint_as_float(vp[j + 1]), F0, F1, zt, dtt, dtm, a.sp, q0o, q1o, p0o, p1o);
-                        vq[j] = __float_as_uint(q0o);
-                        vq[j + 1] = __float_as_uint(q1o);
-                        vp[j] = __float_as_uint(p0o);
-                        vp[j + 1] = __float_as_uint(p1o);
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float F = __uint_as_float(vf[j]);
-                        float qo, po;
-                        integrate<float, MODE>(__uint_as_float(vq[j]), __uint_as_float(vp[j]), __fadd_rn(F, hi), zt,
-                                               dtt, dtm, a.sp, qo, po);
-                        vq[j] = __float_as_uint(qo);
-                        vp[j] = __float_as_uint(po);
-                    }
-                }
-                tmem_st32(tl + COL_Q + c * 32, vq);
-                if constexpr (E4) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) p_tile[(c * 32 + j) * TC_BM + row] = __uint_as_float(vp[j]);
-                } else {
-                    tmem_st32(tl + COL_P + c * 32, vp);
-                }
-                {
-                    // bf16 copy into the operand plane of step t+1 (after the
-                    // last step: the plane a continuing run starts from),
-                    // written directly: a warp's 32 consecutive spins of one
-                    // replica are 64 contiguous bytes.  Entries outside n x R
-                    // are never written and keep the zeros of the initial fill.
-                    __nv_bfloat16 *dst =
-                        a.qop + ((size_t)((st + 1 + a.p0) & 1) * a.rpad + (size_t)(r0 + c * 32)) * a.ldk + i;
-                    if (row_ok && r0 + c * 32 + 32 <= a.R) {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) dst[(size_t)j * a.ldk] = __float2bfloat16_rn(__uint_as_float(vq[j]));
-                    } else if (row_ok) {
-#pragma unroll
+                tc_fence_after();
+                const int st = P.step(t);
+                const float zt = a.zeta[st], dtt = a.dt[st];
+                const float dtm = dtt / a.sp.m;
+                const bool last = (st == a.steps - 1);
+                const bool pre_ro = RO && t + 1 < P.npass && P.readout(t + 1);   // the next pass reads sign(q) of this step
+                // The chunk loop, instantiated once with the update order and the
+                // wall variant as run-time parameters and once for the default
+                // (kick-drift, no momentum zeroing) so that the integrator does
+                // not test them per element.
+                auto chunks = [&](auto mode_tag) {
+                constexpr int MODE = decltype(mode_tag)::value;
+    #pragma unroll 1
+                for (int c = c_begin; c < c_begin + CPH; ++c) {
+                    uint32_t vf[32], vp[32], vq[32];
+                    tmem_ld32(tl + COL_ACC0 + c * 32, vf);
+                    if (two_acc) {
+                        tmem_ld32(tl + COL_ACC1 + c * 32, vp);
+                        tmem_wait_ld();
+    #pragma unroll
                         for (int j = 0; j < 32; ++j)
-                            if (r0 + c * 32 + j < a.R)
-                                dst[(size_t)j * a.ldk] = __float2bfloat16_rn(__uint_as_float(vq[j]));
+                            vf[j] = __float_as_uint(__uint_as_float(vf[j]) + __uint_as_float(vp[j]));
                     }
-                }
-                if (pre_ro && row_ok) {
-                    // sign(q) as the operand of the readout pass (plane 2)
-                    __nv_bfloat16 *dst = a.qop + ((size_t)2 * a.rpad + (size_t)(r0 + c * 32)) * a.ldk + i;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        if (r0 + c * 32 + j < a.R)
-                            dst[(size_t)j * a.ldk] = __float2bfloat16_rn((float)spin_of(__uint_as_float(vq[j])));
-                }
-                if (last && row_ok) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int r = r0 + c * 32 + j;
-                        if (r < a.R) {
-                            const float qv = __uint_as_float(vq[j]);
-                            a.q_state[(size_t)r * a.n + i] = qv;
-                            a.p_state[(size_t)r * a.n + i] = __uint_as_float(vp[j]);
-                            if (a.spins) a.spins[(size_t)r * a.lds + i] = spin_of(qv);
+                    tmem_ld32(tl + COL_Q + c * 32, vq);
+                    if constexpr (E4) {
+    #pragma unroll
+                        for (int j = 0; j < 32; ++j) vp[j] = __float_as_uint(p_tile[(c * 32 + j) * TC_BM + row]);
+                    } else {
+                        tmem_ld32(tl + COL_P + c * 32, vp);
+                    }
+                    tmem_wait_ld();
+                    if constexpr (MODE == 1) {
+    #pragma unroll
+                        for (int j = 0; j < 32; j += 2) {
+                            float F0 = __uint_as_float(vf[j]), F1 = __uint_as_float(vf[j + 1]);
+                            F0 = __fadd_rn(F0, hi);
+                            F1 = __fadd_rn(F1, hi);
+                            float q0o, q1o, p0o, p1o;
+                            integrate2_kd(__uint_as_float(vq[j]), __uint_as_float(vq[j + 1]), __uint_as_float(vp[j]),
+                                          __uint_as_float(vp[j + 1]), F0, F1, zt, dtt, dtm, a.sp, q0o, q1o, p0o, p1o);
+                            vq[j] = __float_as_uint(q0o);
+                            vq[j + 1] = __float_as_uint(q1o);
+                            vp[j] = __float_as_uint(p0o);
+                            vp[j + 1] = __float_as_uint(p1o);
+                        }
+                    } else {
+    #pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const float F = __uint_as_float(vf[j]);
+                            float qo, po;
+                            integrate<float, MODE>(__uint_as_float(vq[j]), __uint_as_float(vp[j]), __fadd_rn(F, hi), zt,
+                                                   dtt, dtm, a.sp, qo, po);
+                            vq[j] = __float_as_uint(qo);
+                            vp[j] = __float_as_uint(po);
+                        }
+                    }
+                    tmem_st32(tl + COL_Q + c * 32, vq);
+                    if constexpr (E4) {
+    #pragma unroll
+                        for (int j = 0; j < 32; ++j) p_tile[(c * 32 + j) * TC_BM + row] = __uint_as_float(vp[j]);
+                    } else {
+                        tmem_st32(tl + COL_P + c * 32, vp);
+                    }
+                    {
+                        // bf16 copy into the operand plane of step t+1 (after the
+                        // last step: the plane a continuing run starts from),
+                        // written directly: a warp's 32 consecutive spins of one
+                        // replica are 64 contiguous bytes.  Entries outside n x R
+                        // are never written and keep the zeros of the initial fill.
+                        __nv_bfloat16 *dst =
+                            a.qop + ((size_t)((st + 1 + a.p0) & 1) * a.rpad + (size_t)(r0 + c * 32)) * a.ldk + i;
+                        if (row_ok && r0 + c * 32 + 32 <= a.R) {
+    #pragma unroll
+                            for (int j = 0; j < 32; ++j) dst[(size_t)j * a.ldk] = __float2bfloat16_rn(__uint_as_float(vq[j]));
+                        } else if (row_ok) {
+    #pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (r0 + c * 32 + j < a.R)
+                                    dst[(size_t)j * a.ldk] = __float2bfloat16_rn(__uint_as_float(vq[j]));
+                        }
+                    }
+                    if (last && row_ok) {
+    #pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            const int r = r0 + c * 32 + j;
+                            if (r < a.R) {
+                                const float qv = __uint_as_float(vq[j]);
+                                a.q_state[(size_t)r * a.n + i] = qv;
+                                a.p_state[(size_t)r * a.n + i] = __uint_as_float(vp[j]);
+                                if (a.spins) a.spins[(size_t)r * a.lds + i] = spin_of(qv);
+                            }
                         }
                     }
                 }
+                };
+                if (a.sp.order == 0 && !a.sp.wall_zero_p)
+                    chunks(std::integral_constant<int, 1>{});
+                else
+                    chunks(std::integral_constant<int, 0>{});
+                tmem_wait_st();
+                if constexpr (RO) {
+                    // sign(q) of this step as the operand of the readout pass
+                    // that follows (plane 2), from the q just stored in tensor
+                    // memory: a pass of its own, so that the chunk loop of every
+                    // step does not carry it
+                    if (pre_ro) {
+#pragma unroll 1
+                        for (int c = c_begin; c < c_begin + CPH; ++c) {
+                            uint32_t vq[32];
+                            tmem_ld32(tl + COL_Q + c * 32, vq);
+                            tmem_wait_ld();
+                            if (row_ok) {
+                                __nv_bfloat16 *dst = a.qop + ((size_t)2 * a.rpad + (size_t)(r0 + c * 32)) * a.ldk + i;
+#pragma unroll
+                                for (int j = 0; j < 32; ++j)
+                                    if (r0 + c * 32 + j < a.R)
+                                        dst[(size_t)j * a.ldk] = __float2bfloat16_rn((float)spin_of(__uint_as_float(vq[j])));
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                // The warp's stores of q are ordered before lane 0's arrivals
+                // (warp barrier), the arrivals (release, CTA scope) before the
+                // publisher's wait (acquire), and that before its release
+                // increment at GPU scope, which the consumers' acquire loads read.
+                __syncwarp();
+                if (lane == 0) {
+                    if (CG2 && !leader) mbar_arrive_remote(mapa_shared(tmem_empty_bar, 0u));
+                    else mbar_arrive(tmem_empty_bar);
+                    mbar_arrive(epi_done_bar);
+                }
+                if (publisher && t + 1 < P.npass) {
+                    // All 8 warps have written their part of q(t+1) (or sign(q(T))): publish.
+                    if (mbar_wait(epi_done_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns))
+                        red_release_gpu_add(a.bar + (size_t)rb * a.mtiles + mt, 1u);
+                }
             }
-            };
-            if (a.sp.order == 0 && !a.sp.wall_zero_p)
-                chunks(std::integral_constant<int, 1>{});
-            else
-                chunks(std::integral_constant<int, 0>{});
-            tmem_wait_st();
-            tc_fence_before();
-            // The warp's stores of q are ordered before lane 0's arrivals
-            // (warp barrier), the arrivals (release, CTA scope) before the
-            // publisher's wait (acquire), and that before its release
-            // increment at GPU scope, which the consumers' acquire loads read.
-            __syncwarp();
-            if (lane == 0) {
-                if (CG2 && !leader) mbar_arrive_remote(mapa_shared(tmem_empty_bar, 0u));
-                else mbar_arrive(tmem_empty_bar);
-                mbar_arrive(epi_done_bar);
-            }
-            if (publisher && t + 1 < P.npass) {
-                // All 8 warps have written their part of q(t+1) (or sign(q(T))): publish.
-                if (mbar_wait(epi_done_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns))
-                    red_release_gpu_add(a.bar + (size_t)rb * a.mtiles + mt, 1u);
+            if constexpr (RO) {
+                if (!run || t >= P.npass) break;
+                // Readout pass t.
+                {
+                    bool ok = true;
+                    if (lane == 0) ok = mbar_wait(accf_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns);
+                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                    if (!ok) break;
+                }
+                tc_fence_after();
+                const int k = P.index(t);
+                const int rc = tc_readout_epi<BN, CPH, CG2>(
+                    tl, c_begin, two_acc, row_ok, (a.watch && a.h8 && row_ok) ? 2 * (int)a.h8[i] : 0,
+                    a.e_sum + (size_t)k * a.R, r0, a.R, lane, warp == TC_EPI_WARP0, t == P.npass - 1, tmem_empty_bar,
+                    epi_done_bar, CG2 && !leader, t, a.bar + (size_t)rb * a.mtiles + mt, a.watch,
+                    a.w_cnt ? a.w_cnt + (size_t)k * a.rblocks + rb : nullptr, (unsigned)(a.mtiles - 1), a.target,
+                    a.w_done, a.w_hit, k, a.err, abort_flag, a.limit_ns);
+                if (rc != 0) break;
+                ++t;
+                if (a.watch) {
+                    // The grid's decision after this readout, while the next
+                    // pass's MMAs run (its producers and MMA warps wait for the
+                    // decision only one pass later): on a stop, the state stays
+                    // that of the readout's step and the next update is not made.
+                    bool okd = true, stop = false;
+                    if (lane == 0) okd = wait_decision(seen, k, stop, a.err, abort_flag, a.limit_ns);
+                    okd = __shfl_sync(0xffffffffu, okd ? 1 : 0, 0) != 0;
+                    stop = __shfl_sync(0xffffffffu, stop ? 1 : 0, 0) != 0;
+                    if (!okd) break;
+                    if (stop) {
+                        tc_write_state<BN, E4>(tl, c_begin, CPH, row_ok, r0, a.R, a.n, i, row, a.q_state, a.p_state,
+                                               a.spins, a.lds, p_tile);
+                        break;
+                    }
+                }
+            } else {
+                break;
             }
         }
     } else if constexpr (E4) {
@@ -1037,14 +1089,19 @@ si_status tc_watch_buffers(Ctx *c, int steps, int every) {
     return SI_OK;
 }
 
-// E = -(sigma^T J sigma + 2 h^T sigma) / 2, the readout's sum (exact: even).
-__global__ void k_watch_energy(const unsigned long long *sum, int R, int32_t *E) {
+// E = -(sigma^T J sigma + 2 h^T sigma) / 2 of the stopping readout (exact:
+// the sum is even), which the kernel picks itself: the first readout that
+// reached the target, else the last one.
+__global__ void k_watch_energy(const unsigned long long *sums, const int *hit, int nread, int R, int32_t *E) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < R) E[r] = (int32_t)(-((long long)sum[r] / 2));
+    const int h = *hit;
+    const int k = (h >= 0 && h < nread) ? h : nread - 1;
+    if (r < R) E[r] = (int32_t)(-((long long)sums[(size_t)k * R + r] / 2));
 }
 
-si_status tc_watch_energy(Ctx *c, int k, int32_t *E) {
-    k_watch_energy<<<cdiv(c->R, 256), 256, 0, c->stream>>>(c->w_sum + (size_t)k * c->R, c->R, E);
+si_status tc_watch_energy(Ctx *c, int nread, int32_t *E) {
+    k_watch_energy<<<cdiv(c->R, 256), 256, 0, c->stream>>>(c->w_sum, reinterpret_cast<const int *>(c->w_ctl + 1),
+                                                           nread, c->R, E);
     SI_CUDA_TRY(cudaGetLastError());
     c->launches += 1;
     return SI_OK;

@@ -81,6 +81,23 @@ __device__ __forceinline__ void st_release_cta_shared(uint32_t addr, unsigned v)
     asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
+// Atomic add with acquire-release semantics at GPU scope (returns the old value).
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ unsigned ld_relaxed_gpu_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Step flags of the CTAs that own the q blocks of a replica block, mirrored
 // into shared memory by one warp of the consuming CTA (mirror_flags), so that
 // the TMA producers test a shared-memory word instead of polling global
@@ -96,11 +113,14 @@ __device__ __forceinline__ void st_release_cta_shared(uint32_t addr, unsigned v)
 // moved for limit_ns (the waiting producer raises the error then).
 //
 // A watched run (w_done non-null) also mirrors the grid's stop decision:
-// lane 0 reads the number of finished readout evaluations (acquire) and
-// then the first readout that reached the target, stores the latter in
-// word MIRROR_HIT and then (release) the number of readouts whose decision
-// is final, floor(w_done / rblocks), in word MIRROR_FINAL.  Once a final
-// readout has reached the target the run ends after it, and the warp stops.
+// lane 0 reads the number of finished readout evaluations with a relaxed
+// load issued with the owners' loads (an acquire load there would hold them
+// back and slow every step's flag propagation); when it has moved, lane 0
+// reads it again with acquire semantics, then the first readout that
+// reached the target, stores the latter in word MIRROR_HIT and then
+// (release) the number of readouts whose decision is final,
+// floor(w_done / rblocks), in word MIRROR_FINAL.  Once a final readout has
+// reached the target the run ends after it, and the warp stops.
 constexpr int MIRROR_MIN = 64;     // word index of the minimum (words 0..63: owners)
 constexpr int MIRROR_FINAL = 65;   // readouts whose stop decision is final
 constexpr int MIRROR_HIT = 66;     // first readout that reached the target (large: none yet)
@@ -114,18 +134,8 @@ __device__ __forceinline__ void mirror_flags(const unsigned *flags, int nown, un
     unsigned long long t_last = globaltimer_ns();
     for (unsigned it = 1;; ++it) {
         bool moved = false, done = true, decided = false;
-        if (w_done && lane == 0) {
-            const unsigned fin = ld_acquire_gpu(w_done) / rblocks;
-            if (fin != mfin) {
-                const int h = ld_volatile_int(w_hit);
-                st_release_cta_shared(seen + 4u * MIRROR_HIT, (unsigned)h);
-                st_release_cta_shared(seen + 4u * MIRROR_FINAL, fin);
-                mfin = fin;
-                moved = true;
-                decided = h < (int)fin;
-            }
-        }
-        if (__any_sync(0xffffffffu, decided)) return;
+        unsigned wd = 0u;
+        if (w_done && lane == 0) wd = ld_relaxed_gpu_u32(w_done);
         unsigned vmin = 0xffffffffu;
         if (lane < nown) {
             const unsigned v = ld_acquire_gpu(flags + lane);
@@ -147,6 +157,16 @@ __device__ __forceinline__ void mirror_flags(const unsigned *flags, int nown, un
             done = done && (int)(v - last) >= 0;
             vmin = min(vmin, v);
         }
+        if (w_done && lane == 0 && wd / rblocks != mfin) {
+            const unsigned fin = ld_acquire_gpu(w_done) / rblocks;
+            const int h = ld_volatile_int(w_hit);
+            st_release_cta_shared(seen + 4u * MIRROR_HIT, (unsigned)h);
+            st_release_cta_shared(seen + 4u * MIRROR_FINAL, fin);
+            mfin = fin;
+            moved = true;
+            decided = h < (int)fin;
+        }
+        if (__any_sync(0xffffffffu, decided)) return;
         vmin = __reduce_min_sync(0xffffffffu, vmin);
         __syncwarp();
         if (lane == 0 && vmin != mmin) {
@@ -232,18 +252,6 @@ __device__ __forceinline__ bool wait_decision(uint32_t seen, int k, bool &stop, 
             }
         }
     }
-}
-
-// Atomic add with acquire-release semantics at GPU scope (returns the old value).
-__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned *p, unsigned v) {
-    unsigned old;
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
-__device__ __forceinline__ unsigned long long ld_relaxed_gpu_u64(const unsigned long long *p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-    return v;
 }
 
 // Column sums of a warp's 32 x 32 block (lane = row, v[j] = column j): a
