@@ -99,6 +99,23 @@ struct TcPasses {
     }
 };
 
+// Walk over the passes in order without a division per pass: the step of
+// the current pass, the next readout pass, and the latest readout passed.
+struct TcWalk {
+    int st = 0, next_ro, k = 0, last_ro = -3, last_k = -1;
+    __device__ __forceinline__ explicit TcWalk(const TcPasses &P) : next_ro(P.next_readout(0)) {}
+    __device__ __forceinline__ bool readout(int t) const { return t == next_ro; }
+    __device__ __forceinline__ void advance(const TcPasses &P, int t) {   // after pass t
+        if (t == next_ro) {
+            last_ro = t;
+            last_k = k++;
+            next_ro = P.next_readout(t + 1);
+        } else {
+            ++st;
+        }
+    }
+};
+
 // ------------------------------------------------------------------ kernel
 // Shared memory: S ring stages (J tile + q tile), then the mbarriers and the
 // mirrored step flags.
@@ -372,21 +389,22 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
             bool ok = true;
             // pair: both CTAs walk the K blocks in the same order (the pair's rows first)
             const int kb0 = (CG2 ? (mt & ~1) : mt) * (TC_BM / TC_BK);
-            for (int t = 0; t < P.npass && ok; ++t) {
+            TcWalk W(P);
+            for (int t = 0; t < P.npass && ok; W.advance(P, t), ++t) {
                 // Watch: the grid's decision after readout pass t - 2 (one for
                 // the grid).  The pass right after a readout is loaded and
                 // multiplied before the decision is known, so that waiting for
                 // it overlaps that pass; its update is applied only if the run
                 // goes on (the epilogue waits for the decision before it).
-                if (a.watch && t > 1 && P.readout(t - 2)) {
+                if (a.watch && t == W.last_ro + 2) {
                     bool stop = false;
-                    if (!wait_decision(seen, P.index(t - 2), stop, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
+                    if (!wait_decision(seen, W.last_k, stop, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
                     if (stop) break;
                 }
                 unsigned long long ready = t == 0 ? ~0ull : 0ull;   // owners known to have published pass t
                 const unsigned need = (unsigned)t + (t == a.stall_step ? 1000000u : 0u);
                 // q of step s in plane (s + p0) & 1; a readout pass reads sign(q) in plane 2
-                const int yb = (P.readout(t) ? 2 : ((P.step(t) + a.p0) & 1)) * a.rpad + r0 + (int)crank * (BN / 2);
+                const int yb = (W.readout(t) ? 2 : ((W.st + a.p0) & 1)) * a.rpad + r0 + (int)crank * (BN / 2);
                 for (int j = ring; j < a.kblocks; j += 2) {
                     int kb = kb0 + j;
                     if (kb >= a.kblocks) kb -= a.kblocks;
@@ -455,10 +473,11 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                 return CG2 ? mbar_wait_cluster(bar, parity, a.err, abort_flag, a.limit_ns)
                            : mbar_wait(bar, parity, a.err, abort_flag, a.limit_ns);
             };
-            for (int t = 0; t < P.npass && ok; ++t) {
-                if (a.watch && t > 1 && P.readout(t - 2)) {
+            TcWalk W(P);
+            for (int t = 0; t < P.npass && ok; W.advance(P, t), ++t) {
+                if (a.watch && t == W.last_ro + 2) {
                     bool stop = false;
-                    if (!wait_decision(seen, P.index(t - 2), stop, a.err, abort_flag, a.limit_ns)) break;
+                    if (!wait_decision(seen, W.last_k, stop, a.err, abort_flag, a.limit_ns)) break;
                     if (stop) break;
                 }
                 if (t > 0) {
@@ -565,8 +584,9 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
 #pragma unroll 1
         while (run && t < P.npass) {
             const int t_end = RO ? P.next_readout(t) : P.npass;
+            int st = P.step(t);
 #pragma unroll 1
-            for (; t < t_end; ++t) {
+            for (; t < t_end; ++t, ++st) {
                 bool ok = true;
                 if (lane == 0)
                     ok = CG2 ? mbar_wait_cluster(accf_bar, (uint32_t)(t & 1), a.err, abort_flag, a.limit_ns)
@@ -577,11 +597,10 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                     break;
                 }
                 tc_fence_after();
-                const int st = P.step(t);
                 const float zt = a.zeta[st], dtt = a.dt[st];
                 const float dtm = dtt / a.sp.m;
                 const bool last = (st == a.steps - 1);
-                const bool pre_ro = RO && t + 1 < P.npass && P.readout(t + 1);   // the next pass reads sign(q) of this step
+                const bool pre_ro = RO && t + 1 == t_end && t_end < P.npass;   // the next pass reads sign(q) of this step
                 // The chunk loop, instantiated once with the update order and the
                 // wall variant as run-time parameters and once for the default
                 // (kick-drift, no momentum zeroing) so that the integrator does
