@@ -735,15 +735,20 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
             }
         };
         // Elementwise part of reverse step tau from the adjoint state (lq, lp)
-        // of step tau + 1 and the fetched slot values: lambda_a and lambda_b
-        // into x0, x1 and the gradient terms into g.
-        auto elem = [&](int tau, const float *lqv, const float *lpv, CompSum<float> *g) {
+        // of step tau + 1 and the fetched slot values, in two halves: lambda_a
+        // and lambda_b into x0, x1 (needed for the next operand), and, after
+        // that operand is published, the gradient terms into g.
+        auto elem = [&](int tau, const float *lqv, const float *lpv) {
+            const float dtm = a.dt[tau] / mq;
+#pragma unroll
+            for (int u = 0; u < W; ++u)
+                if (u < nv) adj_clamps(lqv[u], lpv[u], pre[0][u], pre[1][u], qmax, pmax, dtm, x0[u], x1[u]);
+        };
+        auto terms = [&](int tau, CompSum<float> *g) {
             const float zt = a.zeta[tau], dtt = a.dt[tau];
-            const float dtm = dtt / mq;
 #pragma unroll
             for (int u = 0; u < W; ++u) {
                 if (u < nv) {
-                    adj_clamps(lqv[u], lpv[u], pre[0][u], pre[1][u], qmax, pmax, dtm, x0[u], x1[u]);
                     float g0, g1, g2;
                     adj_terms(x0[u], x1[u], pre[2][u], pre[3][u], pre[1][u], q0, kq, mq, zt, dtt, g0, g1, g2);
                     g[0].add(g0);
@@ -776,9 +781,10 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
             g[1].init();
             g[2].init();
             const int tau = ch.t_start + len - 1;
-            elem(tau, lqv, lpv, g);
+            elem(tau, lqv, lpv);
             pieces(ch.buf0);
             publish();
+            terms(tau, g);
             partials(g, tau);
         }
 
@@ -894,9 +900,10 @@ __global__ void __launch_bounds__(AR_THREADS, 1)
                     g[0].init();
                     g[1].init();
                     g[2].init();
-                    elem(t - 1, lqv, lpv, g);
+                    elem(t - 1, lqv, lpv);
                     pieces(ch.buf0 + ((u + 1) & 1));
                     publish();
+                    terms(t - 1, g);
                     partials(g, t - 1);
                 } else {
 #pragma unroll
