@@ -52,6 +52,7 @@ def _grad(J, h, q0, zeta, dt, K, env, monkeypatch):
     (300, 70, 31, 10, True),      # two replica blocks, ragged n, R, last segment of 1 step, a field
     (120, 5, 47, 7, False),       # one M tile, clusters of 2
     (129, 64, 9, 1, False),       # one-step segments
+    (2000, 64, 500, 50, False),   # the gradient workload itself (10 segments of 50)
 ])
 def test_persistent_sweep_equals_per_step_sweep(n, R, T, K, field, monkeypatch):
     J, h, q0, zeta, dt = _case(n, R, T, seed=5, field=field)

@@ -119,3 +119,34 @@ def test_watch_rejects_what_it_cannot_serve():
     with b.Context(J, replicas=R, steps=T, prec="j_fp8_q_bf16") as c:
         with pytest.raises(b.SpringIsingError):
             c.run_watch(zeta, dt, q0, 0, 0)     # every >= 1
+
+
+def test_watch_at_the_batched_workload():
+    """The time-to-target launch as the bench times it: N=2000 +-1, R=1024,
+    the T=2000 schedule, a readout every 10 steps.  The target is the best
+    energy at the fifth readout of the segmented run, so the watched run
+    stops at the first readout (<= 5) that reaches it, with the segmented
+    run's state and energies, and the oracle's exact energies of its spins."""
+    n, R, T, every = 2000, 1024, 2000, 10
+    J, h, q0, zeta, dt = _case(n, R, T, seed=2)
+    prec = "j_fp8_q_bf16"
+    segs, t = [], 0
+    with b.Context(J, replicas=R, steps=every, prec=prec) as c:
+        for k in range(5):
+            if k == 0:
+                q, p, s = c.run(zeta[:every], dt[:every], q0)
+            else:
+                q, p, s = c.run(zeta[t:t + every], dt[t:t + every], None)
+            E, _, _ = c.energy(None)
+            t += every
+            segs.append((t, q, p, s, E))
+    target = int(segs[4][4].min())
+    k_hit = next(k for k, sg in enumerate(segs) if int(sg[4].min()) <= target)
+    t_hit, q_e, p_e, s_e, E_e = segs[k_hit]
+    with b.Context(J, replicas=R, steps=T, prec=prec) as c:
+        done, q, p, s, E = c.run_watch(zeta, dt, q0, every, target)
+        assert "tile=128x128" in c.describe()
+    assert done == t_hit
+    assert np.array_equal(q, q_e) and np.array_equal(p, p_e) and np.array_equal(s, s_e)
+    assert np.array_equal(E, E_e)
+    assert np.array_equal(E, oracle.energy(J, None, s).astype(np.int32))
