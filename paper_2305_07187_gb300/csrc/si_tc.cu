@@ -139,7 +139,8 @@ struct TcSmem {
     // full[S], empty[S], accf, tmem_empty, epi_done, drain, afull[NA], aempty[NA]
     static constexpr int NBARS = 2 * S + 4 + 2 * NA;
     static constexpr int SEEN = BARS + NBARS * 8 + 16;     // after the tmem slot and abort flag
-    static constexpr int TOTAL = SEEN + 68 * 4;            // mirrored step flags of up to 64 owners, their minimum
+    static constexpr int CNT = SEEN + 68 * 4;              // mirrored step flags of up to 64 owners, their minimum
+    static constexpr int TOTAL = CNT + 4 * 4;              // pair: stages issued per ring by each CTA
     static constexpr int TMEM_COLS = (E4 || 4 * BN > 256) ? 512 : 256;
 };
 
@@ -153,14 +154,19 @@ constexpr int TC_EPI_WARP0 = 1 + TC_MMA_WARPS;             // first epilogue war
 // replica block) share each MMA of M = 256 (tcgen05 cta_group::2): each loads
 // its own 128 rows of J and half of the q tile (BN/2 replicas), so a K block
 // costs a CTA 24 KB of TMA traffic instead of 32 KB.  The even CTA issues the
-// MMAs.  Each CTA's copies complete on its own full barrier; in the odd CTA
-// the two idle MMA warps forward every completed stage to the even CTA's
-// full barrier (which counts its own producer and that forward), so that no
-// copy ever signals the other CTA's memory.  The MMA completions are
-// multicast to the empty and accumulator barriers of both CTAs; the odd CTA's
-// epilogue frees the accumulators on the even CTA's barrier.  Both CTAs stay
-// until a cluster barrier before TMEM is freed, so neither leaves while the
-// other may still read its shared memory or signal its barriers.
+// MMAs.  The copies of both CTAs complete on the even CTA's full barrier
+// (TMA cta_group::2), which the even CTA's producer arms for the bytes of
+// both; the odd CTA's producer only waits for its stage to be free.  The MMA
+// completions are multicast to the empty and accumulator barriers of both
+// CTAs; the odd CTA's epilogue frees the accumulators on the even CTA's
+// barrier.  At the end each producer leaves the number of stages it issued
+// in the even CTA's shared memory; after a cluster barrier (no copy is
+// issued after it) the even CTA settles every stage that only one CTA filled
+// (it arms the ones the odd CTA filled alone and counts the bytes that were
+// never sent) and waits until every copy of both CTAs has landed.  Both
+// CTAs then meet at a second cluster barrier before TMEM is freed, so that
+// neither leaves while a copy or an arrival may still reach its shared
+// memory.
 // Epilogue of a readout pass (one warp): the accumulators hold G = J sigma
 // (integers below 2^24, exact in FP32).  sigma_i (G_ir + h2) per element,
 // h2 = 2 h_i on a watched run (else 0), is added over the warp's 32 rows by
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
-            mbar_init(full_bar(s), CG2 && leader ? 2 : 1);   // pair: own copies + the odd CTA's forward
+            mbar_init(full_bar(s), 1);   // pair: the even CTA's arming counts the bytes of both CTAs
             mbar_init(empty_bar(s), 1);
         }
         for (int k = 0; k < L::NA; ++k) {
@@ -412,17 +418,40 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                     const uint32_t ph = (cnt / HS) & 1u;
                     const uint32_t dA = sbase + s * L::STAGE_BYTES;
                     if (!mbar_wait(empty_bar(s), ph ^ 1u, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
-                    mbar_arrive_expect_tx(full_bar(s), (uint32_t)L::TX_BYTES);
-                    tma_load_2d(dA, &mapA, full_bar(s), kb * TC_BK, m0);
+                    if (CG2 && !leader) {
+                        tma_load_2d_pair(dA, &mapA, mapa_shared(full_bar(s), 0u), kb * TC_BK, m0);
+                    } else {
+                        mbar_arrive_expect_tx(full_bar(s), (uint32_t)(CG2 ? 2 * L::TX_BYTES : L::TX_BYTES));
+                        tma_load_2d(dA, &mapA, full_bar(s), kb * TC_BK, m0);
+                    }
                     ++cnt;
                     const int mo = kb >> 1;
                     bool have = ((ready >> mo) & 1ull) != 0ull;
-                    if (!have) have = wait_owner(seen, mo, need, ready, a.err, abort_flag, a.limit_ns);
+                    if (!have) {
+                        if (!CG2 && mo == mt && t > 0 && t != a.stall_step) {
+                            // This CTA's own rows, written by its epilogue of
+                            // pass t - 1: its barrier orders those stores, and
+                            // the proxy fence makes them visible to the copy,
+                            // without waiting for the published flag.
+                            have = mbar_wait(epi_done_bar, (uint32_t)((t - 1) & 1), a.err, abort_flag, a.limit_ns);
+                            if (have) fence_proxy_async_global();
+                        } else {
+                            have = wait_owner(seen, mo, need, ready, a.err, abort_flag, a.limit_ns);
+                        }
+                    }
                     // The q tile is issued even on abort so that the stage's
                     // transaction count completes and the drain below ends.
-                    tma_load_2d(dA + L::A_STAGE, &mapB, full_bar(s), kb * TC_BK, yb);
+                    if (CG2 && !leader)
+                        tma_load_2d_pair(dA + L::A_STAGE, &mapB, mapa_shared(full_bar(s), 0u), kb * TC_BK, yb);
+                    else
+                        tma_load_2d(dA + L::A_STAGE, &mapB, full_bar(s), kb * TC_BK, yb);
                     if (!have) { ok = false; break; }
                 }
+            }
+            if constexpr (CG2) {
+                // pair: the stages issued, for the even CTA's settlement at the end
+                st_shared_cluster_u32(mapa_shared(sbase + L::CNT + 4u * (2u * crank + (uint32_t)ring), 0u), cnt);
+                cnt = 0u;   // the even CTA waits for the copies of both CTAs
             }
             // Let every copy this thread issued land before the CTA exits.
             const uint32_t first = cnt > (uint32_t)HS ? cnt - HS : 0u;
@@ -447,21 +476,8 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
         // warp 2 the odd ones into accumulator 1; the epilogue adds the two.
         // Two issuing threads keep the tensor pipe fed: one thread alone
         // issues a 128x128x16 MMA no faster than the pipe executes it.
-        // In the odd CTA of a pair the two warps forward its completed
-        // stages to the even CTA instead (ring w each).
-        if (lane == 0 && CG2 && !leader) {
-            const int w = warp - 1;
-            constexpr int HS = S / 2;
-            uint32_t c = 0;
-            bool ok = true;
-            for (int t = 0; t < P.npass && ok; ++t) {
-                for (int j = w; j < a.kblocks; j += TC_MMA_WARPS, ++c) {
-                    const int s = 2 * (int)(c % HS) + w;
-                    if (!mbar_wait(full_bar(s), (c / HS) & 1u, a.err, abort_flag, a.limit_ns)) { ok = false; break; }
-                    mbar_arrive_remote(mapa_shared(full_bar(s), 0u));
-                }
-            }
-        } else if (lane == 0) {
+        // In the odd CTA of a pair the two warps have nothing to do.
+        if (lane == 0 && !(CG2 && !leader)) {
             const int w = warp - 1;
             constexpr uint32_t idesc = idesc_bf16(CG2 ? 2 * TC_BM : TC_BM, BN);
             const uint32_t d_tmem = tmem + (w == 0 ? COL_ACC0 : COL_ACC1);
@@ -812,9 +828,43 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
 
     tc_fence_before();
     __syncthreads();
-    // pair: neither CTA frees TMEM or leaves while the other may still read
-    // its shared memory or arrive on its barriers
-    if constexpr (CG2) cluster_sync_all();
+    if constexpr (CG2) {
+        // No copy is issued after this barrier, and both CTAs' counts of
+        // issued stages are in the even CTA's shared memory.
+        cluster_sync_all();
+        if (leader && warp == 0 && lane < 2) {
+            // Ring `lane`: stage k of the ring (k-th arming or issue) is filled
+            // by both CTAs in the same order, and a CTA fills stage k only after
+            // the MMAs of stage k - S/2 have consumed the same slot, so each
+            // slot has at most one unfinished phase, that of the largest k
+            // mapped to it.  Settle the stages that only one CTA filled, then
+            // wait for the last phase of every slot.
+            constexpr int HS = S / 2;
+            const int ring = lane;
+            const volatile unsigned *cnts = reinterpret_cast<const volatile unsigned *>(smem + L::CNT);
+            const uint32_t own = cnts[ring], odd = cnts[2 + ring];
+            const uint32_t lo = own < odd ? own : odd, hi = own < odd ? odd : own;
+            for (uint32_t k = lo; k < hi; ++k) {
+                const uint32_t bar = full_bar(2 * (int)(k % HS) + ring);
+                if (k >= own) mbar_arrive_expect_tx(bar, (uint32_t)(2 * L::TX_BYTES));   // filled by the odd CTA alone
+                mbar_complete_tx(bar, (uint32_t)L::TX_BYTES);                              // the bytes never sent
+            }
+            const uint32_t first = hi > (uint32_t)HS ? hi - HS : 0u;
+            for (uint32_t k = first; k < hi; ++k) {
+                const unsigned long long t0 = globaltimer_ns();
+                while (!mbar_try_wait_cluster(full_bar(2 * (int)(k % HS) + ring), (k / HS) & 1u)) {
+                    if ((long long)(globaltimer_ns() - t0) > a.limit_ns) {
+                        atomicCAS(a.err, 0, DEV_TIMEOUT_MBAR);
+                        break;
+                    }
+                }
+            }
+        }
+        __syncwarp();
+        // neither CTA frees TMEM or leaves while a copy or an arrival of the
+        // other may still reach its shared memory
+        cluster_sync_all();
+    }
     tc_fence_after();
     if (warp == 1) {
         if constexpr (CG2) {
@@ -1135,7 +1185,7 @@ si_status tc_run(Ctx *c, int steps, int8_t *spins_dev) {
             default: break;
         }
     } else if (c->tc_pair) {
-        return tc_launch_t<128, 6, 8, false, true>(c, steps, spins_dev);
+        return tc_launch_t<128, 8, 8, false, true>(c, steps, spins_dev);
     } else if (c->tc_readout || c->tc_watch_every > 0) {
         switch (c->tile_n) {
             case 64: return tc_launch_t<64, 8, 8, false, false, true>(c, steps, spins_dev);
@@ -1208,8 +1258,8 @@ static bool tc_pair_choice(const Ctx *c) {
     const char *e = std::getenv("SI_TC_PAIR");
     if (!(e && std::atoi(e) == 1)) return false;
     if (c->j_e4m3 || c->prm.tile_n != 0 || c->tile_n != 128) return false;
-    using L = TcSmem<128, 6, false, true>;
-    auto kern = k_tc_run<128, 6, 8, false, true>;
+    using L = TcSmem<128, 8, false, true>;
+    auto kern = k_tc_run<128, 8, 8, false, true>;
     const int smem = L::TOTAL + 1024;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return false;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1334,7 +1384,7 @@ const char *tc_describe(const Ctx *c, char *buf, int len) {
                   "tcgen05 prec=%s J=%s n=%d R=%d tile=128x%d%s stages=%d grid=%d (mtiles=%d rblocks=%d) kblocks=%d",
                   c->prm.prec == SI_PREC_J_FP8_Q_BF16 ? "j_fp8_q_bf16" : "j_bf16_q_bf16",
                   c->j_e4m3 ? "e4m3(1B)" : "bf16(2B)", c->n, c->R, c->tile_n,
-                  c->tc_pair ? " cta_pairs(M=256)" : "", c->tile_n == 128 ? (c->j_e4m3 ? 4 : 6) : 8,
+                  c->tc_pair ? " cta_pairs(M=256)" : "", c->tile_n == 128 ? (c->j_e4m3 ? 4 : (c->tc_pair ? 8 : 6)) : 8,
                   (c->mpad / TC_BM) * (c->rpad / c->tile_n), c->mpad / TC_BM, c->rpad / c->tile_n, c->ldk / TC_BK);
     return buf;
 }

@@ -77,3 +77,29 @@ def test_pair_full_workload_equals_chained_single_steps():
             c1.run_into(z_d[t:t + 1], d_d[t:t + 1], None)
         chained = c1.run(zeta[T - 1:T], dt[T - 1:T], None)
     _same(full, chained)
+
+
+def test_pair_stalled_wait_times_out_and_device_recovers(monkeypatch):
+    """A pair whose step wait runs out (SI_DEBUG_STALL_STEP) leaves the run
+    with SI_ERR_TIMEOUT after every copy of both CTAs has landed on the even
+    CTA's barriers; the context and the device stay usable."""
+    n, R, T = 300, 256, 12
+    J = inputs.pm1_coupling(n, seed=4)
+    zeta, dt = inputs.zeta_ramp(T), inputs.dt_const(T)
+    q0 = inputs.positions(n, R, seed0=40)
+    monkeypatch.setenv("SI_DEBUG_STALL_STEP", "3")
+    monkeypatch.setenv("SI_SPIN_LIMIT_NS", "200000000")
+    with b.Context(J, replicas=R, steps=T, prec="j_fp8_q_bf16") as ctx:
+        assert "cta_pairs" in ctx.describe()
+        for _ in range(2):
+            with pytest.raises(b.SpringIsingError) as ei:
+                ctx.run(zeta, dt, q0)
+            assert ei.value.status == b.SI_ERR_TIMEOUT
+    monkeypatch.delenv("SI_DEBUG_STALL_STEP")
+    monkeypatch.delenv("SI_SPIN_LIMIT_NS")
+    with b.Context(J, replicas=R, steps=T, prec="j_fp8_q_bf16") as ctx:
+        assert "cta_pairs" in ctx.describe()
+        q, p, s = ctx.run(zeta, dt, q0)
+        e, _, _ = ctx.energy(s)
+    assert np.abs(q).max() <= b.SQRT2_F32 and np.abs(p).max() <= 2.0
+    np.testing.assert_array_equal(e, oracle.energy(J, None, s).astype(np.int64))
