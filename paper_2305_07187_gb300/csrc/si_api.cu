@@ -230,6 +230,7 @@ static si_status create_impl(Ctx *c, const float *J, const float *h) {
         if (v > 0) c->spin_limit_ns = v;
     }
     if (const char *e = std::getenv("SI_DEBUG_STALL_STEP")) c->stall_step = std::atoi(e);
+    if (const char *e = std::getenv("SI_DEBUG_STALL_RANK")) c->stall_rank = std::atoi(e);
     DevIn Jd, hd;
     si_status s = stage_in(Jd, J, (size_t)n * n * sizeof(float), c->stream);
     if (s != SI_OK) return s;

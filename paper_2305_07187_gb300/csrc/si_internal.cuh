@@ -75,6 +75,7 @@ struct Ctx {
     // the call must return SI_ERR_TIMEOUT (-1: off).  Set from
     // SI_DEBUG_STALL_STEP at creation.
     int stall_step = -1;
+    int stall_rank = -1;       // CTA pairs: only the CTAs of this pair rank stall (-1: all)
 
     // Storage of J.  FP32/FP64 paths: [n][ldj] in the state precision.
     // Tensor path: [mpad][ldk], zero padded, bf16 or (j_e4m3) e4m3 bytes.

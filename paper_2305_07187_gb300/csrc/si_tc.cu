@@ -57,6 +57,7 @@ struct TcArgs {
     long long limit_ns;
     StepParams sp;
     int stall_step;              // failure-detection test hook (-1: off)
+    int stall_rank;              // CTA pairs: only this pair rank stalls (-1: every CTA)
     int smem_bytes;              // dynamic shared memory the launch provides
     int p0;                      // operand plane holding q(0)
     // Readout passes: after every `every` steps and after the last one, one
@@ -408,7 +409,8 @@ __global__ void __launch_bounds__(tc_threads<EPI, E4>(), 1)
                     if (stop) break;
                 }
                 unsigned long long ready = t == 0 ? ~0ull : 0ull;   // owners known to have published pass t
-                const unsigned need = (unsigned)t + (t == a.stall_step ? 1000000u : 0u);
+                const bool stall = t == a.stall_step && (a.stall_rank < 0 || a.stall_rank == (int)crank);
+                const unsigned need = (unsigned)t + (stall ? 1000000u : 0u);
                 // q of step s in plane (s + p0) & 1; a readout pass reads sign(q) in plane 2
                 const int yb = (W.readout(t) ? 2 : ((W.st + a.p0) & 1)) * a.rpad + r0 + (int)crank * (BN / 2);
                 for (int j = ring; j < a.kblocks; j += 2) {
@@ -1045,6 +1047,7 @@ static si_status tc_launch_t(Ctx *c, int steps, int8_t *spins_dev) {
     a.err = c->derr;
     a.limit_ns = c->spin_limit_ns;
     a.stall_step = c->stall_step;
+    a.stall_rank = c->stall_rank;
     a.sp = StepParams{c->prm.k, c->prm.m, c->prm.q0, c->prm.q_max, c->prm.p_max,
                       c->prm.update_order, c->prm.wall_zero_p};
     a.p0 = c->tc_p0;

@@ -79,15 +79,22 @@ def test_pair_full_workload_equals_chained_single_steps():
     _same(full, chained)
 
 
-def test_pair_stalled_wait_times_out_and_device_recovers(monkeypatch):
+@pytest.mark.parametrize("rank", [None, 0, 1])
+def test_pair_stalled_wait_times_out_and_device_recovers(rank, monkeypatch):
     """A pair whose step wait runs out (SI_DEBUG_STALL_STEP) leaves the run
     with SI_ERR_TIMEOUT after every copy of both CTAs has landed on the even
-    CTA's barriers; the context and the device stay usable."""
+    CTA's barriers; the context and the device stay usable.  With both CTAs
+    stalled they have issued the same stages; with only the even CTA
+    (rank 0) stalled the odd one has filled stages alone, which the even CTA
+    arms at the end; with only the odd CTA (rank 1) stalled the even CTA has
+    armed stages whose odd half never came, whose bytes it counts as done."""
     n, R, T = 300, 256, 12
     J = inputs.pm1_coupling(n, seed=4)
     zeta, dt = inputs.zeta_ramp(T), inputs.dt_const(T)
     q0 = inputs.positions(n, R, seed0=40)
     monkeypatch.setenv("SI_DEBUG_STALL_STEP", "3")
+    if rank is not None:
+        monkeypatch.setenv("SI_DEBUG_STALL_RANK", str(rank))
     monkeypatch.setenv("SI_SPIN_LIMIT_NS", "200000000")
     with b.Context(J, replicas=R, steps=T, prec="j_fp8_q_bf16") as ctx:
         assert "cta_pairs" in ctx.describe()
@@ -96,6 +103,7 @@ def test_pair_stalled_wait_times_out_and_device_recovers(monkeypatch):
                 ctx.run(zeta, dt, q0)
             assert ei.value.status == b.SI_ERR_TIMEOUT
     monkeypatch.delenv("SI_DEBUG_STALL_STEP")
+    monkeypatch.delenv("SI_DEBUG_STALL_RANK", raising=False)
     monkeypatch.delenv("SI_SPIN_LIMIT_NS")
     with b.Context(J, replicas=R, steps=T, prec="j_fp8_q_bf16") as ctx:
         assert "cta_pairs" in ctx.describe()
