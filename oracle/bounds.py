@@ -1,7 +1,7 @@
 """Error bounds of the GPU arithmetic against the FP64 oracle.
 
 TEST INFRASTRUCTURE ONLY, like the rest of this package: the parity tests and
-``__graft_entry__.smoke()`` use these bounds to judge the tensor-core path.
+``__graft_entry__.smoke()`` use these bounds to check the tensor-core path.
 They hold none of the method's arithmetic beyond what a bound needs.
 """
 from __future__ import annotations
